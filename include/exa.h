@@ -1,0 +1,234 @@
+/*
+ * exa.h -- C ABI of the GB300 derivative-evaluation library for SIMD-form NLPs.
+ *
+ * Problem class (Eq. (nlp) and Eq. (simd), Sec. 2.1-2.2):
+ *     min f(x)  s.t.  gl <= c(x) <= gu,  xl <= x <= xu,
+ *     f(x) = sum_l sum_i f_l(x; theta, p_i),
+ *     c(x) = [ base rows g_m(x; theta, q_j) ]  +  sum of augmentation terms h_n(x; theta, s_k),
+ * where every pattern is one expression tree evaluated over its own data array.  Bounds never
+ * enter derivative values and are not part of this interface.
+ *
+ * The calls follow the solver-facing callbacks of Sec. 2.1 (obj, grad!, cons!, jac_structure!,
+ * jac_coord!, hess_structure!, hess_coord!, jprod!, jtprod!, hprod!):
+ *   - structure is queried once, values are recomputed per iterate;
+ *   - Jacobian and Hessian values are written in the partially compressed COO layout of
+ *     Sec. 5.2.2 / 5.3.2: patterns in declaration order, instance k of pattern P owning slots
+ *     [o_P + k * step_P, o_P + (k+1) * step_P); only the lower triangle (row >= col) of the
+ *     Hessian is stored;
+ *   - the CSC calls additionally sum duplicate (row, col) entries into the fully compressed
+ *     pattern (the conversion the paper leaves to the solver, Sec. 5.2.2).
+ *
+ * Conventions for every call below:
+ *   - Indices are 0-based (the paper's Julia code is 1-based).
+ *   - Array arguments of the evaluation and structure calls are DEVICE pointers on the model's
+ *     device, owned by the caller, sized from exa_dims().  Descriptor arguments of exa_create
+ *     are HOST pointers; the library copies what it needs before returning.
+ *   - Evaluation calls are stream-ordered and asynchronous on the model's stream (default: the
+ *     legacy default stream; see exa_set_stream).  They never synchronize the device and never
+ *     allocate device memory.  Inputs must stay valid and unmodified until the enqueued work has
+ *     run; outputs are valid once it has run.
+ *   - Results do not depend on the launch configuration except through floating-point
+ *     summation order (the duplicate sums and the objective reduction are deterministic for a
+ *     fixed configuration).
+ *   - No exception crosses the ABI.  Every call returns an exa_status; the message of the last
+ *     failure is returned by exa_last_error (per model) or exa_create_error (per thread).
+ *   - A model is immutable after creation; concurrent calls on different streams are safe when
+ *     they use different output buffers and different models, or when they are serialised.
+ *     Two calls on one model share its internal work buffers and must not overlap in time.
+ */
+#ifndef EXA_H
+#define EXA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct exa_model exa_model; /* opaque; owned by the library until exa_destroy */
+
+typedef enum {
+    EXA_OK = 0,
+    EXA_E_INVALID = 1,     /* malformed descriptor or argument (NULL, wrong kind, bad opcode) */
+    EXA_E_OOM = 2,         /* device or host allocation failed during exa_create */
+    EXA_E_NVRTC = 3,       /* runtime compilation of the generated kernels failed */
+    EXA_E_CUDA = 4,        /* a CUDA runtime call failed (message holds the CUDA error) */
+    EXA_E_BOUNDS = 5,      /* a resolved variable / parameter / row index is out of range */
+    EXA_E_TIMEOUT = 6,     /* a bounded device-side wait expired */
+    EXA_E_UNSUPPORTED = 7, /* valid request this build cannot serve (e.g. no sm_103 device) */
+    EXA_E_INTERNAL = 8     /* internal consistency check failed */
+} exa_status;
+
+typedef enum {
+    EXA_FP64 = 0,       /* all pattern arithmetic in FP64 */
+    EXA_MIXED_FP32 = 1  /* pattern arithmetic in FP32; FP64 for x loads, trig/exp argument
+                           formation and reduction, all cross-instance sums, and outputs */
+} exa_precision;
+
+/* ------------------------------------------------------------------ pattern IR opcodes */
+/* Value nodes (postorder; children precede parents; the last node is the root). */
+enum {
+    EXA_V_CONST = 0,  /* fval */
+    EXA_V_DATA = 1,   /* data field ival of this instance (int32 fields are converted to double) */
+    EXA_V_VAR = 2,    /* x[index expression rooted at inode a] */
+    EXA_V_PARAM = 3,  /* theta[index expression rooted at inode a] (no derivatives) */
+    EXA_V_NEG = 10, EXA_V_ABS2, EXA_V_INV, EXA_V_EXP, EXA_V_LOG, EXA_V_SIN, EXA_V_COS,
+    EXA_V_SQRT, EXA_V_TAN, EXA_V_TANH, EXA_V_ATAN,
+    EXA_V_POWI = 21,  /* child a raised to the integer ival */
+    EXA_V_ADD = 40, EXA_V_SUB, EXA_V_MUL, EXA_V_DIV,
+    EXA_V_POW = 44    /* a ^ b for real b; a must be positive where derivatives are taken */
+};
+/* Integer index nodes (postorder within the pattern's inode array), 64-bit arithmetic. */
+enum {
+    EXA_I_CONST = 0,  /* ival */
+    EXA_I_FIELD = 1,  /* int32 data field ival of this instance */
+    EXA_I_INST = 2,   /* the instance number k = 0 .. n_inst-1 */
+    EXA_I_ADD = 10, EXA_I_SUB = 11, EXA_I_MUL = 12
+};
+enum { EXA_OBJ = 0, EXA_CON = 1, EXA_AUG = 2 };           /* pattern kinds (Sec. 3.3) */
+enum { EXA_FIELD_I32 = 0, EXA_FIELD_F64 = 1 };            /* data column types */
+
+typedef struct { int32_t op, a, b, pad; int64_t ival; double fval; } exa_vnode;
+typedef struct { int32_t op, a, b, pad; int64_t ival; } exa_inode;
+typedef struct { int32_t type, pad; const void *data; } exa_field; /* host column, n_inst long */
+
+/* One pattern (SIMDFunction plus its data, Sec. 3.4):
+ *   EXA_OBJ: contributes its value to f; gradient slots; Hessian weighted by sigma.
+ *   EXA_CON: instance k defines row row_base + k (row_limit = n_inst rows); Hessian weighted by
+ *            y[row].
+ *   EXA_AUG: instance k adds its value to row row_base + idx(k), idx = the index expression at
+ *            inode row_root, which must lie in [0, row_limit) (the target block's rows);
+ *            Jacobian entries on that row; Hessian weighted by y[that row].
+ * Two Var leaves are the same symbol iff their index subtrees are structurally identical. */
+typedef struct {
+    int32_t kind;
+    int32_t n_fields;
+    int64_t n_inst;
+    int64_t row_base;
+    int64_t row_limit;
+    int32_t row_root;
+    int32_t n_vnodes;
+    int32_t n_inodes;
+    int32_t pad;
+    const exa_vnode *vnodes;
+    const exa_inode *inodes;
+    const exa_field *fields;
+} exa_pattern_desc;
+
+typedef struct {
+    int64_t nvar, ncon, npar;
+    const double *theta;              /* npar host values */
+    int32_t n_patterns;
+    int32_t pad;
+    const exa_pattern_desc *patterns; /* in declaration order: fixes the COO block order */
+} exa_model_desc;
+
+/* Creation options.  Zero-initialised options are valid (FP64, automatic launch shape). */
+typedef struct {
+    int32_t precision;     /* exa_precision */
+    int32_t device;        /* CUDA device ordinal */
+    int32_t block_threads; /* threads per CTA of the evaluation kernel; 0 = automatic */
+    int32_t flags;         /* EXA_FLAG_* */
+} exa_options;
+
+enum {
+    EXA_FLAG_BOUNDS_CHECK = 1, /* every gather index is checked on the device; a violation makes
+                                  the next exa_check_status return EXA_E_BOUNDS */
+    EXA_FLAG_NO_TUNE = 2       /* skip the launch-shape autotuner at creation */
+};
+
+/* Validate the descriptor (Sec. 3.4 SIMDFunction), lower every pattern to generated device
+ * code and compile it with NVRTC for sm_103a, copy the data columns to the device, run the
+ * device structure pass (COO rows/cols of every slot, Sec. 5.3.1) and the device sorts that fix
+ * the COO->CSC permutation and the gradient/augmentation segment pointers.  Synchronizes the
+ * device.  On failure *out is NULL and exa_create_error() holds the message. */
+exa_status exa_create(const exa_model_desc *desc, const exa_options *opt, exa_model **out);
+
+/* Batch of nb models with identical pattern trees (same IR, Sec. 7.4.3) but their own data and
+ * sizes.  The batch behaves as one model whose x, y, c, and every COO array are the members'
+ * arrays concatenated in member order; member b's slice equals what exa_create on member b alone
+ * produces.  Offsets of each member: exa_batch_offsets. */
+exa_status exa_create_batch(const exa_model_desc *const *descs, int32_t nb, const exa_options *opt,
+                            exa_model **out);
+
+void exa_destroy(exa_model *m); /* synchronizes the model's stream, frees device memory */
+
+const char *exa_last_error(const exa_model *m); /* never NULL; "" if no error */
+const char *exa_create_error(void);             /* message of this thread's last failed create */
+
+/* Problem dimensions.  nnzj/nnzh count COO slots (duplicates included); *_csc count the
+ * distinct (row, col) entries.  Any output pointer may be NULL. */
+exa_status exa_dims(const exa_model *m, int64_t *nvar, int64_t *ncon, int64_t *nnzj, int64_t *nnzh,
+                    int64_t *nnzj_csc, int64_t *nnzh_csc);
+
+/* For batch models: per member b (nb + 1 entries each, prefix form) the first variable, row,
+ * Jacobian slot and Hessian slot of member b.  Any pointer may be NULL.  A plain model has nb=1. */
+exa_status exa_batch_offsets(const exa_model *m, int32_t *nb, int64_t *xoff, int64_t *coff,
+                             int64_t *joff, int64_t *hoff);
+
+/* Stream (a cudaStream_t) on which every later call on this model enqueues its work. */
+exa_status exa_set_stream(exa_model *m, void *stream);
+
+/* ------------------------------------------------------------------ callbacks (Sec. 2.1) */
+/* f[0] = f(x).  f: one device double.  Objective terms are reduced in FP64 in two stages
+ * (per-CTA partial sums, then one ordered sum), Sec. 7.2.3. */
+exa_status exa_obj(exa_model *m, const double *x, double *f);
+
+/* g[nvar] = grad f(x): each objective instance writes its own gradient slots, then a gather
+ * segmented sum per variable produces g (Sec. 7.2.3, no atomics). */
+exa_status exa_grad(exa_model *m, const double *x, double *g);
+
+/* c[ncon] = base rows plus augmentation terms (Sec. 3.3, 7.2.3). */
+exa_status exa_cons(exa_model *m, const double *x, double *c);
+
+/* COO structure: rows[nnzj], cols[nnzj] (device int32). */
+exa_status exa_jac_structure(const exa_model *m, int32_t *rows, int32_t *cols);
+/* COO values vals[nnzj] of the constraint Jacobian at x. */
+exa_status exa_jac_coord(exa_model *m, const double *x, double *vals);
+
+/* Lower-triangle COO structure (row >= col), rows[nnzh], cols[nnzh]. */
+exa_status exa_hess_structure(const exa_model *m, int32_t *rows, int32_t *cols);
+/* COO values vals[nnzh] of sigma * Hess f(x) + sum_r y[r] Hess c_r(x).  A slot pairing two
+ * different symbols that resolve to the same variable holds twice the mixed partial, so the
+ * symmetric expansion of the COO sum is the Hessian. */
+exa_status exa_hess_coord(exa_model *m, const double *x, const double *y, double sigma,
+                          double *vals);
+
+/* CSC structure of the Jacobian (ncon x nvar) and of the Hessian's lower triangle (nvar x nvar):
+ * colptr[nvar+1], rowval[nnz*_csc] (rows ascending within a column), coo2csc[nnz*]: the CSC
+ * position of every COO slot.  Built on the device at creation by a stable sort of (col, row). */
+exa_status exa_jac_csc_structure(const exa_model *m, int32_t *colptr, int32_t *rowval,
+                                 int32_t *coo2csc);
+exa_status exa_hess_csc_structure(const exa_model *m, int32_t *colptr, int32_t *rowval,
+                                  int32_t *coo2csc);
+/* CSC values: the COO values of each (row, col) summed in ascending COO order. */
+exa_status exa_jac_csc(exa_model *m, const double *x, double *vals_csc);
+exa_status exa_hess_csc(exa_model *m, const double *x, const double *y, double sigma,
+                        double *vals_csc);
+
+/* Everything in one pass over all patterns.  Any output may be NULL (not computed).
+ * jac/hess are COO values; jac_csc/hess_csc CSC values.  y and sigma are read only when hess or
+ * hess_csc is requested. */
+exa_status exa_eval_all(exa_model *m, const double *x, const double *y, double sigma, double *f,
+                        double *g, double *c, double *jac, double *hess, double *jac_csc,
+                        double *hess_csc);
+
+/* Products at x (NLPModels jprod!/jtprod!/hprod!): Jv[ncon] = J(x) v, Jtw[nvar] = J(x)^T w,
+ * Hv[nvar] = (sigma Hess f + sum y_r Hess c_r)(x) v with the Hessian's full symmetric action. */
+exa_status exa_jprod(exa_model *m, const double *x, const double *v, double *Jv);
+exa_status exa_jtprod(exa_model *m, const double *x, const double *w, double *Jtw);
+exa_status exa_hprod(exa_model *m, const double *x, const double *y, double sigma,
+                     const double *v, double *Hv);
+
+/* Synchronizes the model's stream and reports device-side faults recorded by bounded waits or
+ * bounds checks since the last call (EXA_E_BOUNDS, EXA_E_TIMEOUT), clearing them. */
+exa_status exa_check_status(exa_model *m);
+
+/* Named statistics (host values): "nvrtc_ms", "create_ms", "eval_regs", "eval_block",
+ * "eval_tiles", "device_bytes", "n_patterns", "batch_members".  Unknown key: EXA_E_INVALID. */
+exa_status exa_stat(const exa_model *m, const char *key, double *value);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EXA_H */
