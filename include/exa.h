@@ -39,6 +39,7 @@
 #ifndef EXA_H
 #define EXA_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -223,6 +224,12 @@ exa_status exa_hprod(exa_model *m, const double *x, const double *y, double sigm
 /* Synchronizes the model's stream and reports device-side faults recorded by bounded waits or
  * bounds checks since the last call (EXA_E_BOUNDS, EXA_E_TIMEOUT), clearing them. */
 exa_status exa_check_status(exa_model *m);
+
+/* Validate the descriptor, generate the kernels and compile them with NVRTC for sm_103a without
+ * touching any device (usable on a host without a GPU).  On failure the message (NVRTC log
+ * included) is copied, NUL-terminated, into log[0 .. loglen-1] when log is not NULL. */
+exa_status exa_compile_check(const exa_model_desc *desc, const exa_options *opt, char *log,
+                             size_t loglen);
 
 /* Named statistics (host values): "nvrtc_ms", "create_ms", "eval_regs", "eval_block",
  * "eval_tiles", "device_bytes", "n_patterns", "batch_members".  Unknown key: EXA_E_INVALID. */

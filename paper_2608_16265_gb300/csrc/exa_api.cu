@@ -1,0 +1,1041 @@
+// exa_api.cu -- the C ABI of include/exa.h: model creation (validation, NVRTC compilation of the
+// generated kernels, upload, device structure pass and sorts) and the evaluation callbacks.
+//
+// Evaluation data flow (Sec. 5.3, 7.2.3):
+//   eval kernel (generated; one thread per pattern instance, one CTA per tile of BLOCK instances of
+//   one (member, pattern) pair) writes every COO slot exactly once, constraint base values
+//   c[row], augmentation terms, objective gradient slots and one objective partial per CTA;
+//   then atomic-free gather kernels sum duplicates: dense gradient per variable, augmentation terms
+//   per row, CSC values per (row, col), the objective partials, and the products.
+#include <cuda_runtime.h>
+#include <nvrtc.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "exa_internal.h"
+
+cudaError_t exa_sort_pairs_u64(const unsigned long long *kin, unsigned long long *kout, const int *vin,
+                               int *vout, int n, int end_bit, cudaStream_t s);
+cudaError_t exa_inclusive_sum_i32(const int *in, int *out, int n, cudaStream_t s);
+
+using exa::Mode;
+typedef long long i64;
+
+// ------------------------------------------------------------------ static kernels
+namespace {
+
+// f[0] = sum of the per-CTA objective partials in a fixed order (deterministic).
+__global__ void k_obj_final(const double *__restrict__ part, int n, double *__restrict__ f) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+        f[0] = t;
+    }
+}
+
+// dst[i] = sum_{q in [ptr[i], ptr[i+1])} src[perm[q]]  (ascending q: ascending COO index)
+__global__ void k_seg_sum(const int *__restrict__ ptr, const int *__restrict__ perm,
+                          const double *__restrict__ src, double *__restrict__ dst, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int q = ptr[i], e = ptr[i + 1]; q < e; q++) s += src[perm[q]];
+    dst[i] = s;
+}
+
+// c[rows[i]] += sum of the augmentation terms of that row (rows listed once each)
+__global__ void k_seg_add_rows(const int *__restrict__ rows, const int *__restrict__ ptr,
+                               const int *__restrict__ perm, const double *__restrict__ src,
+                               double *__restrict__ c, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = c[rows[i]];
+    for (int q = ptr[i], e = ptr[i + 1]; q < e; q++) s += src[perm[q]];
+    c[rows[i]] = s;
+}
+
+// out[i] = sum_{q in [ptr[i], ptr[i+1])} val[perm[q]] * v[other[perm[q]]]
+__global__ void k_spmv_gather(const int *__restrict__ ptr, const int *__restrict__ perm,
+                              const double *__restrict__ val, const int *__restrict__ other,
+                              const double *__restrict__ v, double *__restrict__ out, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int q = ptr[i], e = ptr[i + 1]; q < e; q++) {
+        int p = perm[q];
+        s += val[p] * v[other[p]];
+    }
+    out[i] = s;
+}
+
+// Hv[i] = sum over lower entries (i, j) of H v_j  +  sum over lower entries (j, i), j != i, of H v_j
+__global__ void k_hprod(const int *__restrict__ rptr, const int *__restrict__ rperm,
+                        const int *__restrict__ cptr, const int *__restrict__ cperm,
+                        const int *__restrict__ hrow, const int *__restrict__ hcol,
+                        const double *__restrict__ h, const double *__restrict__ v,
+                        double *__restrict__ out, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int q = rptr[i], e = rptr[i + 1]; q < e; q++) {
+        int p = rperm[q];
+        s += h[p] * v[hcol[p]];
+    }
+    for (int q = cptr[i], e = cptr[i + 1]; q < e; q++) {
+        int p = cperm[q];
+        int r = hrow[p];
+        if (r != i) s += h[p] * v[r];
+    }
+    out[i] = s;
+}
+
+// ---- setup kernels
+__global__ void k_iota(int *a, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = i;
+}
+__global__ void k_keys2(const int *__restrict__ hi, const int *__restrict__ lo, unsigned long long *k, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) k[i] = ((unsigned long long)(unsigned)hi[i] << 32) | (unsigned)(lo ? lo[i] : 0);
+}
+__global__ void k_keys1(const int *__restrict__ a, unsigned long long *k, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) k[i] = (unsigned long long)(unsigned)a[i];
+}
+__global__ void k_new_segment(const unsigned long long *__restrict__ k, int *flag, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = (i == 0 || k[i] != k[i - 1]) ? 1 : 0;
+}
+// segment s starts at sorted position segptr[s]; its key is segkey[s]; every sorted position's
+// original index perm[i] maps to its segment in coo2seg (optional)
+__global__ void k_segments(const unsigned long long *__restrict__ k, const int *__restrict__ flag,
+                           const int *__restrict__ segid, const int *__restrict__ perm, int *segptr,
+                           unsigned long long *segkey, int *coo2seg, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int s = segid[i] - 1;
+    if (coo2seg) coo2seg[perm[i]] = s;
+    if (flag[i]) {
+        segptr[s] = i;
+        segkey[s] = k[i];
+    }
+    if (i == n - 1) segptr[s + 1] = n;
+}
+// ptr[c] = first position i with (key[i] >> shift) >= c, for c in [0, nbins]; keys sorted
+__global__ void k_build_ptr(const unsigned long long *__restrict__ k, int shift, int n, int nbins, int *ptr) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    long long lo = (i == 0) ? 0 : (long long)(k[i - 1] >> shift) + 1;
+    long long hi = (i == n) ? nbins : (long long)(k[i] >> shift);
+    for (long long c = lo; c <= hi; c++) ptr[c] = i;
+}
+__global__ void k_low32(const unsigned long long *__restrict__ k, int *out, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (int)(k[i] & 0xffffffffULL);
+}
+
+inline unsigned grid_of(i64 n, int b) { return (unsigned)((n + b - 1) / b); }
+
+thread_local std::string g_create_err;
+
+}  // namespace
+
+// ------------------------------------------------------------------ the model
+struct exa_model {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int precision = EXA_FP64;
+    int block = 128;
+    bool bounds_check = false;
+    i64 nvar = 0, ncon = 0, npar = 0, nnzj = 0, nnzh = 0, nnzj_csc = 0, nnzh_csc = 0, nnzg = 0, naug = 0;
+    int n_aug_rows = 0;
+    int nb = 1;
+    std::vector<i64> xoff, coff, joff, hoff;
+    std::vector<exa::Pattern> pats;
+
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t fn[exa::M_COUNT] = {};
+    int regs[exa::M_COUNT] = {};
+    ExaPM *d_pm = nullptr;
+    ExaTile *d_tiles[exa::M_COUNT] = {};
+    int ntiles[exa::M_COUNT] = {};
+    double *d_theta = nullptr;
+    int *d_status = nullptr;
+    int *d_jrow = nullptr, *d_jcol = nullptr, *d_hrow = nullptr, *d_hcol = nullptr, *d_gvar = nullptr, *d_arow = nullptr;
+    // Jacobian: CSC (segments over the (col,row)-sorted COO) and row grouping
+    int *d_jperm = nullptr, *d_jsegptr = nullptr, *d_jcolptr = nullptr, *d_jrowval = nullptr, *d_jcoo2csc = nullptr;
+    int *d_jcolptr_coo = nullptr, *d_jrperm = nullptr, *d_jrptr = nullptr;
+    // Hessian: same
+    int *d_hperm = nullptr, *d_hsegptr = nullptr, *d_hcolptr = nullptr, *d_hrowval = nullptr, *d_hcoo2csc = nullptr;
+    int *d_hcolptr_coo = nullptr, *d_hrperm = nullptr, *d_hrptr = nullptr;
+    // gradient and augmentation segments
+    int *d_gperm = nullptr, *d_gptr = nullptr;
+    int *d_aperm = nullptr, *d_aptr = nullptr, *d_arows = nullptr;
+    // work buffers
+    double *d_jbuf = nullptr, *d_hbuf = nullptr, *d_gbuf = nullptr, *d_abuf = nullptr, *d_objpart = nullptr,
+           *d_cbuf = nullptr;
+    std::vector<void *> allocs;
+    size_t device_bytes = 0;
+    double nvrtc_ms = 0, create_ms = 0;
+    std::string err;
+};
+
+namespace {
+
+exa_status fail(exa_model *m, exa_status s, const std::string &msg) {
+    if (m) m->err = msg;
+    return s;
+}
+
+template <typename T>
+cudaError_t dalloc(exa_model *m, T **p, i64 count) {
+    *p = nullptr;
+    size_t bytes = (size_t)std::max<i64>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e == cudaSuccess) {
+        m->allocs.push_back(*p);
+        m->device_bytes += bytes;
+    }
+    return e;
+}
+
+#define CR(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(m, e_ == cudaErrorMemoryAllocation ? EXA_E_OOM : EXA_E_CUDA,               \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+    } while (0)
+
+void free_all(exa_model *m) {
+    for (void *p : m->allocs) cudaFree(p);
+    m->allocs.clear();
+    if (m->lib) cudaLibraryUnload(m->lib);
+    m->lib = nullptr;
+}
+
+exa_status nvrtc_compile(exa_model *m, const std::string &src, std::vector<char> &cubin) {
+    nvrtcProgram prog;
+    if (nvrtcCreateProgram(&prog, src.c_str(), "exa_generated.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
+        return fail(m, EXA_E_NVRTC, "nvrtcCreateProgram failed");
+    const char *opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo", "--fmad=true",
+                          "-default-device"};
+    nvrtcResult r = nvrtcCompileProgram(prog, sizeof(opts) / sizeof(opts[0]), opts);
+    if (r != NVRTC_SUCCESS) {
+        size_t n = 0;
+        nvrtcGetProgramLogSize(prog, &n);
+        std::string log(n, '\0');
+        nvrtcGetProgramLog(prog, &log[0]);
+        nvrtcDestroyProgram(&prog);
+        return fail(m, EXA_E_NVRTC, std::string("NVRTC: ") + nvrtcGetErrorString(r) + "\n" + log.substr(0, 4000));
+    }
+    size_t n = 0;
+    nvrtcGetCUBINSize(prog, &n);
+    cubin.resize(n);
+    nvrtcGetCUBIN(prog, cubin.data());
+    nvrtcDestroyProgram(&prog);
+    return EXA_OK;
+}
+
+exa_status compile(exa_model *m, const std::string &src) {
+    auto t0 = std::chrono::steady_clock::now();
+    std::vector<char> cubin;
+    if (exa_status e = nvrtc_compile(m, src, cubin)) return e;
+    m->nvrtc_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    CR(cudaLibraryLoadData(&m->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0));
+    for (int k = 0; k < exa::M_COUNT; k++) {
+        std::string name = std::string("exa_") + exa::kModeName[k];
+        CR(cudaLibraryGetKernel(&m->fn[k], m->lib, name.c_str()));
+        cudaFuncAttributes attr;
+        CR(cudaFuncGetAttributes(&attr, (const void *)m->fn[k]));
+        m->regs[k] = attr.numRegs;
+    }
+    return EXA_OK;
+}
+
+exa_status launch_eval(exa_model *m, Mode mode, const double *x, const double *y, double sigma, ExaOut out) {
+    if (m->ntiles[mode] == 0) return EXA_OK;
+    out.status = m->d_status;
+    ExaStructOut so{};
+    so.status = m->d_status;
+    const double *th = m->d_theta;
+    void *args[] = {&m->d_tiles[mode], &m->d_pm, &x, &y, &th, &sigma, &out, &so};
+    CR(cudaLaunchKernel((const void *)m->fn[mode], dim3(m->ntiles[mode]), dim3(m->block), args, 0, m->stream));
+    return EXA_OK;
+}
+
+exa_status check_model(exa_model *m) {
+    if (!m) return EXA_E_INVALID;
+    CR(cudaSetDevice(m->device));
+    return EXA_OK;
+}
+
+// Sorted-key helpers used by the structure setup -----------------------------------------------
+struct Scratch {
+    exa_model *m;
+    std::vector<void *> mine;
+    ~Scratch() {
+        for (void *p : mine) cudaFree(p);
+    }
+    template <typename T>
+    cudaError_t get(T **p, i64 n) {
+        cudaError_t e = cudaMalloc((void **)p, (size_t)std::max<i64>(n, 1) * sizeof(T));
+        if (e == cudaSuccess) mine.push_back(*p);
+        return e;
+    }
+};
+
+// Sort keys with values 0..n-1 (stable): sorted keys and permutation.
+exa_status sort_with_perm(exa_model *m, Scratch &S, unsigned long long *keys, int n, int end_bit,
+                          unsigned long long **skeys, int *perm) {
+    int *iota = nullptr;
+    CR(S.get(&iota, n));
+    CR(S.get(skeys, n));
+    if (n > 0) {
+        k_iota<<<grid_of(n, 256), 256, 0, m->stream>>>(iota, n);
+        CR(cudaGetLastError());
+        CR(exa_sort_pairs_u64(keys, *skeys, iota, perm, n, end_bit, m->stream));
+    }
+    return EXA_OK;
+}
+
+// Segments of equal sorted keys: count, start positions, keys, and (optional) position -> segment.
+exa_status segments(exa_model *m, Scratch &S, const unsigned long long *skeys, const int *perm, int n,
+                    int *nseg, int **segptr, unsigned long long **segkey, int *coo2seg, bool persistent_ptr) {
+    int *flag = nullptr, *segid = nullptr;
+    CR(S.get(&flag, n));
+    CR(S.get(&segid, n));
+    *nseg = 0;
+    if (n > 0) {
+        k_new_segment<<<grid_of(n, 256), 256, 0, m->stream>>>(skeys, flag, n);
+        CR(cudaGetLastError());
+        CR(exa_inclusive_sum_i32(flag, segid, n, m->stream));
+        CR(cudaMemcpy(nseg, segid + n - 1, sizeof(int), cudaMemcpyDeviceToHost));
+    }
+    if (persistent_ptr) CR(dalloc(m, segptr, (i64)*nseg + 1));
+    else CR(S.get(segptr, (i64)*nseg + 1));
+    CR(S.get(segkey, *nseg));
+    if (n > 0) {
+        k_segments<<<grid_of(n, 256), 256, 0, m->stream>>>(skeys, flag, segid, perm, *segptr, *segkey, coo2seg, n);
+        CR(cudaGetLastError());
+    } else {
+        CR(cudaMemset(*segptr, 0, sizeof(int)));
+    }
+    return EXA_OK;
+}
+
+exa_status build_ptr(exa_model *m, const unsigned long long *skeys, int shift, int n, i64 nbins, int **ptr) {
+    CR(dalloc(m, ptr, nbins + 1));
+    k_build_ptr<<<grid_of((i64)n + 1, 256), 256, 0, m->stream>>>(skeys, shift, n, (int)nbins, *ptr);
+    CR(cudaGetLastError());
+    return EXA_OK;
+}
+
+// Per-model structure: CSC of J and H, row groupings, gradient and augmentation segments.
+exa_status build_structure(exa_model *m) {
+    Scratch S{m};
+    const int nj = (int)m->nnzj, nh = (int)m->nnzh, ng = (int)m->nnzg, na = (int)m->naug;
+    unsigned long long *keys = nullptr, *skeys = nullptr, *segkey = nullptr;
+    int nseg = 0;
+    // ---- Jacobian CSC: sort (col, row)
+    CR(S.get(&keys, std::max({nj, nh, ng, na, 1})));
+    CR(dalloc(m, &m->d_jperm, nj));
+    CR(dalloc(m, &m->d_jcoo2csc, nj));
+    if (nj) {
+        k_keys2<<<grid_of(nj, 256), 256, 0, m->stream>>>(m->d_jcol, m->d_jrow, keys, nj);
+        CR(cudaGetLastError());
+    }
+    if (exa_status e = sort_with_perm(m, S, keys, nj, 64, &skeys, m->d_jperm)) return e;
+    if (exa_status e = segments(m, S, skeys, m->d_jperm, nj, &nseg, &m->d_jsegptr, &segkey, m->d_jcoo2csc, true)) return e;
+    m->nnzj_csc = nseg;
+    CR(dalloc(m, &m->d_jrowval, nseg));
+    if (nseg) {
+        k_low32<<<grid_of(nseg, 256), 256, 0, m->stream>>>(segkey, m->d_jrowval, nseg);
+        CR(cudaGetLastError());
+    }
+    if (exa_status e = build_ptr(m, segkey, 32, nseg, m->nvar, &m->d_jcolptr)) return e;
+    if (exa_status e = build_ptr(m, skeys, 32, nj, m->nvar, &m->d_jcolptr_coo)) return e;
+    // ---- Jacobian row grouping
+    CR(dalloc(m, &m->d_jrperm, nj));
+    if (nj) {
+        k_keys1<<<grid_of(nj, 256), 256, 0, m->stream>>>(m->d_jrow, keys, nj);
+        CR(cudaGetLastError());
+    }
+    if (exa_status e = sort_with_perm(m, S, keys, nj, 32, &skeys, m->d_jrperm)) return e;
+    if (exa_status e = build_ptr(m, skeys, 0, nj, m->ncon, &m->d_jrptr)) return e;
+
+    // ---- Hessian CSC
+    CR(dalloc(m, &m->d_hperm, nh));
+    CR(dalloc(m, &m->d_hcoo2csc, nh));
+    if (nh) {
+        k_keys2<<<grid_of(nh, 256), 256, 0, m->stream>>>(m->d_hcol, m->d_hrow, keys, nh);
+        CR(cudaGetLastError());
+    }
+    if (exa_status e = sort_with_perm(m, S, keys, nh, 64, &skeys, m->d_hperm)) return e;
+    if (exa_status e = segments(m, S, skeys, m->d_hperm, nh, &nseg, &m->d_hsegptr, &segkey, m->d_hcoo2csc, true)) return e;
+    m->nnzh_csc = nseg;
+    CR(dalloc(m, &m->d_hrowval, nseg));
+    if (nseg) {
+        k_low32<<<grid_of(nseg, 256), 256, 0, m->stream>>>(segkey, m->d_hrowval, nseg);
+        CR(cudaGetLastError());
+    }
+    if (exa_status e = build_ptr(m, segkey, 32, nseg, m->nvar, &m->d_hcolptr)) return e;
+    if (exa_status e = build_ptr(m, skeys, 32, nh, m->nvar, &m->d_hcolptr_coo)) return e;
+    CR(dalloc(m, &m->d_hrperm, nh));
+    if (nh) {
+        k_keys1<<<grid_of(nh, 256), 256, 0, m->stream>>>(m->d_hrow, keys, nh);
+        CR(cudaGetLastError());
+    }
+    if (exa_status e = sort_with_perm(m, S, keys, nh, 32, &skeys, m->d_hrperm)) return e;
+    if (exa_status e = build_ptr(m, skeys, 0, nh, m->nvar, &m->d_hrptr)) return e;
+
+    // ---- gradient segments by variable
+    CR(dalloc(m, &m->d_gperm, ng));
+    if (ng) {
+        k_keys1<<<grid_of(ng, 256), 256, 0, m->stream>>>(m->d_gvar, keys, ng);
+        CR(cudaGetLastError());
+    }
+    if (exa_status e = sort_with_perm(m, S, keys, ng, 32, &skeys, m->d_gperm)) return e;
+    if (exa_status e = build_ptr(m, skeys, 0, ng, m->nvar, &m->d_gptr)) return e;
+
+    // ---- augmentation segments by row (only rows that receive terms)
+    CR(dalloc(m, &m->d_aperm, na));
+    if (na) {
+        k_keys1<<<grid_of(na, 256), 256, 0, m->stream>>>(m->d_arow, keys, na);
+        CR(cudaGetLastError());
+    }
+    if (exa_status e = sort_with_perm(m, S, keys, na, 32, &skeys, m->d_aperm)) return e;
+    if (exa_status e = segments(m, S, skeys, m->d_aperm, na, &nseg, &m->d_aptr, &segkey, nullptr, true)) return e;
+    m->n_aug_rows = nseg;
+    CR(dalloc(m, &m->d_arows, nseg));
+    if (nseg) {
+        k_low32<<<grid_of(nseg, 256), 256, 0, m->stream>>>(segkey, m->d_arows, nseg);
+        CR(cudaGetLastError());
+    }
+    CR(cudaStreamSynchronize(m->stream));
+    return EXA_OK;
+}
+
+bool same_ir(const exa_pattern_desc &a, const exa_pattern_desc &b) {
+    if (a.kind != b.kind || a.n_vnodes != b.n_vnodes || a.n_inodes != b.n_inodes || a.n_fields != b.n_fields ||
+        a.row_root != b.row_root)
+        return false;
+    for (int i = 0; i < a.n_vnodes; i++) {
+        const exa_vnode &u = a.vnodes[i], &v = b.vnodes[i];
+        if (u.op != v.op || u.a != v.a || u.b != v.b || u.ival != v.ival ||
+            std::memcmp(&u.fval, &v.fval, sizeof(double)) != 0)
+            return false;
+    }
+    for (int i = 0; i < a.n_inodes; i++) {
+        const exa_inode &u = a.inodes[i], &v = b.inodes[i];
+        if (u.op != v.op || u.a != v.a || u.b != v.b || u.ival != v.ival) return false;
+    }
+    for (int f = 0; f < a.n_fields; f++)
+        if (a.fields[f].type != b.fields[f].type) return false;
+    return true;
+}
+
+exa_status load_patterns(const exa_model_desc &d0, exa_model *m) {
+    const int np = d0.n_patterns;
+    m->pats.resize(np);
+    for (int p = 0; p < np; p++) {
+        const exa_pattern_desc &pd = d0.patterns[p];
+        exa::Pattern &P = m->pats[p];
+        P.kind = pd.kind;
+        P.n_inst = pd.n_inst;
+        P.row_base = pd.row_base;
+        P.row_limit = pd.row_limit;
+        P.row_root = pd.row_root;
+        for (int i = 0; i < pd.n_vnodes; i++) {
+            const exa_vnode &v = pd.vnodes[i];
+            P.v.push_back({v.op, v.a, v.b, v.ival, v.fval});
+        }
+        for (int i = 0; i < pd.n_inodes; i++) {
+            const exa_inode &v = pd.inodes[i];
+            P.ix.push_back({v.op, v.a, v.b, v.ival});
+        }
+        for (int f = 0; f < pd.n_fields; f++) P.ftype.push_back(pd.fields[f].type);
+        std::string e = exa::analyse_pattern(P);
+        if (!e.empty()) return fail(m, EXA_E_INVALID, "pattern " + std::to_string(p) + ": " + e);
+    }
+    return EXA_OK;
+}
+
+exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_options *opt, exa_model *m) {
+    auto t0 = std::chrono::steady_clock::now();
+    exa_options o{};
+    if (opt) o = *opt;
+    if (o.precision != EXA_FP64 && o.precision != EXA_MIXED_FP32) return fail(m, EXA_E_INVALID, "unknown precision");
+    if (o.precision == EXA_MIXED_FP32) return fail(m, EXA_E_UNSUPPORTED, "mixed precision is not built yet");
+    m->precision = o.precision;
+    m->device = o.device;
+    m->bounds_check = (o.flags & EXA_FLAG_BOUNDS_CHECK) != 0;
+    m->block = o.block_threads ? o.block_threads : 128;
+    if (m->block % 32 || m->block < 32 || m->block > 1024) return fail(m, EXA_E_INVALID, "block_threads must be a multiple of 32 in [32, 1024]");
+    if (nb < 1) return fail(m, EXA_E_INVALID, "empty batch");
+    for (int b = 0; b < nb; b++) {
+        const exa_model_desc *d = descs[b];
+        if (!d) return fail(m, EXA_E_INVALID, "NULL model descriptor");
+        if (d->nvar < 0 || d->ncon < 0 || d->npar < 0 || d->n_patterns < 0) return fail(m, EXA_E_INVALID, "negative size");
+        if (d->n_patterns > 0 && !d->patterns) return fail(m, EXA_E_INVALID, "NULL pattern array");
+        if (d->npar > 0 && !d->theta) return fail(m, EXA_E_INVALID, "NULL theta");
+        if (d->n_patterns != descs[0]->n_patterns) return fail(m, EXA_E_INVALID, "batch members differ in pattern count");
+        for (int p = 0; p < d->n_patterns; p++) {
+            const exa_pattern_desc &pd = d->patterns[p];
+            if ((pd.n_vnodes > 0 && !pd.vnodes) || (pd.n_inodes > 0 && !pd.inodes) || (pd.n_fields > 0 && !pd.fields))
+                return fail(m, EXA_E_INVALID, "NULL node or field array");
+            if (pd.n_vnodes < 0 || pd.n_inodes < 0 || pd.n_fields < 0) return fail(m, EXA_E_INVALID, "negative node count");
+            for (int f = 0; f < pd.n_fields; f++)
+                if (pd.n_inst > 0 && !pd.fields[f].data) return fail(m, EXA_E_INVALID, "NULL data column");
+            if (b > 0 && !same_ir(pd, descs[0]->patterns[p]))
+                return fail(m, EXA_E_INVALID, "batch members must share identical pattern trees");
+        }
+    }
+    CR(cudaSetDevice(m->device));
+    int major = 0, minor = 0;
+    CR(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, m->device));
+    CR(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, m->device));
+    if (major != 10 || minor != 3)
+        return fail(m, EXA_E_UNSUPPORTED, "this build targets sm_103a (GB300); device is sm_" +
+                                                 std::to_string(major) + std::to_string(minor));
+
+    // patterns from member 0 (the IR is shared)
+    const exa_model_desc &d0 = *descs[0];
+    const int np = d0.n_patterns;
+    if (exa_status e = load_patterns(d0, m)) return e;
+
+    // per-member sizes and offsets; validate row blocks
+    m->nb = nb;
+    m->xoff.assign(nb + 1, 0); m->coff.assign(nb + 1, 0); m->joff.assign(nb + 1, 0); m->hoff.assign(nb + 1, 0);
+    std::vector<i64> goff(nb + 1, 0), aoff(nb + 1, 0), poff(nb + 1, 0);
+    std::vector<ExaPM> pms((size_t)nb * np);
+    for (int b = 0; b < nb; b++) {
+        const exa_model_desc &d = *descs[b];
+        if (d.nvar >= (1LL << 31) || d.ncon >= (1LL << 31)) return fail(m, EXA_E_INVALID, "size too large");
+        std::vector<int> covered(d.ncon, 0);
+        i64 oj = 0, oh = 0, og = 0, oa = 0;
+        for (int p = 0; p < np; p++) {
+            const exa_pattern_desc &pd = d.patterns[p];
+            const exa::Pattern &P = m->pats[p];
+            if (pd.n_inst < 0 || pd.n_inst >= (1LL << 31)) return fail(m, EXA_E_INVALID, "bad instance count");
+            if (P.kind == EXA_CON) {
+                if (pd.row_base < 0 || pd.row_base + pd.n_inst > d.ncon) return fail(m, EXA_E_BOUNDS, "constraint block out of range");
+                for (i64 r = pd.row_base; r < pd.row_base + pd.n_inst; r++)
+                    if (covered[r]++) return fail(m, EXA_E_INVALID, "constraint blocks overlap");
+            }
+            if (P.kind == EXA_AUG) {
+                if (pd.row_base < 0 || pd.row_limit < 0 || pd.row_base + pd.row_limit > d.ncon)
+                    return fail(m, EXA_E_BOUNDS, "augmentation target block out of range");
+                if (pd.n_inst > 0 && pd.row_limit == 0) return fail(m, EXA_E_INVALID, "augmentation target block is empty");
+            }
+            ExaPM &pm = pms[(size_t)b * np + p];
+            std::memset(&pm, 0, sizeof pm);
+            pm.n_inst = pd.n_inst;
+            pm.nvar_m = d.nvar;
+            pm.npar_m = d.npar;
+            pm.rbase = pd.row_base;  // member offset added below
+            pm.rlimit = pd.row_limit;
+            pm.pat = p;
+            pm.member = b;
+            pm.hbase = oh; oh += pd.n_inst * P.nh();
+            if (P.kind == EXA_OBJ) { pm.gbase = og; og += pd.n_inst * P.nj(); }
+            else { pm.jbase = oj; oj += pd.n_inst * P.nj(); }
+            if (P.kind == EXA_AUG) { pm.abase = oa; oa += pd.n_inst; }
+        }
+        for (i64 r = 0; r < d.ncon; r++)
+            if (!covered[r]) return fail(m, EXA_E_INVALID, "every constraint row must belong to exactly one base constraint pattern");
+        m->xoff[b + 1] = m->xoff[b] + d.nvar;
+        m->coff[b + 1] = m->coff[b] + d.ncon;
+        m->joff[b + 1] = m->joff[b] + oj;
+        m->hoff[b + 1] = m->hoff[b] + oh;
+        goff[b + 1] = goff[b] + og;
+        aoff[b + 1] = aoff[b] + oa;
+        poff[b + 1] = poff[b] + d.npar;
+    }
+    m->nvar = m->xoff[nb]; m->ncon = m->coff[nb]; m->nnzj = m->joff[nb]; m->nnzh = m->hoff[nb];
+    m->nnzg = goff[nb]; m->naug = aoff[nb]; m->npar = poff[nb];
+    if (m->nvar >= (1LL << 31) || m->ncon >= (1LL << 31) || m->nnzj >= (1LL << 31) || m->nnzh >= (1LL << 31) ||
+        m->nnzg >= (1LL << 31) || m->naug >= (1LL << 31))
+        return fail(m, EXA_E_INVALID, "model exceeds 2^31-1 variables, rows or nonzeros");
+
+    // generate and compile
+    exa::CodegenOptions cg;
+    cg.precision = m->precision;
+    cg.block = m->block;
+    cg.bounds_check = m->bounds_check;
+    std::string gerr;
+    std::string src = exa::generate_source(m->pats, cg, &gerr);
+    if (!gerr.empty()) return fail(m, EXA_E_INTERNAL, gerr);
+    if (getenv("EXA_DUMP_SOURCE")) {
+        FILE *fp = fopen(getenv("EXA_DUMP_SOURCE"), "w");
+        if (fp) { fputs(src.c_str(), fp); fclose(fp); }
+    }
+    if (exa_status e = compile(m, src)) return e;
+
+    // upload theta and data columns (identical host columns are uploaded once)
+    CR(dalloc(m, &m->d_theta, m->npar));
+    CR(dalloc(m, &m->d_status, 1));
+    CR(cudaMemset(m->d_status, 0, sizeof(int)));
+    for (int b = 0; b < nb; b++) {
+        const exa_model_desc &d = *descs[b];
+        if (d.npar) CR(cudaMemcpy(m->d_theta + poff[b], d.theta, sizeof(double) * d.npar, cudaMemcpyHostToDevice));
+        std::map<const void *, const void *> uploaded;
+        for (int p = 0; p < np; p++) {
+            const exa_pattern_desc &pd = d.patterns[p];
+            ExaPM &pm = pms[(size_t)b * np + p];
+            pm.xoff = m->xoff[b];
+            pm.poff = poff[b];
+            pm.rbase += m->coff[b];
+            pm.jbase += m->joff[b];
+            pm.hbase += m->hoff[b];
+            pm.gbase += goff[b];
+            pm.abase += aoff[b];
+            for (int f = 0; f < pd.n_fields; f++) {
+                const void *h = pd.fields[f].data;
+                auto it = uploaded.find(h);
+                if (it != uploaded.end() && pd.n_inst > 0) { pm.f[f] = it->second; continue; }
+                size_t es = pd.fields[f].type == EXA_FIELD_I32 ? 4 : 8;
+                void *dp = nullptr;
+                CR(dalloc(m, (char **)&dp, (i64)(pd.n_inst * es)));
+                if (pd.n_inst) CR(cudaMemcpy(dp, h, es * pd.n_inst, cudaMemcpyHostToDevice));
+                pm.f[f] = dp;
+                uploaded[h] = dp;
+            }
+        }
+    }
+    CR(dalloc(m, &m->d_pm, (i64)pms.size()));
+    CR(cudaMemcpy(m->d_pm, pms.data(), sizeof(ExaPM) * pms.size(), cudaMemcpyHostToDevice));
+
+    // tile lists per kernel kind: member-major, then patterns in declaration order
+    for (int k = 0; k < exa::M_COUNT; k++) {
+        std::vector<ExaTile> tiles;
+        for (int b = 0; b < nb; b++)
+            for (int p = 0; p < np; p++) {
+                const exa::Pattern &P = m->pats[p];
+                bool in = true;
+                switch (k) {
+                case exa::M_OBJ: case exa::M_GRAD: in = P.kind == EXA_OBJ; break;
+                case exa::M_CON: case exa::M_JAC: in = P.kind != EXA_OBJ; break;
+                case exa::M_HESS: in = P.nh() > 0; break;
+                default: break;
+                }
+                if (!in) continue;
+                const ExaPM &pm = pms[(size_t)b * np + p];
+                for (i64 s = 0; s < pm.n_inst; s += m->block) tiles.push_back({b * np + p, (int)s});
+            }
+        m->ntiles[k] = (int)tiles.size();
+        CR(dalloc(m, &m->d_tiles[k], (i64)tiles.size()));
+        if (!tiles.empty())
+            CR(cudaMemcpy(m->d_tiles[k], tiles.data(), sizeof(ExaTile) * tiles.size(), cudaMemcpyHostToDevice));
+    }
+
+    // structure pass on the device
+    CR(dalloc(m, &m->d_jrow, m->nnzj));
+    CR(dalloc(m, &m->d_jcol, m->nnzj));
+    CR(dalloc(m, &m->d_hrow, m->nnzh));
+    CR(dalloc(m, &m->d_hcol, m->nnzh));
+    CR(dalloc(m, &m->d_gvar, m->nnzg));
+    CR(dalloc(m, &m->d_arow, m->naug));
+    if (m->ntiles[exa::M_STRUCT]) {
+        ExaOut out{};
+        out.status = m->d_status;
+        ExaStructOut so{m->d_jrow, m->d_jcol, m->d_hrow, m->d_hcol, m->d_gvar, m->d_arow, m->d_status};
+        const double *nul = nullptr;
+        double sigma = 0;
+        void *args[] = {&m->d_tiles[exa::M_STRUCT], &m->d_pm, &nul, &nul, &m->d_theta, &sigma, &out, &so};
+        CR(cudaLaunchKernel((const void *)m->fn[exa::M_STRUCT], dim3(m->ntiles[exa::M_STRUCT]), dim3(m->block),
+                            args, 0, m->stream));
+        CR(cudaStreamSynchronize(m->stream));
+        int st = 0;
+        CR(cudaMemcpy(&st, m->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (st) return fail(m, EXA_E_BOUNDS, "a resolved variable, parameter or row index is out of range");
+    }
+    if (exa_status e = build_structure(m)) return e;
+
+    // work buffers
+    CR(dalloc(m, &m->d_jbuf, m->nnzj));
+    CR(dalloc(m, &m->d_hbuf, m->nnzh));
+    CR(dalloc(m, &m->d_gbuf, m->nnzg));
+    CR(dalloc(m, &m->d_abuf, m->naug));
+    CR(dalloc(m, &m->d_cbuf, m->ncon));
+    int maxt = 1;
+    for (int k = 0; k < exa::M_COUNT; k++) maxt = std::max(maxt, m->ntiles[k]);
+    CR(dalloc(m, &m->d_objpart, maxt));
+    CR(cudaDeviceSynchronize());
+    m->create_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return EXA_OK;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+extern "C" {
+
+const char *exa_create_error(void) { return g_create_err.c_str(); }
+
+const char *exa_last_error(const exa_model *m) { return m ? m->err.c_str() : "NULL model"; }
+
+exa_status exa_create_batch(const exa_model_desc *const *descs, int32_t nb, const exa_options *opt, exa_model **out) {
+    if (!out) return EXA_E_INVALID;
+    *out = nullptr;
+    if (!descs) {
+        g_create_err = "NULL descriptor array";
+        return EXA_E_INVALID;
+    }
+    exa_model *m = new (std::nothrow) exa_model();
+    if (!m) {
+        g_create_err = "host allocation failed";
+        return EXA_E_OOM;
+    }
+    exa_status s;
+    try {
+        s = create_impl(descs, nb, opt, m);
+    } catch (const std::exception &e) {
+        s = fail(m, EXA_E_OOM, std::string("host exception: ") + e.what());
+    }
+    if (s != EXA_OK) {
+        g_create_err = m->err;
+        free_all(m);
+        delete m;
+        return s;
+    }
+    g_create_err.clear();
+    *out = m;
+    return EXA_OK;
+}
+
+exa_status exa_create(const exa_model_desc *desc, const exa_options *opt, exa_model **out) {
+    const exa_model_desc *d[1] = {desc};
+    return exa_create_batch(d, 1, opt, out);
+}
+
+void exa_destroy(exa_model *m) {
+    if (!m) return;
+    cudaSetDevice(m->device);
+    cudaStreamSynchronize(m->stream);
+    free_all(m);
+    delete m;
+}
+
+exa_status exa_dims(const exa_model *m, int64_t *nvar, int64_t *ncon, int64_t *nnzj, int64_t *nnzh,
+                    int64_t *nnzj_csc, int64_t *nnzh_csc) {
+    if (!m) return EXA_E_INVALID;
+    if (nvar) *nvar = m->nvar;
+    if (ncon) *ncon = m->ncon;
+    if (nnzj) *nnzj = m->nnzj;
+    if (nnzh) *nnzh = m->nnzh;
+    if (nnzj_csc) *nnzj_csc = m->nnzj_csc;
+    if (nnzh_csc) *nnzh_csc = m->nnzh_csc;
+    return EXA_OK;
+}
+
+exa_status exa_batch_offsets(const exa_model *m, int32_t *nb, int64_t *xoff, int64_t *coff, int64_t *joff,
+                             int64_t *hoff) {
+    if (!m) return EXA_E_INVALID;
+    if (nb) *nb = m->nb;
+    for (int b = 0; b <= m->nb; b++) {
+        if (xoff) xoff[b] = m->xoff[b];
+        if (coff) coff[b] = m->coff[b];
+        if (joff) joff[b] = m->joff[b];
+        if (hoff) hoff[b] = m->hoff[b];
+    }
+    return EXA_OK;
+}
+
+exa_status exa_set_stream(exa_model *m, void *stream) {
+    if (!m) return EXA_E_INVALID;
+    m->stream = (cudaStream_t)stream;
+    return EXA_OK;
+}
+
+#define CHECK_PTRS(...)                                                                            \
+    do {                                                                                           \
+        const void *ps_[] = {__VA_ARGS__};                                                         \
+        for (const void *p_ : ps_)                                                                 \
+            if (!p_) return fail(m, EXA_E_INVALID, "NULL array argument");                         \
+    } while (0)
+
+exa_status exa_obj(exa_model *m, const double *x, double *f) {
+    if (exa_status e = check_model(m)) return e;
+    CHECK_PTRS(x, f);
+    ExaOut o{};
+    o.obj_part = m->d_objpart;
+    if (exa_status e = launch_eval(m, exa::M_OBJ, x, nullptr, 0.0, o)) return e;
+    k_obj_final<<<1, 256, 0, m->stream>>>(m->d_objpart, m->ntiles[exa::M_OBJ], f);
+    CR(cudaGetLastError());
+    return EXA_OK;
+}
+
+exa_status exa_grad(exa_model *m, const double *x, double *g) {
+    if (exa_status e = check_model(m)) return e;
+    CHECK_PTRS(x, g);
+    ExaOut o{};
+    o.gbuf = m->d_gbuf;
+    if (exa_status e = launch_eval(m, exa::M_GRAD, x, nullptr, 0.0, o)) return e;
+    if (m->nvar) {
+        k_seg_sum<<<grid_of(m->nvar, 256), 256, 0, m->stream>>>(m->d_gptr, m->d_gperm, m->d_gbuf, g, (int)m->nvar);
+        CR(cudaGetLastError());
+    }
+    return EXA_OK;
+}
+
+static exa_status aug_rows(exa_model *m, double *c) {
+    if (m->n_aug_rows) {
+        k_seg_add_rows<<<grid_of(m->n_aug_rows, 256), 256, 0, m->stream>>>(m->d_arows, m->d_aptr, m->d_aperm,
+                                                                              m->d_abuf, c, m->n_aug_rows);
+        CR(cudaGetLastError());
+    }
+    return EXA_OK;
+}
+
+exa_status exa_cons(exa_model *m, const double *x, double *c) {
+    if (exa_status e = check_model(m)) return e;
+    if (m->ncon == 0) return EXA_OK;
+    CHECK_PTRS(x, c);
+    ExaOut o{};
+    o.c = c;
+    o.abuf = m->d_abuf;
+    if (exa_status e = launch_eval(m, exa::M_CON, x, nullptr, 0.0, o)) return e;
+    return aug_rows(m, c);
+}
+
+exa_status exa_jac_structure(const exa_model *mc, int32_t *rows, int32_t *cols) {
+    exa_model *m = const_cast<exa_model *>(mc);
+    if (exa_status e = check_model(m)) return e;
+    if (!m->nnzj) return EXA_OK;
+    CHECK_PTRS(rows, cols);
+    CR(cudaMemcpyAsync(rows, m->d_jrow, sizeof(int) * m->nnzj, cudaMemcpyDeviceToDevice, m->stream));
+    CR(cudaMemcpyAsync(cols, m->d_jcol, sizeof(int) * m->nnzj, cudaMemcpyDeviceToDevice, m->stream));
+    return EXA_OK;
+}
+
+exa_status exa_hess_structure(const exa_model *mc, int32_t *rows, int32_t *cols) {
+    exa_model *m = const_cast<exa_model *>(mc);
+    if (exa_status e = check_model(m)) return e;
+    if (!m->nnzh) return EXA_OK;
+    CHECK_PTRS(rows, cols);
+    CR(cudaMemcpyAsync(rows, m->d_hrow, sizeof(int) * m->nnzh, cudaMemcpyDeviceToDevice, m->stream));
+    CR(cudaMemcpyAsync(cols, m->d_hcol, sizeof(int) * m->nnzh, cudaMemcpyDeviceToDevice, m->stream));
+    return EXA_OK;
+}
+
+exa_status exa_jac_coord(exa_model *m, const double *x, double *vals) {
+    if (exa_status e = check_model(m)) return e;
+    if (!m->nnzj) return EXA_OK;
+    CHECK_PTRS(x, vals);
+    ExaOut o{};
+    o.jac = vals;
+    return launch_eval(m, exa::M_JAC, x, nullptr, 0.0, o);
+}
+
+exa_status exa_hess_coord(exa_model *m, const double *x, const double *y, double sigma, double *vals) {
+    if (exa_status e = check_model(m)) return e;
+    if (!m->nnzh) return EXA_OK;
+    CHECK_PTRS(x, vals);
+    if (m->ncon && !y) return fail(m, EXA_E_INVALID, "NULL y");
+    ExaOut o{};
+    o.hess = vals;
+    return launch_eval(m, exa::M_HESS, x, y, sigma, o);
+}
+
+static exa_status csc_structure(exa_model *m, i64 nnz, i64 nnz_csc, const int *dcolptr, const int *drowval,
+                                const int *dmap, int32_t *colptr, int32_t *rowval, int32_t *coo2csc) {
+    CHECK_PTRS(colptr);
+    CR(cudaMemcpyAsync(colptr, dcolptr, sizeof(int) * (m->nvar + 1), cudaMemcpyDeviceToDevice, m->stream));
+    if (nnz_csc) {
+        CHECK_PTRS(rowval);
+        CR(cudaMemcpyAsync(rowval, drowval, sizeof(int) * nnz_csc, cudaMemcpyDeviceToDevice, m->stream));
+    }
+    if (nnz && coo2csc) CR(cudaMemcpyAsync(coo2csc, dmap, sizeof(int) * nnz, cudaMemcpyDeviceToDevice, m->stream));
+    return EXA_OK;
+}
+
+exa_status exa_jac_csc_structure(const exa_model *mc, int32_t *colptr, int32_t *rowval, int32_t *coo2csc) {
+    exa_model *m = const_cast<exa_model *>(mc);
+    if (exa_status e = check_model(m)) return e;
+    return csc_structure(m, m->nnzj, m->nnzj_csc, m->d_jcolptr, m->d_jrowval, m->d_jcoo2csc, colptr, rowval, coo2csc);
+}
+
+exa_status exa_hess_csc_structure(const exa_model *mc, int32_t *colptr, int32_t *rowval, int32_t *coo2csc) {
+    exa_model *m = const_cast<exa_model *>(mc);
+    if (exa_status e = check_model(m)) return e;
+    return csc_structure(m, m->nnzh, m->nnzh_csc, m->d_hcolptr, m->d_hrowval, m->d_hcoo2csc, colptr, rowval, coo2csc);
+}
+
+static exa_status scatter_csc(exa_model *m, const int *segptr, const int *perm, const double *coo, double *csc,
+                              i64 n) {
+    if (!n) return EXA_OK;
+    k_seg_sum<<<grid_of(n, 256), 256, 0, m->stream>>>(segptr, perm, coo, csc, (int)n);
+    CR(cudaGetLastError());
+    return EXA_OK;
+}
+
+exa_status exa_jac_csc(exa_model *m, const double *x, double *vals_csc) {
+    if (exa_status e = check_model(m)) return e;
+    if (!m->nnzj) return EXA_OK;
+    CHECK_PTRS(x, vals_csc);
+    ExaOut o{};
+    o.jac = m->d_jbuf;
+    if (exa_status e = launch_eval(m, exa::M_JAC, x, nullptr, 0.0, o)) return e;
+    return scatter_csc(m, m->d_jsegptr, m->d_jperm, m->d_jbuf, vals_csc, m->nnzj_csc);
+}
+
+exa_status exa_hess_csc(exa_model *m, const double *x, const double *y, double sigma, double *vals_csc) {
+    if (exa_status e = check_model(m)) return e;
+    if (!m->nnzh) return EXA_OK;
+    CHECK_PTRS(x, vals_csc);
+    if (m->ncon && !y) return fail(m, EXA_E_INVALID, "NULL y");
+    ExaOut o{};
+    o.hess = m->d_hbuf;
+    if (exa_status e = launch_eval(m, exa::M_HESS, x, y, sigma, o)) return e;
+    return scatter_csc(m, m->d_hsegptr, m->d_hperm, m->d_hbuf, vals_csc, m->nnzh_csc);
+}
+
+exa_status exa_eval_all(exa_model *m, const double *x, const double *y, double sigma, double *f, double *g,
+                        double *c, double *jac, double *hess, double *jac_csc, double *hess_csc) {
+    if (exa_status e = check_model(m)) return e;
+    CHECK_PTRS(x);
+    const bool want_h = hess || hess_csc;
+    if (want_h && m->ncon && !y) return fail(m, EXA_E_INVALID, "NULL y");
+    ExaOut o{};
+    o.obj_part = m->d_objpart;
+    o.c = c ? c : m->d_cbuf;
+    o.abuf = m->d_abuf;
+    o.gbuf = m->d_gbuf;
+    o.jac = jac ? jac : m->d_jbuf;
+    o.hess = hess ? hess : m->d_hbuf;
+    Mode mode = want_h ? exa::M_ALL : exa::M_FIRST;
+    if (exa_status e = launch_eval(m, mode, x, y, sigma, o)) return e;
+    if (f) {
+        k_obj_final<<<1, 256, 0, m->stream>>>(m->d_objpart, m->ntiles[mode], f);
+        CR(cudaGetLastError());
+    }
+    if (g && m->nvar) {
+        k_seg_sum<<<grid_of(m->nvar, 256), 256, 0, m->stream>>>(m->d_gptr, m->d_gperm, m->d_gbuf, g, (int)m->nvar);
+        CR(cudaGetLastError());
+    }
+    if (c)
+        if (exa_status e = aug_rows(m, c)) return e;
+    if (jac_csc)
+        if (exa_status e = scatter_csc(m, m->d_jsegptr, m->d_jperm, o.jac, jac_csc, m->nnzj_csc)) return e;
+    if (hess_csc)
+        if (exa_status e = scatter_csc(m, m->d_hsegptr, m->d_hperm, o.hess, hess_csc, m->nnzh_csc)) return e;
+    return EXA_OK;
+}
+
+exa_status exa_jprod(exa_model *m, const double *x, const double *v, double *Jv) {
+    if (exa_status e = check_model(m)) return e;
+    if (!m->ncon) return EXA_OK;
+    CHECK_PTRS(x, v, Jv);
+    ExaOut o{};
+    o.jac = m->d_jbuf;
+    if (exa_status e = launch_eval(m, exa::M_JAC, x, nullptr, 0.0, o)) return e;
+    k_spmv_gather<<<grid_of(m->ncon, 256), 256, 0, m->stream>>>(m->d_jrptr, m->d_jrperm, m->d_jbuf, m->d_jcol, v, Jv,
+                                                                 (int)m->ncon);
+    CR(cudaGetLastError());
+    return EXA_OK;
+}
+
+exa_status exa_jtprod(exa_model *m, const double *x, const double *w, double *Jtw) {
+    if (exa_status e = check_model(m)) return e;
+    if (!m->nvar) return EXA_OK;
+    CHECK_PTRS(x, Jtw);
+    if (m->ncon && !w) return fail(m, EXA_E_INVALID, "NULL w");
+    ExaOut o{};
+    o.jac = m->d_jbuf;
+    if (exa_status e = launch_eval(m, exa::M_JAC, x, nullptr, 0.0, o)) return e;
+    k_spmv_gather<<<grid_of(m->nvar, 256), 256, 0, m->stream>>>(m->d_jcolptr_coo, m->d_jperm, m->d_jbuf, m->d_jrow, w,
+                                                                 Jtw, (int)m->nvar);
+    CR(cudaGetLastError());
+    return EXA_OK;
+}
+
+exa_status exa_hprod(exa_model *m, const double *x, const double *y, double sigma, const double *v, double *Hv) {
+    if (exa_status e = check_model(m)) return e;
+    if (!m->nvar) return EXA_OK;
+    CHECK_PTRS(x, v, Hv);
+    if (m->ncon && !y) return fail(m, EXA_E_INVALID, "NULL y");
+    ExaOut o{};
+    o.hess = m->d_hbuf;
+    if (exa_status e = launch_eval(m, exa::M_HESS, x, y, sigma, o)) return e;
+    k_hprod<<<grid_of(m->nvar, 256), 256, 0, m->stream>>>(m->d_hrptr, m->d_hrperm, m->d_hcolptr_coo, m->d_hperm,
+                                                           m->d_hrow, m->d_hcol, m->d_hbuf, v, Hv, (int)m->nvar);
+    CR(cudaGetLastError());
+    return EXA_OK;
+}
+
+exa_status exa_check_status(exa_model *m) {
+    if (exa_status e = check_model(m)) return e;
+    CR(cudaStreamSynchronize(m->stream));
+    int st = 0;
+    CR(cudaMemcpy(&st, m->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    CR(cudaMemset(m->d_status, 0, sizeof(int)));
+    if (st & 1) return fail(m, EXA_E_BOUNDS, "device bounds check failed");
+    if (st & 2) return fail(m, EXA_E_TIMEOUT, "device wait timed out");
+    return EXA_OK;
+}
+
+exa_status exa_compile_check(const exa_model_desc *desc, const exa_options *opt, char *log, size_t loglen) {
+    exa_model tmp;
+    exa_status s = EXA_OK;
+    if (!desc || desc->n_patterns < 0 || (desc->n_patterns > 0 && !desc->patterns)) {
+        s = fail(&tmp, EXA_E_INVALID, "NULL or malformed descriptor");
+    } else {
+        exa_options o{};
+        if (opt) o = *opt;
+        s = load_patterns(*desc, &tmp);
+        if (s == EXA_OK) {
+            exa::CodegenOptions cg;
+            cg.precision = o.precision;
+            cg.block = o.block_threads ? o.block_threads : 128;
+            cg.bounds_check = (o.flags & EXA_FLAG_BOUNDS_CHECK) != 0;
+            std::string gerr;
+            std::string src = exa::generate_source(tmp.pats, cg, &gerr);
+            if (!gerr.empty()) s = fail(&tmp, EXA_E_INTERNAL, gerr);
+            else {
+                if (getenv("EXA_DUMP_SOURCE")) {
+                    FILE *fp = fopen(getenv("EXA_DUMP_SOURCE"), "w");
+                    if (fp) { fputs(src.c_str(), fp); fclose(fp); }
+                }
+                std::vector<char> cubin;
+                s = nvrtc_compile(&tmp, src, cubin);
+            }
+        }
+    }
+    if (log && loglen) {
+        std::snprintf(log, loglen, "%s", tmp.err.c_str());
+    }
+    return s;
+}
+
+exa_status exa_stat(const exa_model *m, const char *key, double *value) {
+    if (!m || !key || !value) return EXA_E_INVALID;
+    std::string k(key);
+    if (k == "nvrtc_ms") *value = m->nvrtc_ms;
+    else if (k == "create_ms") *value = m->create_ms;
+    else if (k == "eval_regs") *value = m->regs[exa::M_ALL];
+    else if (k == "eval_regs_hess") *value = m->regs[exa::M_HESS];
+    else if (k == "eval_regs_jac") *value = m->regs[exa::M_JAC];
+    else if (k == "eval_block") *value = m->block;
+    else if (k == "eval_tiles") *value = m->ntiles[exa::M_ALL];
+    else if (k == "device_bytes") *value = (double)m->device_bytes;
+    else if (k == "n_patterns") *value = (double)m->pats.size();
+    else if (k == "batch_members") *value = m->nb;
+    else return EXA_E_INVALID;
+    return EXA_OK;
+}
+
+}  // extern "C"

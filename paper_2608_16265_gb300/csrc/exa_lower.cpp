@@ -1,0 +1,782 @@
+// exa_lower.cpp -- host-side lowering of the pattern IR to generated CUDA code.
+//
+//  1. analyse_pattern: validates one pattern tree and computes its symbols and slot tables.
+//     Symbols are Var leaves with identical index subtrees (Sec. 4.2.2).  First-order slots are the
+//     symbols in the order a reverse pass meets their leaves (pre-order, left operand first;
+//     Sec. 5.2.1).  Hessian slots follow the reverse-over-reverse pass of Sec. 5.1.3 structurally:
+//     a child's second adjoint is possibly nonzero if its parent's is or the parent's own second
+//     partial for that child is not identically zero; leaves with a possibly nonzero second
+//     adjoint give a diagonal entry; a binary node, once both children are done, gives every
+//     (leaf of child 1) x (leaf of child 2) pair if its own second adjoint or mixed second partial
+//     is possibly nonzero.  Entries are deduplicated as unordered symbol pairs (the Compressor of
+//     Sec. 5.2.2).
+//
+//  2. generate_source: builds, per pattern, a hash-consed expression graph holding the value, the
+//     reverse-mode first derivatives and the second derivatives obtained by reverse over reverse
+//     (edge pushing: second adjoints pushed to the leaves, cross terms at binary nodes weighted by
+//     products of subtree gradients), with structurally zero terms removed at construction
+//     (Sec. 7.2.2, affine-node specialisation).  It then prints straight-line CUDA code per
+//     (pattern, callback), one kernel per callback over a tile list, for NVRTC.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <set>
+#include <sstream>
+#include <tuple>
+
+#include "exa_internal.h"
+
+namespace exa {
+
+#define EXA_STR2(...) #__VA_ARGS__
+#define EXA_STR(...) EXA_STR2(__VA_ARGS__)
+const char *const kDeviceStructs = EXA_STR(EXA_DEVICE_STRUCTS);
+const char *const kModeName[M_COUNT] = {"obj", "con", "grad", "jac", "hess", "all", "first", "struct"};
+
+static bool is_unary(int op) { return op >= EXA_V_NEG && op <= EXA_V_POWI; }
+static bool is_binary(int op) { return op >= EXA_V_ADD && op <= EXA_V_POW; }
+static bool is_leaf(int op) { return op >= EXA_V_CONST && op <= EXA_V_PARAM; }
+
+// Is the op's second partial identically zero?  which: 1 = d2/du1^2, 2 = d2/du2^2, 3 = mixed.
+static bool second_partial_nonzero(const VNode &n, int which) {
+    switch (n.op) {
+    case EXA_V_NEG: case EXA_V_ADD: case EXA_V_SUB: return false;
+    case EXA_V_POWI: return !(n.iv == 0 || n.iv == 1);
+    case EXA_V_MUL: return which == 3;
+    case EXA_V_DIV: return which != 1;
+    default: return true;
+    }
+}
+
+// ------------------------------------------------------------------ index-expression keys
+static std::string idx_key(const Pattern &p, int r) {
+    const INode &n = p.ix[r];
+    switch (n.op) {
+    case EXA_I_CONST: return "c" + std::to_string(n.iv);
+    case EXA_I_FIELD: return "f" + std::to_string(n.iv);
+    case EXA_I_INST: return "k";
+    default: {
+        const char *o = n.op == EXA_I_ADD ? "+" : n.op == EXA_I_SUB ? "-" : "*";
+        return std::string("(") + idx_key(p, n.a) + o + idx_key(p, n.b) + ")";
+    }
+    }
+}
+
+static std::string check_idx(const Pattern &p, int r, int limit, int depth = 0) {
+    if (depth > 64) return "index expression too deep";
+    if (r < 0 || r >= limit) return "index node reference out of range or not before its parent";
+    const INode &n = p.ix[r];
+    switch (n.op) {
+    case EXA_I_CONST: case EXA_I_INST: return "";
+    case EXA_I_FIELD:
+        if (n.iv < 0 || n.iv >= (long long)p.ftype.size() || p.ftype[n.iv] != EXA_FIELD_I32)
+            return "index expression reads a missing or non-int32 data field";
+        return "";
+    case EXA_I_ADD: case EXA_I_SUB: case EXA_I_MUL: {
+        std::string e = check_idx(p, n.a, r, depth + 1);
+        return e.empty() ? check_idx(p, n.b, r, depth + 1) : e;
+    }
+    default: return "unknown index opcode";
+    }
+}
+
+std::string analyse_pattern(Pattern &p) {
+    const int nv = (int)p.v.size();
+    if (p.kind < EXA_OBJ || p.kind > EXA_AUG) return "bad pattern kind";
+    if (p.n_inst < 0) return "negative instance count";
+    if (p.n_inst >= (1LL << 31)) return "more than 2^31-1 instances in one pattern";
+    if (nv < 1) return "empty pattern tree";
+    if ((int)p.ftype.size() > EXA_MAXF) return "more than 16 data fields in one pattern";
+    for (int t : p.ftype)
+        if (t != EXA_FIELD_I32 && t != EXA_FIELD_F64) return "bad data field type";
+    // opcodes, child order, tree shape (every non-root node has exactly one parent)
+    std::vector<int> parents(nv, 0);
+    for (int i = 0; i < nv; i++) {
+        const VNode &n = p.v[i];
+        if (n.op == EXA_V_CONST) continue;
+        if (n.op == EXA_V_DATA) {
+            if (n.iv < 0 || n.iv >= (long long)p.ftype.size()) return "data field out of range";
+            continue;
+        }
+        if (n.op == EXA_V_VAR || n.op == EXA_V_PARAM) {
+            std::string e = check_idx(p, n.a, (int)p.ix.size());
+            if (!e.empty()) return e;
+            continue;
+        }
+        if (is_unary(n.op)) {
+            if (n.a < 0 || n.a >= i) return "child must precede its parent";
+            parents[n.a]++;
+            if (n.op == EXA_V_POWI && (n.iv > 64 || n.iv < -64)) return "integer power beyond +-64";
+            continue;
+        }
+        if (is_binary(n.op)) {
+            if (n.a < 0 || n.a >= i || n.b < 0 || n.b >= i) return "child must precede its parent";
+            parents[n.a]++;
+            parents[n.b]++;
+            continue;
+        }
+        return "unknown value opcode";
+    }
+    for (int i = 0; i < nv - 1; i++)
+        if (parents[i] != 1) return "value nodes must form a tree rooted at the last node";
+    if (parents[nv - 1] != 0) return "the root must not have a parent";
+    if (p.kind == EXA_AUG) {
+        std::string e = check_idx(p, p.row_root, (int)p.ix.size());
+        if (!e.empty()) return "augmentation row: " + e;
+        if (p.row_limit <= 0 && p.n_inst > 0) return "augmentation target block is empty";
+    }
+
+    // symbols by first occurrence in pre-order (left operand first)
+    p.sym_of.assign(nv, -1);
+    p.sym_root.clear();
+    std::map<std::string, int> sym_by_key;
+    std::vector<int> preorder_leaves;  // VAR nodes in pre-order
+    {
+        std::vector<int> stack{nv - 1};
+        while (!stack.empty()) {
+            int i = stack.back();
+            stack.pop_back();
+            const VNode &n = p.v[i];
+            if (n.op == EXA_V_VAR) {
+                preorder_leaves.push_back(i);
+            } else if (is_unary(n.op)) {
+                stack.push_back(n.a);
+            } else if (is_binary(n.op)) {
+                stack.push_back(n.b);
+                stack.push_back(n.a);
+            }
+        }
+    }
+    for (int i : preorder_leaves) {
+        std::string key = idx_key(p, p.v[i].a);
+        auto it = sym_by_key.find(key);
+        int s;
+        if (it == sym_by_key.end()) {
+            s = (int)p.sym_root.size();
+            sym_by_key[key] = s;
+            p.sym_root.push_back(p.v[i].a);
+        } else {
+            s = it->second;
+        }
+        p.sym_of[i] = s;
+    }
+    p.nsym = (int)p.sym_root.size();
+    // first-order slots: unique symbols in visit order == symbol ids in order
+    p.jsym.resize(p.nsym);
+    for (int s = 0; s < p.nsym; s++) p.jsym[s] = s;
+
+    // Hessian slots
+    std::vector<char> has_var(nv, 0);
+    std::vector<std::vector<int>> leaves(nv);  // symbols of Var leaves in pre-order
+    for (int i = 0; i < nv; i++) {
+        const VNode &n = p.v[i];
+        if (n.op == EXA_V_VAR) {
+            has_var[i] = 1;
+            leaves[i] = {p.sym_of[i]};
+        } else if (is_unary(n.op)) {
+            has_var[i] = has_var[n.a];
+            leaves[i] = leaves[n.a];
+        } else if (is_binary(n.op)) {
+            has_var[i] = has_var[n.a] || has_var[n.b];
+            leaves[i] = leaves[n.a];
+            leaves[i].insert(leaves[i].end(), leaves[n.b].begin(), leaves[n.b].end());
+        }
+    }
+    std::vector<char> z2(nv, 0);  // "second adjoint possibly nonzero", set top-down
+    for (int i = nv - 1; i >= 0; i--) {
+        const VNode &n = p.v[i];
+        if (is_unary(n.op)) z2[n.a] = z2[i] || second_partial_nonzero(n, 1);
+        else if (is_binary(n.op)) {
+            z2[n.a] = z2[i] || second_partial_nonzero(n, 1);
+            z2[n.b] = z2[i] || second_partial_nonzero(n, 2);
+        }
+    }
+    p.hpair.clear();
+    std::set<std::pair<int, int>> seen;
+    auto emit = [&](int a, int b) {
+        std::pair<int, int> key(std::min(a, b), std::max(a, b));
+        if (seen.insert(key).second) p.hpair.emplace_back(a, b);
+    };
+    // post-order traversal from the root: children (left, right), then the node itself
+    {
+        std::vector<std::pair<int, int>> stack{{nv - 1, 0}};
+        while (!stack.empty()) {
+            auto &top = stack.back();
+            int i = top.first;
+            const VNode &n = p.v[i];
+            if (top.second == 0) {
+                top.second = 1;
+                if (is_unary(n.op)) { stack.push_back({n.a, 0}); continue; }
+                if (is_binary(n.op)) {
+                    int a = n.a, b = n.b;
+                    stack.push_back({b, 0});
+                    stack.push_back({a, 0});
+                    continue;
+                }
+            }
+            stack.pop_back();
+            if (n.op == EXA_V_VAR) {
+                if (z2[i]) emit(p.sym_of[i], p.sym_of[i]);
+            } else if (is_binary(n.op) && has_var[n.a] && has_var[n.b] &&
+                       (z2[i] || second_partial_nonzero(n, 3))) {
+                for (int a : leaves[n.a])
+                    for (int b : leaves[n.b]) emit(a, b);
+            }
+        }
+    }
+    return "";
+}
+
+// ------------------------------------------------------------------ expression graph
+namespace {
+
+enum SOp {
+    S_LIT, S_IN, S_NEG, S_ADD, S_SUB, S_MUL, S_DIV,
+    S_EXP, S_LOG, S_SIN, S_COS, S_SQRT, S_TAN, S_TANH, S_ATAN, S_POW
+};
+
+struct SN {
+    int op;
+    int a, b;
+    double lit;
+    std::string in;  // input expression (S_IN)
+};
+
+class Graph {
+  public:
+    std::vector<SN> n;
+    std::map<std::tuple<int, int, int, uint64_t>, int> memo;
+    std::map<std::string, int> inputs;
+
+    int lit(double v) {
+        uint64_t bits;
+        std::memcpy(&bits, &v, 8);
+        auto key = std::make_tuple((int)S_LIT, -1, -1, bits);
+        auto it = memo.find(key);
+        if (it != memo.end()) return it->second;
+        n.push_back({S_LIT, -1, -1, v, ""});
+        return memo[key] = (int)n.size() - 1;
+    }
+    int input(const std::string &expr) {
+        auto it = inputs.find(expr);
+        if (it != inputs.end()) return it->second;
+        n.push_back({S_IN, -1, -1, 0.0, expr});
+        return inputs[expr] = (int)n.size() - 1;
+    }
+    int node(int op, int a, int b = -1) {
+        auto key = std::make_tuple(op, a, b, (uint64_t)0);
+        auto it = memo.find(key);
+        if (it != memo.end()) return it->second;
+        n.push_back({op, a, b, 0.0, ""});
+        return memo[key] = (int)n.size() - 1;
+    }
+    bool is_lit(int i) const { return n[i].op == S_LIT; }
+    bool is(int i, double v) const { return n[i].op == S_LIT && n[i].lit == v; }
+    bool zero(int i) const { return is(i, 0.0); }
+
+    int neg(int a) {
+        if (is_lit(a)) return lit(-n[a].lit);
+        if (n[a].op == S_NEG) return n[a].a;
+        return node(S_NEG, a);
+    }
+    int add(int a, int b) {
+        if (zero(a)) return b;
+        if (zero(b)) return a;
+        if (is_lit(a) && is_lit(b)) return lit(n[a].lit + n[b].lit);
+        if (a > b) std::swap(a, b);  // a + b == b + a exactly
+        return node(S_ADD, a, b);
+    }
+    int sub(int a, int b) {
+        if (zero(b)) return a;
+        if (zero(a)) return neg(b);
+        if (is_lit(a) && is_lit(b)) return lit(n[a].lit - n[b].lit);
+        return node(S_SUB, a, b);
+    }
+    int mul(int a, int b) {
+        if (zero(a) || zero(b)) return lit(0.0);
+        if (is(a, 1.0)) return b;
+        if (is(b, 1.0)) return a;
+        if (is(a, -1.0)) return neg(b);
+        if (is(b, -1.0)) return neg(a);
+        if (is_lit(a) && is_lit(b)) return lit(n[a].lit * n[b].lit);
+        if (a > b) std::swap(a, b);
+        return node(S_MUL, a, b);
+    }
+    int div(int a, int b) {
+        if (is(b, 1.0)) return a;
+        if (zero(a)) return lit(0.0);
+        if (is_lit(a) && is_lit(b)) return lit(n[a].lit / n[b].lit);
+        return node(S_DIV, a, b);
+    }
+    int fn(int op, int a) { return node(op, a); }
+    int powi(int u, long long m) {
+        if (m == 0) return lit(1.0);
+        if (m < 0) return div(lit(1.0), powi(u, -m));
+        if (m == 1) return u;
+        int h = powi(u, m / 2);
+        int sq = mul(h, h);
+        return (m % 2) ? mul(sq, u) : sq;
+    }
+};
+
+struct PatternGraph {
+    Graph g;
+    std::vector<int> val, d1, d2, h11, h12, h22, adj, adj2;
+    int value = -1;
+    std::vector<int> grad;                    // per symbol
+    std::map<std::pair<int, int>, int> hess;  // unordered symbol pair -> entry
+    std::string err;
+};
+
+static std::string fmt_double(double v) {
+    char buf[64];
+    std::snprintf(buf, sizeof buf, "%.17g", v);
+    std::string s(buf);
+    if (!std::isfinite(v)) {
+        uint64_t bits;
+        std::memcpy(&bits, &v, 8);
+        return "__longlong_as_double(" + std::to_string((long long)bits) + "LL)";
+    }
+    if (s.find_first_of(".eE") == std::string::npos) s += ".0";
+    if (v < 0 || (v == 0 && std::signbit(v))) s = "(" + s + ")";
+    return s;
+}
+
+// Builds value, gradient over symbols and Hessian over symbol pairs for one pattern.
+static void build_graph(const Pattern &p, PatternGraph &G) {
+    Graph &g = G.g;
+    const int nv = (int)p.v.size();
+    G.val.assign(nv, -1);
+    int Z = g.lit(0.0), ONE = g.lit(1.0);
+    G.d1.assign(nv, Z); G.d2.assign(nv, Z);
+    G.h11.assign(nv, Z); G.h12.assign(nv, Z); G.h22.assign(nv, Z);
+    std::vector<char> hv(nv, 0);
+    for (int i = 0; i < nv; i++) {
+        const VNode &nd = p.v[i];
+        int u = nd.a >= 0 && !is_leaf(nd.op) ? G.val[nd.a] : -1;
+        int w = nd.b >= 0 && is_binary(nd.op) ? G.val[nd.b] : -1;
+        int v = Z, d1 = Z, d2 = Z, h11 = Z, h12 = Z, h22 = Z;
+        switch (nd.op) {
+        case EXA_V_CONST: v = g.lit(nd.fv); break;
+        case EXA_V_DATA: v = g.input("D" + std::to_string(nd.iv)); break;
+        case EXA_V_VAR: v = g.input("X" + std::to_string(p.sym_of[i])); hv[i] = 1; break;
+        case EXA_V_PARAM: v = g.input("P" + std::to_string(i)); break;
+        case EXA_V_NEG: v = g.neg(u); d1 = g.lit(-1.0); break;
+        case EXA_V_ABS2: v = g.mul(u, u); d1 = g.mul(g.lit(2.0), u); h11 = g.lit(2.0); break;
+        case EXA_V_INV:
+            v = g.div(ONE, u);
+            d1 = g.neg(g.mul(v, v));
+            h11 = g.mul(g.lit(2.0), g.mul(v, g.mul(v, v)));
+            break;
+        case EXA_V_EXP: v = g.fn(S_EXP, u); d1 = v; h11 = v; break;
+        case EXA_V_LOG: v = g.fn(S_LOG, u); d1 = g.div(ONE, u); h11 = g.neg(g.mul(d1, d1)); break;
+        case EXA_V_SIN: v = g.fn(S_SIN, u); d1 = g.fn(S_COS, u); h11 = g.neg(v); break;
+        case EXA_V_COS: v = g.fn(S_COS, u); d1 = g.neg(g.fn(S_SIN, u)); h11 = g.neg(v); break;
+        case EXA_V_SQRT:
+            v = g.fn(S_SQRT, u);
+            d1 = g.div(g.lit(0.5), v);
+            h11 = g.neg(g.div(g.lit(0.25), g.mul(u, v)));
+            break;
+        case EXA_V_TAN: v = g.fn(S_TAN, u); d1 = g.add(ONE, g.mul(v, v)); h11 = g.mul(g.lit(2.0), g.mul(v, d1)); break;
+        case EXA_V_TANH: v = g.fn(S_TANH, u); d1 = g.sub(ONE, g.mul(v, v)); h11 = g.mul(g.lit(-2.0), g.mul(v, d1)); break;
+        case EXA_V_ATAN:
+            v = g.fn(S_ATAN, u);
+            d1 = g.div(ONE, g.add(ONE, g.mul(u, u)));
+            h11 = g.mul(g.lit(-2.0), g.mul(u, g.mul(d1, d1)));
+            break;
+        case EXA_V_POWI:
+            v = g.powi(u, nd.iv);
+            d1 = g.mul(g.lit((double)nd.iv), g.powi(u, nd.iv - 1));
+            h11 = g.mul(g.lit((double)nd.iv * (double)(nd.iv - 1)), g.powi(u, nd.iv - 2));
+            break;
+        case EXA_V_ADD: v = g.add(u, w); d1 = ONE; d2 = ONE; break;
+        case EXA_V_SUB: v = g.sub(u, w); d1 = ONE; d2 = g.lit(-1.0); break;
+        case EXA_V_MUL: v = g.mul(u, w); d1 = w; d2 = u; h12 = ONE; break;
+        case EXA_V_DIV: {
+            v = g.div(u, w);
+            int r = g.div(ONE, w);
+            d1 = r;
+            d2 = g.neg(g.mul(v, r));
+            h12 = g.neg(g.mul(r, r));
+            h22 = g.mul(g.lit(2.0), g.mul(v, g.mul(r, r)));
+            break;
+        }
+        case EXA_V_POW: {
+            v = g.node(S_POW, u, w);
+            int lu = g.fn(S_LOG, u);
+            int vu = g.div(v, u);
+            d1 = g.mul(w, vu);
+            d2 = g.mul(v, lu);
+            h11 = g.mul(g.mul(w, g.sub(w, ONE)), g.div(vu, u));
+            h12 = g.mul(vu, g.add(ONE, g.mul(w, lu)));
+            h22 = g.mul(v, g.mul(lu, lu));
+            break;
+        }
+        }
+        if (is_unary(nd.op)) hv[i] = hv[nd.a];
+        if (is_binary(nd.op)) hv[i] = hv[nd.a] || hv[nd.b];
+        G.val[i] = v; G.d1[i] = d1; G.d2[i] = d2; G.h11[i] = h11; G.h12[i] = h12; G.h22[i] = h22;
+    }
+    G.value = G.val[nv - 1];
+
+    // first-order reverse pass (adjoints), then second-order (edge pushing) with tangent gradients
+    G.adj.assign(nv, Z);
+    G.adj2.assign(nv, Z);
+    G.grad.assign(p.nsym, Z);
+    G.adj[nv - 1] = ONE;
+    // tangent gradient of every subtree over symbols (bottom-up)
+    std::vector<std::map<int, int>> tg(nv);
+    for (int i = 0; i < nv; i++) {
+        const VNode &nd = p.v[i];
+        if (nd.op == EXA_V_VAR) tg[i][p.sym_of[i]] = ONE;
+        else if (is_unary(nd.op)) {
+            for (auto &kv : tg[nd.a]) tg[i][kv.first] = g.mul(G.d1[i], kv.second);
+        } else if (is_binary(nd.op)) {
+            for (auto &kv : tg[nd.a]) tg[i][kv.first] = g.mul(G.d1[i], kv.second);
+            for (auto &kv : tg[nd.b]) {
+                int t = g.mul(G.d2[i], kv.second);
+                auto it = tg[i].find(kv.first);
+                if (it == tg[i].end()) tg[i][kv.first] = t;
+                else it->second = g.add(it->second, t);
+            }
+        }
+    }
+    auto hacc = [&](int s, int t, int c) {
+        std::pair<int, int> key(std::min(s, t), std::max(s, t));
+        auto it = G.hess.find(key);
+        if (it == G.hess.end()) G.hess[key] = c;
+        else it->second = g.add(it->second, c);
+    };
+    for (int i = nv - 1; i >= 0; i--) {
+        const VNode &nd = p.v[i];
+        int a1 = G.adj[i], a2 = G.adj2[i];
+        if (nd.op == EXA_V_VAR) {
+            int s = p.sym_of[i];
+            G.grad[s] = g.add(G.grad[s], a1);
+            if (!g.zero(a2)) hacc(s, s, a2);
+        } else if (is_unary(nd.op)) {
+            if (!hv[nd.a]) continue;
+            G.adj[nd.a] = g.mul(a1, G.d1[i]);
+            G.adj2[nd.a] = g.add(g.mul(a2, g.mul(G.d1[i], G.d1[i])), g.mul(a1, G.h11[i]));
+        } else if (is_binary(nd.op)) {
+            if (hv[nd.a]) {
+                G.adj[nd.a] = g.mul(a1, G.d1[i]);
+                G.adj2[nd.a] = g.add(g.mul(a2, g.mul(G.d1[i], G.d1[i])), g.mul(a1, G.h11[i]));
+            }
+            if (hv[nd.b]) {
+                G.adj[nd.b] = g.mul(a1, G.d2[i]);
+                G.adj2[nd.b] = g.add(g.mul(a2, g.mul(G.d2[i], G.d2[i])), g.mul(a1, G.h22[i]));
+            }
+            if (hv[nd.a] && hv[nd.b]) {
+                int w = g.add(g.mul(a2, g.mul(G.d1[i], G.d2[i])), g.mul(a1, G.h12[i]));
+                if (g.zero(w)) continue;
+                for (auto &ka : tg[nd.a])
+                    for (auto &kb : tg[nd.b]) {
+                        int c = g.mul(w, g.mul(ka.second, kb.second));
+                        if (ka.first == kb.first) c = g.mul(g.lit(2.0), c);
+                        hacc(ka.first, kb.first, c);
+                    }
+            }
+        }
+    }
+    // every computed entry must be a structural slot
+    std::set<std::pair<int, int>> slots;
+    for (auto &pr : p.hpair) slots.insert({std::min(pr.first, pr.second), std::max(pr.first, pr.second)});
+    for (auto &kv : G.hess)
+        if (!g.zero(kv.second) && !slots.count(kv.first)) {
+            G.err = "internal: second-order entry outside the structural slots";
+            return;
+        }
+}
+
+// ------------------------------------------------------------------ CUDA emission
+struct Emitter {
+    const Pattern &p;
+    const PatternGraph &G;
+    const CodegenOptions &opt;
+    std::ostringstream os;
+
+    Emitter(const Pattern &p_, const PatternGraph &G_, const CodegenOptions &o) : p(p_), G(G_), opt(o) {}
+
+    std::string idx_expr(int r) {
+        const INode &n = p.ix[r];
+        switch (n.op) {
+        case EXA_I_CONST: return "(" + std::to_string(n.iv) + "LL)";
+        case EXA_I_FIELD: return "((long long)F" + std::to_string(n.iv) + ")";
+        case EXA_I_INST: return "kk";
+        default: {
+            const char *o = n.op == EXA_I_ADD ? " + " : n.op == EXA_I_SUB ? " - " : " * ";
+            return "(" + idx_expr(n.a) + o + idx_expr(n.b) + ")";
+        }
+        }
+    }
+    void fields_of_idx(int r, std::set<int> &f) {
+        const INode &n = p.ix[r];
+        if (n.op == EXA_I_FIELD) f.insert((int)n.iv);
+        else if (n.op >= EXA_I_ADD) { fields_of_idx(n.a, f); fields_of_idx(n.b, f); }
+    }
+
+    static const char *fname(int op) {
+        switch (op) {
+        case S_EXP: return "exp"; case S_LOG: return "log"; case S_SIN: return "sin";
+        case S_COS: return "cos"; case S_SQRT: return "sqrt"; case S_TAN: return "tan";
+        case S_TANH: return "tanh"; case S_ATAN: return "atan"; default: return "?";
+        }
+    }
+
+    // Emits the body computing the requested graph nodes; returns the C expression of each.
+    void body(const std::vector<int> &roots, std::map<int, std::string> &name) {
+        const Graph &g = G.g;
+        std::vector<char> need(g.n.size(), 0);
+        std::function<void(int)> mark = [&](int i) {
+            if (need[i]) return;
+            need[i] = 1;
+            if (g.n[i].a >= 0) mark(g.n[i].a);
+            if (g.n[i].b >= 0) mark(g.n[i].b);
+        };
+        for (int r : roots) mark(r);
+        // sin and cos of one argument share a sincos call
+        std::map<int, std::pair<int, int>> sc;  // argument -> (sin node, cos node)
+        for (size_t i = 0; i < g.n.size(); i++) {
+            if (!need[i]) continue;
+            if (g.n[i].op == S_SIN) sc[g.n[i].a].first = (int)i + 1;
+            if (g.n[i].op == S_COS) sc[g.n[i].a].second = (int)i + 1;
+        }
+        for (size_t i = 0; i < g.n.size(); i++) {
+            if (!need[i]) continue;
+            const SN &s = g.n[i];
+            std::string t = "t" + std::to_string(i);
+            switch (s.op) {
+            case S_LIT: name[i] = fmt_double(s.lit); continue;
+            case S_IN: name[i] = s.in; continue;
+            default: break;
+            }
+            name[i] = t;
+            auto A = [&]() { return name.at(s.a); };
+            auto B = [&]() { return name.at(s.b); };
+            switch (s.op) {
+            case S_NEG: os << "  const double " << t << " = -" << A() << ";\n"; break;
+            case S_ADD: os << "  const double " << t << " = " << A() << " + " << B() << ";\n"; break;
+            case S_SUB: os << "  const double " << t << " = " << A() << " - " << B() << ";\n"; break;
+            case S_MUL: os << "  const double " << t << " = " << A() << " * " << B() << ";\n"; break;
+            case S_DIV: os << "  const double " << t << " = " << A() << " / " << B() << ";\n"; break;
+            case S_POW: os << "  const double " << t << " = pow(" << A() << ", " << B() << ");\n"; break;
+            case S_SIN: case S_COS: {
+                auto pr = sc[s.a];
+                if (pr.first && pr.second) {
+                    int si = pr.first - 1, ci = pr.second - 1;
+                    if ((int)i == std::min(si, ci)) {
+                        os << "  double t" << si << ", t" << ci << ";\n  sincos(" << A() << ", &t" << si
+                           << ", &t" << ci << ");\n";
+                    }
+                    name[i] = t;
+                } else {
+                    os << "  const double " << t << " = " << fname(s.op) << "(" << A() << ");\n";
+                }
+                break;
+            }
+            default: os << "  const double " << t << " = " << fname(s.op) << "(" << A() << ");\n"; break;
+            }
+        }
+    }
+
+    // One device function per (pattern, mode).
+    std::string function(int pid, Mode mode) {
+        os.str("");
+        const bool obj = p.kind == EXA_OBJ;
+        const bool all = mode == M_ALL || mode == M_FIRST;
+        const bool want_val = (mode == M_OBJ && obj) || (mode == M_CON && !obj) || all;
+        const bool want_grad = (mode == M_GRAD && obj) || (mode == M_JAC && !obj) || all;
+        const bool want_hess = (mode == M_HESS || mode == M_ALL) && p.nh() > 0;
+        const bool want_struct = mode == M_STRUCT;
+        os << "static __device__ __forceinline__ void pat" << pid << "_" << kModeName[mode]
+           << "(const ExaPM& pm, const int k, const double* __restrict__ x, const double* __restrict__ y,"
+              " const double* __restrict__ th, const double sigma, const ExaOut& o,"
+              " const ExaStructOut& so, double& objv) {\n";
+        os << "  const long long kk = k;\n";
+        std::vector<int> roots;
+        if (want_val) roots.push_back(G.value);
+        if (want_grad) for (int s : p.jsym) roots.push_back(G.grad[s]);
+        std::vector<int> hroots;
+        if (want_hess)
+            for (auto &pr : p.hpair) {
+                auto it = G.hess.find({std::min(pr.first, pr.second), std::max(pr.first, pr.second)});
+                hroots.push_back(it == G.hess.end() ? (int)G.g.n.size() : it->second);
+            }
+        for (int r : hroots) if (r < (int)G.g.n.size()) roots.push_back(r);
+        // which inputs are needed
+        std::set<int> syms, fields, params;
+        bool need_row = (!obj) && (want_val || want_hess || want_struct);
+        {
+            std::vector<char> seen(G.g.n.size(), 0);
+            std::function<void(int)> walk = [&](int i) {
+                if (seen[i]) return;
+                seen[i] = 1;
+                const SN &s = G.g.n[i];
+                if (s.op == S_IN) {
+                    int id = std::stoi(s.in.substr(1));
+                    if (s.in[0] == 'X') syms.insert(id);
+                    else if (s.in[0] == 'D') fields.insert(id);
+                    else if (s.in[0] == 'P') params.insert(id);
+                }
+                if (s.a >= 0) walk(s.a);
+                if (s.b >= 0) walk(s.b);
+            };
+            for (int r : roots) walk(r);
+        }
+        std::set<int> idx_syms = syms;  // symbols whose index is needed
+        if (want_struct) for (int s = 0; s < p.nsym; s++) idx_syms.insert(s);
+        if (want_hess)
+            for (auto &pr : p.hpair)
+                if (pr.first != pr.second) { idx_syms.insert(pr.first); idx_syms.insert(pr.second); }
+        std::set<int> ifields;
+        for (int s : idx_syms) fields_of_idx(p.sym_root[s], ifields);
+        for (int pn : params) fields_of_idx(p.v[pn].a, ifields);
+        if (p.kind == EXA_AUG && need_row) fields_of_idx(p.row_root, ifields);
+        std::set<int> all_fields = fields;
+        all_fields.insert(ifields.begin(), ifields.end());
+        for (int f : all_fields) {
+            if (p.ftype[f] == EXA_FIELD_I32)
+                os << "  const int F" << f << " = __ldg((const int*)pm.f[" << f << "] + k);\n";
+            else
+                os << "  const double F" << f << " = __ldg((const double*)pm.f[" << f << "] + k);\n";
+        }
+        for (int f : fields)
+            os << "  const double D" << f << " = " << (p.ftype[f] == EXA_FIELD_I32 ? "(double)F" : "F") << f << ";\n";
+        for (int s : idx_syms) {
+            os << "  const long long i" << s << " = " << idx_expr(p.sym_root[s]) << ";\n";
+            if (opt.bounds_check || want_struct)
+                os << "  if ((unsigned long long)i" << s << " >= (unsigned long long)pm.nvar_m) { atomicOr(o.status, 1); return; }\n";
+        }
+        for (int pn : params) {
+            os << "  const long long q" << pn << " = " << idx_expr(p.v[pn].a) << ";\n";
+            if (opt.bounds_check || want_struct)
+                os << "  if ((unsigned long long)q" << pn << " >= (unsigned long long)pm.npar_m) { atomicOr(o.status, 1); return; }\n";
+        }
+        if (need_row) {
+            if (p.kind == EXA_CON) os << "  const long long row = pm.rbase + kk;\n";
+            else {
+                os << "  const long long lrow = " << idx_expr(p.row_root) << ";\n";
+                if (opt.bounds_check || want_struct)
+                    os << "  if ((unsigned long long)lrow >= (unsigned long long)pm.rlimit) { atomicOr(o.status, 1); return; }\n";
+                os << "  const long long row = pm.rbase + lrow;\n";
+            }
+        }
+        if (want_struct) {
+            if (obj) {
+                for (int j = 0; j < p.nj(); j++)
+                    os << "  so.gvar[pm.gbase + kk * " << p.nj() << " + " << j << "] = (int)(pm.xoff + i" << p.jsym[j] << ");\n";
+            } else {
+                for (int j = 0; j < p.nj(); j++) {
+                    os << "  so.jrow[pm.jbase + kk * " << p.nj() << " + " << j << "] = (int)row;\n";
+                    os << "  so.jcol[pm.jbase + kk * " << p.nj() << " + " << j << "] = (int)(pm.xoff + i" << p.jsym[j] << ");\n";
+                }
+                if (p.kind == EXA_AUG) os << "  so.arow[pm.abase + kk] = (int)row;\n";
+            }
+            for (int j = 0; j < p.nh(); j++) {
+                int a = p.hpair[j].first, b = p.hpair[j].second;
+                os << "  { const long long ga = pm.xoff + i" << a << ", gb = pm.xoff + i" << b << ";\n"
+                   << "    so.hrow[pm.hbase + kk * " << p.nh() << " + " << j << "] = (int)(ga > gb ? ga : gb);\n"
+                   << "    so.hcol[pm.hbase + kk * " << p.nh() << " + " << j << "] = (int)(ga > gb ? gb : ga); }\n";
+            }
+            os << "}\n";
+            return os.str();
+        }
+        for (int s : syms) os << "  const double X" << s << " = __ldg(x + pm.xoff + i" << s << ");\n";
+        for (int pn : params) os << "  const double P" << pn << " = __ldg(th + pm.poff + q" << pn << ");\n";
+        std::map<int, std::string> name;
+        body(roots, name);
+        if (want_val) {
+            const std::string &v = name.at(G.value);
+            if (obj) os << "  objv = " << v << ";\n";
+            else if (p.kind == EXA_CON) os << "  o.c[row] = " << v << ";\n";
+            else os << "  o.abuf[pm.abase + kk] = " << v << ";\n";
+        }
+        if (want_grad && p.nj() > 0) {
+            if (obj) os << "  double* __restrict__ GO = o.gbuf + pm.gbase + kk * " << p.nj() << ";\n";
+            else os << "  double* __restrict__ GO = o.jac + pm.jbase + kk * " << p.nj() << ";\n";
+            for (int j = 0; j < p.nj(); j++) os << "  GO[" << j << "] = " << name.at(G.grad[p.jsym[j]]) << ";\n";
+        }
+        if (want_hess) {
+            if (obj) os << "  const double w = sigma;\n";
+            else os << "  const double w = __ldg(y + row);\n";
+            os << "  const double w2 = w + w;\n";
+            os << "  double* __restrict__ HO = o.hess + pm.hbase + kk * " << p.nh() << ";\n";
+            for (int j = 0; j < p.nh(); j++) {
+                int a = p.hpair[j].first, b = p.hpair[j].second;
+                int r = hroots[j];
+                std::string v = r < (int)G.g.n.size() ? name.at(r) : "0.0";
+                if (a == b) os << "  HO[" << j << "] = w * " << v << ";\n";
+                else os << "  HO[" << j << "] = (i" << a << " == i" << b << " ? w2 : w) * " << v << ";\n";
+            }
+        }
+        os << "}\n";
+        return os.str();
+    }
+};
+
+}  // namespace
+
+static bool pattern_in_mode(const Pattern &p, Mode m) {
+    switch (m) {
+    case M_OBJ: case M_GRAD: return p.kind == EXA_OBJ;
+    case M_CON: case M_JAC: return p.kind != EXA_OBJ;
+    case M_HESS: return p.nh() > 0;
+    default: return true;
+    }
+}
+
+std::string generate_source(const std::vector<Pattern> &pats, const CodegenOptions &opt, std::string *err) {
+    std::ostringstream src;
+    src << "// generated by exa_lower.cpp\n";
+    src << kDeviceStructs << "\n";
+    src << "#define EXA_BLOCK " << opt.block << "\n";
+    std::vector<PatternGraph> graphs(pats.size());
+    for (size_t i = 0; i < pats.size(); i++) {
+        build_graph(pats[i], graphs[i]);
+        if (!graphs[i].err.empty()) {
+            *err = graphs[i].err;
+            return "";
+        }
+    }
+    for (int m = 0; m < M_COUNT; m++) {
+        for (size_t i = 0; i < pats.size(); i++) {
+            if (!pattern_in_mode(pats[i], (Mode)m)) continue;
+            Emitter e(pats[i], graphs[i], opt);
+            src << e.function((int)i, (Mode)m);
+        }
+        const bool objred = (m == M_OBJ || m == M_ALL || m == M_FIRST);
+        src << "extern \"C\" __global__ void __launch_bounds__(EXA_BLOCK) exa_" << kModeName[m]
+            << "(const ExaTile* __restrict__ tiles, const ExaPM* __restrict__ pms, const double* __restrict__ x,"
+               " const double* __restrict__ y, const double* __restrict__ th, const double sigma, const ExaOut o,"
+               " const ExaStructOut so) {\n"
+               "  const ExaTile tl = tiles[blockIdx.x];\n"
+               "  const ExaPM& pm = pms[tl.pm];\n"
+               "  const int k = tl.begin + (int)threadIdx.x;\n"
+               "  double objv = 0.0;\n"
+               "  if (k < pm.n_inst) {\n"
+               "    switch (pm.pat) {\n";
+        for (size_t i = 0; i < pats.size(); i++) {
+            if (!pattern_in_mode(pats[i], (Mode)m)) continue;
+            src << "      case " << i << ": pat" << i << "_" << kModeName[m] << "(pm, k, x, y, th, sigma, o, so, objv); break;\n";
+        }
+        src << "      default: break;\n    }\n  }\n";
+        if (objred) {
+            src << "  for (int off = 16; off > 0; off >>= 1) objv += __shfl_xor_sync(0xffffffffu, objv, off);\n"
+                   "  __shared__ double red[EXA_BLOCK / 32];\n"
+                   "  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = objv;\n"
+                   "  __syncthreads();\n"
+                   "  if (threadIdx.x == 0) {\n"
+                   "    double s = 0.0;\n"
+                   "    for (int i = 0; i < EXA_BLOCK / 32; i++) s += red[i];\n"
+                   "    o.obj_part[blockIdx.x] = s;\n"
+                   "  }\n";
+        }
+        src << "}\n";
+    }
+    return src.str();
+}
+
+}  // namespace exa

@@ -1,0 +1,229 @@
+"""GPU path (through the C ABI) against the CPU oracle on identical seeded inputs.
+
+Bar: structures and CSC maps bit-exact; FP64 values within 1e-12 relative, normwise per output
+array.  Sizes span several tiles with ragged tails; full-size configurations are compared on
+sampled batch members or whole outputs where the oracle finishes in seconds."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.helpers import all_ops_model, all_ops_point, normwise
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+def _B():
+    from paper_2608_16265_gb300 import binding
+    return binding
+
+
+def _t(a, dtype=torch.float64):
+    return torch.as_tensor(np.asarray(a), dtype=dtype, device="cuda")
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def check_model(flat, x, y, s, block=0, tol=TOL, o=None):
+    B = _B()
+    o = o or oracle.Oracle(flat)
+    m = B.exa_create(flat, block=block)
+    assert (m.nvar, m.ncon, m.nnzj, m.nnzh, m.nnzj_csc, m.nnzh_csc) == \
+        (o.nvar, o.ncon, o.nnzj, o.nnzh, o.nnzj_csc, o.nnzh_csc)
+    # structures: bit-exact
+    for got, want in ((m.jac_structure(), o.jac_structure()), (m.hess_structure(), o.hess_structure())):
+        assert np.array_equal(_np(got[0]), want[0]) and np.array_equal(_np(got[1]), want[1])
+    for got, want in ((m.jac_csc_structure(), o.jac_csc_structure()),
+                      (m.hess_csc_structure(), o.hess_csc_structure())):
+        for g_, w_ in zip(got, want):
+            assert np.array_equal(_np(g_), w_)
+    xt, yt = _t(x), _t(y if len(y) else np.zeros(1))
+    f = float(_np(m.obj(xt))[0])
+    fo = o.obj(x)
+    assert abs(f - fo) <= tol * max(abs(fo), 1e-300) or f == fo
+    errs = {}
+    errs["grad"] = normwise(_np(m.grad(xt)), o.grad(x))
+    errs["cons"] = normwise(_np(m.cons(xt)), o.cons(x))
+    errs["jac"] = normwise(_np(m.jac_coord(xt)), o.jac_coord(x))
+    errs["hess"] = normwise(_np(m.hess_coord(xt, yt, s)), o.hess_coord(x, y, s))
+    errs["jac_csc"] = normwise(_np(m.jac_csc(xt)), o.jac_csc(x))
+    errs["hess_csc"] = normwise(_np(m.hess_csc(xt, yt, s)), o.hess_csc(x, y, s))
+    rng = np.random.default_rng(5)
+    v = rng.standard_normal(o.nvar)
+    w = rng.standard_normal(o.ncon)
+    errs["jprod"] = normwise(_np(m.jprod(xt, _t(v))), o.jprod(x, v))
+    errs["jtprod"] = normwise(_np(m.jtprod(xt, _t(w if len(w) else np.zeros(1)))), o.jtprod(x, w))
+    errs["hprod"] = normwise(_np(m.hprod(xt, yt, s, _t(v))), o.hprod(x, y, s, v))
+    allv = m.eval_all(xt, yt, s, csc=True)
+    errs["all_f"] = abs(float(_np(allv["f"])[0]) - fo) / max(abs(fo), 1e-300)
+    errs["all_g"] = normwise(_np(allv["g"]), o.grad(x))
+    errs["all_c"] = normwise(_np(allv["c"]), o.cons(x))
+    errs["all_jac"] = normwise(_np(allv["jac"]), o.jac_coord(x))
+    errs["all_hess"] = normwise(_np(allv["hess"]), o.hess_coord(x, y, s))
+    errs["all_jac_csc"] = normwise(_np(allv["jac_csc"]), o.jac_csc(x))
+    errs["all_hess_csc"] = normwise(_np(allv["hess_csc"]), o.hess_csc(x, y, s))
+    m.exa_check_status()
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, bad
+    return m, errs
+
+
+CASES = {
+    "all_ops": lambda: (all_ops_model().flat(), all_ops_point()),
+    "rosenbrock_1000": lambda: (lambda w: (w.flat, synth.rosenbrock_point(w, 0)))(synth.rosenbrock(1000)),
+    "acopf_small": lambda: (lambda w: (w.flat, synth.acopf_point(w, 0)))(synth.acopf(500, 700, 100, seed=1)),
+    "acopf_shunts": lambda: (lambda w: (w.flat, synth.acopf_point(w, 3)))(synth.acopf(37, 61, 9, seed=4, shunts=True)),
+    "pde_41": lambda: (lambda w: (w.flat, synth.pde_point(w, 2)))(synth.pde(41)),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_parity_small(name):
+    flat, (x, y, s) = CASES[name]()
+    check_model(flat, x, y, s)
+
+
+@pytest.mark.parametrize("block", [32, 64, 256])
+def test_parity_block_sizes(block):
+    wl = synth.acopf(200, 300, 40, seed=8)
+    x, y, s = synth.acopf_point(wl, 1)
+    check_model(wl.flat, x, y, s, block=block)
+
+
+def test_rosenbrock_ten_points():
+    wl = synth.rosenbrock(1000)
+    o = oracle.Oracle(wl.flat)
+    for seed in range(10):
+        x, y, s = synth.rosenbrock_point(wl, seed)
+        check_model(wl.flat, x, y, s, o=o)
+
+
+def test_empty_and_degenerate_patterns():
+    from paper_2608_16265_gb300.ir import Model
+    m = Model()
+    x = m.add_var(5)
+    m.add_obj(lambda d: x[d.k] ** 2, n=0)                       # empty objective pattern
+    blk = m.add_con(lambda d: x[d.k] * x[d.k + 1], n=4)
+    m.add_con_aug(blk, lambda d: (d.r, x[d.k]), data=dict(r=np.zeros(0, np.int32)))  # empty aug
+    m.add_con_aug(blk, lambda d: (d.r, 3.0 * x[4]), data=dict(r=np.array([1, 1, 3], np.int32)))
+    m.add_obj(lambda d: x[d.a] * x[d.b], data=dict(a=np.array([0, 2], np.int32), b=np.array([0, 3], np.int32)))
+    x0 = np.array([0.5, -1.0, 2.0, 0.25, 1.5])
+    check_model(m.flat(), x0, np.array([1.0, -2.0, 0.5, 3.0]), 0.7)
+
+
+def test_no_constraints_and_no_objective():
+    from paper_2608_16265_gb300.ir import Model, exp
+    m = Model()
+    x = m.add_var(300)
+    m.add_obj(lambda d: exp(x[d.k]) * x[d.k + 1], n=299)
+    check_model(m.flat(), np.linspace(-1, 1, 300), np.zeros(0), 1.3)
+    m = Model()
+    x = m.add_var(300)
+    m.add_con(lambda d: exp(x[d.k]) * x[d.k + 1], n=299)
+    check_model(m.flat(), np.linspace(-1, 1, 300), np.linspace(1, 2, 299), 1.0)
+
+
+def test_determinism():
+    wl = synth.acopf(500, 700, 100, seed=1)
+    x, y, s = synth.acopf_point(wl, 0)
+    m = _B().exa_create(wl.flat)
+    a = m.eval_all(_t(x), _t(y), s, csc=True)
+    b = m.eval_all(_t(x), _t(y), s, csc=True)
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+
+
+def test_create_errors():
+    from paper_2608_16265_gb300.ir import Model
+    B = _B()
+    m = Model()
+    x = m.add_var(3)
+    m.add_obj(lambda d: x[d.i] ** 2, data=dict(i=np.array([0, 3], np.int32)))
+    with pytest.raises(B.ExaError) as e:
+        B.exa_create(m.flat())
+    assert e.value.status == B.EXA_E_BOUNDS
+    m = Model()
+    x = m.add_var(3)
+    b = m.add_con(lambda d: x[d.k], n=2)
+    m.add_con_aug(b, lambda d: (d.r, x[0]), data=dict(r=np.array([2], np.int32)))
+    with pytest.raises(B.ExaError) as e:
+        B.exa_create(m.flat())
+    assert e.value.status == B.EXA_E_BOUNDS
+
+
+# ------------------------------------------------------------------ batch
+def test_batch_matches_members():
+    B = _B()
+    wls = synth.acopf_batch(6, seed=3, bmin=20, bmax=400)
+    flats = [w.flat for w in wls]
+    mb = B.exa_create_batch(flats)
+    pts = [synth.acopf_point(w, i) for i, w in enumerate(wls)]
+    x = np.concatenate([p[0] for p in pts])
+    y = np.concatenate([p[1] for p in pts])
+    jb = _np(mb.jac_coord(_t(x)))
+    hb = _np(mb.hess_coord(_t(x), _t(y), 1.0))
+    cb = _np(mb.cons(_t(x)))
+    gb = _np(mb.grad(_t(x)))
+    rb, cbs = (_np(t) for t in mb.jac_structure())
+    for i, (w, (xi, yi, si)) in enumerate(zip(wls, pts)):
+        o = oracle.Oracle(w.flat)
+        js = slice(mb.joff[i], mb.joff[i + 1])
+        hs = slice(mb.hoff[i], mb.hoff[i + 1])
+        cs = slice(mb.coff[i], mb.coff[i + 1])
+        xs = slice(mb.xoff[i], mb.xoff[i + 1])
+        r, c = o.jac_structure()
+        assert np.array_equal(rb[js] - mb.coff[i], r) and np.array_equal(cbs[js] - mb.xoff[i], c)
+        assert normwise(jb[js], o.jac_coord(xi)) <= TOL
+        assert normwise(hb[hs], o.hess_coord(xi, yi, si)) <= TOL
+        assert normwise(cb[cs], o.cons(xi)) <= TOL
+        assert normwise(gb[xs], o.grad(xi)) <= TOL
+        # the member alone gives bitwise the same COO values as its batch slice
+        mi = B.exa_create(w.flat)
+        assert np.array_equal(_np(mi.jac_coord(_t(xi))), jb[js])
+        assert np.array_equal(_np(mi.hess_coord(_t(xi), _t(yi), si)), hb[hs])
+    f = float(_np(mb.obj(_t(x)))[0])
+    fo = sum(oracle.Oracle(w.flat).obj(p[0]) for w, p in zip(wls, pts))
+    assert abs(f - fo) <= TOL * abs(fo)
+
+
+# ------------------------------------------------------------------ full-size configurations
+@pytest.mark.slow
+def test_full_acopf_large():
+    wl = synth.acopf(30000, 45000, 5000, seed=2)
+    x, y, s = synth.acopf_point(wl, 0)
+    check_model(wl.flat, x, y, s)
+
+
+@pytest.mark.slow
+def test_full_pde():
+    wl = synth.pde(1000)
+    x, y, s = synth.pde_point(wl, 0)
+    check_model(wl.flat, x, y, s)
+
+
+@pytest.mark.slow
+def test_full_batch_sampled_members():
+    """The 256-instance batch exactly as the benchmark creates it; members compared against the
+    oracle: the smallest, the largest and two drawn at random."""
+    B = _B()
+    wls = synth.acopf_batch(256)
+    mb = B.exa_create_batch([w.flat for w in wls])
+    pts = [synth.acopf_point(w, i) for i, w in enumerate(wls)]
+    x = np.concatenate([p[0] for p in pts])
+    y = np.concatenate([p[1] for p in pts])
+    out = mb.eval_all(_t(x), _t(y), 1.0, csc=False)
+    jb, hb, cb = _np(out["jac"]), _np(out["hess"]), _np(out["c"])
+    sizes = [w.meta["B"] for w in wls]
+    picks = {int(np.argmin(sizes)), int(np.argmax(sizes))}
+    picks |= set(np.random.default_rng(0).choice(256, 2, replace=False).tolist())
+    for i in sorted(picks):
+        o = oracle.Oracle(wls[i].flat)
+        xi, yi, si = pts[i]
+        assert normwise(jb[mb.joff[i]:mb.joff[i + 1]], o.jac_coord(xi)) <= TOL
+        assert normwise(hb[mb.hoff[i]:mb.hoff[i + 1]], o.hess_coord(xi, yi, si)) <= TOL
+        assert normwise(cb[mb.coff[i]:mb.coff[i + 1]], o.cons(xi)) <= TOL
