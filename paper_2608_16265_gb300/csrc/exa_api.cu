@@ -16,6 +16,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -250,12 +251,28 @@ exa_status nvrtc_compile(exa_model *m, const std::string &src, std::vector<char>
     return EXA_OK;
 }
 
+// Process-wide cache of compiled modules keyed by the generated source: models that share their
+// pattern trees and options (batch members, or the same model created twice) compile once.
+std::mutex g_cubin_mu;
+std::map<std::string, std::shared_ptr<std::vector<char>>> g_cubins;
+
 exa_status compile(exa_model *m, const std::string &src) {
     auto t0 = std::chrono::steady_clock::now();
-    std::vector<char> cubin;
-    if (exa_status e = nvrtc_compile(m, src, cubin)) return e;
+    std::shared_ptr<std::vector<char>> cubin;
+    {
+        std::lock_guard<std::mutex> lk(g_cubin_mu);
+        auto it = g_cubins.find(src);
+        if (it != g_cubins.end()) cubin = it->second;
+    }
+    if (!cubin) {
+        cubin = std::make_shared<std::vector<char>>();
+        if (exa_status e = nvrtc_compile(m, src, *cubin)) return e;
+        std::lock_guard<std::mutex> lk(g_cubin_mu);
+        if (g_cubins.size() > 64) g_cubins.clear();
+        g_cubins[src] = cubin;
+    }
     m->nvrtc_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    CR(cudaLibraryLoadData(&m->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0));
+    CR(cudaLibraryLoadData(&m->lib, cubin->data(), nullptr, nullptr, 0, nullptr, nullptr, 0));
     for (int k = 0; k < exa::M_COUNT; k++) {
         std::string name = std::string("exa_") + exa::kModeName[k];
         CR(cudaLibraryGetKernel(&m->fn[k], m->lib, name.c_str()));
@@ -429,19 +446,21 @@ exa_status build_structure(exa_model *m) {
     return EXA_OK;
 }
 
-bool same_ir(const exa_pattern_desc &a, const exa_pattern_desc &b) {
+// Same tree shape: identical nodes except for the values of constants (index constants and
+// value constants may differ between batch members; they become per-member descriptor values).
+bool same_shape(const exa_pattern_desc &a, const exa_pattern_desc &b) {
     if (a.kind != b.kind || a.n_vnodes != b.n_vnodes || a.n_inodes != b.n_inodes || a.n_fields != b.n_fields ||
         a.row_root != b.row_root)
         return false;
     for (int i = 0; i < a.n_vnodes; i++) {
         const exa_vnode &u = a.vnodes[i], &v = b.vnodes[i];
-        if (u.op != v.op || u.a != v.a || u.b != v.b || u.ival != v.ival ||
-            std::memcmp(&u.fval, &v.fval, sizeof(double)) != 0)
-            return false;
+        if (u.op != v.op || u.a != v.a || u.b != v.b) return false;
+        if (u.op != EXA_V_CONST && u.ival != v.ival) return false;
     }
     for (int i = 0; i < a.n_inodes; i++) {
         const exa_inode &u = a.inodes[i], &v = b.inodes[i];
-        if (u.op != v.op || u.a != v.a || u.b != v.b || u.ival != v.ival) return false;
+        if (u.op != v.op || u.a != v.a || u.b != v.b) return false;
+        if (u.op != EXA_I_CONST && u.ival != v.ival) return false;
     }
     for (int f = 0; f < a.n_fields; f++)
         if (a.fields[f].type != b.fields[f].type) return false;
@@ -500,8 +519,8 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
             if (pd.n_vnodes < 0 || pd.n_inodes < 0 || pd.n_fields < 0) return fail(m, EXA_E_INVALID, "negative node count");
             for (int f = 0; f < pd.n_fields; f++)
                 if (pd.n_inst > 0 && !pd.fields[f].data) return fail(m, EXA_E_INVALID, "NULL data column");
-            if (b > 0 && !same_ir(pd, descs[0]->patterns[p]))
-                return fail(m, EXA_E_INVALID, "batch members must share identical pattern trees");
+            if (b > 0 && !same_shape(pd, descs[0]->patterns[p]))
+                return fail(m, EXA_E_INVALID, "batch members must share the same pattern trees");
         }
     }
     CR(cudaSetDevice(m->device));
@@ -516,6 +535,37 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     const exa_model_desc &d0 = *descs[0];
     const int np = d0.n_patterns;
     if (exa_status e = load_patterns(d0, m)) return e;
+    // constants that differ between members, and the symbol partition every member must share
+    for (int p = 0; p < np; p++) {
+        exa::Pattern &P = m->pats[p];
+        for (int b = 1; b < nb; b++) {
+            const exa_pattern_desc &pd = descs[b]->patterns[p];
+            for (int i = 0; i < pd.n_inodes; i++)
+                if (pd.inodes[i].op == EXA_I_CONST && pd.inodes[i].ival != P.ix[i].iv && !P.ivary.count(i)) {
+                    int slot = (int)P.ivary.size();
+                    P.ivary[i] = slot;
+                }
+            for (int i = 0; i < pd.n_vnodes; i++)
+                if (pd.vnodes[i].op == EXA_V_CONST && std::memcmp(&pd.vnodes[i].fval, &P.v[i].fv, 8) != 0 &&
+                    !P.fvary.count(i)) {
+                    int slot = (int)P.fvary.size();
+                    P.fvary[i] = slot;
+                }
+        }
+        if (P.ivary.size() > 8 || P.fvary.size() > 8)
+            return fail(m, EXA_E_UNSUPPORTED, "more than 8 constants of one pattern differ between batch members");
+        if (!P.ivary.empty()) {
+            for (int b = 1; b < nb; b++) {
+                const exa_pattern_desc &pd = descs[b]->patterns[p];
+                std::vector<exa::INode> ix;
+                for (int i = 0; i < pd.n_inodes; i++)
+                    ix.push_back({pd.inodes[i].op, pd.inodes[i].a, pd.inodes[i].b, pd.inodes[i].ival});
+                if (exa::symbol_partition(P, ix) != exa::symbol_partition(P, P.ix))
+                    return fail(m, EXA_E_INVALID, "batch members of pattern " + std::to_string(p) +
+                                                      " identify variable references differently");
+            }
+        }
+    }
 
     // per-member sizes and offsets; validate row blocks
     m->nb = nb;
@@ -550,6 +600,8 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
             pm.rlimit = pd.row_limit;
             pm.pat = p;
             pm.member = b;
+            for (auto &kv : P.ivary) pm.ic[kv.second] = pd.inodes[kv.first].ival;
+            for (auto &kv : P.fvary) pm.fc[kv.second] = pd.vnodes[kv.first].fval;
             pm.hbase = oh; oh += pd.n_inst * P.nh();
             if (P.kind == EXA_OBJ) { pm.gbase = og; og += pd.n_inst * P.nj(); }
             else { pm.jbase = oj; oj += pd.n_inst * P.nj(); }

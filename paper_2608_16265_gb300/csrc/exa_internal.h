@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <map>
 #include <string>
 #include <utility>
 #include <vector>
@@ -26,6 +27,8 @@
         long long abase;          /* first augmentation-buffer entry (augmentation patterns) */     \
         long long poff;           /* first parameter of the member */                               \
         long long npar_m;         /* parameters of the member */                                    \
+        long long ic[8];          /* index constants that differ between batch members */           \
+        double fc[8];             /* value constants that differ between batch members */           \
         int pat;                  /* pattern id */                                                  \
         int member;               /* batch member */                                                \
     };                                                                                              \
@@ -73,6 +76,8 @@ struct Pattern {
     std::vector<int> sym_root;  // per symbol: its index-expression root
     std::vector<int> jsym;      // first-order slot -> symbol
     std::vector<std::pair<int, int>> hpair;  // Hessian slot -> symbol pair (as first emitted)
+    // constants that differ between batch members: node index -> slot in ExaPM::ic / ExaPM::fc
+    std::map<int, int> ivary, fvary;
     int nj() const { return (int)jsym.size(); }
     int nh() const { return (int)hpair.size(); }
 };
@@ -91,5 +96,9 @@ std::string generate_source(const std::vector<Pattern> &pats, const CodegenOptio
                             std::string *err);
 
 extern const char *const kDeviceStructs;
+
+// Symbol id of every Var leaf of the pattern's tree when its index nodes are `ix` (a batch member
+// may carry other constants than member 0); -1 for other nodes.
+std::vector<int> symbol_partition(const Pattern &p, const std::vector<INode> &ix);
 
 }  // namespace exa

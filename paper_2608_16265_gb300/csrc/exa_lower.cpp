@@ -51,17 +51,39 @@ static bool second_partial_nonzero(const VNode &n, int which) {
 }
 
 // ------------------------------------------------------------------ index-expression keys
-static std::string idx_key(const Pattern &p, int r) {
-    const INode &n = p.ix[r];
+static std::string idx_key(const std::vector<INode> &ix, int r) {
+    const INode &n = ix[r];
     switch (n.op) {
     case EXA_I_CONST: return "c" + std::to_string(n.iv);
     case EXA_I_FIELD: return "f" + std::to_string(n.iv);
     case EXA_I_INST: return "k";
     default: {
         const char *o = n.op == EXA_I_ADD ? "+" : n.op == EXA_I_SUB ? "-" : "*";
-        return std::string("(") + idx_key(p, n.a) + o + idx_key(p, n.b) + ")";
+        return std::string("(") + idx_key(ix, n.a) + o + idx_key(ix, n.b) + ")";
     }
     }
+}
+
+std::vector<int> symbol_partition(const Pattern &p, const std::vector<INode> &ix) {
+    const int nv = (int)p.v.size();
+    std::vector<int> out(nv, -1);
+    std::map<std::string, int> ids;
+    std::vector<int> stack{nv - 1};
+    while (!stack.empty()) {
+        int i = stack.back();
+        stack.pop_back();
+        const VNode &n = p.v[i];
+        if (n.op == EXA_V_VAR) {
+            auto r = ids.emplace(idx_key(ix, n.a), (int)ids.size());
+            out[i] = r.first->second;
+        } else if (is_unary(n.op)) {
+            stack.push_back(n.a);
+        } else if (is_binary(n.op)) {
+            stack.push_back(n.b);
+            stack.push_back(n.a);
+        }
+    }
+    return out;
 }
 
 static std::string check_idx(const Pattern &p, int r, int limit, int depth = 0) {
@@ -150,7 +172,7 @@ std::string analyse_pattern(Pattern &p) {
         }
     }
     for (int i : preorder_leaves) {
-        std::string key = idx_key(p, p.v[i].a);
+        std::string key = idx_key(p.ix, p.v[i].a);
         auto it = sym_by_key.find(key);
         int s;
         if (it == sym_by_key.end()) {
@@ -359,7 +381,11 @@ static void build_graph(const Pattern &p, PatternGraph &G) {
         int w = nd.b >= 0 && is_binary(nd.op) ? G.val[nd.b] : -1;
         int v = Z, d1 = Z, d2 = Z, h11 = Z, h12 = Z, h22 = Z;
         switch (nd.op) {
-        case EXA_V_CONST: v = g.lit(nd.fv); break;
+        case EXA_V_CONST: {
+            auto it = p.fvary.find(i);
+            v = it != p.fvary.end() ? g.input("C" + std::to_string(it->second)) : g.lit(nd.fv);
+            break;
+        }
         case EXA_V_DATA: v = g.input("D" + std::to_string(nd.iv)); break;
         case EXA_V_VAR: v = g.input("X" + std::to_string(p.sym_of[i])); hv[i] = 1; break;
         case EXA_V_PARAM: v = g.input("P" + std::to_string(i)); break;
@@ -503,7 +529,11 @@ struct Emitter {
     std::string idx_expr(int r) {
         const INode &n = p.ix[r];
         switch (n.op) {
-        case EXA_I_CONST: return "(" + std::to_string(n.iv) + "LL)";
+        case EXA_I_CONST: {
+            auto it = p.ivary.find(r);
+            if (it != p.ivary.end()) return "pm.ic[" + std::to_string(it->second) + "]";
+            return "(" + std::to_string(n.iv) + "LL)";
+        }
         case EXA_I_FIELD: return "((long long)F" + std::to_string(n.iv) + ")";
         case EXA_I_INST: return "kk";
         default: {
@@ -607,7 +637,7 @@ struct Emitter {
             }
         for (int r : hroots) if (r < (int)G.g.n.size()) roots.push_back(r);
         // which inputs are needed
-        std::set<int> syms, fields, params;
+        std::set<int> syms, fields, params, fconsts;
         bool need_row = (!obj) && (want_val || want_hess || want_struct);
         {
             std::vector<char> seen(G.g.n.size(), 0);
@@ -620,6 +650,7 @@ struct Emitter {
                     if (s.in[0] == 'X') syms.insert(id);
                     else if (s.in[0] == 'D') fields.insert(id);
                     else if (s.in[0] == 'P') params.insert(id);
+                    else if (s.in[0] == 'C') fconsts.insert(id);
                 }
                 if (s.a >= 0) walk(s.a);
                 if (s.b >= 0) walk(s.b);
@@ -685,6 +716,7 @@ struct Emitter {
             return os.str();
         }
         for (int s : syms) os << "  const double X" << s << " = __ldg(x + pm.xoff + i" << s << ");\n";
+        for (int s : fconsts) os << "  const double C" << s << " = pm.fc[" << s << "];\n";
         for (int pn : params) os << "  const double P" << pn << " = __ldg(th + pm.poff + q" << pn << ");\n";
         std::map<int, std::string> name;
         body(roots, name);
