@@ -97,6 +97,7 @@ class ClockSampler:
         self.path = None
 
     def start(self):
+        """Starts sampling and waits until the first sample has arrived."""
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
@@ -105,6 +106,10 @@ class ClockSampler:
                  "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+            time.sleep(0.05)
 
     def stop(self):
         if self.proc is None:
@@ -132,7 +137,7 @@ class ClockSampler:
         pw = np.array([num(r[3]) for r in rows])
         loaded = pw >= np.nanmedian(pw) if len(pw) > 2 else np.ones(len(pw), bool)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = [n for j, n in enumerate(names) if any("Active" in r[5 + j] for r in rows)]
+        reasons = [n for j, n in enumerate(names) if any(r[5 + j].strip() == "Active" for r in rows)]
         return {"sm_mhz": float(np.nanmedian(sm[loaded])), "sm_max_mhz": float(smax), "reasons": reasons,
                 "samples": len(rows), "power_w_max": float(np.nanmax(pw))}
 
@@ -168,8 +173,8 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    wls, pts = make_batch(0)
-    steps, warm = args.steps, args.warmup
+    wls, pts = make_batch(0, args.members)
+    steps, warm = (args.steps if args.steps > 0 else 5), args.warmup
     # bounded per-step sample so the whole run stays within a few minutes
     per_step = max(1.0, min(20.0, 150.0 / max(1, steps + warm)))
     for _ in range(warm):
@@ -209,7 +214,7 @@ def run_exa(args):
 
     prec = B.EXA_MIXED_FP32 if args.precision == "mixed" else B.EXA_FP64
     t0 = time.perf_counter()
-    wls, pts = make_batch(rank)
+    wls, pts = make_batch(rank, args.members)
     flats = [w.flat for w in wls]
     t_gen = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -247,6 +252,13 @@ def run_exa(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    if args.steps <= 0:  # auto: about two seconds of timed work
+        probe = timed(step, 3)
+        args.steps = int(min(5000, max(20, 2000.0 / max(probe, 1e-3))))
+        if pg is not None:
+            t = torch.tensor([args.steps], device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            args.steps = int(t.item())
     barrier()
     clk = ClockSampler(local)
     clk.start()
@@ -261,9 +273,9 @@ def run_exa(args):
     value = ws * nnz_rank / (ms * 1e-3)
 
     # dominant kernel alone: the generated evaluation kernel writing J and H (no reductions)
-    kern_ms = timed(lambda: m.exa_eval_all(xt, yt, sigma, jac=jac, hess=hess), max(5, args.steps))
+    kern_ms = timed(lambda: m.exa_eval_all(xt, yt, sigma, jac=jac, hess=hess), max(5, min(args.steps, 200)))
     # Jacobian + Hessian callbacks alone (exa_jac_coord + exa_hess_coord)
-    jh_ms = timed(lambda: (m.exa_jac_coord(xt, jac), m.exa_hess_coord(xt, yt, sigma, hess)), max(5, args.steps))
+    jh_ms = timed(lambda: (m.exa_jac_coord(xt, jac), m.exa_hess_coord(xt, yt, sigma, hess)), max(5, min(args.steps, 200)))
     nbytes = algorithmic_bytes(flats, m.nnzj, m.nnzh, m.nvar, m.ncon,
                                sum(p.n_inst for fl in flats for p in fl.patterns if p.kind == 2),
                                sum(p.n_inst for fl in flats for p in fl.patterns if p.kind == 0))
@@ -317,7 +329,7 @@ def run_exa(args):
 
     for _ in range(2):
         e2e_step()
-    e2e_ms = timed(e2e_step, max(3, args.steps // 2))
+    e2e_ms = timed(e2e_step, max(3, min(args.steps // 2, 200)))
     if pg is not None:
         t = torch.tensor([e2e_ms], device=dev)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
@@ -337,7 +349,7 @@ def run_exa(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == B.EXA_FP64 else "f32+f64",
         "data": "synthetic (seeded generator; paper's suites not available)",
-        "config": {"workload": WORKLOAD, "members": 256, "buses": "log-uniform 200-20000",
+        "config": {"workload": WORKLOAD if args.members == 256 else f"acopf_batch_{args.members}", "members": args.members, "buses": "log-uniform 200-20000",
                    "nnz_per_rank": nnz_rank, "precision": args.precision, "parallelism": f"replicas{ws}",
                    "l2": "inputs+outputs ~2 GB per step > 129 MB L2 (no flush needed)"},
         "e2e": {"value": ws * nnz_rank / (e2e_ms * 1e-3), "unit": UNIT,
@@ -360,7 +372,8 @@ def run_exa(args):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=0, help="timed steps (0: about two seconds of work)")
+    ap.add_argument("--members", type=int, default=256, help="batch members (256 is the benchmark workload)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["exa", "reference"], default="exa")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")

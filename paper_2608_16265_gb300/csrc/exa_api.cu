@@ -498,7 +498,7 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     exa_options o{};
     if (opt) o = *opt;
     if (o.precision != EXA_FP64 && o.precision != EXA_MIXED_FP32) return fail(m, EXA_E_INVALID, "unknown precision");
-    if (o.precision == EXA_MIXED_FP32) return fail(m, EXA_E_UNSUPPORTED, "mixed precision is not built yet");
+    
     m->precision = o.precision;
     m->device = o.device;
     m->bounds_check = (o.flags & EXA_FLAG_BOUNDS_CHECK) != 0;

@@ -256,86 +256,96 @@ namespace {
 
 enum SOp {
     S_LIT, S_IN, S_NEG, S_ADD, S_SUB, S_MUL, S_DIV,
-    S_EXP, S_LOG, S_SIN, S_COS, S_SQRT, S_TAN, S_TANH, S_ATAN, S_POW
+    S_EXP, S_LOG, S_SIN, S_COS, S_SQRT, S_TAN, S_TANH, S_ATAN, S_POW,
+    S_CVT,              // convert the operand to this node's precision
+    S_SINR, S_COSR,     // float sin / cos of an FP64 argument reduced in FP64
+    S_EXPR              // float exp of an FP64 argument reduced in FP64
 };
+enum Prec { PD = 0, PF = 1 };  // FP64, FP32
 
 struct SN {
     int op;
+    int prec;
     int a, b;
     double lit;
-    std::string in;  // input expression (S_IN)
+    char ikind;  // S_IN: 'X' variable symbol, 'D' data field, 'P' parameter node, 'C' member constant
+    int iid;
 };
 
 class Graph {
   public:
     std::vector<SN> n;
     std::map<std::tuple<int, int, int, uint64_t>, int> memo;
-    std::map<std::string, int> inputs;
 
-    int lit(double v) {
+    int lit(double v, int prec) {
+        if (prec == PF) v = (double)(float)v;
         uint64_t bits;
         std::memcpy(&bits, &v, 8);
-        auto key = std::make_tuple((int)S_LIT, -1, -1, bits);
+        auto key = std::make_tuple((int)S_LIT * 2 + prec, -1, -1, bits);
         auto it = memo.find(key);
         if (it != memo.end()) return it->second;
-        n.push_back({S_LIT, -1, -1, v, ""});
+        n.push_back({S_LIT, prec, -1, -1, v, 0, 0});
         return memo[key] = (int)n.size() - 1;
     }
-    int input(const std::string &expr) {
-        auto it = inputs.find(expr);
-        if (it != inputs.end()) return it->second;
-        n.push_back({S_IN, -1, -1, 0.0, expr});
-        return inputs[expr] = (int)n.size() - 1;
-    }
-    int node(int op, int a, int b = -1) {
-        auto key = std::make_tuple(op, a, b, (uint64_t)0);
+    int input(char kind, int id, int prec) {
+        auto key = std::make_tuple((int)S_IN * 2 + prec, (int)kind, id, (uint64_t)0);
         auto it = memo.find(key);
         if (it != memo.end()) return it->second;
-        n.push_back({op, a, b, 0.0, ""});
+        n.push_back({S_IN, prec, -1, -1, 0.0, kind, id});
         return memo[key] = (int)n.size() - 1;
     }
+    int node(int op, int prec, int a, int b = -1) {
+        auto key = std::make_tuple(op * 2 + prec, a, b, (uint64_t)0);
+        auto it = memo.find(key);
+        if (it != memo.end()) return it->second;
+        n.push_back({op, prec, a, b, 0.0, 0, 0});
+        return memo[key] = (int)n.size() - 1;
+    }
+    int P(int i) const { return n[i].prec; }
     bool is_lit(int i) const { return n[i].op == S_LIT; }
     bool is(int i, double v) const { return n[i].op == S_LIT && n[i].lit == v; }
     bool zero(int i) const { return is(i, 0.0); }
+    double fold(double v, int prec) const { return prec == PF ? (double)(float)v : v; }
 
     int neg(int a) {
-        if (is_lit(a)) return lit(-n[a].lit);
+        if (is_lit(a)) return lit(-n[a].lit, P(a));
         if (n[a].op == S_NEG) return n[a].a;
-        return node(S_NEG, a);
+        return node(S_NEG, P(a), a);
     }
     int add(int a, int b) {
         if (zero(a)) return b;
         if (zero(b)) return a;
-        if (is_lit(a) && is_lit(b)) return lit(n[a].lit + n[b].lit);
+        if (is_lit(a) && is_lit(b)) return lit(fold(n[a].lit + n[b].lit, P(a)), P(a));
         if (a > b) std::swap(a, b);  // a + b == b + a exactly
-        return node(S_ADD, a, b);
+        return node(S_ADD, P(a), a, b);
     }
     int sub(int a, int b) {
         if (zero(b)) return a;
         if (zero(a)) return neg(b);
-        if (is_lit(a) && is_lit(b)) return lit(n[a].lit - n[b].lit);
-        return node(S_SUB, a, b);
+        if (is_lit(a) && is_lit(b)) return lit(fold(n[a].lit - n[b].lit, P(a)), P(a));
+        return node(S_SUB, P(a), a, b);
     }
     int mul(int a, int b) {
-        if (zero(a) || zero(b)) return lit(0.0);
+        if (zero(a) || zero(b)) return lit(0.0, P(a));
         if (is(a, 1.0)) return b;
         if (is(b, 1.0)) return a;
         if (is(a, -1.0)) return neg(b);
         if (is(b, -1.0)) return neg(a);
-        if (is_lit(a) && is_lit(b)) return lit(n[a].lit * n[b].lit);
+        if (is_lit(a) && is_lit(b)) return lit(fold(n[a].lit * n[b].lit, P(a)), P(a));
         if (a > b) std::swap(a, b);
-        return node(S_MUL, a, b);
+        return node(S_MUL, P(a), a, b);
     }
     int div(int a, int b) {
         if (is(b, 1.0)) return a;
-        if (zero(a)) return lit(0.0);
-        if (is_lit(a) && is_lit(b)) return lit(n[a].lit / n[b].lit);
-        return node(S_DIV, a, b);
+        if (zero(a)) return lit(0.0, P(a));
+        if (is_lit(a) && is_lit(b)) return lit(fold(n[a].lit / n[b].lit, P(a)), P(a));
+        return node(S_DIV, P(a), a, b);
     }
-    int fn(int op, int a) { return node(op, a); }
+    int fn(int op, int a) { return node(op, P(a), a); }
+    int fn_at(int op, int prec, int a) { return node(op, prec, a); }
     int powi(int u, long long m) {
-        if (m == 0) return lit(1.0);
-        if (m < 0) return div(lit(1.0), powi(u, -m));
+        if (m == 0) return lit(1.0, P(u));
+        if (m < 0) return div(lit(1.0, P(u)), powi(u, -m));
         if (m == 1) return u;
         int h = powi(u, m / 2);
         int sq = mul(h, h);
@@ -353,28 +363,82 @@ struct PatternGraph {
 };
 
 static std::string fmt_double(double v) {
-    char buf[64];
-    std::snprintf(buf, sizeof buf, "%.17g", v);
-    std::string s(buf);
     if (!std::isfinite(v)) {
         uint64_t bits;
         std::memcpy(&bits, &v, 8);
         return "__longlong_as_double(" + std::to_string((long long)bits) + "LL)";
     }
+    char buf[64];
+    std::snprintf(buf, sizeof buf, "%.17g", v);
+    std::string s(buf);
     if (s.find_first_of(".eE") == std::string::npos) s += ".0";
     if (v < 0 || (v == 0 && std::signbit(v))) s = "(" + s + ")";
     return s;
 }
 
+static std::string fmt_float(double v) {
+    float f = (float)v;
+    if (!std::isfinite(f)) {
+        uint32_t bits;
+        std::memcpy(&bits, &f, 4);
+        return "__int_as_float(" + std::to_string((int)bits) + ")";
+    }
+    char buf[64];
+    std::snprintf(buf, sizeof buf, "%.9g", (double)f);
+    std::string s(buf);
+    if (s.find_first_of(".eE") == std::string::npos) s += ".0";
+    s += "f";
+    if (f < 0 || (f == 0 && std::signbit(f))) s = "(" + s + ")";
+    return s;
+}
+
 // Builds value, gradient over symbols and Hessian over symbol pairs for one pattern.
-static void build_graph(const Pattern &p, PatternGraph &G) {
+// FP64 mode: every node in FP64.  Mixed mode: every node in FP32 except the primal subtrees that
+// form the arguments of sin / cos / tan / exp, which are evaluated in FP64 and reduced in FP64.
+static void build_graph(const Pattern &p, PatternGraph &G, bool mixed) {
     Graph &g = G.g;
     const int nv = (int)p.v.size();
+    const int W = mixed ? PF : PD;  // working precision of pattern arithmetic
     G.val.assign(nv, -1);
-    int Z = g.lit(0.0), ONE = g.lit(1.0);
+    int Z = g.lit(0.0, W), ONE = g.lit(1.0, W), TWO = g.lit(2.0, W);
     G.d1.assign(nv, Z); G.d2.assign(nv, Z);
     G.h11.assign(nv, Z); G.h12.assign(nv, Z); G.h22.assign(nv, Z);
     std::vector<char> hv(nv, 0);
+    // FP64 primal value of a subtree (argument formation in mixed mode)
+    std::vector<int> dmemo(nv, -1);
+    std::function<int(int)> dval = [&](int i) -> int {
+        if (dmemo[i] >= 0) return dmemo[i];
+        const VNode &nd = p.v[i];
+        int r = -1;
+        switch (nd.op) {
+        case EXA_V_CONST: {
+            auto it = p.fvary.find(i);
+            r = it != p.fvary.end() ? g.input('C', it->second, PD) : g.lit(nd.fv, PD);
+            break;
+        }
+        case EXA_V_DATA: r = g.input('D', (int)nd.iv, PD); break;
+        case EXA_V_VAR: r = g.input('X', p.sym_of[i], PD); break;
+        case EXA_V_PARAM: r = g.input('P', i, PD); break;
+        case EXA_V_NEG: r = g.neg(dval(nd.a)); break;
+        case EXA_V_ABS2: { int u = dval(nd.a); r = g.mul(u, u); break; }
+        case EXA_V_INV: r = g.div(g.lit(1.0, PD), dval(nd.a)); break;
+        case EXA_V_EXP: r = g.fn(S_EXP, dval(nd.a)); break;
+        case EXA_V_LOG: r = g.fn(S_LOG, dval(nd.a)); break;
+        case EXA_V_SIN: r = g.fn(S_SIN, dval(nd.a)); break;
+        case EXA_V_COS: r = g.fn(S_COS, dval(nd.a)); break;
+        case EXA_V_SQRT: r = g.fn(S_SQRT, dval(nd.a)); break;
+        case EXA_V_TAN: r = g.fn(S_TAN, dval(nd.a)); break;
+        case EXA_V_TANH: r = g.fn(S_TANH, dval(nd.a)); break;
+        case EXA_V_ATAN: r = g.fn(S_ATAN, dval(nd.a)); break;
+        case EXA_V_POWI: r = g.powi(dval(nd.a), nd.iv); break;
+        case EXA_V_ADD: r = g.add(dval(nd.a), dval(nd.b)); break;
+        case EXA_V_SUB: r = g.sub(dval(nd.a), dval(nd.b)); break;
+        case EXA_V_MUL: r = g.mul(dval(nd.a), dval(nd.b)); break;
+        case EXA_V_DIV: r = g.div(dval(nd.a), dval(nd.b)); break;
+        case EXA_V_POW: r = g.node(S_POW, PD, dval(nd.a), dval(nd.b)); break;
+        }
+        return dmemo[i] = r;
+    };
     for (int i = 0; i < nv; i++) {
         const VNode &nd = p.v[i];
         int u = nd.a >= 0 && !is_leaf(nd.op) ? G.val[nd.a] : -1;
@@ -383,42 +447,57 @@ static void build_graph(const Pattern &p, PatternGraph &G) {
         switch (nd.op) {
         case EXA_V_CONST: {
             auto it = p.fvary.find(i);
-            v = it != p.fvary.end() ? g.input("C" + std::to_string(it->second)) : g.lit(nd.fv);
+            v = it != p.fvary.end() ? g.input('C', it->second, W) : g.lit(nd.fv, W);
             break;
         }
-        case EXA_V_DATA: v = g.input("D" + std::to_string(nd.iv)); break;
-        case EXA_V_VAR: v = g.input("X" + std::to_string(p.sym_of[i])); hv[i] = 1; break;
-        case EXA_V_PARAM: v = g.input("P" + std::to_string(i)); break;
-        case EXA_V_NEG: v = g.neg(u); d1 = g.lit(-1.0); break;
-        case EXA_V_ABS2: v = g.mul(u, u); d1 = g.mul(g.lit(2.0), u); h11 = g.lit(2.0); break;
+        case EXA_V_DATA: v = g.input('D', (int)nd.iv, W); break;
+        case EXA_V_VAR: v = g.input('X', p.sym_of[i], W); hv[i] = 1; break;
+        case EXA_V_PARAM: v = g.input('P', i, W); break;
+        case EXA_V_NEG: v = g.neg(u); d1 = g.lit(-1.0, W); break;
+        case EXA_V_ABS2: v = g.mul(u, u); d1 = g.mul(TWO, u); h11 = TWO; break;
         case EXA_V_INV:
             v = g.div(ONE, u);
             d1 = g.neg(g.mul(v, v));
-            h11 = g.mul(g.lit(2.0), g.mul(v, g.mul(v, v)));
+            h11 = g.mul(TWO, g.mul(v, g.mul(v, v)));
             break;
-        case EXA_V_EXP: v = g.fn(S_EXP, u); d1 = v; h11 = v; break;
+        case EXA_V_EXP:
+            v = mixed ? g.fn_at(S_EXPR, PF, dval(nd.a)) : g.fn(S_EXP, u);
+            d1 = v; h11 = v;
+            break;
         case EXA_V_LOG: v = g.fn(S_LOG, u); d1 = g.div(ONE, u); h11 = g.neg(g.mul(d1, d1)); break;
-        case EXA_V_SIN: v = g.fn(S_SIN, u); d1 = g.fn(S_COS, u); h11 = g.neg(v); break;
-        case EXA_V_COS: v = g.fn(S_COS, u); d1 = g.neg(g.fn(S_SIN, u)); h11 = g.neg(v); break;
+        case EXA_V_SIN:
+            if (mixed) { v = g.fn_at(S_SINR, PF, dval(nd.a)); d1 = g.fn_at(S_COSR, PF, dval(nd.a)); }
+            else { v = g.fn(S_SIN, u); d1 = g.fn(S_COS, u); }
+            h11 = g.neg(v);
+            break;
+        case EXA_V_COS:
+            if (mixed) { v = g.fn_at(S_COSR, PF, dval(nd.a)); d1 = g.neg(g.fn_at(S_SINR, PF, dval(nd.a))); }
+            else { v = g.fn(S_COS, u); d1 = g.neg(g.fn(S_SIN, u)); }
+            h11 = g.neg(v);
+            break;
         case EXA_V_SQRT:
             v = g.fn(S_SQRT, u);
-            d1 = g.div(g.lit(0.5), v);
-            h11 = g.neg(g.div(g.lit(0.25), g.mul(u, v)));
+            d1 = g.div(g.lit(0.5, W), v);
+            h11 = g.neg(g.div(g.lit(0.25, W), g.mul(u, v)));
             break;
-        case EXA_V_TAN: v = g.fn(S_TAN, u); d1 = g.add(ONE, g.mul(v, v)); h11 = g.mul(g.lit(2.0), g.mul(v, d1)); break;
-        case EXA_V_TANH: v = g.fn(S_TANH, u); d1 = g.sub(ONE, g.mul(v, v)); h11 = g.mul(g.lit(-2.0), g.mul(v, d1)); break;
+        case EXA_V_TAN:
+            v = mixed ? g.div(g.fn_at(S_SINR, PF, dval(nd.a)), g.fn_at(S_COSR, PF, dval(nd.a))) : g.fn(S_TAN, u);
+            d1 = g.add(ONE, g.mul(v, v));
+            h11 = g.mul(TWO, g.mul(v, d1));
+            break;
+        case EXA_V_TANH: v = g.fn(S_TANH, u); d1 = g.sub(ONE, g.mul(v, v)); h11 = g.mul(g.lit(-2.0, W), g.mul(v, d1)); break;
         case EXA_V_ATAN:
             v = g.fn(S_ATAN, u);
             d1 = g.div(ONE, g.add(ONE, g.mul(u, u)));
-            h11 = g.mul(g.lit(-2.0), g.mul(u, g.mul(d1, d1)));
+            h11 = g.mul(g.lit(-2.0, W), g.mul(u, g.mul(d1, d1)));
             break;
         case EXA_V_POWI:
             v = g.powi(u, nd.iv);
-            d1 = g.mul(g.lit((double)nd.iv), g.powi(u, nd.iv - 1));
-            h11 = g.mul(g.lit((double)nd.iv * (double)(nd.iv - 1)), g.powi(u, nd.iv - 2));
+            d1 = g.mul(g.lit((double)nd.iv, W), g.powi(u, nd.iv - 1));
+            h11 = g.mul(g.lit((double)nd.iv * (double)(nd.iv - 1), W), g.powi(u, nd.iv - 2));
             break;
         case EXA_V_ADD: v = g.add(u, w); d1 = ONE; d2 = ONE; break;
-        case EXA_V_SUB: v = g.sub(u, w); d1 = ONE; d2 = g.lit(-1.0); break;
+        case EXA_V_SUB: v = g.sub(u, w); d1 = ONE; d2 = g.lit(-1.0, W); break;
         case EXA_V_MUL: v = g.mul(u, w); d1 = w; d2 = u; h12 = ONE; break;
         case EXA_V_DIV: {
             v = g.div(u, w);
@@ -426,11 +505,11 @@ static void build_graph(const Pattern &p, PatternGraph &G) {
             d1 = r;
             d2 = g.neg(g.mul(v, r));
             h12 = g.neg(g.mul(r, r));
-            h22 = g.mul(g.lit(2.0), g.mul(v, g.mul(r, r)));
+            h22 = g.mul(TWO, g.mul(v, g.mul(r, r)));
             break;
         }
         case EXA_V_POW: {
-            v = g.node(S_POW, u, w);
+            v = g.node(S_POW, W, u, w);
             int lu = g.fn(S_LOG, u);
             int vu = g.div(v, u);
             d1 = g.mul(w, vu);
@@ -452,8 +531,7 @@ static void build_graph(const Pattern &p, PatternGraph &G) {
     G.adj2.assign(nv, Z);
     G.grad.assign(p.nsym, Z);
     G.adj[nv - 1] = ONE;
-    // tangent gradient of every subtree over symbols (bottom-up)
-    std::vector<std::map<int, int>> tg(nv);
+    std::vector<std::map<int, int>> tg(nv);  // subtree gradient over symbols (bottom-up)
     for (int i = 0; i < nv; i++) {
         const VNode &nd = p.v[i];
         if (nd.op == EXA_V_VAR) tg[i][p.sym_of[i]] = ONE;
@@ -501,13 +579,12 @@ static void build_graph(const Pattern &p, PatternGraph &G) {
                 for (auto &ka : tg[nd.a])
                     for (auto &kb : tg[nd.b]) {
                         int c = g.mul(w, g.mul(ka.second, kb.second));
-                        if (ka.first == kb.first) c = g.mul(g.lit(2.0), c);
+                        if (ka.first == kb.first) c = g.mul(TWO, c);
                         hacc(ka.first, kb.first, c);
                     }
             }
         }
     }
-    // every computed entry must be a structural slot
     std::set<std::pair<int, int>> slots;
     for (auto &pr : p.hpair) slots.insert({std::min(pr.first, pr.second), std::max(pr.first, pr.second)});
     for (auto &kv : G.hess)
@@ -548,15 +625,18 @@ struct Emitter {
         else if (n.op >= EXA_I_ADD) { fields_of_idx(n.a, f); fields_of_idx(n.b, f); }
     }
 
-    static const char *fname(int op) {
-        switch (op) {
-        case S_EXP: return "exp"; case S_LOG: return "log"; case S_SIN: return "sin";
-        case S_COS: return "cos"; case S_SQRT: return "sqrt"; case S_TAN: return "tan";
-        case S_TANH: return "tanh"; case S_ATAN: return "atan"; default: return "?";
-        }
+    static const char *fname(int op, int prec) {
+        static const char *d[] = {"exp", "log", "sin", "cos", "sqrt", "tan", "tanh", "atan"};
+        static const char *f[] = {"expf", "logf", "sinf", "cosf", "sqrtf", "tanf", "tanhf", "atanf"};
+        int k = op - S_EXP;
+        return prec == PF ? f[k] : d[k];
+    }
+    static const char *ty(int prec) { return prec == PF ? "float" : "double"; }
+    static std::string in_name(const SN &s) {
+        return std::string(1, s.ikind) + (s.prec == PF ? "F" : "") + std::to_string(s.iid);
     }
 
-    // Emits the body computing the requested graph nodes; returns the C expression of each.
+    // Emits the nodes the roots need, in creation (dependency) order; names every node.
     void body(const std::vector<int> &roots, std::map<int, std::string> &name) {
         const Graph &g = G.g;
         std::vector<char> need(g.n.size(), 0);
@@ -567,47 +647,54 @@ struct Emitter {
             if (g.n[i].b >= 0) mark(g.n[i].b);
         };
         for (int r : roots) mark(r);
-        // sin and cos of one argument share a sincos call
-        std::map<int, std::pair<int, int>> sc;  // argument -> (sin node, cos node)
+        // sin and cos of one argument share one call
+        std::map<std::pair<int, int>, std::pair<int, int>> sc;  // (arg, reduced?) -> (sin+1, cos+1)
         for (size_t i = 0; i < g.n.size(); i++) {
             if (!need[i]) continue;
-            if (g.n[i].op == S_SIN) sc[g.n[i].a].first = (int)i + 1;
-            if (g.n[i].op == S_COS) sc[g.n[i].a].second = (int)i + 1;
+            int op = g.n[i].op;
+            bool red = op == S_SINR || op == S_COSR;
+            if (op == S_SIN || op == S_SINR) sc[{g.n[i].a, red}].first = (int)i + 1;
+            if (op == S_COS || op == S_COSR) sc[{g.n[i].a, red}].second = (int)i + 1;
         }
         for (size_t i = 0; i < g.n.size(); i++) {
             if (!need[i]) continue;
             const SN &s = g.n[i];
-            std::string t = "t" + std::to_string(i);
-            switch (s.op) {
-            case S_LIT: name[i] = fmt_double(s.lit); continue;
-            case S_IN: name[i] = s.in; continue;
-            default: break;
-            }
+            const std::string t = "t" + std::to_string(i);
+            const char *T = ty(s.prec);
+            if (s.op == S_LIT) { name[i] = s.prec == PF ? fmt_float(s.lit) : fmt_double(s.lit); continue; }
+            if (s.op == S_IN) { name[i] = in_name(s); continue; }
             name[i] = t;
             auto A = [&]() { return name.at(s.a); };
             auto B = [&]() { return name.at(s.b); };
             switch (s.op) {
-            case S_NEG: os << "  const double " << t << " = -" << A() << ";\n"; break;
-            case S_ADD: os << "  const double " << t << " = " << A() << " + " << B() << ";\n"; break;
-            case S_SUB: os << "  const double " << t << " = " << A() << " - " << B() << ";\n"; break;
-            case S_MUL: os << "  const double " << t << " = " << A() << " * " << B() << ";\n"; break;
-            case S_DIV: os << "  const double " << t << " = " << A() << " / " << B() << ";\n"; break;
-            case S_POW: os << "  const double " << t << " = pow(" << A() << ", " << B() << ");\n"; break;
-            case S_SIN: case S_COS: {
-                auto pr = sc[s.a];
-                if (pr.first && pr.second) {
-                    int si = pr.first - 1, ci = pr.second - 1;
-                    if ((int)i == std::min(si, ci)) {
-                        os << "  double t" << si << ", t" << ci << ";\n  sincos(" << A() << ", &t" << si
-                           << ", &t" << ci << ");\n";
+            case S_NEG: os << "  const " << T << " " << t << " = -" << A() << ";\n"; break;
+            case S_ADD: os << "  const " << T << " " << t << " = " << A() << " + " << B() << ";\n"; break;
+            case S_SUB: os << "  const " << T << " " << t << " = " << A() << " - " << B() << ";\n"; break;
+            case S_MUL: os << "  const " << T << " " << t << " = " << A() << " * " << B() << ";\n"; break;
+            case S_DIV: os << "  const " << T << " " << t << " = " << A() << " / " << B() << ";\n"; break;
+            case S_POW:
+                os << "  const " << T << " " << t << " = " << (s.prec == PF ? "powf(" : "pow(") << A() << ", " << B() << ");\n";
+                break;
+            case S_CVT: os << "  const " << T << " " << t << " = (" << T << ")" << A() << ";\n"; break;
+            case S_EXPR: os << "  const float " << t << " = exa_exp_red(" << A() << ");\n"; break;
+            case S_SIN: case S_COS: case S_SINR: case S_COSR: {
+                bool red = s.op == S_SINR || s.op == S_COSR;
+                auto pr = sc[{s.a, red}];
+                int si = pr.first - 1, ci = pr.second - 1;
+                if (red || (si >= 0 && ci >= 0)) {
+                    if ((int)i == (si >= 0 && ci >= 0 ? std::min(si, ci) : (int)i)) {
+                        std::string sn = si >= 0 ? "t" + std::to_string(si) : t + "_s";
+                        std::string cn = ci >= 0 ? "t" + std::to_string(ci) : t + "_c";
+                        os << "  " << T << " " << sn << ", " << cn << ";\n";
+                        if (red) os << "  exa_sincos_red(" << A() << ", &" << sn << ", &" << cn << ");\n";
+                        else os << "  " << (s.prec == PF ? "sincosf(" : "sincos(") << A() << ", &" << sn << ", &" << cn << ");\n";
                     }
-                    name[i] = t;
                 } else {
-                    os << "  const double " << t << " = " << fname(s.op) << "(" << A() << ");\n";
+                    os << "  const " << T << " " << t << " = " << fname(s.op, s.prec) << "(" << A() << ");\n";
                 }
                 break;
             }
-            default: os << "  const double " << t << " = " << fname(s.op) << "(" << A() << ");\n"; break;
+            default: os << "  const " << T << " " << t << " = " << fname(s.op, s.prec) << "(" << A() << ");\n"; break;
             }
         }
     }
@@ -615,6 +702,8 @@ struct Emitter {
     // One device function per (pattern, mode).
     std::string function(int pid, Mode mode) {
         os.str("");
+        const bool mixed = opt.precision == EXA_MIXED_FP32;
+        const char *W = mixed ? "float" : "double";
         const bool obj = p.kind == EXA_OBJ;
         const bool all = mode == M_ALL || mode == M_FIRST;
         const bool want_val = (mode == M_OBJ && obj) || (mode == M_CON && !obj) || all;
@@ -633,12 +722,12 @@ struct Emitter {
         if (want_hess)
             for (auto &pr : p.hpair) {
                 auto it = G.hess.find({std::min(pr.first, pr.second), std::max(pr.first, pr.second)});
-                hroots.push_back(it == G.hess.end() ? (int)G.g.n.size() : it->second);
+                hroots.push_back(it == G.hess.end() ? -1 : it->second);
             }
-        for (int r : hroots) if (r < (int)G.g.n.size()) roots.push_back(r);
-        // which inputs are needed
-        std::set<int> syms, fields, params, fconsts;
-        bool need_row = (!obj) && (want_val || want_hess || want_struct);
+        for (int r : hroots) if (r >= 0) roots.push_back(r);
+        // inputs the roots need, by kind and precision
+        std::set<int> syms, fields, params, fconsts;            // FP64 copies (loaded)
+        std::set<int> fsyms, ffields, fparams, ffconsts;        // FP32 copies (converted)
         {
             std::vector<char> seen(G.g.n.size(), 0);
             std::function<void(int)> walk = [&](int i) {
@@ -646,17 +735,17 @@ struct Emitter {
                 seen[i] = 1;
                 const SN &s = G.g.n[i];
                 if (s.op == S_IN) {
-                    int id = std::stoi(s.in.substr(1));
-                    if (s.in[0] == 'X') syms.insert(id);
-                    else if (s.in[0] == 'D') fields.insert(id);
-                    else if (s.in[0] == 'P') params.insert(id);
-                    else if (s.in[0] == 'C') fconsts.insert(id);
+                    std::set<int> *d = s.ikind == 'X' ? &syms : s.ikind == 'D' ? &fields : s.ikind == 'P' ? &params : &fconsts;
+                    std::set<int> *f = s.ikind == 'X' ? &fsyms : s.ikind == 'D' ? &ffields : s.ikind == 'P' ? &fparams : &ffconsts;
+                    d->insert(s.iid);
+                    if (s.prec == PF) f->insert(s.iid);
                 }
                 if (s.a >= 0) walk(s.a);
                 if (s.b >= 0) walk(s.b);
             };
             for (int r : roots) walk(r);
         }
+        const bool need_row = (!obj) && (want_val || want_hess || want_struct);
         std::set<int> idx_syms = syms;  // symbols whose index is needed
         if (want_struct) for (int s = 0; s < p.nsym; s++) idx_syms.insert(s);
         if (want_hess)
@@ -716,12 +805,17 @@ struct Emitter {
             return os.str();
         }
         for (int s : syms) os << "  const double X" << s << " = __ldg(x + pm.xoff + i" << s << ");\n";
-        for (int s : fconsts) os << "  const double C" << s << " = pm.fc[" << s << "];\n";
         for (int pn : params) os << "  const double P" << pn << " = __ldg(th + pm.poff + q" << pn << ");\n";
+        for (int c : fconsts) os << "  const double C" << c << " = pm.fc[" << c << "];\n";
+        for (int s : fsyms) os << "  const float XF" << s << " = (float)X" << s << ";\n";
+        for (int f : ffields) os << "  const float DF" << f << " = (float)D" << f << ";\n";
+        for (int pn : fparams) os << "  const float PF" << pn << " = (float)P" << pn << ";\n";
+        for (int c : ffconsts) os << "  const float CF" << c << " = (float)C" << c << ";\n";
         std::map<int, std::string> name;
         body(roots, name);
+        auto widen = [&](int r) { return mixed ? "(double)" + name.at(r) : name.at(r); };
         if (want_val) {
-            const std::string &v = name.at(G.value);
+            const std::string v = widen(G.value);
             if (obj) os << "  objv = " << v << ";\n";
             else if (p.kind == EXA_CON) os << "  o.c[row] = " << v << ";\n";
             else os << "  o.abuf[pm.abase + kk] = " << v << ";\n";
@@ -729,25 +823,54 @@ struct Emitter {
         if (want_grad && p.nj() > 0) {
             if (obj) os << "  double* __restrict__ GO = o.gbuf + pm.gbase + kk * " << p.nj() << ";\n";
             else os << "  double* __restrict__ GO = o.jac + pm.jbase + kk * " << p.nj() << ";\n";
-            for (int j = 0; j < p.nj(); j++) os << "  GO[" << j << "] = " << name.at(G.grad[p.jsym[j]]) << ";\n";
+            for (int j = 0; j < p.nj(); j++) os << "  GO[" << j << "] = " << widen(G.grad[p.jsym[j]]) << ";\n";
         }
         if (want_hess) {
-            if (obj) os << "  const double w = sigma;\n";
-            else os << "  const double w = __ldg(y + row);\n";
-            os << "  const double w2 = w + w;\n";
+            if (obj) os << "  const " << W << " w = (" << W << ")sigma;\n";
+            else os << "  const " << W << " w = (" << W << ")__ldg(y + row);\n";
+            os << "  const " << W << " w2 = w + w;\n";
             os << "  double* __restrict__ HO = o.hess + pm.hbase + kk * " << p.nh() << ";\n";
             for (int j = 0; j < p.nh(); j++) {
                 int a = p.hpair[j].first, b = p.hpair[j].second;
                 int r = hroots[j];
-                std::string v = r < (int)G.g.n.size() ? name.at(r) : "0.0";
-                if (a == b) os << "  HO[" << j << "] = w * " << v << ";\n";
-                else os << "  HO[" << j << "] = (i" << a << " == i" << b << " ? w2 : w) * " << v << ";\n";
+                std::string v = r >= 0 ? name.at(r) : (mixed ? "0.0f" : "0.0");
+                std::string wt = a == b ? "w" : "(i" + std::to_string(a) + " == i" + std::to_string(b) + " ? w2 : w)";
+                if (mixed) os << "  HO[" << j << "] = (double)(" << wt << " * " << v << ");\n";
+                else os << "  HO[" << j << "] = " << wt << " * " << v << ";\n";
             }
         }
         os << "}\n";
         return os.str();
     }
 };
+
+// Mixed-mode helpers.  Cody-Waite reduction (Cody & Waite, 1980) in FP64 with a two-part constant:
+// the high part carries 32 significant bits, so q * HI is exact for |q| < 2^21 and r = a - q*HI - q*LO
+// is accurate to about 1e-16 |a|; the reduced argument is then rounded to FP32 and passed to the
+// single-precision functions.  Outside the exact range the FP64 function is used.
+// PIO2_HI / PIO2_LO: pi/2 rounded to 32 bits and the rounded remainder; LN2_HI / LN2_LO likewise
+// for ln 2 (computed with 300-bit arithmetic).
+static const char *kMixedHelpers = R"(
+static __device__ __forceinline__ void exa_sincos_red(const double a, float* s, float* c) {
+  if (!(fabs(a) < 1.0e6)) { double sd, cd; sincos(a, &sd, &cd); *s = (float)sd; *c = (float)cd; return; }
+  const double q = rint(a * 0x1.45f306dc9c883p-1);
+  const double r = fma(-q, 0x1.0b4611a626331p-34, fma(-q, 0x1.921fb54400000p+0, a));
+  float sr, cr;
+  sincosf((float)r, &sr, &cr);
+  switch (((int)q) & 3) {
+    case 0: *s = sr; *c = cr; break;
+    case 1: *s = cr; *c = -sr; break;
+    case 2: *s = -sr; *c = -cr; break;
+    default: *s = -cr; *c = sr; break;
+  }
+}
+static __device__ __forceinline__ float exa_exp_red(const double a) {
+  if (!(fabs(a) < 80.0)) return (float)exp(a);
+  const double k = rint(a * 0x1.71547652b82fep+0);
+  const double r = fma(-k, -0x1.718432a1b0e26p-35, fma(-k, 0x1.62e42ff000000p-1, a));
+  return ldexpf(expf((float)r), (int)k);
+}
+)";
 
 }  // namespace
 
@@ -762,12 +885,14 @@ static bool pattern_in_mode(const Pattern &p, Mode m) {
 
 std::string generate_source(const std::vector<Pattern> &pats, const CodegenOptions &opt, std::string *err) {
     std::ostringstream src;
-    src << "// generated by exa_lower.cpp\n";
+    const bool mixed = opt.precision == EXA_MIXED_FP32;
+    src << "// generated by exa_lower.cpp (" << (mixed ? "mixed FP32/FP64" : "FP64") << ")\n";
     src << kDeviceStructs << "\n";
     src << "#define EXA_BLOCK " << opt.block << "\n";
+    if (mixed) src << kMixedHelpers;
     std::vector<PatternGraph> graphs(pats.size());
     for (size_t i = 0; i < pats.size(); i++) {
-        build_graph(pats[i], graphs[i]);
+        build_graph(pats[i], graphs[i], mixed);
         if (!graphs[i].err.empty()) {
             *err = graphs[i].err;
             return "";
