@@ -313,6 +313,20 @@ def run_exa(args):
         extras["sequential_per_instance_nnz_per_s"] = nnz_rank / (seq_ms * 1e-3)
         for s_ in singles:
             s_.destroy()
+        # the same batch in the other precision mode, timed the same way
+        other = B.EXA_FP64 if prec == B.EXA_MIXED_FP32 else B.EXA_MIXED_FP32
+        m2 = B.exa_create_batch(flats, precision=other, device=local)
+        step2 = lambda: m2.exa_eval_all(xt, yt, sigma, f=f, g=g, c=c, jac=jac, hess=hess, jac_csc=jcsc, hess_csc=hcsc)
+        step2()
+        ms2 = timed(step2, max(5, min(args.steps, 200)))
+        k2 = timed(lambda: m2.exa_eval_all(xt, yt, sigma, jac=jac, hess=hess), max(5, min(args.steps, 200)))
+        tag = "mixed" if other == B.EXA_MIXED_FP32 else "fp64"
+        extras[f"{tag}_step_ms"] = ms2
+        extras[f"{tag}_nnz_per_s"] = nnz_rank / (ms2 * 1e-3)
+        extras[f"{tag}_kernel_ms"] = k2
+        extras[f"{tag}_kernel_hbm_frac"] = nbytes / (k2 * 1e-3) / 1e9 / peak
+        extras[f"{tag}_eval_regs"] = m2.stat("eval_regs")
+        m2.destroy()
 
     # end to end through the public API: pinned host x, y in; f, g, c back to pinned host
     xh = torch.as_tensor(x).pin_memory()
