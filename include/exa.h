@@ -175,6 +175,19 @@ exa_status exa_set_stream(exa_model *m, void *stream);
  * (per-CTA partial sums, then one ordered sum), Sec. 7.2.3. */
 exa_status exa_obj(exa_model *m, const double *x, double *f);
 
+/* f[0] = f(x), like exa_obj, but without the scratch buffer that exa_create allocates: the
+ * per-CTA partial sums go to a fixed static device array of 65536 doubles (512 KiB) that every GPU
+ * which loads the library holds until the process exits.  For callers that cannot allocate device
+ * memory (their memory belongs to another allocator, or they run where cudaMalloc is not allowed);
+ * this call allocates nothing.  The paper has no counterpart; it is an addition of this library.
+ *   - Limit: at most 65536 objective tiles (EXA_E_UNSUPPORTED beyond, with the count in the
+ *     message), i.e. 8,388,608 objective instances at 128 threads per tile.
+ *   - The first call on a device looks up the array's device address on that device (a CUDA
+ *     runtime query, no allocation); make that first call before any stream capture.
+ *   - Every call shares the one array: calls that overlap on the same GPU race.  Nothing needs
+ *     clearing between calls; each call overwrites the partials it reads. */
+exa_status exa_obj_noalloc(exa_model *m, const double *x, double *f);
+
 /* g[nvar] = grad f(x): each objective instance writes its own gradient slots, then a gather
  * segmented sum per variable produces g (Sec. 7.2.3, no atomics). */
 exa_status exa_grad(exa_model *m, const double *x, double *g);

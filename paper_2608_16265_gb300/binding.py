@@ -29,7 +29,7 @@ STATUS_NAMES = ["EXA_OK", "EXA_E_INVALID", "EXA_E_OOM", "EXA_E_NVRTC", "EXA_E_CU
 
 # Every function include/exa.h declares.
 EXPORTS = ["exa_create", "exa_create_batch", "exa_destroy", "exa_last_error", "exa_create_error",
-           "exa_dims", "exa_batch_offsets", "exa_set_stream", "exa_obj", "exa_grad", "exa_cons",
+           "exa_dims", "exa_batch_offsets", "exa_set_stream", "exa_obj", "exa_obj_noalloc", "exa_grad", "exa_cons",
            "exa_jac_structure", "exa_jac_coord", "exa_hess_structure", "exa_hess_coord",
            "exa_jac_csc_structure", "exa_hess_csc_structure", "exa_jac_csc", "exa_hess_csc",
            "exa_eval_all", "exa_jprod", "exa_jtprod", "exa_hprod", "exa_check_status",
@@ -92,6 +92,7 @@ def load():
             "exa_batch_offsets": [vp, C.POINTER(C.c_int32), i64p, i64p, i64p, i64p],
             "exa_set_stream": [vp, vp],
             "exa_obj": [vp, dp, dp],
+            "exa_obj_noalloc": [vp, dp, dp],
             "exa_grad": [vp, dp, dp],
             "exa_cons": [vp, dp, dp],
             "exa_jac_structure": [vp, i32p, i32p],
@@ -242,6 +243,7 @@ class Model:
 
     # ---- raw calls (outputs preallocated by the caller)
     def exa_obj(self, x, f): self._call("exa_obj", _ptr(x), _ptr(f))
+    def exa_obj_noalloc(self, x, f): self._call("exa_obj_noalloc", _ptr(x), _ptr(f))
     def exa_grad(self, x, g): self._call("exa_grad", _ptr(x), _ptr(g))
     def exa_cons(self, x, c): self._call("exa_cons", _ptr(x), _ptr(c))
     def exa_jac_structure(self, r, c): self._call("exa_jac_structure", _ptr(r), _ptr(c))

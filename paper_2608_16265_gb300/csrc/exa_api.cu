@@ -831,6 +831,59 @@ exa_status exa_obj(exa_model *m, const double *x, double *f) {
     return EXA_OK;
 }
 
+// ---- objective without a scratch allocation -------------------------------------------------
+// Callers that cannot allocate device memory themselves (their memory is owned by another
+// allocator, or they run where cudaMalloc is not allowed) still need somewhere to put the
+// per-CTA partial sums of the two-stage objective reduction.  exa_obj_noalloc uses this fixed
+// array, which every GPU that loads the library holds until the process exits, instead of any
+// allocated buffer.  Each launch overwrites the partials it reads, so nothing has to start at
+// zero; calls that overlap on one GPU (any model, any stream) share the array and race.
+#define EXA_NOALLOC_MAX_PARTIALS 65536
+static __device__ __align__(256) double g_noalloc_partials[EXA_NOALLOC_MAX_PARTIALS];
+
+namespace {
+std::mutex g_noalloc_mu;
+std::map<int, double *> g_noalloc_addr;  // device ordinal -> device address of the array
+
+// The array's name is a host-side stand-in in host code; its device address must be asked for
+// once per device, with that device current.
+exa_status noalloc_partials(exa_model *m, double **out) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    auto it = g_noalloc_addr.find(m->device);
+    if (it != g_noalloc_addr.end()) {
+        *out = it->second;
+        return EXA_OK;
+    }
+    double *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_partials);
+    if (e != cudaSuccess || !p)
+        return fail(m, EXA_E_CUDA, std::string("cudaGetSymbolAddress of the static objective scratch: ") +
+                                       cudaGetErrorString(e));
+    g_noalloc_addr[m->device] = p;
+    *out = p;
+    return EXA_OK;
+}
+}  // namespace
+
+exa_status exa_obj_noalloc(exa_model *m, const double *x, double *f) {
+    if (exa_status e = check_model(m)) return e;
+    CHECK_PTRS(x, f);
+    if (m->ntiles[exa::M_OBJ] > EXA_NOALLOC_MAX_PARTIALS)
+        return fail(m, EXA_E_UNSUPPORTED,
+                    "exa_obj_noalloc: the objective needs " + std::to_string(m->ntiles[exa::M_OBJ]) +
+                        " partial sums (one per tile of " + std::to_string(m->block) +
+                        " objective instances); the static scratch holds at most " +
+                        std::to_string(EXA_NOALLOC_MAX_PARTIALS));
+    double *part = nullptr;
+    if (exa_status e = noalloc_partials(m, &part)) return e;
+    ExaOut o{};
+    o.obj_part = part;
+    if (exa_status e = launch_eval(m, exa::M_OBJ, x, nullptr, 0.0, o)) return e;
+    k_obj_final<<<1, 256, 0, m->stream>>>(part, m->ntiles[exa::M_OBJ], f);
+    CR(cudaGetLastError());
+    return EXA_OK;
+}
+
 exa_status exa_grad(exa_model *m, const double *x, double *g) {
     if (exa_status e = check_model(m)) return e;
     CHECK_PTRS(x, g);
