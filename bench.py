@@ -74,6 +74,21 @@ def algorithmic_bytes(flats, nnzj, nnzh, nvar, ncon, naug, nnzg):
     return 8 * nvar + 8 * ncon + data + 8 * (nnzj + nnzh) + 8 * ncon + 8 * naug + 8 * nnzg
 
 
+def reduce_max(v: float, pg, device) -> float:
+    """Max over ranks (the only collective of a multi-rank run: timing, not data)."""
+    if pg is None:
+        return v
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(nnz_per_rank: int, world_size: int, ms_max: float) -> float:
+    """Weak scaling: every rank evaluates its own batch; all ranks' nonzeros over the slowest rank."""
+    return world_size * nnz_per_rank / (ms_max * 1e-3)
+
+
 def read_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -255,22 +270,16 @@ def run_exa(args):
     if args.steps <= 0:  # auto: about two seconds of timed work
         probe = timed(step, 3)
         args.steps = int(min(5000, max(20, 2000.0 / max(probe, 1e-3))))
-        if pg is not None:
-            t = torch.tensor([args.steps], device=dev)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            args.steps = int(t.item())
+        args.steps = int(reduce_max(args.steps, pg, dev))
     barrier()
     clk = ClockSampler(local)
     clk.start()
     ms = timed(step, args.steps)
     clocks = clk.stop()
     barrier()
-    if pg is not None:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ms, pg, dev)
     nnz_rank = m.nnzj + m.nnzh
-    value = ws * nnz_rank / (ms * 1e-3)
+    value = whole_job_rate(nnz_rank, ws, ms)
 
     # dominant kernel alone: the generated evaluation kernel writing J and H (no reductions)
     kern_ms = timed(lambda: m.exa_eval_all(xt, yt, sigma, jac=jac, hess=hess), max(5, min(args.steps, 200)))
@@ -344,10 +353,7 @@ def run_exa(args):
     for _ in range(2):
         e2e_step()
     e2e_ms = timed(e2e_step, max(3, min(args.steps // 2, 200)))
-    if pg is not None:
-        t = torch.tensor([e2e_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = reduce_max(e2e_ms, pg, dev)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -366,7 +372,7 @@ def run_exa(args):
         "config": {"workload": WORKLOAD if args.members == 256 else f"acopf_batch_{args.members}", "members": args.members, "buses": "log-uniform 200-20000",
                    "nnz_per_rank": nnz_rank, "precision": args.precision, "parallelism": f"replicas{ws}",
                    "l2": "inputs+outputs ~2 GB per step > 129 MB L2 (no flush needed)"},
-        "e2e": {"value": ws * nnz_rank / (e2e_ms * 1e-3), "unit": UNIT,
+        "e2e": {"value": whole_job_rate(nnz_rank, ws, e2e_ms), "unit": UNIT,
                 "h2d_bytes_per_step": int(xh.numel() * 8 + yh.numel() * 8),
                 "d2h_bytes_per_step": int((1 + m.nvar + m.ncon) * 8), "ms_per_step": e2e_ms},
         "gpu_launches": launches_per_step * args.steps,

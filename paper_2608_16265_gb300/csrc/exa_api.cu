@@ -57,6 +57,13 @@ __global__ void k_seg_sum(const int *__restrict__ ptr, const int *__restrict__ p
     dst[i] = s;
 }
 
+// dst[i] = src[perm[i]]  (CSC of a COO pattern without duplicate entries: a pure permutation)
+__global__ void k_permute(const int *__restrict__ perm, const double *__restrict__ src,
+                          double *__restrict__ dst, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[perm[i]];
+}
+
 // c[rows[i]] += sum of the augmentation terms of that row (rows listed once each)
 __global__ void k_seg_add_rows(const int *__restrict__ rows, const int *__restrict__ ptr,
                                const int *__restrict__ perm, const double *__restrict__ src,
@@ -173,6 +180,7 @@ struct exa_model {
     ExaPM *d_pm = nullptr;
     ExaTile *d_tiles[exa::M_COUNT] = {};
     int ntiles[exa::M_COUNT] = {};
+    int nobj[exa::M_COUNT] = {};  // objective partial sums written by each kernel kind
     double *d_theta = nullptr;
     int *d_status = nullptr;
     int *d_jrow = nullptr, *d_jcol = nullptr, *d_hrow = nullptr, *d_hcol = nullptr, *d_gvar = nullptr, *d_arow = nullptr;
@@ -686,7 +694,9 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
                 }
                 if (!in) continue;
                 const ExaPM &pm = pms[(size_t)b * np + p];
-                for (i64 s = 0; s < pm.n_inst; s += m->block) tiles.push_back({b * np + p, (int)s});
+                const bool part = P.kind == EXA_OBJ && (k == exa::M_OBJ || k == exa::M_ALL || k == exa::M_FIRST);
+                for (i64 s = 0; s < pm.n_inst; s += m->block)
+                    tiles.push_back({b * np + p, (int)s, part ? m->nobj[k]++ : -1});
             }
         m->ntiles[k] = (int)tiles.size();
         CR(dalloc(m, &m->d_tiles[k], (i64)tiles.size()));
@@ -724,7 +734,7 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     CR(dalloc(m, &m->d_abuf, m->naug));
     CR(dalloc(m, &m->d_cbuf, m->ncon));
     int maxt = 1;
-    for (int k = 0; k < exa::M_COUNT; k++) maxt = std::max(maxt, m->ntiles[k]);
+    for (int k = 0; k < exa::M_COUNT; k++) maxt = std::max(maxt, m->nobj[k]);
     CR(dalloc(m, &m->d_objpart, maxt));
     CR(cudaDeviceSynchronize());
     m->create_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -826,7 +836,7 @@ exa_status exa_obj(exa_model *m, const double *x, double *f) {
     ExaOut o{};
     o.obj_part = m->d_objpart;
     if (exa_status e = launch_eval(m, exa::M_OBJ, x, nullptr, 0.0, o)) return e;
-    k_obj_final<<<1, 256, 0, m->stream>>>(m->d_objpart, m->ntiles[exa::M_OBJ], f);
+    k_obj_final<<<1, 256, 0, m->stream>>>(m->d_objpart, m->nobj[exa::M_OBJ], f);
     CR(cudaGetLastError());
     return EXA_OK;
 }
@@ -981,9 +991,10 @@ exa_status exa_hess_csc_structure(const exa_model *mc, int32_t *colptr, int32_t 
 }
 
 static exa_status scatter_csc(exa_model *m, const int *segptr, const int *perm, const double *coo, double *csc,
-                              i64 n) {
+                              i64 n, i64 nnz) {
     if (!n) return EXA_OK;
-    k_seg_sum<<<grid_of(n, 256), 256, 0, m->stream>>>(segptr, perm, coo, csc, (int)n);
+    if (n == nnz) k_permute<<<grid_of(n, 256), 256, 0, m->stream>>>(perm, coo, csc, (int)n);
+    else k_seg_sum<<<grid_of(n, 256), 256, 0, m->stream>>>(segptr, perm, coo, csc, (int)n);
     CR(cudaGetLastError());
     return EXA_OK;
 }
@@ -995,7 +1006,7 @@ exa_status exa_jac_csc(exa_model *m, const double *x, double *vals_csc) {
     ExaOut o{};
     o.jac = m->d_jbuf;
     if (exa_status e = launch_eval(m, exa::M_JAC, x, nullptr, 0.0, o)) return e;
-    return scatter_csc(m, m->d_jsegptr, m->d_jperm, m->d_jbuf, vals_csc, m->nnzj_csc);
+    return scatter_csc(m, m->d_jsegptr, m->d_jperm, m->d_jbuf, vals_csc, m->nnzj_csc, m->nnzj);
 }
 
 exa_status exa_hess_csc(exa_model *m, const double *x, const double *y, double sigma, double *vals_csc) {
@@ -1006,7 +1017,7 @@ exa_status exa_hess_csc(exa_model *m, const double *x, const double *y, double s
     ExaOut o{};
     o.hess = m->d_hbuf;
     if (exa_status e = launch_eval(m, exa::M_HESS, x, y, sigma, o)) return e;
-    return scatter_csc(m, m->d_hsegptr, m->d_hperm, m->d_hbuf, vals_csc, m->nnzh_csc);
+    return scatter_csc(m, m->d_hsegptr, m->d_hperm, m->d_hbuf, vals_csc, m->nnzh_csc, m->nnzh);
 }
 
 exa_status exa_eval_all(exa_model *m, const double *x, const double *y, double sigma, double *f, double *g,
@@ -1025,7 +1036,7 @@ exa_status exa_eval_all(exa_model *m, const double *x, const double *y, double s
     Mode mode = want_h ? exa::M_ALL : exa::M_FIRST;
     if (exa_status e = launch_eval(m, mode, x, y, sigma, o)) return e;
     if (f) {
-        k_obj_final<<<1, 256, 0, m->stream>>>(m->d_objpart, m->ntiles[mode], f);
+        k_obj_final<<<1, 256, 0, m->stream>>>(m->d_objpart, m->nobj[mode], f);
         CR(cudaGetLastError());
     }
     if (g && m->nvar) {
@@ -1035,9 +1046,9 @@ exa_status exa_eval_all(exa_model *m, const double *x, const double *y, double s
     if (c)
         if (exa_status e = aug_rows(m, c)) return e;
     if (jac_csc)
-        if (exa_status e = scatter_csc(m, m->d_jsegptr, m->d_jperm, o.jac, jac_csc, m->nnzj_csc)) return e;
+        if (exa_status e = scatter_csc(m, m->d_jsegptr, m->d_jperm, o.jac, jac_csc, m->nnzj_csc, m->nnzj)) return e;
     if (hess_csc)
-        if (exa_status e = scatter_csc(m, m->d_hsegptr, m->d_hperm, o.hess, hess_csc, m->nnzh_csc)) return e;
+        if (exa_status e = scatter_csc(m, m->d_hsegptr, m->d_hperm, o.hess, hess_csc, m->nnzh_csc, m->nnzh)) return e;
     return EXA_OK;
 }
 

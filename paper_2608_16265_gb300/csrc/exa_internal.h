@@ -35,6 +35,7 @@
     struct ExaTile {              /* BLOCK consecutive instances of one (member, pattern) */        \
         int pm;                                                                                     \
         int begin;                                                                                  \
+        int oslot;                /* objective tiles: index of this tile's partial sum; else -1 */  \
     };                                                                                              \
     struct ExaOut {                                                                                 \
         double *obj_part;         /* one objective partial sum per tile */                          \

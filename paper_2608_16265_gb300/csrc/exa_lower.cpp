@@ -920,15 +920,17 @@ std::string generate_source(const std::vector<Pattern> &pats, const CodegenOptio
             src << "      case " << i << ": pat" << i << "_" << kModeName[m] << "(pm, k, x, y, th, sigma, o, so, objv); break;\n";
         }
         src << "      default: break;\n    }\n  }\n";
-        if (objred) {
-            src << "  for (int off = 16; off > 0; off >>= 1) objv += __shfl_xor_sync(0xffffffffu, objv, off);\n"
-                   "  __shared__ double red[EXA_BLOCK / 32];\n"
-                   "  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = objv;\n"
-                   "  __syncthreads();\n"
-                   "  if (threadIdx.x == 0) {\n"
-                   "    double s = 0.0;\n"
-                   "    for (int i = 0; i < EXA_BLOCK / 32; i++) s += red[i];\n"
-                   "    o.obj_part[blockIdx.x] = s;\n"
+        if (objred) {  // only objective tiles reduce (tl.oslot is uniform over the CTA)
+            src << "  if (tl.oslot >= 0) {\n"
+                   "    for (int off = 16; off > 0; off >>= 1) objv += __shfl_xor_sync(0xffffffffu, objv, off);\n"
+                   "    __shared__ double red[EXA_BLOCK / 32];\n"
+                   "    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = objv;\n"
+                   "    __syncthreads();\n"
+                   "    if (threadIdx.x == 0) {\n"
+                   "      double s = 0.0;\n"
+                   "      for (int i = 0; i < EXA_BLOCK / 32; i++) s += red[i];\n"
+                   "      o.obj_part[tl.oslot] = s;\n"
+                   "    }\n"
                    "  }\n";
         }
         src << "}\n";
