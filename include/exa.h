@@ -128,14 +128,20 @@ typedef struct {
 typedef struct {
     int32_t precision;     /* exa_precision */
     int32_t device;        /* CUDA device ordinal */
-    int32_t block_threads; /* threads per CTA of the evaluation kernel; 0 = automatic */
+    int32_t block_threads; /* threads per CTA of the evaluation kernels (multiple of 32, <= 1024);
+                              0 = chosen by the autotuner among 64 / 128 / 256 */
     int32_t flags;         /* EXA_FLAG_* */
+    int32_t grid_factor;   /* evaluation grid: 0 = chosen by the autotuner (one CTA per tile when
+                              tuning is off), -1 = one CTA per tile, n > 0 = persistent grid of n
+                              waves of resident CTAs looping over the tiles */
+    int32_t pad;
 } exa_options;
 
 enum {
     EXA_FLAG_BOUNDS_CHECK = 1, /* every gather index is checked on the device; a violation makes
                                   the next exa_check_status return EXA_E_BOUNDS */
-    EXA_FLAG_NO_TUNE = 2       /* skip the launch-shape autotuner at creation */
+    EXA_FLAG_NO_TUNE = 2,      /* skip the launch-shape autotuner at creation */
+    EXA_FLAG_NO_FUSE = 4       /* evaluate every pattern in its own thread (no fused groups) */
 };
 
 /* Validate the descriptor (Sec. 3.4 SIMDFunction), lower every pattern to generated device

@@ -23,7 +23,7 @@ from . import ir
 EXA_OK, EXA_E_INVALID, EXA_E_OOM, EXA_E_NVRTC, EXA_E_CUDA, EXA_E_BOUNDS, EXA_E_TIMEOUT, \
     EXA_E_UNSUPPORTED, EXA_E_INTERNAL = range(9)
 EXA_FP64, EXA_MIXED_FP32 = 0, 1
-EXA_FLAG_BOUNDS_CHECK, EXA_FLAG_NO_TUNE = 1, 2
+EXA_FLAG_BOUNDS_CHECK, EXA_FLAG_NO_TUNE, EXA_FLAG_NO_FUSE = 1, 2, 4
 STATUS_NAMES = ["EXA_OK", "EXA_E_INVALID", "EXA_E_OOM", "EXA_E_NVRTC", "EXA_E_CUDA", "EXA_E_BOUNDS",
                 "EXA_E_TIMEOUT", "EXA_E_UNSUPPORTED", "EXA_E_INTERNAL"]
 
@@ -66,7 +66,7 @@ class exa_model_desc(C.Structure):
 
 class exa_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("device", C.c_int32), ("block_threads", C.c_int32),
-                ("flags", C.c_int32)]
+                ("flags", C.c_int32), ("grid_factor", C.c_int32), ("pad", C.c_int32)]
 
 
 _lib = None
@@ -157,8 +157,8 @@ class _Desc:
                                    theta.ctypes.data_as(C.POINTER(C.c_double)), len(flat.patterns), 0, pats)
 
 
-def _opts(precision, block, flags, device):
-    return exa_options(precision, device, block, flags)
+def _opts(precision, block, flags, device, grid_factor=0):
+    return exa_options(precision, device, block, flags, grid_factor, 0)
 
 
 def _ptr(t) -> Optional[int]:
@@ -174,17 +174,17 @@ def _stream():
 
 # ------------------------------------------------------------------ ABI-named functions
 def exa_create(flat: ir.FlatModel, precision: int = EXA_FP64, block: int = 0, flags: int = 0,
-               device: int = 0) -> "Model":
-    return exa_create_batch([flat], precision, block, flags, device)
+               device: int = 0, grid_factor: int = 0) -> "Model":
+    return exa_create_batch([flat], precision, block, flags, device, grid_factor)
 
 
 def exa_create_batch(flats: Sequence[ir.FlatModel], precision: int = EXA_FP64, block: int = 0,
-                     flags: int = 0, device: int = 0) -> "Model":
+                     flags: int = 0, device: int = 0, grid_factor: int = 0) -> "Model":
     lib = load()
     descs = [_Desc(f) for f in flats]
     arr = (C.POINTER(exa_model_desc) * len(descs))(*[C.pointer(d.desc) for d in descs])
     h = C.c_void_p()
-    opt = _opts(precision, block, flags, device)
+    opt = _opts(precision, block, flags, device, grid_factor)
     rc = lib.exa_create_batch(arr, len(descs), C.byref(opt), C.byref(h))
     if rc != EXA_OK:
         raise ExaError(rc, lib.exa_create_error().decode())

@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <set>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -173,6 +174,7 @@ struct exa_model {
     int nb = 1;
     std::vector<i64> xoff, coff, joff, hoff;
     std::vector<exa::Pattern> pats;
+    std::vector<exa::Group> groups;
 
     cudaLibrary_t lib = nullptr;
     cudaKernel_t fn[exa::M_COUNT] = {};
@@ -181,6 +183,9 @@ struct exa_model {
     ExaTile *d_tiles[exa::M_COUNT] = {};
     int ntiles[exa::M_COUNT] = {};
     int nobj[exa::M_COUNT] = {};  // objective partial sums written by each kernel kind
+    int grid[exa::M_COUNT] = {};  // CTAs launched per kernel kind (<= ntiles: persistent tile loop)
+    int persist = 0;              // persistent grid factor chosen by the tuner (0: one CTA per tile)
+    std::vector<ExaPM> h_pms;     // host copy of the group descriptors
     double *d_theta = nullptr;
     int *d_status = nullptr;
     int *d_jrow = nullptr, *d_jcol = nullptr, *d_hrow = nullptr, *d_hcol = nullptr, *d_gvar = nullptr, *d_arow = nullptr;
@@ -198,7 +203,7 @@ struct exa_model {
            *d_cbuf = nullptr;
     std::vector<void *> allocs;
     size_t device_bytes = 0;
-    double nvrtc_ms = 0, create_ms = 0;
+    double nvrtc_ms = 0, create_ms = 0, tune_ms = 0;
     std::string err;
 };
 
@@ -230,6 +235,10 @@ cudaError_t dalloc(exa_model *m, T **p, i64 count) {
     } while (0)
 
 void free_all(exa_model *m) {
+    for (int k = 0; k < exa::M_COUNT; k++) {
+        if (m->d_tiles[k]) cudaFree(m->d_tiles[k]);
+        m->d_tiles[k] = nullptr;
+    }
     for (void *p : m->allocs) cudaFree(p);
     m->allocs.clear();
     if (m->lib) cudaLibraryUnload(m->lib);
@@ -297,8 +306,10 @@ exa_status launch_eval(exa_model *m, Mode mode, const double *x, const double *y
     ExaStructOut so{};
     so.status = m->d_status;
     const double *th = m->d_theta;
-    void *args[] = {&m->d_tiles[mode], &m->d_pm, &x, &y, &th, &sigma, &out, &so};
-    CR(cudaLaunchKernel((const void *)m->fn[mode], dim3(m->ntiles[mode]), dim3(m->block), args, 0, m->stream));
+    int nt = m->ntiles[mode];
+    void *args[] = {&m->d_tiles[mode], &nt, &m->d_pm, &x, &y, &th, &sigma, &out, &so};
+    const int grid = m->grid[mode] > 0 ? m->grid[mode] : nt;
+    CR(cudaLaunchKernel((const void *)m->fn[mode], dim3(grid), dim3(m->block), args, 0, m->stream));
     return EXA_OK;
 }
 
@@ -501,6 +512,224 @@ exa_status load_patterns(const exa_model_desc &d0, exa_model *m) {
     return EXA_OK;
 }
 
+// Generates, compiles and loads the kernels for `block` threads per CTA and rebuilds the tile lists
+// (member-major, then groups in declaration order; BLOCK instances per tile).
+exa_status setup_kernels(exa_model *m, int block) {
+    m->block = block;
+    exa::CodegenOptions cg;
+    cg.precision = m->precision;
+    cg.block = block;
+    cg.bounds_check = m->bounds_check;
+    std::string gerr;
+    std::string src = exa::generate_source(m->pats, m->groups, cg, &gerr);
+    if (!gerr.empty()) return fail(m, EXA_E_INTERNAL, gerr);
+    if (getenv("EXA_DUMP_SOURCE")) {
+        FILE *fp = fopen(getenv("EXA_DUMP_SOURCE"), "w");
+        if (fp) { fputs(src.c_str(), fp); fclose(fp); }
+    }
+    if (m->lib) {
+        cudaLibraryUnload(m->lib);
+        m->lib = nullptr;
+    }
+    if (exa_status e = compile(m, src)) return e;
+    const int ng = (int)m->groups.size(), nb = m->nb;
+    for (int k = 0; k < exa::M_COUNT; k++) {
+        std::vector<ExaTile> tiles;
+        m->nobj[k] = 0;
+        for (int b = 0; b < nb; b++)
+            for (int gi = 0; gi < ng; gi++) {
+                bool in = false, part = false;
+                for (int p : m->groups[gi].pats) {
+                    const bool act = exa::pattern_in_mode(m->pats[p], (exa::Mode)k);
+                    in = in || act;
+                    part = part || (act && m->pats[p].kind == EXA_OBJ &&
+                                    (k == exa::M_OBJ || k == exa::M_ALL || k == exa::M_FIRST));
+                }
+                if (!in) continue;
+                const ExaPM &pm = m->h_pms[(size_t)b * ng + gi];
+                for (i64 s = 0; s < pm.n_inst; s += block)
+                    tiles.push_back({b * ng + gi, (int)s, part ? m->nobj[k]++ : -1});
+            }
+        m->ntiles[k] = (int)tiles.size();
+        m->grid[k] = m->ntiles[k];
+        if (m->d_tiles[k]) cudaFree(m->d_tiles[k]);
+        m->d_tiles[k] = nullptr;
+        CR(cudaMalloc((void **)&m->d_tiles[k], sizeof(ExaTile) * std::max<size_t>(tiles.size(), 1)));
+        if (!tiles.empty())
+            CR(cudaMemcpy(m->d_tiles[k], tiles.data(), sizeof(ExaTile) * tiles.size(), cudaMemcpyHostToDevice));
+    }
+    return EXA_OK;
+}
+
+// Persistent grid for every kernel kind: factor x resident CTAs per SM x SMs (0: one CTA per tile).
+exa_status apply_grid(exa_model *m, int factor) {
+    m->persist = factor;
+    int sms = 0;
+    CR(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
+    for (int k = 0; k < exa::M_COUNT; k++) {
+        m->grid[k] = m->ntiles[k];
+        if (factor <= 0 || k == exa::M_STRUCT) continue;
+        int occ = 0;
+        CR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)m->fn[k], m->block, 0));
+        const long long g = (long long)factor * std::max(occ, 1) * sms;
+        if (g < m->ntiles[k]) m->grid[k] = (int)g;
+    }
+    return EXA_OK;
+}
+
+// Launch-shape autotuner: times the fused evaluation kernel (everything, at x = 1, y = 1) for
+// 64 / 128 / 256 threads per CTA and for one CTA per tile versus persistent grids of 1, 2 and 4
+// waves of resident CTAs; keeps the fastest.  Models too small to fill the GPU are not tuned.
+exa_status autotune(exa_model *m) {
+    int sms = 0;
+    CR(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
+    if (m->ntiles[exa::M_ALL] < 4 * sms) return EXA_OK;
+    Scratch S{m};
+    double *x = nullptr, *y = nullptr, *part = nullptr;
+    CR(S.get(&x, m->nvar));
+    CR(S.get(&y, m->ncon));
+    std::vector<double> ones((size_t)std::max(m->nvar, m->ncon), 1.0);
+    CR(cudaMemcpy(x, ones.data(), sizeof(double) * m->nvar, cudaMemcpyHostToDevice));
+    if (m->ncon) CR(cudaMemcpy(y, ones.data(), sizeof(double) * m->ncon, cudaMemcpyHostToDevice));
+    cudaEvent_t e0, e1;
+    CR(cudaEventCreate(&e0));
+    CR(cudaEventCreate(&e1));
+    double best = 1e30;
+    int best_block = m->block, best_factor = 0;
+    const int blocks[] = {64, 128, 256};
+    for (int B : blocks) {
+        if (exa_status e = setup_kernels(m, B)) return e;
+        CR(S.get(&part, std::max(m->nobj[exa::M_ALL], 1)));
+        ExaOut o{};
+        o.obj_part = part;
+        o.c = m->d_cbuf;
+        o.abuf = m->d_abuf;
+        o.gbuf = m->d_gbuf;
+        o.jac = m->d_jbuf;
+        o.hess = m->d_hbuf;
+        for (int factor : {0, 1, 2, 4}) {
+            if (exa_status e = apply_grid(m, factor)) return e;
+            if (factor > 0 && m->grid[exa::M_ALL] == m->ntiles[exa::M_ALL]) continue;
+            if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
+            CR(cudaEventRecord(e0, m->stream));
+            for (int r = 0; r < 5; r++)
+                if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
+            CR(cudaEventRecord(e1, m->stream));
+            CR(cudaEventSynchronize(e1));
+            float ms = 0;
+            CR(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                best_block = B;
+                best_factor = factor;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (m->block != best_block)
+        if (exa_status e = setup_kernels(m, best_block)) return e;
+    if (exa_status e = apply_grid(m, best_factor)) return e;
+    m->tune_ms = best / 5.0;
+    return EXA_OK;
+}
+
+// Fused groups: patterns whose instance counts are equal in every member are evaluated by one
+// thread per instance (declaration order), so loads and subexpressions they share are computed
+// once.  Data columns that are the same host array in every member become one group column;
+// constants that differ between members get one descriptor slot per distinct value vector.  A
+// group is closed when it would exceed 16 patterns, columns or constant slots.
+exa_status build_groups(exa_model *m, const exa_model_desc *const *descs, int nb, bool fuse) {
+    const int np = (int)m->pats.size();
+    struct Acc {
+        std::vector<long long> ninst;
+        std::map<std::pair<int, std::vector<const void *>>, int> cols;
+        std::map<std::vector<long long>, int> ics;
+        std::map<std::vector<uint64_t>, int> fcs;
+    };
+    std::vector<Acc> acc;
+    m->groups.clear();
+    for (int p = 0; p < np; p++) {
+        exa::Pattern &P = m->pats[p];
+        std::vector<long long> ninst;
+        for (int b = 0; b < nb; b++) ninst.push_back(descs[b]->patterns[p].n_inst);
+        // keys of this pattern's columns and member-varying constants
+        std::vector<std::pair<int, std::vector<const void *>>> colkeys;
+        for (int f = 0; f < (int)P.ftype.size(); f++) {
+            std::vector<const void *> ptrs;
+            for (int b = 0; b < nb; b++) ptrs.push_back(descs[b]->patterns[p].fields[f].data);
+            colkeys.push_back({P.ftype[f], ptrs});
+        }
+        std::vector<std::pair<int, std::vector<long long>>> ikeys;
+        for (int i = 0; i < (int)P.ix.size(); i++) {
+            if (P.ix[i].op != EXA_I_CONST) continue;
+            std::vector<long long> vals;
+            bool differ = false;
+            for (int b = 0; b < nb; b++) {
+                vals.push_back(descs[b]->patterns[p].inodes[i].ival);
+                differ = differ || vals.back() != vals[0];
+            }
+            if (differ) ikeys.push_back({i, vals});
+        }
+        std::vector<std::pair<int, std::vector<uint64_t>>> fkeys;
+        for (int i = 0; i < (int)P.v.size(); i++) {
+            if (P.v[i].op != EXA_V_CONST) continue;
+            std::vector<uint64_t> vals;
+            bool differ = false;
+            for (int b = 0; b < nb; b++) {
+                uint64_t u;
+                std::memcpy(&u, &descs[b]->patterns[p].vnodes[i].fval, 8);
+                vals.push_back(u);
+                differ = differ || vals.back() != vals[0];
+            }
+            if (differ) fkeys.push_back({i, vals});
+        }
+        if (colkeys.size() > EXA_MAXF || ikeys.size() > 16 || fkeys.size() > 16)
+            return fail(m, EXA_E_UNSUPPORTED, "pattern " + std::to_string(p) +
+                                                  ": more than 16 data columns or member-varying constants");
+        int gi = -1;
+        if (fuse) {
+            for (int g = (int)acc.size() - 1; g >= 0 && gi < 0; g--) {
+                if (acc[g].ninst != ninst || m->groups[g].pats.size() >= EXA_MAXG) continue;
+                std::set<std::pair<int, std::vector<const void *>>> c;
+                for (auto &kv : acc[g].cols) c.insert(kv.first);
+                for (auto &k : colkeys) c.insert(k);
+                std::set<std::vector<long long>> ic;
+                for (auto &kv : acc[g].ics) ic.insert(kv.first);
+                for (auto &k : ikeys) ic.insert(k.second);
+                std::set<std::vector<uint64_t>> fc;
+                for (auto &kv : acc[g].fcs) fc.insert(kv.first);
+                for (auto &k : fkeys) fc.insert(k.second);
+                if (c.size() <= EXA_MAXF && ic.size() <= 16 && fc.size() <= 16) gi = g;
+                break;  // only the most recent group with these instance counts is extended
+            }
+        }
+        if (gi < 0) {
+            gi = (int)acc.size();
+            acc.push_back(Acc{ninst, {}, {}, {}});
+            m->groups.emplace_back();
+        }
+        exa::Group &G = m->groups[gi];
+        Acc &A = acc[gi];
+        G.pats.push_back(p);
+        std::vector<int> fmap;
+        for (auto &k : colkeys) {
+            auto r = A.cols.emplace(k, (int)A.cols.size());
+            if (r.second) G.ftype.push_back(k.first);
+            fmap.push_back(r.first->second);
+        }
+        G.field.push_back(fmap);
+        P.ivary.clear();
+        P.fvary.clear();
+        for (auto &k : ikeys) P.ivary[k.first] = A.ics.emplace(k.second, (int)A.ics.size()).first->second;
+        for (auto &k : fkeys) P.fvary[k.first] = A.fcs.emplace(k.second, (int)A.fcs.size()).first->second;
+        G.nic = (int)A.ics.size();
+        G.nfc = (int)A.fcs.size();
+    }
+    for (auto &G : m->groups) exa::finalize_group(G, m->pats);
+    return EXA_OK;
+}
+
 exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_options *opt, exa_model *m) {
     auto t0 = std::chrono::steady_clock::now();
     exa_options o{};
@@ -512,6 +741,7 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     m->bounds_check = (o.flags & EXA_FLAG_BOUNDS_CHECK) != 0;
     m->block = o.block_threads ? o.block_threads : 128;
     if (m->block % 32 || m->block < 32 || m->block > 1024) return fail(m, EXA_E_INVALID, "block_threads must be a multiple of 32 in [32, 1024]");
+    if (o.grid_factor < -1 || o.grid_factor > 64) return fail(m, EXA_E_INVALID, "grid_factor must be in [-1, 64]");
     if (nb < 1) return fail(m, EXA_E_INVALID, "empty batch");
     for (int b = 0; b < nb; b++) {
         const exa_model_desc *d = descs[b];
@@ -543,43 +773,29 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     const exa_model_desc &d0 = *descs[0];
     const int np = d0.n_patterns;
     if (exa_status e = load_patterns(d0, m)) return e;
-    // constants that differ between members, and the symbol partition every member must share
-    for (int p = 0; p < np; p++) {
-        exa::Pattern &P = m->pats[p];
+    // every member must identify variable references the same way as member 0
+    for (int p = 0; p < np && nb > 1; p++) {
+        const exa::Pattern &P = m->pats[p];
+        const std::vector<int> ref = exa::symbol_partition(P, P.ix);
         for (int b = 1; b < nb; b++) {
             const exa_pattern_desc &pd = descs[b]->patterns[p];
+            std::vector<exa::INode> ix;
             for (int i = 0; i < pd.n_inodes; i++)
-                if (pd.inodes[i].op == EXA_I_CONST && pd.inodes[i].ival != P.ix[i].iv && !P.ivary.count(i)) {
-                    int slot = (int)P.ivary.size();
-                    P.ivary[i] = slot;
-                }
-            for (int i = 0; i < pd.n_vnodes; i++)
-                if (pd.vnodes[i].op == EXA_V_CONST && std::memcmp(&pd.vnodes[i].fval, &P.v[i].fv, 8) != 0 &&
-                    !P.fvary.count(i)) {
-                    int slot = (int)P.fvary.size();
-                    P.fvary[i] = slot;
-                }
-        }
-        if (P.ivary.size() > 8 || P.fvary.size() > 8)
-            return fail(m, EXA_E_UNSUPPORTED, "more than 8 constants of one pattern differ between batch members");
-        if (!P.ivary.empty()) {
-            for (int b = 1; b < nb; b++) {
-                const exa_pattern_desc &pd = descs[b]->patterns[p];
-                std::vector<exa::INode> ix;
-                for (int i = 0; i < pd.n_inodes; i++)
-                    ix.push_back({pd.inodes[i].op, pd.inodes[i].a, pd.inodes[i].b, pd.inodes[i].ival});
-                if (exa::symbol_partition(P, ix) != exa::symbol_partition(P, P.ix))
-                    return fail(m, EXA_E_INVALID, "batch members of pattern " + std::to_string(p) +
-                                                      " identify variable references differently");
-            }
+                ix.push_back({pd.inodes[i].op, pd.inodes[i].a, pd.inodes[i].b, pd.inodes[i].ival});
+            if (exa::symbol_partition(P, ix) != ref)
+                return fail(m, EXA_E_INVALID, "batch members of pattern " + std::to_string(p) +
+                                                  " identify variable references differently");
         }
     }
+    if (exa_status e = build_groups(m, descs, nb, (o.flags & EXA_FLAG_NO_FUSE) == 0)) return e;
+    const int ng = (int)m->groups.size();
 
     // per-member sizes and offsets; validate row blocks
     m->nb = nb;
     m->xoff.assign(nb + 1, 0); m->coff.assign(nb + 1, 0); m->joff.assign(nb + 1, 0); m->hoff.assign(nb + 1, 0);
     std::vector<i64> goff(nb + 1, 0), aoff(nb + 1, 0), poff(nb + 1, 0);
-    std::vector<ExaPM> pms((size_t)nb * np);
+    struct PatOff { i64 n_inst, rbase, rlimit, jbase, hbase, gbase, abase; };
+    std::vector<PatOff> po((size_t)nb * np);
     for (int b = 0; b < nb; b++) {
         const exa_model_desc &d = *descs[b];
         if (d.nvar >= (1LL << 31) || d.ncon >= (1LL << 31)) return fail(m, EXA_E_INVALID, "size too large");
@@ -599,17 +815,8 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
                     return fail(m, EXA_E_BOUNDS, "augmentation target block out of range");
                 if (pd.n_inst > 0 && pd.row_limit == 0) return fail(m, EXA_E_INVALID, "augmentation target block is empty");
             }
-            ExaPM &pm = pms[(size_t)b * np + p];
-            std::memset(&pm, 0, sizeof pm);
-            pm.n_inst = pd.n_inst;
-            pm.nvar_m = d.nvar;
-            pm.npar_m = d.npar;
-            pm.rbase = pd.row_base;  // member offset added below
-            pm.rlimit = pd.row_limit;
-            pm.pat = p;
-            pm.member = b;
-            for (auto &kv : P.ivary) pm.ic[kv.second] = pd.inodes[kv.first].ival;
-            for (auto &kv : P.fvary) pm.fc[kv.second] = pd.vnodes[kv.first].fval;
+            PatOff &pm = po[(size_t)b * np + p];
+            pm = PatOff{pd.n_inst, pd.row_base, pd.row_limit, 0, 0, 0, 0};  // member offsets added below
             pm.hbase = oh; oh += pd.n_inst * P.nh();
             if (P.kind == EXA_OBJ) { pm.gbase = og; og += pd.n_inst * P.nj(); }
             else { pm.jbase = oj; oj += pd.n_inst * P.nj(); }
@@ -631,78 +838,60 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
         m->nnzg >= (1LL << 31) || m->naug >= (1LL << 31))
         return fail(m, EXA_E_INVALID, "model exceeds 2^31-1 variables, rows or nonzeros");
 
-    // generate and compile
-    exa::CodegenOptions cg;
-    cg.precision = m->precision;
-    cg.block = m->block;
-    cg.bounds_check = m->bounds_check;
-    std::string gerr;
-    std::string src = exa::generate_source(m->pats, cg, &gerr);
-    if (!gerr.empty()) return fail(m, EXA_E_INTERNAL, gerr);
-    if (getenv("EXA_DUMP_SOURCE")) {
-        FILE *fp = fopen(getenv("EXA_DUMP_SOURCE"), "w");
-        if (fp) { fputs(src.c_str(), fp); fclose(fp); }
-    }
-    if (exa_status e = compile(m, src)) return e;
-
     // upload theta and data columns (identical host columns are uploaded once)
     CR(dalloc(m, &m->d_theta, m->npar));
     CR(dalloc(m, &m->d_status, 1));
     CR(cudaMemset(m->d_status, 0, sizeof(int)));
+    std::vector<ExaPM> pms((size_t)nb * ng);
     for (int b = 0; b < nb; b++) {
         const exa_model_desc &d = *descs[b];
         if (d.npar) CR(cudaMemcpy(m->d_theta + poff[b], d.theta, sizeof(double) * d.npar, cudaMemcpyHostToDevice));
         std::map<const void *, const void *> uploaded;
-        for (int p = 0; p < np; p++) {
-            const exa_pattern_desc &pd = d.patterns[p];
-            ExaPM &pm = pms[(size_t)b * np + p];
+        for (int gi = 0; gi < ng; gi++) {
+            const exa::Group &G = m->groups[gi];
+            ExaPM &pm = pms[(size_t)b * ng + gi];
+            std::memset(&pm, 0, sizeof pm);
+            pm.n_inst = po[(size_t)b * np + G.pats[0]].n_inst;
             pm.xoff = m->xoff[b];
+            pm.nvar_m = d.nvar;
             pm.poff = poff[b];
-            pm.rbase += m->coff[b];
-            pm.jbase += m->joff[b];
-            pm.hbase += m->hoff[b];
-            pm.gbase += goff[b];
-            pm.abase += aoff[b];
-            for (int f = 0; f < pd.n_fields; f++) {
-                const void *h = pd.fields[f].data;
-                auto it = uploaded.find(h);
-                if (it != uploaded.end() && pd.n_inst > 0) { pm.f[f] = it->second; continue; }
-                size_t es = pd.fields[f].type == EXA_FIELD_I32 ? 4 : 8;
-                void *dp = nullptr;
-                CR(dalloc(m, (char **)&dp, (i64)(pd.n_inst * es)));
-                if (pd.n_inst) CR(cudaMemcpy(dp, h, es * pd.n_inst, cudaMemcpyHostToDevice));
-                pm.f[f] = dp;
-                uploaded[h] = dp;
+            pm.npar_m = d.npar;
+            pm.grp = gi;
+            pm.member = b;
+            for (size_t pos = 0; pos < G.pats.size(); pos++) {
+                const int p = G.pats[pos];
+                const exa::Pattern &P = m->pats[p];
+                const exa_pattern_desc &pd = d.patterns[p];
+                const PatOff &q = po[(size_t)b * np + p];
+                pm.rbase[pos] = q.rbase + m->coff[b];
+                pm.rlimit[pos] = q.rlimit;
+                pm.jbase[pos] = q.jbase + m->joff[b];
+                pm.hbase[pos] = q.hbase + m->hoff[b];
+                pm.gbase[pos] = q.gbase + goff[b];
+                pm.abase[pos] = q.abase + aoff[b];
+                for (auto &kv : P.ivary) pm.ic[kv.second] = pd.inodes[kv.first].ival;
+                for (auto &kv : P.fvary) pm.fc[kv.second] = pd.vnodes[kv.first].fval;
+                for (int f = 0; f < pd.n_fields; f++) {
+                    const int c = G.field[pos][f];
+                    if (pm.f[c]) continue;
+                    const void *h = pd.fields[f].data;
+                    auto it = uploaded.find(h);
+                    if (it != uploaded.end() && pd.n_inst > 0) { pm.f[c] = it->second; continue; }
+                    size_t es = pd.fields[f].type == EXA_FIELD_I32 ? 4 : 8;
+                    void *dp = nullptr;
+                    CR(dalloc(m, (char **)&dp, (i64)(pd.n_inst * es)));
+                    if (pd.n_inst) CR(cudaMemcpy(dp, h, es * pd.n_inst, cudaMemcpyHostToDevice));
+                    pm.f[c] = dp;
+                    uploaded[h] = dp;
+                }
             }
         }
     }
     CR(dalloc(m, &m->d_pm, (i64)pms.size()));
     CR(cudaMemcpy(m->d_pm, pms.data(), sizeof(ExaPM) * pms.size(), cudaMemcpyHostToDevice));
 
-    // tile lists per kernel kind: member-major, then patterns in declaration order
-    for (int k = 0; k < exa::M_COUNT; k++) {
-        std::vector<ExaTile> tiles;
-        for (int b = 0; b < nb; b++)
-            for (int p = 0; p < np; p++) {
-                const exa::Pattern &P = m->pats[p];
-                bool in = true;
-                switch (k) {
-                case exa::M_OBJ: case exa::M_GRAD: in = P.kind == EXA_OBJ; break;
-                case exa::M_CON: case exa::M_JAC: in = P.kind != EXA_OBJ; break;
-                case exa::M_HESS: in = P.nh() > 0; break;
-                default: break;
-                }
-                if (!in) continue;
-                const ExaPM &pm = pms[(size_t)b * np + p];
-                const bool part = P.kind == EXA_OBJ && (k == exa::M_OBJ || k == exa::M_ALL || k == exa::M_FIRST);
-                for (i64 s = 0; s < pm.n_inst; s += m->block)
-                    tiles.push_back({b * np + p, (int)s, part ? m->nobj[k]++ : -1});
-            }
-        m->ntiles[k] = (int)tiles.size();
-        CR(dalloc(m, &m->d_tiles[k], (i64)tiles.size()));
-        if (!tiles.empty())
-            CR(cudaMemcpy(m->d_tiles[k], tiles.data(), sizeof(ExaTile) * tiles.size(), cudaMemcpyHostToDevice));
-    }
+    m->h_pms = pms;
+    if (exa_status e = setup_kernels(m, m->block)) return e;
 
     // structure pass on the device
     CR(dalloc(m, &m->d_jrow, m->nnzj));
@@ -717,7 +906,8 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
         ExaStructOut so{m->d_jrow, m->d_jcol, m->d_hrow, m->d_hcol, m->d_gvar, m->d_arow, m->d_status};
         const double *nul = nullptr;
         double sigma = 0;
-        void *args[] = {&m->d_tiles[exa::M_STRUCT], &m->d_pm, &nul, &nul, &m->d_theta, &sigma, &out, &so};
+        int nt = m->ntiles[exa::M_STRUCT];
+        void *args[] = {&m->d_tiles[exa::M_STRUCT], &nt, &m->d_pm, &nul, &nul, &m->d_theta, &sigma, &out, &so};
         CR(cudaLaunchKernel((const void *)m->fn[exa::M_STRUCT], dim3(m->ntiles[exa::M_STRUCT]), dim3(m->block),
                             args, 0, m->stream));
         CR(cudaStreamSynchronize(m->stream));
@@ -733,6 +923,10 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     CR(dalloc(m, &m->d_gbuf, m->nnzg));
     CR(dalloc(m, &m->d_abuf, m->naug));
     CR(dalloc(m, &m->d_cbuf, m->ncon));
+    if (!(o.flags & EXA_FLAG_NO_TUNE) && !o.block_threads && o.grid_factor == 0)
+        if (exa_status e = autotune(m)) return e;
+    if (o.grid_factor != 0)
+        if (exa_status e = apply_grid(m, std::max(o.grid_factor, 0))) return e;
     int maxt = 1;
     for (int k = 0; k < exa::M_COUNT; k++) maxt = std::max(maxt, m->nobj[k]);
     CR(dalloc(m, &m->d_objpart, maxt));
@@ -1113,13 +1307,15 @@ exa_status exa_compile_check(const exa_model_desc *desc, const exa_options *opt,
         exa_options o{};
         if (opt) o = *opt;
         s = load_patterns(*desc, &tmp);
+        const exa_model_desc *d1[1] = {desc};
+        if (s == EXA_OK) s = build_groups(&tmp, d1, 1, (o.flags & EXA_FLAG_NO_FUSE) == 0);
         if (s == EXA_OK) {
             exa::CodegenOptions cg;
             cg.precision = o.precision;
             cg.block = o.block_threads ? o.block_threads : 128;
             cg.bounds_check = (o.flags & EXA_FLAG_BOUNDS_CHECK) != 0;
             std::string gerr;
-            std::string src = exa::generate_source(tmp.pats, cg, &gerr);
+            std::string src = exa::generate_source(tmp.pats, tmp.groups, cg, &gerr);
             if (!gerr.empty()) s = fail(&tmp, EXA_E_INTERNAL, gerr);
             else {
                 if (getenv("EXA_DUMP_SOURCE")) {
@@ -1146,6 +1342,9 @@ exa_status exa_stat(const exa_model *m, const char *key, double *value) {
     else if (k == "eval_regs_hess") *value = m->regs[exa::M_HESS];
     else if (k == "eval_regs_jac") *value = m->regs[exa::M_JAC];
     else if (k == "eval_block") *value = m->block;
+    else if (k == "eval_persist") *value = m->persist;
+    else if (k == "eval_grid") *value = m->grid[exa::M_ALL];
+    else if (k == "tune_ms") *value = m->tune_ms;
     else if (k == "eval_tiles") *value = m->ntiles[exa::M_ALL];
     else if (k == "device_bytes") *value = (double)m->device_bytes;
     else if (k == "n_patterns") *value = (double)m->pats.size();

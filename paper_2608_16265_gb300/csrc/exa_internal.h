@@ -12,33 +12,34 @@
 // Device-visible descriptors.  The same text is compiled into the host library and, via the
 // stringised copy kDeviceStructs, into every NVRTC-generated module, so both sides agree on the
 // layout by construction.
-#define EXA_MAXF 16
+#define EXA_MAXF 16  /* data columns per fused group */
+#define EXA_MAXG 16  /* patterns per fused group */
 #define EXA_DEVICE_STRUCTS                                                                          \
-    struct ExaPM {                /* one (batch member, pattern) pair */                            \
-        const void *f[16];        /* device data columns of this member's pattern */               \
-        long long n_inst;         /* instances */                                                   \
+    struct ExaPM {                /* one (batch member, fused pattern group) pair */               \
+        const void *f[16];        /* device data columns of the group (shared columns once) */     \
+        long long n_inst;         /* instances (equal for every pattern of the group) */           \
         long long xoff;           /* first variable of the member */                                \
         long long nvar_m;         /* variables of the member */                                     \
-        long long rbase;          /* CON: row of instance 0; AUG: first row of target block */      \
-        long long rlimit;         /* AUG: rows of the target block */                               \
-        long long jbase;          /* first Jacobian COO slot of this block */                       \
-        long long hbase;          /* first Hessian COO slot of this block */                        \
-        long long gbase;          /* first gradient-buffer slot (objective patterns) */             \
-        long long abase;          /* first augmentation-buffer entry (augmentation patterns) */     \
         long long poff;           /* first parameter of the member */                               \
         long long npar_m;         /* parameters of the member */                                    \
-        long long ic[8];          /* index constants that differ between batch members */           \
-        double fc[8];             /* value constants that differ between batch members */           \
-        int pat;                  /* pattern id */                                                  \
+        long long ic[16];         /* index constants that differ between batch members */           \
+        double fc[16];            /* value constants that differ between batch members */           \
+        long long rbase[16];      /* per pattern: CON row of instance 0 / AUG first target row */   \
+        long long rlimit[16];     /* per pattern: AUG rows of the target block */                   \
+        long long jbase[16];      /* per pattern: first Jacobian COO slot */                        \
+        long long hbase[16];      /* per pattern: first Hessian COO slot */                         \
+        long long gbase[16];      /* per pattern: first gradient-buffer slot */                     \
+        long long abase[16];      /* per pattern: first augmentation-buffer entry */                \
+        int grp;                  /* group id */                                                    \
         int member;               /* batch member */                                                \
     };                                                                                              \
-    struct ExaTile {              /* BLOCK consecutive instances of one (member, pattern) */        \
+    struct ExaTile {              /* BLOCK consecutive instances of one (member, group) */          \
         int pm;                                                                                     \
         int begin;                                                                                  \
-        int oslot;                /* objective tiles: index of this tile's partial sum; else -1 */  \
+        int oslot;                /* tiles with objective terms: index of the partial; else -1 */   \
     };                                                                                              \
     struct ExaOut {                                                                                 \
-        double *obj_part;         /* one objective partial sum per tile */                          \
+        double *obj_part;         /* one objective partial sum per objective tile */                \
         double *c;                /* constraint base values, indexed by global row */               \
         double *abuf;             /* augmentation terms */                                          \
         double *gbuf;             /* objective gradient slots */                                    \
@@ -78,10 +79,25 @@ struct Pattern {
     std::vector<int> jsym;      // first-order slot -> symbol
     std::vector<std::pair<int, int>> hpair;  // Hessian slot -> symbol pair (as first emitted)
     // constants that differ between batch members: node index -> slot in ExaPM::ic / ExaPM::fc
+    // (slots are numbered per fused group)
     std::map<int, int> ivary, fvary;
     int nj() const { return (int)jsym.size(); }
     int nh() const { return (int)hpair.size(); }
 };
+
+// Patterns evaluated by one thread per instance (equal instance counts in every batch member).
+struct Group {
+    std::vector<int> pats;                  // pattern ids in declaration order
+    std::vector<int> ftype;                 // per group data column
+    std::vector<std::vector<int>> field;    // [position][pattern field] -> group column
+    std::vector<std::vector<int>> sym;      // [position][pattern symbol] -> group symbol
+    std::vector<std::pair<int, int>> sym_root;  // group symbol -> (position, index root) defining it
+    int nic = 0, nfc = 0;                   // member-varying constant slots in use
+};
+
+// Unifies the symbols of a group's patterns: equal index expressions (columns compared as group
+// columns, member-varying constants as slots) are one group symbol.
+void finalize_group(Group &g, const std::vector<Pattern> &pats);
 
 // Validates a pattern (tree shape, opcodes, field types) and computes symbols and slot tables.
 // Returns an empty string on success, else the error message.
@@ -93,8 +109,9 @@ struct CodegenOptions {
     int block = 128;
     bool bounds_check = false;
 };
-std::string generate_source(const std::vector<Pattern> &pats, const CodegenOptions &opt,
-                            std::string *err);
+std::string generate_source(const std::vector<Pattern> &pats, const std::vector<Group> &groups,
+                            const CodegenOptions &opt, std::string *err);
+bool pattern_in_mode(const Pattern &p, Mode m);
 
 extern const char *const kDeviceStructs;
 

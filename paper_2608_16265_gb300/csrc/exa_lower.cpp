@@ -323,6 +323,7 @@ class Graph {
         if (zero(b)) return a;
         if (zero(a)) return neg(b);
         if (is_lit(a) && is_lit(b)) return lit(fold(n[a].lit - n[b].lit, P(a)), P(a));
+        if (a > b) return neg(node(S_SUB, P(a), b, a));  // a - b == -(b - a) exactly: one canonical form
         return node(S_SUB, P(a), a, b);
     }
     int mul(int a, int b) {
@@ -341,8 +342,13 @@ class Graph {
         if (is_lit(a) && is_lit(b)) return lit(fold(n[a].lit / n[b].lit, P(a)), P(a));
         return node(S_DIV, P(a), a, b);
     }
-    int fn(int op, int a) { return node(op, P(a), a); }
-    int fn_at(int op, int prec, int a) { return node(op, prec, a); }
+    int fn(int op, int a) { return fn_at(op, P(a), a); }
+    int fn_at(int op, int prec, int a) {
+        // sin(-u) = -sin(u), cos(-u) = cos(u): lets sin/cos of opposite arguments share one call
+        if (n[a].op == S_NEG && (op == S_SIN || op == S_SINR)) return neg(node(op, prec, n[a].a));
+        if (n[a].op == S_NEG && (op == S_COS || op == S_COSR)) return node(op, prec, n[a].a);
+        return node(op, prec, a);
+    }
     int powi(int u, long long m) {
         if (m == 0) return lit(1.0, P(u));
         if (m < 0) return div(lit(1.0, P(u)), powi(u, -m));
@@ -354,11 +360,10 @@ class Graph {
 };
 
 struct PatternGraph {
-    Graph g;
     std::vector<int> val, d1, d2, h11, h12, h22, adj, adj2;
     int value = -1;
-    std::vector<int> grad;                    // per symbol
-    std::map<std::pair<int, int>, int> hess;  // unordered symbol pair -> entry
+    std::vector<int> grad;                    // per pattern symbol
+    std::map<std::pair<int, int>, int> hess;  // unordered pattern-symbol pair -> entry
     std::string err;
 };
 
@@ -392,11 +397,18 @@ static std::string fmt_float(double v) {
     return s;
 }
 
-// Builds value, gradient over symbols and Hessian over symbol pairs for one pattern.
-// FP64 mode: every node in FP64.  Mixed mode: every node in FP32 except the primal subtrees that
-// form the arguments of sin / cos / tan / exp, which are evaluated in FP64 and reduced in FP64.
-static void build_graph(const Pattern &p, PatternGraph &G, bool mixed) {
-    Graph &g = G.g;
+// Group-level input ids of one pattern: 'X' group symbol, 'D' group column, 'C' constant slot,
+// 'P' parameter node (position * 65536 + node).
+struct InputMap {
+    const std::vector<int> *sym;
+    const std::vector<int> *field;
+    int pos;
+};
+
+// Builds value, gradient over symbols and Hessian over symbol pairs of one pattern into the
+// group's shared graph.  FP64 mode: every node in FP64.  Mixed mode: every node in FP32 except the
+// primal subtrees that form the arguments of sin / cos / tan / exp, evaluated and reduced in FP64.
+static void build_graph(const Pattern &p, const InputMap &im, Graph &g, PatternGraph &G, bool mixed) {
     const int nv = (int)p.v.size();
     const int W = mixed ? PF : PD;  // working precision of pattern arithmetic
     G.val.assign(nv, -1);
@@ -404,6 +416,13 @@ static void build_graph(const Pattern &p, PatternGraph &G, bool mixed) {
     G.d1.assign(nv, Z); G.d2.assign(nv, Z);
     G.h11.assign(nv, Z); G.h12.assign(nv, Z); G.h22.assign(nv, Z);
     std::vector<char> hv(nv, 0);
+    auto X = [&](int i, int prec) { return g.input('X', (*im.sym)[p.sym_of[i]], prec); };
+    auto D = [&](int f, int prec) { return g.input('D', (*im.field)[f], prec); };
+    auto Pm = [&](int i, int prec) { return g.input('P', im.pos * 65536 + i, prec); };
+    auto K = [&](int i, int prec) {
+        auto it = p.fvary.find(i);
+        return it != p.fvary.end() ? g.input('C', it->second, prec) : g.lit(p.v[i].fv, prec);
+    };
     // FP64 primal value of a subtree (argument formation in mixed mode)
     std::vector<int> dmemo(nv, -1);
     std::function<int(int)> dval = [&](int i) -> int {
@@ -411,14 +430,10 @@ static void build_graph(const Pattern &p, PatternGraph &G, bool mixed) {
         const VNode &nd = p.v[i];
         int r = -1;
         switch (nd.op) {
-        case EXA_V_CONST: {
-            auto it = p.fvary.find(i);
-            r = it != p.fvary.end() ? g.input('C', it->second, PD) : g.lit(nd.fv, PD);
-            break;
-        }
-        case EXA_V_DATA: r = g.input('D', (int)nd.iv, PD); break;
-        case EXA_V_VAR: r = g.input('X', p.sym_of[i], PD); break;
-        case EXA_V_PARAM: r = g.input('P', i, PD); break;
+        case EXA_V_CONST: r = K(i, PD); break;
+        case EXA_V_DATA: r = D((int)nd.iv, PD); break;
+        case EXA_V_VAR: r = X(i, PD); break;
+        case EXA_V_PARAM: r = Pm(i, PD); break;
         case EXA_V_NEG: r = g.neg(dval(nd.a)); break;
         case EXA_V_ABS2: { int u = dval(nd.a); r = g.mul(u, u); break; }
         case EXA_V_INV: r = g.div(g.lit(1.0, PD), dval(nd.a)); break;
@@ -445,14 +460,10 @@ static void build_graph(const Pattern &p, PatternGraph &G, bool mixed) {
         int w = nd.b >= 0 && is_binary(nd.op) ? G.val[nd.b] : -1;
         int v = Z, d1 = Z, d2 = Z, h11 = Z, h12 = Z, h22 = Z;
         switch (nd.op) {
-        case EXA_V_CONST: {
-            auto it = p.fvary.find(i);
-            v = it != p.fvary.end() ? g.input('C', it->second, W) : g.lit(nd.fv, W);
-            break;
-        }
-        case EXA_V_DATA: v = g.input('D', (int)nd.iv, W); break;
-        case EXA_V_VAR: v = g.input('X', p.sym_of[i], W); hv[i] = 1; break;
-        case EXA_V_PARAM: v = g.input('P', i, W); break;
+        case EXA_V_CONST: v = K(i, W); break;
+        case EXA_V_DATA: v = D((int)nd.iv, W); break;
+        case EXA_V_VAR: v = X(i, W); hv[i] = 1; break;
+        case EXA_V_PARAM: v = Pm(i, W); break;
         case EXA_V_NEG: v = g.neg(u); d1 = g.lit(-1.0, W); break;
         case EXA_V_ABS2: v = g.mul(u, u); d1 = g.mul(TWO, u); h11 = TWO; break;
         case EXA_V_INV:
@@ -526,12 +537,12 @@ static void build_graph(const Pattern &p, PatternGraph &G, bool mixed) {
     }
     G.value = G.val[nv - 1];
 
-    // first-order reverse pass (adjoints), then second-order (edge pushing) with tangent gradients
+    // first-order reverse pass (adjoints), then second order by edge pushing with tangent gradients
     G.adj.assign(nv, Z);
     G.adj2.assign(nv, Z);
     G.grad.assign(p.nsym, Z);
     G.adj[nv - 1] = ONE;
-    std::vector<std::map<int, int>> tg(nv);  // subtree gradient over symbols (bottom-up)
+    std::vector<std::map<int, int>> tg(nv);  // subtree gradient over pattern symbols (bottom-up)
     for (int i = 0; i < nv; i++) {
         const VNode &nd = p.v[i];
         if (nd.op == EXA_V_VAR) tg[i][p.sym_of[i]] = ONE;
@@ -594,16 +605,69 @@ static void build_graph(const Pattern &p, PatternGraph &G, bool mixed) {
         }
 }
 
+}  // namespace
+
+// ------------------------------------------------------------------ group symbols
+static std::string group_idx_key(const Pattern &p, const std::vector<int> &field, int r) {
+    const INode &n = p.ix[r];
+    switch (n.op) {
+    case EXA_I_CONST: {
+        auto it = p.ivary.find(r);
+        if (it != p.ivary.end()) return "v" + std::to_string(it->second);
+        return "c" + std::to_string(n.iv);
+    }
+    case EXA_I_FIELD: return "f" + std::to_string(field[n.iv]);
+    case EXA_I_INST: return "k";
+    default: {
+        const char *o = n.op == EXA_I_ADD ? "+" : n.op == EXA_I_SUB ? "-" : "*";
+        return std::string("(") + group_idx_key(p, field, n.a) + o + group_idx_key(p, field, n.b) + ")";
+    }
+    }
+}
+
+void finalize_group(Group &g, const std::vector<Pattern> &pats) {
+    std::map<std::string, int> ids;
+    g.sym.assign(g.pats.size(), {});
+    g.sym_root.clear();
+    for (size_t pos = 0; pos < g.pats.size(); pos++) {
+        const Pattern &p = pats[g.pats[pos]];
+        g.sym[pos].resize(p.nsym);
+        for (int s = 0; s < p.nsym; s++) {
+            auto r = ids.emplace(group_idx_key(p, g.field[pos], p.sym_root[s]), (int)ids.size());
+            if (r.second) g.sym_root.push_back({(int)pos, p.sym_root[s]});
+            g.sym[pos][s] = r.first->second;
+        }
+    }
+}
+
+bool pattern_in_mode(const Pattern &p, Mode m) {
+    switch (m) {
+    case M_OBJ: case M_GRAD: return p.kind == EXA_OBJ;
+    case M_CON: case M_JAC: return p.kind != EXA_OBJ;
+    case M_HESS: return p.nh() > 0;
+    default: return true;
+    }
+}
+
+namespace {
+
 // ------------------------------------------------------------------ CUDA emission
 struct Emitter {
-    const Pattern &p;
-    const PatternGraph &G;
+    const std::vector<Pattern> &pats;
+    const Group &grp;
+    const Graph &g;
+    const std::vector<PatternGraph> &PG;  // per position in the group
     const CodegenOptions &opt;
     std::ostringstream os;
 
-    Emitter(const Pattern &p_, const PatternGraph &G_, const CodegenOptions &o) : p(p_), G(G_), opt(o) {}
+    Emitter(const std::vector<Pattern> &p_, const Group &g_, const Graph &gr, const std::vector<PatternGraph> &pg,
+            const CodegenOptions &o)
+        : pats(p_), grp(g_), g(gr), PG(pg), opt(o) {}
 
-    std::string idx_expr(int r) {
+    const Pattern &pat(int pos) const { return pats[grp.pats[pos]]; }
+
+    std::string idx_expr(int pos, int r) {
+        const Pattern &p = pat(pos);
         const INode &n = p.ix[r];
         switch (n.op) {
         case EXA_I_CONST: {
@@ -611,18 +675,18 @@ struct Emitter {
             if (it != p.ivary.end()) return "pm.ic[" + std::to_string(it->second) + "]";
             return "(" + std::to_string(n.iv) + "LL)";
         }
-        case EXA_I_FIELD: return "((long long)F" + std::to_string(n.iv) + ")";
+        case EXA_I_FIELD: return "((long long)F" + std::to_string(grp.field[pos][n.iv]) + ")";
         case EXA_I_INST: return "kk";
         default: {
             const char *o = n.op == EXA_I_ADD ? " + " : n.op == EXA_I_SUB ? " - " : " * ";
-            return "(" + idx_expr(n.a) + o + idx_expr(n.b) + ")";
+            return "(" + idx_expr(pos, n.a) + o + idx_expr(pos, n.b) + ")";
         }
         }
     }
-    void fields_of_idx(int r, std::set<int> &f) {
-        const INode &n = p.ix[r];
-        if (n.op == EXA_I_FIELD) f.insert((int)n.iv);
-        else if (n.op >= EXA_I_ADD) { fields_of_idx(n.a, f); fields_of_idx(n.b, f); }
+    void fields_of_idx(int pos, int r, std::set<int> &f) {
+        const INode &n = pat(pos).ix[r];
+        if (n.op == EXA_I_FIELD) f.insert(grp.field[pos][n.iv]);
+        else if (n.op >= EXA_I_ADD) { fields_of_idx(pos, n.a, f); fields_of_idx(pos, n.b, f); }
     }
 
     static const char *fname(int op, int prec) {
@@ -638,7 +702,6 @@ struct Emitter {
 
     // Emits the nodes the roots need, in creation (dependency) order; names every node.
     void body(const std::vector<int> &roots, std::map<int, std::string> &name) {
-        const Graph &g = G.g;
         std::vector<char> need(g.n.size(), 0);
         std::function<void(int)> mark = [&](int i) {
             if (need[i]) return;
@@ -647,7 +710,6 @@ struct Emitter {
             if (g.n[i].b >= 0) mark(g.n[i].b);
         };
         for (int r : roots) mark(r);
-        // sin and cos of one argument share one call
         std::map<std::pair<int, int>, std::pair<int, int>> sc;  // (arg, reduced?) -> (sin+1, cos+1)
         for (size_t i = 0; i < g.n.size(); i++) {
             if (!need[i]) continue;
@@ -699,41 +761,52 @@ struct Emitter {
         }
     }
 
-    // One device function per (pattern, mode).
-    std::string function(int pid, Mode mode) {
+    // One device function per (group, mode): every active pattern of the group for one instance.
+    std::string function(int gid, Mode mode) {
         os.str("");
         const bool mixed = opt.precision == EXA_MIXED_FP32;
         const char *W = mixed ? "float" : "double";
-        const bool obj = p.kind == EXA_OBJ;
         const bool all = mode == M_ALL || mode == M_FIRST;
-        const bool want_val = (mode == M_OBJ && obj) || (mode == M_CON && !obj) || all;
-        const bool want_grad = (mode == M_GRAD && obj) || (mode == M_JAC && !obj) || all;
-        const bool want_hess = (mode == M_HESS || mode == M_ALL) && p.nh() > 0;
         const bool want_struct = mode == M_STRUCT;
-        os << "static __device__ __forceinline__ void pat" << pid << "_" << kModeName[mode]
+        std::vector<int> act;
+        for (size_t pos = 0; pos < grp.pats.size(); pos++)
+            if (pattern_in_mode(pat((int)pos), mode)) act.push_back((int)pos);
+        os << "static __device__ __forceinline__ void grp" << gid << "_" << kModeName[mode]
            << "(const ExaPM& pm, const int k, const double* __restrict__ x, const double* __restrict__ y,"
               " const double* __restrict__ th, const double sigma, const ExaOut& o,"
               " const ExaStructOut& so, double& objv) {\n";
         os << "  const long long kk = k;\n";
+        struct Want { bool val, grad, hess, row; };
+        std::vector<Want> want(grp.pats.size(), {false, false, false, false});
         std::vector<int> roots;
-        if (want_val) roots.push_back(G.value);
-        if (want_grad) for (int s : p.jsym) roots.push_back(G.grad[s]);
-        std::vector<int> hroots;
-        if (want_hess)
-            for (auto &pr : p.hpair) {
-                auto it = G.hess.find({std::min(pr.first, pr.second), std::max(pr.first, pr.second)});
-                hroots.push_back(it == G.hess.end() ? -1 : it->second);
-            }
-        for (int r : hroots) if (r >= 0) roots.push_back(r);
+        std::vector<std::vector<int>> hroots(grp.pats.size());
+        for (int pos : act) {
+            const Pattern &p = pat(pos);
+            const bool obj = p.kind == EXA_OBJ;
+            Want &w = want[pos];
+            w.val = (mode == M_OBJ && obj) || (mode == M_CON && !obj) || all;
+            w.grad = (mode == M_GRAD && obj) || (mode == M_JAC && !obj) || all;
+            w.hess = (mode == M_HESS || mode == M_ALL) && p.nh() > 0;
+            w.row = !obj && (w.val || w.hess || want_struct);
+            const PatternGraph &G = PG[pos];
+            if (w.val) roots.push_back(G.value);
+            if (w.grad) for (int s : p.jsym) roots.push_back(G.grad[s]);
+            if (w.hess)
+                for (auto &pr : p.hpair) {
+                    auto it = G.hess.find({std::min(pr.first, pr.second), std::max(pr.first, pr.second)});
+                    hroots[pos].push_back(it == G.hess.end() ? -1 : it->second);
+                    if (it != G.hess.end()) roots.push_back(it->second);
+                }
+        }
         // inputs the roots need, by kind and precision
-        std::set<int> syms, fields, params, fconsts;            // FP64 copies (loaded)
-        std::set<int> fsyms, ffields, fparams, ffconsts;        // FP32 copies (converted)
+        std::set<int> syms, fields, params, fconsts;       // FP64 copies (loaded)
+        std::set<int> fsyms, ffields, fparams, ffconsts;   // FP32 copies (converted)
         {
-            std::vector<char> seen(G.g.n.size(), 0);
+            std::vector<char> seen(g.n.size(), 0);
             std::function<void(int)> walk = [&](int i) {
                 if (seen[i]) return;
                 seen[i] = 1;
-                const SN &s = G.g.n[i];
+                const SN &s = g.n[i];
                 if (s.op == S_IN) {
                     std::set<int> *d = s.ikind == 'X' ? &syms : s.ikind == 'D' ? &fields : s.ikind == 'P' ? &params : &fconsts;
                     std::set<int> *f = s.ikind == 'X' ? &fsyms : s.ikind == 'D' ? &ffields : s.ikind == 'P' ? &fparams : &ffconsts;
@@ -745,98 +818,118 @@ struct Emitter {
             };
             for (int r : roots) walk(r);
         }
-        const bool need_row = (!obj) && (want_val || want_hess || want_struct);
-        std::set<int> idx_syms = syms;  // symbols whose index is needed
-        if (want_struct) for (int s = 0; s < p.nsym; s++) idx_syms.insert(s);
-        if (want_hess)
-            for (auto &pr : p.hpair)
-                if (pr.first != pr.second) { idx_syms.insert(pr.first); idx_syms.insert(pr.second); }
-        std::set<int> ifields;
-        for (int s : idx_syms) fields_of_idx(p.sym_root[s], ifields);
-        for (int pn : params) fields_of_idx(p.v[pn].a, ifields);
-        if (p.kind == EXA_AUG && need_row) fields_of_idx(p.row_root, ifields);
+        std::set<int> idx_syms = syms;  // group symbols whose index is needed
+        for (int pos : act) {
+            const Pattern &p = pat(pos);
+            if (want_struct) for (int s = 0; s < p.nsym; s++) idx_syms.insert(grp.sym[pos][s]);
+            if (want[pos].hess)
+                for (auto &pr : p.hpair)
+                    if (pr.first != pr.second) { idx_syms.insert(grp.sym[pos][pr.first]); idx_syms.insert(grp.sym[pos][pr.second]); }
+        }
         std::set<int> all_fields = fields;
-        all_fields.insert(ifields.begin(), ifields.end());
+        for (int s : idx_syms) fields_of_idx(grp.sym_root[s].first, grp.sym_root[s].second, all_fields);
+        for (int pid : params) fields_of_idx(pid / 65536, pat(pid / 65536).v[pid % 65536].a, all_fields);
+        for (int pos : act)
+            if (want[pos].row && pat(pos).kind == EXA_AUG) fields_of_idx(pos, pat(pos).row_root, all_fields);
         for (int f : all_fields) {
-            if (p.ftype[f] == EXA_FIELD_I32)
+            if (grp.ftype[f] == EXA_FIELD_I32)
                 os << "  const int F" << f << " = __ldg((const int*)pm.f[" << f << "] + k);\n";
             else
                 os << "  const double F" << f << " = __ldg((const double*)pm.f[" << f << "] + k);\n";
         }
         for (int f : fields)
-            os << "  const double D" << f << " = " << (p.ftype[f] == EXA_FIELD_I32 ? "(double)F" : "F") << f << ";\n";
+            os << "  const double D" << f << " = " << (grp.ftype[f] == EXA_FIELD_I32 ? "(double)F" : "F") << f << ";\n";
         for (int s : idx_syms) {
-            os << "  const long long i" << s << " = " << idx_expr(p.sym_root[s]) << ";\n";
+            os << "  const long long i" << s << " = " << idx_expr(grp.sym_root[s].first, grp.sym_root[s].second) << ";\n";
             if (opt.bounds_check || want_struct)
                 os << "  if ((unsigned long long)i" << s << " >= (unsigned long long)pm.nvar_m) { atomicOr(o.status, 1); return; }\n";
         }
-        for (int pn : params) {
-            os << "  const long long q" << pn << " = " << idx_expr(p.v[pn].a) << ";\n";
+        for (int pid : params) {
+            int pos = pid / 65536, node = pid % 65536;
+            os << "  const long long q" << pid << " = " << idx_expr(pos, pat(pos).v[node].a) << ";\n";
             if (opt.bounds_check || want_struct)
-                os << "  if ((unsigned long long)q" << pn << " >= (unsigned long long)pm.npar_m) { atomicOr(o.status, 1); return; }\n";
+                os << "  if ((unsigned long long)q" << pid << " >= (unsigned long long)pm.npar_m) { atomicOr(o.status, 1); return; }\n";
         }
-        if (need_row) {
-            if (p.kind == EXA_CON) os << "  const long long row = pm.rbase + kk;\n";
+        for (int pos : act) {
+            if (!want[pos].row) continue;
+            const Pattern &p = pat(pos);
+            if (p.kind == EXA_CON) os << "  const long long row" << pos << " = pm.rbase[" << pos << "] + kk;\n";
             else {
-                os << "  const long long lrow = " << idx_expr(p.row_root) << ";\n";
+                os << "  const long long lrow" << pos << " = " << idx_expr(pos, p.row_root) << ";\n";
                 if (opt.bounds_check || want_struct)
-                    os << "  if ((unsigned long long)lrow >= (unsigned long long)pm.rlimit) { atomicOr(o.status, 1); return; }\n";
-                os << "  const long long row = pm.rbase + lrow;\n";
+                    os << "  if ((unsigned long long)lrow" << pos << " >= (unsigned long long)pm.rlimit[" << pos
+                       << "]) { atomicOr(o.status, 1); return; }\n";
+                os << "  const long long row" << pos << " = pm.rbase[" << pos << "] + lrow" << pos << ";\n";
             }
         }
         if (want_struct) {
-            if (obj) {
-                for (int j = 0; j < p.nj(); j++)
-                    os << "  so.gvar[pm.gbase + kk * " << p.nj() << " + " << j << "] = (int)(pm.xoff + i" << p.jsym[j] << ");\n";
-            } else {
-                for (int j = 0; j < p.nj(); j++) {
-                    os << "  so.jrow[pm.jbase + kk * " << p.nj() << " + " << j << "] = (int)row;\n";
-                    os << "  so.jcol[pm.jbase + kk * " << p.nj() << " + " << j << "] = (int)(pm.xoff + i" << p.jsym[j] << ");\n";
+            for (int pos : act) {
+                const Pattern &p = pat(pos);
+                const std::string P = std::to_string(pos);
+                auto gs = [&](int s) { return "i" + std::to_string(grp.sym[pos][s]); };
+                if (p.kind == EXA_OBJ) {
+                    for (int j = 0; j < p.nj(); j++)
+                        os << "  so.gvar[pm.gbase[" << P << "] + kk * " << p.nj() << " + " << j << "] = (int)(pm.xoff + " << gs(p.jsym[j]) << ");\n";
+                } else {
+                    for (int j = 0; j < p.nj(); j++) {
+                        os << "  so.jrow[pm.jbase[" << P << "] + kk * " << p.nj() << " + " << j << "] = (int)row" << P << ";\n";
+                        os << "  so.jcol[pm.jbase[" << P << "] + kk * " << p.nj() << " + " << j << "] = (int)(pm.xoff + " << gs(p.jsym[j]) << ");\n";
+                    }
+                    if (p.kind == EXA_AUG) os << "  so.arow[pm.abase[" << P << "] + kk] = (int)row" << P << ";\n";
                 }
-                if (p.kind == EXA_AUG) os << "  so.arow[pm.abase + kk] = (int)row;\n";
-            }
-            for (int j = 0; j < p.nh(); j++) {
-                int a = p.hpair[j].first, b = p.hpair[j].second;
-                os << "  { const long long ga = pm.xoff + i" << a << ", gb = pm.xoff + i" << b << ";\n"
-                   << "    so.hrow[pm.hbase + kk * " << p.nh() << " + " << j << "] = (int)(ga > gb ? ga : gb);\n"
-                   << "    so.hcol[pm.hbase + kk * " << p.nh() << " + " << j << "] = (int)(ga > gb ? gb : ga); }\n";
+                for (int j = 0; j < p.nh(); j++) {
+                    int a = p.hpair[j].first, b = p.hpair[j].second;
+                    os << "  { const long long ga = pm.xoff + " << gs(a) << ", gb = pm.xoff + " << gs(b) << ";\n"
+                       << "    so.hrow[pm.hbase[" << P << "] + kk * " << p.nh() << " + " << j << "] = (int)(ga > gb ? ga : gb);\n"
+                       << "    so.hcol[pm.hbase[" << P << "] + kk * " << p.nh() << " + " << j << "] = (int)(ga > gb ? gb : ga); }\n";
+                }
             }
             os << "}\n";
             return os.str();
         }
         for (int s : syms) os << "  const double X" << s << " = __ldg(x + pm.xoff + i" << s << ");\n";
-        for (int pn : params) os << "  const double P" << pn << " = __ldg(th + pm.poff + q" << pn << ");\n";
+        for (int pid : params) os << "  const double P" << pid << " = __ldg(th + pm.poff + q" << pid << ");\n";
         for (int c : fconsts) os << "  const double C" << c << " = pm.fc[" << c << "];\n";
         for (int s : fsyms) os << "  const float XF" << s << " = (float)X" << s << ";\n";
         for (int f : ffields) os << "  const float DF" << f << " = (float)D" << f << ";\n";
-        for (int pn : fparams) os << "  const float PF" << pn << " = (float)P" << pn << ";\n";
+        for (int pid : fparams) os << "  const float PF" << pid << " = (float)P" << pid << ";\n";
         for (int c : ffconsts) os << "  const float CF" << c << " = (float)C" << c << ";\n";
         std::map<int, std::string> name;
         body(roots, name);
         auto widen = [&](int r) { return mixed ? "(double)" + name.at(r) : name.at(r); };
-        if (want_val) {
-            const std::string v = widen(G.value);
-            if (obj) os << "  objv = " << v << ";\n";
-            else if (p.kind == EXA_CON) os << "  o.c[row] = " << v << ";\n";
-            else os << "  o.abuf[pm.abase + kk] = " << v << ";\n";
-        }
-        if (want_grad && p.nj() > 0) {
-            if (obj) os << "  double* __restrict__ GO = o.gbuf + pm.gbase + kk * " << p.nj() << ";\n";
-            else os << "  double* __restrict__ GO = o.jac + pm.jbase + kk * " << p.nj() << ";\n";
-            for (int j = 0; j < p.nj(); j++) os << "  GO[" << j << "] = " << widen(G.grad[p.jsym[j]]) << ";\n";
-        }
-        if (want_hess) {
-            if (obj) os << "  const " << W << " w = (" << W << ")sigma;\n";
-            else os << "  const " << W << " w = (" << W << ")__ldg(y + row);\n";
-            os << "  const " << W << " w2 = w + w;\n";
-            os << "  double* __restrict__ HO = o.hess + pm.hbase + kk * " << p.nh() << ";\n";
-            for (int j = 0; j < p.nh(); j++) {
-                int a = p.hpair[j].first, b = p.hpair[j].second;
-                int r = hroots[j];
-                std::string v = r >= 0 ? name.at(r) : (mixed ? "0.0f" : "0.0");
-                std::string wt = a == b ? "w" : "(i" + std::to_string(a) + " == i" + std::to_string(b) + " ? w2 : w)";
-                if (mixed) os << "  HO[" << j << "] = (double)(" << wt << " * " << v << ");\n";
-                else os << "  HO[" << j << "] = " << wt << " * " << v << ";\n";
+        bool objw = false;
+        for (int pos : act) {
+            const Pattern &p = pat(pos);
+            const PatternGraph &G = PG[pos];
+            const Want &w = want[pos];
+            const std::string P = std::to_string(pos);
+            const bool obj = p.kind == EXA_OBJ;
+            if (w.val) {
+                const std::string v = widen(G.value);
+                if (obj) { os << "  objv " << (objw ? "+=" : "=") << " " << v << ";\n"; objw = true; }
+                else if (p.kind == EXA_CON) os << "  o.c[row" << P << "] = " << v << ";\n";
+                else os << "  o.abuf[pm.abase[" << P << "] + kk] = " << v << ";\n";
+            }
+            if (w.grad && p.nj() > 0) {
+                os << "  { double* __restrict__ GO = " << (obj ? "o.gbuf + pm.gbase[" : "o.jac + pm.jbase[") << P
+                   << "] + kk * " << p.nj() << ";\n";
+                for (int j = 0; j < p.nj(); j++) os << "    GO[" << j << "] = " << widen(G.grad[p.jsym[j]]) << ";\n";
+                os << "  }\n";
+            }
+            if (w.hess) {
+                os << "  { const " << W << " w = (" << W << ")" << (obj ? "sigma" : "__ldg(y + row" + P + ")") << ";\n";
+                os << "    const " << W << " w2 = w + w;\n";
+                os << "    double* __restrict__ HO = o.hess + pm.hbase[" << P << "] + kk * " << p.nh() << ";\n";
+                for (int j = 0; j < p.nh(); j++) {
+                    int a = p.hpair[j].first, b = p.hpair[j].second;
+                    int r = hroots[pos][j];
+                    std::string v = r >= 0 ? name.at(r) : (mixed ? "0.0f" : "0.0");
+                    std::string wt = a == b ? "w" : "(i" + std::to_string(grp.sym[pos][a]) + " == i" +
+                                                        std::to_string(grp.sym[pos][b]) + " ? w2 : w)";
+                    if (mixed) os << "    HO[" << j << "] = (double)(" << wt << " * " << v << ");\n";
+                    else os << "    HO[" << j << "] = " << wt << " * " << v << ";\n";
+                }
+                os << "  }\n";
             }
         }
         os << "}\n";
@@ -874,56 +967,60 @@ static __device__ __forceinline__ float exa_exp_red(const double a) {
 
 }  // namespace
 
-static bool pattern_in_mode(const Pattern &p, Mode m) {
-    switch (m) {
-    case M_OBJ: case M_GRAD: return p.kind == EXA_OBJ;
-    case M_CON: case M_JAC: return p.kind != EXA_OBJ;
-    case M_HESS: return p.nh() > 0;
-    default: return true;
-    }
-}
-
-std::string generate_source(const std::vector<Pattern> &pats, const CodegenOptions &opt, std::string *err) {
+std::string generate_source(const std::vector<Pattern> &pats, const std::vector<Group> &groups,
+                            const CodegenOptions &opt, std::string *err) {
     std::ostringstream src;
     const bool mixed = opt.precision == EXA_MIXED_FP32;
     src << "// generated by exa_lower.cpp (" << (mixed ? "mixed FP32/FP64" : "FP64") << ")\n";
     src << kDeviceStructs << "\n";
     src << "#define EXA_BLOCK " << opt.block << "\n";
     if (mixed) src << kMixedHelpers;
-    std::vector<PatternGraph> graphs(pats.size());
-    for (size_t i = 0; i < pats.size(); i++) {
-        build_graph(pats[i], graphs[i], mixed);
-        if (!graphs[i].err.empty()) {
-            *err = graphs[i].err;
-            return "";
+    // one shared expression graph per group
+    std::vector<Graph> graphs(groups.size());
+    std::vector<std::vector<PatternGraph>> pgs(groups.size());
+    for (size_t gi = 0; gi < groups.size(); gi++) {
+        const Group &grp = groups[gi];
+        pgs[gi].resize(grp.pats.size());
+        for (size_t pos = 0; pos < grp.pats.size(); pos++) {
+            InputMap im{&grp.sym[pos], &grp.field[pos], (int)pos};
+            build_graph(pats[grp.pats[pos]], im, graphs[gi], pgs[gi][pos], mixed);
+            if (!pgs[gi][pos].err.empty()) {
+                *err = pgs[gi][pos].err;
+                return "";
+            }
         }
     }
     for (int m = 0; m < M_COUNT; m++) {
-        for (size_t i = 0; i < pats.size(); i++) {
-            if (!pattern_in_mode(pats[i], (Mode)m)) continue;
-            Emitter e(pats[i], graphs[i], opt);
-            src << e.function((int)i, (Mode)m);
+        std::vector<int> gl;
+        for (size_t gi = 0; gi < groups.size(); gi++) {
+            bool any = false;
+            for (int pid : groups[gi].pats) any = any || pattern_in_mode(pats[pid], (Mode)m);
+            if (!any) continue;
+            gl.push_back((int)gi);
+            Emitter e(pats, groups[gi], graphs[gi], pgs[gi], opt);
+            src << e.function((int)gi, (Mode)m);
         }
         const bool objred = (m == M_OBJ || m == M_ALL || m == M_FIRST);
+        // Tile loop: with gridDim.x == ntiles every CTA takes one tile; a smaller (persistent) grid
+        // strides over the tile list.  tl.oslot and the trip count are uniform over the CTA.
         src << "extern \"C\" __global__ void __launch_bounds__(EXA_BLOCK) exa_" << kModeName[m]
-            << "(const ExaTile* __restrict__ tiles, const ExaPM* __restrict__ pms, const double* __restrict__ x,"
-               " const double* __restrict__ y, const double* __restrict__ th, const double sigma, const ExaOut o,"
-               " const ExaStructOut so) {\n"
-               "  const ExaTile tl = tiles[blockIdx.x];\n"
+            << "(const ExaTile* __restrict__ tiles, const int ntiles, const ExaPM* __restrict__ pms,"
+               " const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ th,"
+               " const double sigma, const ExaOut o, const ExaStructOut so) {\n";
+        if (objred) src << "  __shared__ double red[EXA_BLOCK / 32];\n";
+        src << "  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {\n"
+               "  const ExaTile tl = tiles[t];\n"
                "  const ExaPM& pm = pms[tl.pm];\n"
                "  const int k = tl.begin + (int)threadIdx.x;\n"
                "  double objv = 0.0;\n"
                "  if (k < pm.n_inst) {\n"
-               "    switch (pm.pat) {\n";
-        for (size_t i = 0; i < pats.size(); i++) {
-            if (!pattern_in_mode(pats[i], (Mode)m)) continue;
-            src << "      case " << i << ": pat" << i << "_" << kModeName[m] << "(pm, k, x, y, th, sigma, o, so, objv); break;\n";
-        }
+               "    switch (pm.grp) {\n";
+        for (int gi : gl)
+            src << "      case " << gi << ": grp" << gi << "_" << kModeName[m] << "(pm, k, x, y, th, sigma, o, so, objv); break;\n";
         src << "      default: break;\n    }\n  }\n";
-        if (objred) {  // only objective tiles reduce (tl.oslot is uniform over the CTA)
+        if (objred) {
             src << "  if (tl.oslot >= 0) {\n"
                    "    for (int off = 16; off > 0; off >>= 1) objv += __shfl_xor_sync(0xffffffffu, objv, off);\n"
-                   "    __shared__ double red[EXA_BLOCK / 32];\n"
                    "    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = objv;\n"
                    "    __syncthreads();\n"
                    "    if (threadIdx.x == 0) {\n"
@@ -931,9 +1028,10 @@ std::string generate_source(const std::vector<Pattern> &pats, const CodegenOptio
                    "      for (int i = 0; i < EXA_BLOCK / 32; i++) s += red[i];\n"
                    "      o.obj_part[tl.oslot] = s;\n"
                    "    }\n"
+                   "    __syncthreads();\n"
                    "  }\n";
         }
-        src << "}\n";
+        src << "  }\n}\n";
     }
     return src.str();
 }

@@ -29,10 +29,10 @@ def _np(t):
     return t.detach().cpu().numpy()
 
 
-def check_model(flat, x, y, s, block=0, tol=TOL, o=None):
+def check_model(flat, x, y, s, block=0, tol=TOL, o=None, flags=0, precision=0, grid_factor=0):
     B = _B()
     o = o or oracle.Oracle(flat)
-    m = B.exa_create(flat, block=block)
+    m = B.exa_create(flat, block=block, flags=flags, precision=precision, grid_factor=grid_factor)
     assert (m.nvar, m.ncon, m.nnzj, m.nnzh, m.nnzj_csc, m.nnzh_csc) == \
         (o.nvar, o.ncon, o.nnzj, o.nnzh, o.nnzj_csc, o.nnzh_csc)
     # structures: bit-exact
@@ -86,6 +86,30 @@ CASES = {
 def test_parity_small(name):
     flat, (x, y, s) = CASES[name]()
     check_model(flat, x, y, s)
+
+
+@pytest.mark.parametrize("name", ["all_ops", "acopf_shunts", "pde_41"])
+def test_parity_unfused(name):
+    """Every pattern in its own thread (no fused groups) gives the same results."""
+    flat, (x, y, s) = CASES[name]()
+    check_model(flat, x, y, s, flags=_B().EXA_FLAG_NO_FUSE)
+
+
+@pytest.mark.parametrize("grid_factor", [1, 2])
+def test_parity_persistent_grid(grid_factor):
+    """A persistent grid (CTAs loop over the tile list) gives the same results."""
+    wl = synth.pde(600)  # ~5600 tiles of 128: more than two waves of resident CTAs
+    x, y, s = synth.pde_point(wl, 1)
+    m, _ = check_model(wl.flat, x, y, s, grid_factor=grid_factor)
+    assert m.stat("eval_persist") == grid_factor and m.stat("eval_grid") < m.stat("eval_tiles")
+
+
+def test_autotuned_model():
+    """Default creation tunes block size and grid shape on models large enough to fill the GPU."""
+    wl = synth.pde(300)
+    x, y, s = synth.pde_point(wl, 3)
+    m, _ = check_model(wl.flat, x, y, s)
+    assert m.stat("eval_block") in (64, 128, 256) and m.stat("tune_ms") > 0
 
 
 @pytest.mark.parametrize("block", [32, 64, 256])
