@@ -298,6 +298,7 @@ def run_exa(args):
               "nnzj": m.nnzj, "nnzh": m.nnzh, "nnzj_csc": m.nnzj_csc, "nnzh_csc": m.nnzh_csc,
               "nvar": m.nvar, "ncon": m.ncon, "create_s": t_create, "generate_s": t_gen,
               "eval_regs": m.stat("eval_regs"), "eval_block": m.stat("eval_block"),
+              "eval_persist": m.stat("eval_persist"), "eval_grid": m.stat("eval_grid"), "eval_tiles": m.stat("eval_tiles"),
               "device_bytes": m.stat("device_bytes")}
     if not args.no_extras:
         v = torch.randn(m.nvar, dtype=torch.float64, device=dev)
@@ -330,6 +331,18 @@ def run_exa(args):
         ms2 = timed(step2, max(5, min(args.steps, 200)))
         k2 = timed(lambda: m2.exa_eval_all(xt, yt, sigma, jac=jac, hess=hess), max(5, min(args.steps, 200)))
         tag = "mixed" if other == B.EXA_MIXED_FP32 else "fp64"
+        # error of the mixed outputs against the FP64 outputs on the whole batch (the FP64 path
+        # itself matches the CPU oracle to 1e-12 in the parity tests)
+        outs = {}
+        for mm in (m, m2):
+            r = {k: E(n) for k, n in (("f", 1), ("g", m.nvar), ("c", m.ncon), ("jac", m.nnzj), ("hess", m.nnzh),
+                                       ("jac_csc", m.nnzj_csc), ("hess_csc", m.nnzh_csc))}
+            mm.exa_eval_all(xt, yt, sigma, **r)
+            outs[mm is m] = r
+        ref, mix = (outs[True], outs[False]) if tag == "mixed" else (outs[False], outs[True])
+        extras["mixed_rel_err_vs_fp64"] = {
+            k: float(torch.linalg.vector_norm(mix[k] - ref[k]) / torch.linalg.vector_norm(ref[k])) for k in ref}
+        del outs, ref, mix
         extras[f"{tag}_step_ms"] = ms2
         extras[f"{tag}_nnz_per_s"] = nnz_rank / (ms2 * 1e-3)
         extras[f"{tag}_kernel_ms"] = k2

@@ -141,7 +141,9 @@ enum {
     EXA_FLAG_BOUNDS_CHECK = 1, /* every gather index is checked on the device; a violation makes
                                   the next exa_check_status return EXA_E_BOUNDS */
     EXA_FLAG_NO_TUNE = 2,      /* skip the launch-shape autotuner at creation */
-    EXA_FLAG_NO_FUSE = 4       /* evaluate every pattern in its own thread (no fused groups) */
+    EXA_FLAG_NO_FUSE = 4,      /* evaluate every pattern in its own thread (no fused groups) */
+    EXA_FLAG_NO_GRAPH = 8      /* exa_eval_all launches its kernels directly instead of replaying a
+                                  cached CUDA graph */
 };
 
 /* Validate the descriptor (Sec. 3.4 SIMDFunction), lower every pattern to generated device
@@ -228,7 +230,9 @@ exa_status exa_hess_csc(exa_model *m, const double *x, const double *y, double s
 
 /* Everything in one pass over all patterns.  Any output may be NULL (not computed).
  * jac/hess are COO values; jac_csc/hess_csc CSC values.  y and sigma are read only when hess or
- * hess_csc is requested. */
+ * hess_csc is requested.  The launches are replayed from a CUDA graph cached per argument tuple
+ * (4 tuples kept; the first call with a new tuple captures it); when the model's stream is being
+ * captured by the caller, the launches are recorded into that capture instead. */
 exa_status exa_eval_all(exa_model *m, const double *x, const double *y, double sigma, double *f,
                         double *g, double *c, double *jac, double *hess, double *jac_csc,
                         double *hess_csc);

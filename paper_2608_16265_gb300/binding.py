@@ -23,7 +23,7 @@ from . import ir
 EXA_OK, EXA_E_INVALID, EXA_E_OOM, EXA_E_NVRTC, EXA_E_CUDA, EXA_E_BOUNDS, EXA_E_TIMEOUT, \
     EXA_E_UNSUPPORTED, EXA_E_INTERNAL = range(9)
 EXA_FP64, EXA_MIXED_FP32 = 0, 1
-EXA_FLAG_BOUNDS_CHECK, EXA_FLAG_NO_TUNE, EXA_FLAG_NO_FUSE = 1, 2, 4
+EXA_FLAG_BOUNDS_CHECK, EXA_FLAG_NO_TUNE, EXA_FLAG_NO_FUSE, EXA_FLAG_NO_GRAPH = 1, 2, 4, 8
 STATUS_NAMES = ["EXA_OK", "EXA_E_INVALID", "EXA_E_OOM", "EXA_E_NVRTC", "EXA_E_CUDA", "EXA_E_BOUNDS",
                 "EXA_E_TIMEOUT", "EXA_E_UNSUPPORTED", "EXA_E_INTERNAL"]
 

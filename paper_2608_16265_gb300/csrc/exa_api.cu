@@ -11,6 +11,7 @@
 #include <nvrtc.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -186,6 +187,16 @@ struct exa_model {
     int grid[exa::M_COUNT] = {};  // CTAs launched per kernel kind (<= ntiles: persistent tile loop)
     int persist = 0;              // persistent grid factor chosen by the tuner (0: one CTA per tile)
     std::vector<ExaPM> h_pms;     // host copy of the group descriptors
+    // CUDA graphs of exa_eval_all, one per argument tuple
+    struct GraphEntry {
+        std::array<const void *, 10> key;
+        cudaGraphExec_t exec;
+        uint64_t last_use;
+    };
+    std::vector<GraphEntry> graphs;
+    uint64_t graph_clock = 0;
+    bool use_graphs = true;
+    cudaStream_t cap_stream = nullptr;
     double *d_theta = nullptr;
     int *d_status = nullptr;
     int *d_jrow = nullptr, *d_jcol = nullptr, *d_hrow = nullptr, *d_hcol = nullptr, *d_gvar = nullptr, *d_arow = nullptr;
@@ -235,6 +246,10 @@ cudaError_t dalloc(exa_model *m, T **p, i64 count) {
     } while (0)
 
 void free_all(exa_model *m) {
+    for (auto &ge : m->graphs) cudaGraphExecDestroy(ge.exec);
+    m->graphs.clear();
+    if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+    m->cap_stream = nullptr;
     for (int k = 0; k < exa::M_COUNT; k++) {
         if (m->d_tiles[k]) cudaFree(m->d_tiles[k]);
         m->d_tiles[k] = nullptr;
@@ -739,6 +754,7 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     m->precision = o.precision;
     m->device = o.device;
     m->bounds_check = (o.flags & EXA_FLAG_BOUNDS_CHECK) != 0;
+    m->use_graphs = (o.flags & EXA_FLAG_NO_GRAPH) == 0;
     m->block = o.block_threads ? o.block_threads : 128;
     if (m->block % 32 || m->block < 32 || m->block > 1024) return fail(m, EXA_E_INVALID, "block_threads must be a multiple of 32 in [32, 1024]");
     if (o.grid_factor < -1 || o.grid_factor > 64) return fail(m, EXA_E_INVALID, "grid_factor must be in [-1, 64]");
@@ -1214,12 +1230,10 @@ exa_status exa_hess_csc(exa_model *m, const double *x, const double *y, double s
     return scatter_csc(m, m->d_hsegptr, m->d_hperm, m->d_hbuf, vals_csc, m->nnzh_csc, m->nnzh);
 }
 
-exa_status exa_eval_all(exa_model *m, const double *x, const double *y, double sigma, double *f, double *g,
-                        double *c, double *jac, double *hess, double *jac_csc, double *hess_csc) {
-    if (exa_status e = check_model(m)) return e;
-    CHECK_PTRS(x);
+static exa_status eval_all_launches(exa_model *m, const double *x, const double *y, double sigma, double *f,
+                                    double *g, double *c, double *jac, double *hess, double *jac_csc,
+                                    double *hess_csc) {
     const bool want_h = hess || hess_csc;
-    if (want_h && m->ncon && !y) return fail(m, EXA_E_INVALID, "NULL y");
     ExaOut o{};
     o.obj_part = m->d_objpart;
     o.c = c ? c : m->d_cbuf;
@@ -1243,6 +1257,56 @@ exa_status exa_eval_all(exa_model *m, const double *x, const double *y, double s
         if (exa_status e = scatter_csc(m, m->d_jsegptr, m->d_jperm, o.jac, jac_csc, m->nnzj_csc, m->nnzj)) return e;
     if (hess_csc)
         if (exa_status e = scatter_csc(m, m->d_hsegptr, m->d_hperm, o.hess, hess_csc, m->nnzh_csc, m->nnzh)) return e;
+    return EXA_OK;
+}
+
+// exa_eval_all replays a CUDA graph of its launches (evaluation kernel plus the reductions it needs),
+// captured once per argument tuple on a private stream and cached (at most 4 tuples, least recently
+// used evicted).  When the model's stream is itself being captured, the launches go straight into
+// the caller's capture instead.
+exa_status exa_eval_all(exa_model *m, const double *x, const double *y, double sigma, double *f, double *g,
+                        double *c, double *jac, double *hess, double *jac_csc, double *hess_csc) {
+    if (exa_status e = check_model(m)) return e;
+    CHECK_PTRS(x);
+    if ((hess || hess_csc) && m->ncon && !y) return fail(m, EXA_E_INVALID, "NULL y");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CR(cudaStreamIsCapturing(m->stream, &cs));
+    if (!m->use_graphs || cs != cudaStreamCaptureStatusNone)
+        return eval_all_launches(m, x, y, sigma, f, g, c, jac, hess, jac_csc, hess_csc);
+    uint64_t sb;
+    std::memcpy(&sb, &sigma, 8);
+    const std::array<const void *, 10> key = {x, y, f, g, c, jac, hess, jac_csc, hess_csc, (const void *)(uintptr_t)sb};
+    for (auto &ge : m->graphs)
+        if (ge.key == key) {
+            ge.last_use = ++m->graph_clock;
+            CR(cudaGraphLaunch(ge.exec, m->stream));
+            return EXA_OK;
+        }
+    if (!m->cap_stream) CR(cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t user = m->stream;
+    m->stream = m->cap_stream;
+    CR(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
+    exa_status st = eval_all_launches(m, x, y, sigma, f, g, c, jac, hess, jac_csc, hess_csc);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(m->cap_stream, &graph);
+    m->stream = user;
+    if (st != EXA_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (ce != cudaSuccess) return fail(m, EXA_E_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
+    cudaGraphExec_t exec = nullptr;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return fail(m, EXA_E_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ce));
+    if (m->graphs.size() >= 4) {
+        auto lru = std::min_element(m->graphs.begin(), m->graphs.end(),
+                                    [](const exa_model::GraphEntry &a, const exa_model::GraphEntry &b) { return a.last_use < b.last_use; });
+        cudaGraphExecDestroy(lru->exec);
+        m->graphs.erase(lru);
+    }
+    m->graphs.push_back({key, exec, ++m->graph_clock});
+    CR(cudaGraphLaunch(exec, m->stream));
     return EXA_OK;
 }
 

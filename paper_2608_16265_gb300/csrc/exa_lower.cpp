@@ -771,11 +771,18 @@ struct Emitter {
         std::vector<int> act;
         for (size_t pos = 0; pos < grp.pats.size(); pos++)
             if (pattern_in_mode(pat((int)pos), mode)) act.push_back((int)pos);
+        // k is the thread's instance clamped to the last one; act says whether it is its own.  Every
+        // lane of a warp runs the function so that outputs can be staged per warp in shared memory
+        // (ws) and written back as contiguous, coalesced runs.
         os << "static __device__ __forceinline__ void grp" << gid << "_" << kModeName[mode]
-           << "(const ExaPM& pm, const int k, const double* __restrict__ x, const double* __restrict__ y,"
-              " const double* __restrict__ th, const double sigma, const ExaOut& o,"
-              " const ExaStructOut& so, double& objv) {\n";
+           << "(const ExaPM& pm, const int k, const bool act, const double* __restrict__ x,"
+              " const double* __restrict__ y, const double* __restrict__ th, const double sigma, const ExaOut& o,"
+              " const ExaStructOut& so, double& objv, double* __restrict__ ws) {\n";
         os << "  const long long kk = k;\n";
+        if (!want_struct)
+            os << "  const int lane = threadIdx.x & 31;\n"
+                  "  const int nact = __popc(__ballot_sync(0xffffffffu, act));\n"
+                  "  const long long kw = __shfl_sync(0xffffffffu, kk, 0);  // instance of lane 0 (active)\n";
         struct Want { bool val, grad, hess, row; };
         std::vector<Want> want(grp.pats.size(), {false, false, false, false});
         std::vector<int> roots;
@@ -840,29 +847,30 @@ struct Emitter {
         for (int f : fields)
             os << "  const double D" << f << " = " << (grp.ftype[f] == EXA_FIELD_I32 ? "(double)F" : "F") << f << ";\n";
         for (int s : idx_syms) {
-            os << "  const long long i" << s << " = " << idx_expr(grp.sym_root[s].first, grp.sym_root[s].second) << ";\n";
+            os << "  long long i" << s << " = " << idx_expr(grp.sym_root[s].first, grp.sym_root[s].second) << ";\n";
             if (opt.bounds_check || want_struct)
-                os << "  if ((unsigned long long)i" << s << " >= (unsigned long long)pm.nvar_m) { atomicOr(o.status, 1); return; }\n";
+                os << "  if ((unsigned long long)i" << s << " >= (unsigned long long)pm.nvar_m) { atomicOr(o.status, 1); i" << s << " = 0; }\n";
         }
         for (int pid : params) {
             int pos = pid / 65536, node = pid % 65536;
-            os << "  const long long q" << pid << " = " << idx_expr(pos, pat(pos).v[node].a) << ";\n";
+            os << "  long long q" << pid << " = " << idx_expr(pos, pat(pos).v[node].a) << ";\n";
             if (opt.bounds_check || want_struct)
-                os << "  if ((unsigned long long)q" << pid << " >= (unsigned long long)pm.npar_m) { atomicOr(o.status, 1); return; }\n";
+                os << "  if ((unsigned long long)q" << pid << " >= (unsigned long long)pm.npar_m) { atomicOr(o.status, 1); q" << pid << " = 0; }\n";
         }
         for (int pos : act) {
             if (!want[pos].row) continue;
             const Pattern &p = pat(pos);
             if (p.kind == EXA_CON) os << "  const long long row" << pos << " = pm.rbase[" << pos << "] + kk;\n";
             else {
-                os << "  const long long lrow" << pos << " = " << idx_expr(pos, p.row_root) << ";\n";
+                os << "  long long lrow" << pos << " = " << idx_expr(pos, p.row_root) << ";\n";
                 if (opt.bounds_check || want_struct)
                     os << "  if ((unsigned long long)lrow" << pos << " >= (unsigned long long)pm.rlimit[" << pos
-                       << "]) { atomicOr(o.status, 1); return; }\n";
+                       << "]) { atomicOr(o.status, 1); lrow" << pos << " = 0; }\n";
                 os << "  const long long row" << pos << " = pm.rbase[" << pos << "] + lrow" << pos << ";\n";
             }
         }
         if (want_struct) {
+            os << "  if (!act) return;\n";
             for (int pos : act) {
                 const Pattern &p = pat(pos);
                 const std::string P = std::to_string(pos);
@@ -890,13 +898,13 @@ struct Emitter {
         for (int s : syms) os << "  const double X" << s << " = __ldg(x + pm.xoff + i" << s << ");\n";
         for (int pid : params) os << "  const double P" << pid << " = __ldg(th + pm.poff + q" << pid << ");\n";
         for (int c : fconsts) os << "  const double C" << c << " = pm.fc[" << c << "];\n";
-        for (int s : fsyms) os << "  const float XF" << s << " = (float)X" << s << ";\n";
-        for (int f : ffields) os << "  const float DF" << f << " = (float)D" << f << ";\n";
-        for (int pid : fparams) os << "  const float PF" << pid << " = (float)P" << pid << ";\n";
-        for (int c : ffconsts) os << "  const float CF" << c << " = (float)C" << c << ";\n";
+        for (int s : fsyms) os << "  const float XF" << s << " = exa_d2f(X" << s << ");\n";
+        for (int f : ffields) os << "  const float DF" << f << " = exa_d2f(D" << f << ");\n";
+        for (int pid : fparams) os << "  const float PF" << pid << " = exa_d2f(P" << pid << ");\n";
+        for (int c : ffconsts) os << "  const float CF" << c << " = exa_d2f(C" << c << ");\n";
         std::map<int, std::string> name;
         body(roots, name);
-        auto widen = [&](int r) { return mixed ? "(double)" + name.at(r) : name.at(r); };
+        auto widen = [&](int r) { return mixed ? "exa_f2d(" + name.at(r) + ")" : name.at(r); };
         bool objw = false;
         for (int pos : act) {
             const Pattern &p = pat(pos);
@@ -906,29 +914,39 @@ struct Emitter {
             const bool obj = p.kind == EXA_OBJ;
             if (w.val) {
                 const std::string v = widen(G.value);
-                if (obj) { os << "  objv " << (objw ? "+=" : "=") << " " << v << ";\n"; objw = true; }
-                else if (p.kind == EXA_CON) os << "  o.c[row" << P << "] = " << v << ";\n";
-                else os << "  o.abuf[pm.abase[" << P << "] + kk] = " << v << ";\n";
+                if (obj) { os << "  objv " << (objw ? "+=" : "=") << " act ? " << v << " : 0.0;\n"; objw = true; }
+                else if (p.kind == EXA_CON) os << "  if (act) o.c[row" << P << "] = " << v << ";\n";
+                else os << "  if (act) o.abuf[pm.abase[" << P << "] + kk] = " << v << ";\n";
             }
+            // a block of S slots per instance: stage the warp's 32 x S values, then write the warp's
+            // contiguous run of nact x S values with consecutive lanes on consecutive addresses
+            auto staged = [&](const std::string &base, int S, const std::vector<std::string> &vals) {
+                os << "  __syncwarp();\n";
+                for (int j = 0; j < S; j++) os << "  ws[lane * " << S << " + " << j << "] = " << vals[j] << ";\n";
+                os << "  __syncwarp();\n"
+                   << "  { double* __restrict__ dst = " << base << " + kw * " << S << ";\n"
+                   << "    for (int e = lane; e < nact * " << S << "; e += 32) dst[e] = ws[e]; }\n";
+            };
             if (w.grad && p.nj() > 0) {
-                os << "  { double* __restrict__ GO = " << (obj ? "o.gbuf + pm.gbase[" : "o.jac + pm.jbase[") << P
-                   << "] + kk * " << p.nj() << ";\n";
-                for (int j = 0; j < p.nj(); j++) os << "    GO[" << j << "] = " << widen(G.grad[p.jsym[j]]) << ";\n";
-                os << "  }\n";
+                std::vector<std::string> vals;
+                for (int j = 0; j < p.nj(); j++) vals.push_back(widen(G.grad[p.jsym[j]]));
+                staged(std::string(obj ? "o.gbuf + pm.gbase[" : "o.jac + pm.jbase[") + P + "]", p.nj(), vals);
             }
             if (w.hess) {
-                os << "  { const " << W << " w = (" << W << ")" << (obj ? "sigma" : "__ldg(y + row" + P + ")") << ";\n";
+                os << "  { const " << W << " w = " << (obj ? (mixed ? "exa_d2f(sigma)" : "sigma")
+                                                          : (mixed ? "exa_d2f(__ldg(y + row" + P + "))" : "__ldg(y + row" + P + ")"))
+                   << ";\n";
                 os << "    const " << W << " w2 = w + w;\n";
-                os << "    double* __restrict__ HO = o.hess + pm.hbase[" << P << "] + kk * " << p.nh() << ";\n";
+                std::vector<std::string> vals;
                 for (int j = 0; j < p.nh(); j++) {
                     int a = p.hpair[j].first, b = p.hpair[j].second;
                     int r = hroots[pos][j];
                     std::string v = r >= 0 ? name.at(r) : (mixed ? "0.0f" : "0.0");
                     std::string wt = a == b ? "w" : "(i" + std::to_string(grp.sym[pos][a]) + " == i" +
                                                         std::to_string(grp.sym[pos][b]) + " ? w2 : w)";
-                    if (mixed) os << "    HO[" << j << "] = (double)(" << wt << " * " << v << ");\n";
-                    else os << "    HO[" << j << "] = " << wt << " * " << v << ";\n";
+                    vals.push_back(mixed ? "exa_f2d(" + wt + " * " + v + ")" : wt + " * " + v);
                 }
+                staged("o.hess + pm.hbase[" + P + "]", p.nh(), vals);
                 os << "  }\n";
             }
         }
@@ -943,13 +961,39 @@ struct Emitter {
 // single-precision functions.  Outside the exact range the FP64 function is used.
 // PIO2_HI / PIO2_LO: pi/2 rounded to 32 bits and the rounded remainder; LN2_HI / LN2_LO likewise
 // for ln 2 (computed with 300-bit arithmetic).
+// FP32 <-> FP64 conversions done with integer operations (the IEEE-754 encodings, round to nearest
+// even), exact for every value whose result is a normal number or zero; the remaining cases
+// (subnormal results, infinities, NaN) take the hardware conversion.  On GB300 the hardware
+// conversions issue on the narrow FP64 pipe, the integer ops do not.
 static const char *kMixedHelpers = R"(
+static __device__ __forceinline__ double exa_f2d(const float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e - 1u < 254u)
+    return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu)), (int)(u << 29));
+  if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  return (double)f;
+}
+static __device__ __forceinline__ float exa_d2f(const double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e - 897u < 254u) {
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1fffffffu;
+    const unsigned bits = (hi & 0x80000000u) | ((e - 896u) << 23) | m;
+    return __uint_as_float(bits + ((rest > 0x10000000u) | ((rest == 0x10000000u) & (m & 1u))));
+  }
+  if (((hi & 0x7fffffffu) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
+  return (float)d;
+}
+)"
+R"(
 static __device__ __forceinline__ void exa_sincos_red(const double a, float* s, float* c) {
   if (!(fabs(a) < 1.0e6)) { double sd, cd; sincos(a, &sd, &cd); *s = (float)sd; *c = (float)cd; return; }
   const double q = rint(a * 0x1.45f306dc9c883p-1);
   const double r = fma(-q, 0x1.0b4611a626331p-34, fma(-q, 0x1.921fb54400000p+0, a));
   float sr, cr;
-  sincosf((float)r, &sr, &cr);
+  sincosf(exa_d2f(r), &sr, &cr);
   switch (((int)q) & 3) {
     case 0: *s = sr; *c = cr; break;
     case 1: *s = cr; *c = -sr; break;
@@ -961,7 +1005,7 @@ static __device__ __forceinline__ float exa_exp_red(const double a) {
   if (!(fabs(a) < 80.0)) return (float)exp(a);
   const double k = rint(a * 0x1.71547652b82fep+0);
   const double r = fma(-k, -0x1.718432a1b0e26p-35, fma(-k, 0x1.62e42ff000000p-1, a));
-  return ldexpf(expf((float)r), (int)k);
+  return ldexpf(expf(exa_d2f(r)), (int)k);
 }
 )";
 
@@ -1008,15 +1052,25 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
                " const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ th,"
                " const double sigma, const ExaOut o, const ExaStructOut so) {\n";
         if (objred) src << "  __shared__ double red[EXA_BLOCK / 32];\n";
+        int smax = 1;  // widest slot block staged in this kernel
+        for (const Pattern &p : pats)
+            if (pattern_in_mode(p, (Mode)m)) smax = std::max(smax, std::max(p.nj(), p.nh()));
+        if (m != M_STRUCT)
+            src << "  __shared__ double stage[EXA_BLOCK * " << smax << "];\n"
+                   "  double* __restrict__ ws = stage + (threadIdx.x & ~31u) * " << smax << ";\n";
+        else
+            src << "  double* ws = nullptr;\n";
         src << "  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {\n"
                "  const ExaTile tl = tiles[t];\n"
                "  const ExaPM& pm = pms[tl.pm];\n"
-               "  const int k = tl.begin + (int)threadIdx.x;\n"
+               "  const int k0 = tl.begin + (int)threadIdx.x;\n"
+               "  const bool act = k0 < pm.n_inst;\n"
+               "  const int k = act ? k0 : (int)pm.n_inst - 1;\n"
                "  double objv = 0.0;\n"
-               "  if (k < pm.n_inst) {\n"
+               "  if (__any_sync(0xffffffffu, act)) {\n"
                "    switch (pm.grp) {\n";
         for (int gi : gl)
-            src << "      case " << gi << ": grp" << gi << "_" << kModeName[m] << "(pm, k, x, y, th, sigma, o, so, objv); break;\n";
+            src << "      case " << gi << ": grp" << gi << "_" << kModeName[m] << "(pm, k, act, x, y, th, sigma, o, so, objv, ws); break;\n";
         src << "      default: break;\n    }\n  }\n";
         if (objred) {
             src << "  if (tl.oslot >= 0) {\n"

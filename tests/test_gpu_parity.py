@@ -251,3 +251,32 @@ def test_full_batch_sampled_members():
         assert normwise(jb[mb.joff[i]:mb.joff[i + 1]], o.jac_coord(xi)) <= TOL
         assert normwise(hb[mb.hoff[i]:mb.hoff[i + 1]], o.hess_coord(xi, yi, si)) <= TOL
         assert normwise(cb[mb.coff[i]:mb.coff[i + 1]], o.cons(xi)) <= TOL
+
+
+def test_eval_all_graph_replay_matches_direct_launches():
+    """exa_eval_all replays a cached CUDA graph; results equal those of direct launches, also
+    after switching between argument tuples and after changing x in place."""
+    B = _B()
+    wl = synth.acopf(200, 300, 40, seed=8)
+    x, y, s = synth.acopf_point(wl, 1)
+    mg = B.exa_create(wl.flat)
+    md = B.exa_create(wl.flat, flags=B.EXA_FLAG_NO_GRAPH)
+    xt, yt = _t(x), _t(y)
+    outs = {}
+    for name, m in (("graph", mg), ("direct", md)):
+        res = []
+        for sigma in (1.0, 0.5, 1.0):
+            o = {k: torch.empty(n, dtype=torch.float64, device="cuda") for k, n in
+                 (("f", 1), ("g", m.nvar), ("c", m.ncon), ("jac", m.nnzj), ("hess", m.nnzh),
+                  ("jac_csc", m.nnzj_csc), ("hess_csc", m.nnzh_csc))}
+            m.exa_eval_all(xt, yt, sigma, **o)
+            m.exa_eval_all(xt, yt, sigma, **o)  # second call with the same tuple replays
+            res.append({k: v.clone() for k, v in o.items()})
+        xt.mul_(1.01)
+        m.exa_eval_all(xt, yt, 1.0, **o)
+        res.append({k: v.clone() for k, v in o.items()})
+        xt.div_(1.01)
+        outs[name] = res
+    for a, b in zip(outs["graph"], outs["direct"]):
+        for k in a:
+            assert torch.equal(a[k], b[k]), k
