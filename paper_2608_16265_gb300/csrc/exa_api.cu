@@ -49,14 +49,31 @@ __global__ void k_obj_final(const double *__restrict__ part, int n, double *__re
     }
 }
 
-// dst[i] = sum_{q in [ptr[i], ptr[i+1])} src[perm[q]]  (ascending q: ascending COO index)
-__global__ void k_seg_sum(const int *__restrict__ ptr, const int *__restrict__ perm,
-                          const double *__restrict__ src, double *__restrict__ dst, int n) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double s = 0.0;
-    for (int q = ptr[i], e = ptr[i + 1]; q < e; q++) s += src[perm[q]];
-    dst[i] = s;
+// dst[i] = sum_{q in [ptr[i], ptr[i+1])} src[perm[q]], q ascending (ascending COO index).  One warp
+// per 32 consecutive segments: the warp first gathers the values of its segments (one contiguous
+// range of sorted positions) into shared memory with every lane loading in parallel, then each lane
+// adds its own segment in ascending order.
+#define EXA_SEG_CHUNK 256
+__global__ void __launch_bounds__(256) k_seg_sum_warp(const int *__restrict__ ptr, const int *__restrict__ perm,
+                                                      const double *__restrict__ src, double *__restrict__ dst, int n) {
+    __shared__ double buf[8][EXA_SEG_CHUNK];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long s0 = ((long long)blockIdx.x * 8 + w) * 32;
+    if (s0 >= n) return;
+    const int s = (int)s0 + lane;
+    const bool valid = s < n;
+    const int beg = ptr[s0], end = ptr[min((long long)n, s0 + 32)];
+    const int myb = valid ? ptr[s] : end, mye = valid ? ptr[s + 1] : end;
+    double acc = 0.0;
+    for (int c0 = beg; c0 < end; c0 += EXA_SEG_CHUNK) {
+        const int c1 = min(c0 + EXA_SEG_CHUNK, end);
+        for (int e = c0 + lane; e < c1; e += 32) buf[w][e - c0] = __ldg(src + __ldg(perm + e));
+        __syncwarp();
+        const int qb = max(myb, c0), qe = min(mye, c1);
+        for (int q = qb; q < qe; q++) acc += buf[w][q - c0];
+        __syncwarp();
+    }
+    if (valid) dst[s] = acc;
 }
 
 // dst[i] = src[perm[i]]  (CSC of a COO pattern without duplicate entries: a pure permutation)
@@ -1111,7 +1128,7 @@ exa_status exa_grad(exa_model *m, const double *x, double *g) {
     o.gbuf = m->d_gbuf;
     if (exa_status e = launch_eval(m, exa::M_GRAD, x, nullptr, 0.0, o)) return e;
     if (m->nvar) {
-        k_seg_sum<<<grid_of(m->nvar, 256), 256, 0, m->stream>>>(m->d_gptr, m->d_gperm, m->d_gbuf, g, (int)m->nvar);
+        k_seg_sum_warp<<<grid_of(m->nvar, 256), 256, 0, m->stream>>>(m->d_gptr, m->d_gperm, m->d_gbuf, g, (int)m->nvar);
         CR(cudaGetLastError());
     }
     return EXA_OK;
@@ -1204,7 +1221,7 @@ static exa_status scatter_csc(exa_model *m, const int *segptr, const int *perm, 
                               i64 n, i64 nnz) {
     if (!n) return EXA_OK;
     if (n == nnz) k_permute<<<grid_of(n, 256), 256, 0, m->stream>>>(perm, coo, csc, (int)n);
-    else k_seg_sum<<<grid_of(n, 256), 256, 0, m->stream>>>(segptr, perm, coo, csc, (int)n);
+    else k_seg_sum_warp<<<grid_of(n, 256), 256, 0, m->stream>>>(segptr, perm, coo, csc, (int)n);
     CR(cudaGetLastError());
     return EXA_OK;
 }
@@ -1215,6 +1232,12 @@ exa_status exa_jac_csc(exa_model *m, const double *x, double *vals_csc) {
     CHECK_PTRS(x, vals_csc);
     ExaOut o{};
     o.jac = m->d_jbuf;
+    if (m->nnzj_csc == m->nnzj) {  // permutation: written directly by the evaluation kernel
+        o.jac = nullptr;
+        o.jcsc = vals_csc;
+        o.jmap = m->d_jcoo2csc;
+        return launch_eval(m, exa::M_JAC, x, nullptr, 0.0, o);
+    }
     if (exa_status e = launch_eval(m, exa::M_JAC, x, nullptr, 0.0, o)) return e;
     return scatter_csc(m, m->d_jsegptr, m->d_jperm, m->d_jbuf, vals_csc, m->nnzj_csc, m->nnzj);
 }
@@ -1226,6 +1249,12 @@ exa_status exa_hess_csc(exa_model *m, const double *x, const double *y, double s
     if (m->ncon && !y) return fail(m, EXA_E_INVALID, "NULL y");
     ExaOut o{};
     o.hess = m->d_hbuf;
+    if (m->nnzh_csc == m->nnzh) {
+        o.hess = nullptr;
+        o.hcsc = vals_csc;
+        o.hmap = m->d_hcoo2csc;
+        return launch_eval(m, exa::M_HESS, x, y, sigma, o);
+    }
     if (exa_status e = launch_eval(m, exa::M_HESS, x, y, sigma, o)) return e;
     return scatter_csc(m, m->d_hsegptr, m->d_hperm, m->d_hbuf, vals_csc, m->nnzh_csc, m->nnzh);
 }
@@ -1241,6 +1270,19 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
     o.gbuf = m->d_gbuf;
     o.jac = jac ? jac : m->d_jbuf;
     o.hess = hess ? hess : m->d_hbuf;
+    // a CSC without duplicates is a permutation of the COO slots: the evaluation kernel writes it
+    // directly, and the COO copy is skipped when the caller did not ask for it
+    const bool jdirect = jac_csc && m->nnzj_csc == m->nnzj, hdirect = hess_csc && m->nnzh_csc == m->nnzh;
+    if (jdirect) {
+        o.jcsc = jac_csc;
+        o.jmap = m->d_jcoo2csc;
+        if (!jac) o.jac = nullptr;
+    }
+    if (hdirect) {
+        o.hcsc = hess_csc;
+        o.hmap = m->d_hcoo2csc;
+        if (!hess) o.hess = nullptr;
+    }
     Mode mode = want_h ? exa::M_ALL : exa::M_FIRST;
     if (exa_status e = launch_eval(m, mode, x, y, sigma, o)) return e;
     if (f) {
@@ -1248,14 +1290,14 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
         CR(cudaGetLastError());
     }
     if (g && m->nvar) {
-        k_seg_sum<<<grid_of(m->nvar, 256), 256, 0, m->stream>>>(m->d_gptr, m->d_gperm, m->d_gbuf, g, (int)m->nvar);
+        k_seg_sum_warp<<<grid_of(m->nvar, 256), 256, 0, m->stream>>>(m->d_gptr, m->d_gperm, m->d_gbuf, g, (int)m->nvar);
         CR(cudaGetLastError());
     }
     if (c)
         if (exa_status e = aug_rows(m, c)) return e;
-    if (jac_csc)
+    if (jac_csc && !jdirect)
         if (exa_status e = scatter_csc(m, m->d_jsegptr, m->d_jperm, o.jac, jac_csc, m->nnzj_csc, m->nnzj)) return e;
-    if (hess_csc)
+    if (hess_csc && !hdirect)
         if (exa_status e = scatter_csc(m, m->d_hsegptr, m->d_hperm, o.hess, hess_csc, m->nnzh_csc, m->nnzh)) return e;
     return EXA_OK;
 }

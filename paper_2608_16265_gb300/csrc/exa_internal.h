@@ -45,6 +45,10 @@
         double *gbuf;             /* objective gradient slots */                                    \
         double *jac;              /* Jacobian COO values */                                         \
         double *hess;             /* Hessian COO values */                                          \
+        double *jcsc;             /* if set: Jacobian CSC values written directly (no duplicates) */\
+        const int *jmap;          /* Jacobian COO slot -> CSC position */                           \
+        double *hcsc;             /* if set: Hessian CSC values written directly (no duplicates) */ \
+        const int *hmap;          /* Hessian COO slot -> CSC position */                            \
         int *status;              /* device fault word (bounds) */                                  \
     };                                                                                              \
     struct ExaStructOut {                                                                           \

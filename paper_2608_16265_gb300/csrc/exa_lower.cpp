@@ -920,17 +920,25 @@ struct Emitter {
             }
             // a block of S slots per instance: stage the warp's 32 x S values, then write the warp's
             // contiguous run of nact x S values with consecutive lanes on consecutive addresses
-            auto staged = [&](const std::string &base, int S, const std::vector<std::string> &vals) {
+            // csc/map: optional direct CSC output (a pure permutation of the COO slots); out/slot are
+            // the COO array and the block's first slot
+            auto staged = [&](const std::string &out, const std::string &slot0, int S, const std::vector<std::string> &vals,
+                              const char *csc, const char *map) {
                 os << "  __syncwarp();\n";
                 for (int j = 0; j < S; j++) os << "  ws[lane * " << S << " + " << j << "] = " << vals[j] << ";\n";
                 os << "  __syncwarp();\n"
-                   << "  { double* __restrict__ dst = " << base << " + kw * " << S << ";\n"
-                   << "    for (int e = lane; e < nact * " << S << "; e += 32) dst[e] = ws[e]; }\n";
+                   << "  { const long long q0 = " << slot0 << " + kw * " << S << ";\n"
+                   << "    if (" << out << ") for (int e = lane; e < nact * " << S << "; e += 32) " << out << "[q0 + e] = ws[e];\n";
+                if (csc)
+                    os << "    if (" << csc << ") for (int e = lane; e < nact * " << S << "; e += 32) "
+                       << csc << "[" << map << "[q0 + e]] = ws[e];\n";
+                os << "  }\n";
             };
             if (w.grad && p.nj() > 0) {
                 std::vector<std::string> vals;
                 for (int j = 0; j < p.nj(); j++) vals.push_back(widen(G.grad[p.jsym[j]]));
-                staged(std::string(obj ? "o.gbuf + pm.gbase[" : "o.jac + pm.jbase[") + P + "]", p.nj(), vals);
+                if (obj) staged("o.gbuf", "pm.gbase[" + P + "]", p.nj(), vals, nullptr, nullptr);
+                else staged("o.jac", "pm.jbase[" + P + "]", p.nj(), vals, "o.jcsc", "o.jmap");
             }
             if (w.hess) {
                 os << "  { const " << W << " w = " << (obj ? (mixed ? "exa_d2f(sigma)" : "sigma")
@@ -946,7 +954,7 @@ struct Emitter {
                                                         std::to_string(grp.sym[pos][b]) + " ? w2 : w)";
                     vals.push_back(mixed ? "exa_f2d(" + wt + " * " + v + ")" : wt + " * " + v);
                 }
-                staged("o.hess + pm.hbase[" + P + "]", p.nh(), vals);
+                staged("o.hess", "pm.hbase[" + P + "]", p.nh(), vals, "o.hcsc", "o.hmap");
                 os << "  }\n";
             }
         }
