@@ -312,10 +312,15 @@ class Graph {
         if (n[a].op == S_NEG) return n[a].a;
         return node(S_NEG, P(a), a);
     }
+    // Negations are pulled outward ((-a) b = -(a b), a + (-b) = a - b, ...; exact in IEEE
+    // arithmetic) so that expressions differing only in signs share one node.
+    bool isneg(int i) const { return n[i].op == S_NEG; }
     int add(int a, int b) {
         if (zero(a)) return b;
         if (zero(b)) return a;
         if (is_lit(a) && is_lit(b)) return lit(fold(n[a].lit + n[b].lit, P(a)), P(a));
+        if (isneg(b)) return sub(a, n[b].a);
+        if (isneg(a)) return sub(b, n[a].a);
         if (a > b) std::swap(a, b);  // a + b == b + a exactly
         return node(S_ADD, P(a), a, b);
     }
@@ -323,6 +328,8 @@ class Graph {
         if (zero(b)) return a;
         if (zero(a)) return neg(b);
         if (is_lit(a) && is_lit(b)) return lit(fold(n[a].lit - n[b].lit, P(a)), P(a));
+        if (isneg(b)) return add(a, n[b].a);
+        if (isneg(a)) return neg(add(n[a].a, b));
         if (a > b) return neg(node(S_SUB, P(a), b, a));  // a - b == -(b - a) exactly: one canonical form
         return node(S_SUB, P(a), a, b);
     }
@@ -333,6 +340,8 @@ class Graph {
         if (is(a, -1.0)) return neg(b);
         if (is(b, -1.0)) return neg(a);
         if (is_lit(a) && is_lit(b)) return lit(fold(n[a].lit * n[b].lit, P(a)), P(a));
+        if (isneg(a)) return neg(mul(n[a].a, b));
+        if (isneg(b)) return neg(mul(a, n[b].a));
         if (a > b) std::swap(a, b);
         return node(S_MUL, P(a), a, b);
     }
@@ -340,6 +349,8 @@ class Graph {
         if (is(b, 1.0)) return a;
         if (zero(a)) return lit(0.0, P(a));
         if (is_lit(a) && is_lit(b)) return lit(fold(n[a].lit / n[b].lit, P(a)), P(a));
+        if (isneg(a)) return neg(div(n[a].a, b));
+        if (isneg(b)) return neg(div(a, n[b].a));
         return node(S_DIV, P(a), a, b);
     }
     int fn(int op, int a) { return fn_at(op, P(a), a); }
