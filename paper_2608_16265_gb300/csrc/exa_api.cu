@@ -880,6 +880,7 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
         const exa_model_desc &d = *descs[b];
         if (d.npar) CR(cudaMemcpy(m->d_theta + poff[b], d.theta, sizeof(double) * d.npar, cudaMemcpyHostToDevice));
         std::map<const void *, const void *> uploaded;
+        std::map<const void *, float *> uploaded32;
         for (int gi = 0; gi < ng; gi++) {
             const exa::Group &G = m->groups[gi];
             ExaPM &pm = pms[(size_t)b * ng + gi];
@@ -917,6 +918,21 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
                     pm.f[c] = dp;
                     uploaded[h] = dp;
                 }
+                if (m->precision == EXA_MIXED_FP32)  // FP32 copies of f64 columns
+                    for (int f = 0; f < pd.n_fields; f++) {
+                        const int c = G.field[pos][f];
+                        if (pd.fields[f].type != EXA_FIELD_F64 || pm.f32[c]) continue;
+                        const void *h = pd.fields[f].data;
+                        auto it = uploaded32.find(h);
+                        if (it != uploaded32.end() && pd.n_inst > 0) { pm.f32[c] = it->second; continue; }
+                        std::vector<float> tmp((size_t)pd.n_inst);
+                        for (i64 i = 0; i < pd.n_inst; i++) tmp[i] = (float)((const double *)h)[i];
+                        float *dp = nullptr;
+                        CR(dalloc(m, &dp, pd.n_inst));
+                        if (pd.n_inst) CR(cudaMemcpy(dp, tmp.data(), sizeof(float) * pd.n_inst, cudaMemcpyHostToDevice));
+                        pm.f32[c] = dp;
+                        uploaded32[h] = dp;
+                    }
             }
         }
     }

@@ -17,6 +17,7 @@
 #define EXA_DEVICE_STRUCTS                                                                          \
     struct ExaPM {                /* one (batch member, fused pattern group) pair */               \
         const void *f[16];        /* device data columns of the group (shared columns once) */     \
+        const float *f32[16];     /* mixed mode: FP32 copies of the f64 columns */                  \
         long long n_inst;         /* instances (equal for every pattern of the group) */           \
         long long xoff;           /* first variable of the member */                                \
         long long nvar_m;         /* variables of the member */                                     \

@@ -844,7 +844,26 @@ struct Emitter {
                 for (auto &pr : p.hpair)
                     if (pr.first != pr.second) { idx_syms.insert(grp.sym[pos][pr.first]); idx_syms.insert(grp.sym[pos][pr.second]); }
         }
-        std::set<int> all_fields = fields;
+        // columns used as FP64 values (D) and as FP32 values (DF); in mixed mode f64 columns have an
+        // FP32 copy (pm.f32) that FP32 uses load directly
+        std::set<int> dfields, fcopy;
+        {
+            std::vector<char> seen(g.n.size(), 0);
+            std::function<void(int)> walk = [&](int i) {
+                if (seen[i]) return;
+                seen[i] = 1;
+                const SN &sn = g.n[i];
+                if (sn.op == S_IN && sn.ikind == 'D') {
+                    if (sn.prec == PD) dfields.insert(sn.iid);
+                    else if (grp.ftype[sn.iid] == EXA_FIELD_F64) fcopy.insert(sn.iid);
+                    else dfields.insert(sn.iid);  // int32 column used as an FP32 value: convert the int
+                }
+                if (sn.a >= 0) walk(sn.a);
+                if (sn.b >= 0) walk(sn.b);
+            };
+            for (int r : roots) walk(r);
+        }
+        std::set<int> all_fields = dfields;
         for (int s : idx_syms) fields_of_idx(grp.sym_root[s].first, grp.sym_root[s].second, all_fields);
         for (int pid : params) fields_of_idx(pid / 65536, pat(pid / 65536).v[pid % 65536].a, all_fields);
         for (int pos : act)
@@ -855,8 +874,9 @@ struct Emitter {
             else
                 os << "  const double F" << f << " = __ldg((const double*)pm.f[" << f << "] + k);\n";
         }
-        for (int f : fields)
+        for (int f : dfields)
             os << "  const double D" << f << " = " << (grp.ftype[f] == EXA_FIELD_I32 ? "(double)F" : "F") << f << ";\n";
+        for (int f : fcopy) os << "  const float DF" << f << " = __ldg(pm.f32[" << f << "] + k);\n";
         for (int s : idx_syms) {
             os << "  long long i" << s << " = " << idx_expr(grp.sym_root[s].first, grp.sym_root[s].second) << ";\n";
             if (opt.bounds_check || want_struct)
@@ -910,7 +930,8 @@ struct Emitter {
         for (int pid : params) os << "  const double P" << pid << " = __ldg(th + pm.poff + q" << pid << ");\n";
         for (int c : fconsts) os << "  const double C" << c << " = pm.fc[" << c << "];\n";
         for (int s : fsyms) os << "  const float XF" << s << " = exa_d2f(X" << s << ");\n";
-        for (int f : ffields) os << "  const float DF" << f << " = exa_d2f(D" << f << ");\n";
+        for (int f : ffields)
+            if (!fcopy.count(f)) os << "  const float DF" << f << " = (float)F" << f << ";\n";  // int32 column
         for (int pid : fparams) os << "  const float PF" << pid << " = exa_d2f(P" << pid << ");\n";
         for (int c : ffconsts) os << "  const float CF" << c << " = exa_d2f(C" << c << ");\n";
         std::map<int, std::string> name;
