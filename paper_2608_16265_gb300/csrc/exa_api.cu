@@ -203,6 +203,8 @@ struct exa_model {
     int nobj[exa::M_COUNT] = {};  // objective partial sums written by each kernel kind
     int grid[exa::M_COUNT] = {};  // CTAs launched per kernel kind (<= ntiles: persistent tile loop)
     int persist = 0;              // persistent grid factor chosen by the tuner (0: one CTA per tile)
+    bool split_all = false;       // exa_eval_all: first- and second-order kernels instead of one
+    bool csc_direct = false;      // duplicate-free CSC written by the evaluation kernel (scatter)
     std::vector<ExaPM> h_pms;     // host copy of the group descriptors
     // CUDA graphs of exa_eval_all, one per argument tuple
     struct GraphEntry {
@@ -223,6 +225,12 @@ struct exa_model {
     // Hessian: same
     int *d_hperm = nullptr, *d_hsegptr = nullptr, *d_hcolptr = nullptr, *d_hrowval = nullptr, *d_hcoo2csc = nullptr;
     int *d_hcolptr_coo = nullptr, *d_hrperm = nullptr, *d_hrptr = nullptr;
+    // compressed Hessian (per-instance sums of a group's slots with equal (row, col)): structure,
+    // permutation sorted by (col, row) and segment pointers per Hessian CSC entry
+    i64 nnzhc = 0;
+    bool use_hcomp = false;
+    int *d_hcrow = nullptr, *d_hccol = nullptr, *d_hcperm = nullptr, *d_hcsegptr = nullptr;
+    double *d_hcbuf = nullptr;
     // gradient and augmentation segments
     int *d_gperm = nullptr, *d_gptr = nullptr;
     int *d_aperm = nullptr, *d_aptr = nullptr, *d_arows = nullptr;
@@ -234,6 +242,12 @@ struct exa_model {
     double nvrtc_ms = 0, create_ms = 0, tune_ms = 0;
     std::string err;
 };
+
+extern "C" {
+static exa_status eval_all_launches(exa_model *m, const double *x, const double *y, double sigma, double *f,
+                                    double *g, double *c, double *jac, double *hess, double *jac_csc,
+                                    double *hess_csc);
+}
 
 namespace {
 
@@ -470,6 +484,21 @@ exa_status build_structure(exa_model *m) {
     if (exa_status e = sort_with_perm(m, S, keys, nh, 32, &skeys, m->d_hrperm)) return e;
     if (exa_status e = build_ptr(m, skeys, 0, nh, m->nvar, &m->d_hrptr)) return e;
 
+    // ---- compressed Hessian: its (col, row)-sorted segments are the Hessian CSC entries
+    if (m->use_hcomp) {
+        const int nc = (int)m->nnzhc;
+        unsigned long long *ck = nullptr;
+        CR(S.get(&ck, nc));
+        CR(dalloc(m, &m->d_hcperm, nc));
+        k_keys2<<<grid_of(nc, 256), 256, 0, m->stream>>>(m->d_hccol, m->d_hcrow, ck, nc);
+        CR(cudaGetLastError());
+        if (exa_status e = sort_with_perm(m, S, ck, nc, 64, &skeys, m->d_hcperm)) return e;
+        int nsc = 0;
+        if (exa_status e = segments(m, S, skeys, m->d_hcperm, nc, &nsc, &m->d_hcsegptr, &segkey, nullptr, true)) return e;
+        if (nsc != m->nnzh_csc) return fail(m, EXA_E_INTERNAL, "compressed Hessian does not cover the CSC entries");
+        CR(dalloc(m, &m->d_hcbuf, nc));
+    }
+
     // ---- gradient segments by variable
     CR(dalloc(m, &m->d_gperm, ng));
     if (ng) {
@@ -657,12 +686,42 @@ exa_status autotune(exa_model *m) {
             }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (m->block != best_block)
         if (exa_status e = setup_kernels(m, best_block)) return e;
     if (exa_status e = apply_grid(m, best_factor)) return e;
     m->tune_ms = best / 5.0;
+    // exa_eval_all with every output: one kernel or first/second order split, CSC by a separate
+    // permutation kernel or scattered by the evaluation kernel
+    double *f = nullptr, *g = nullptr, *jc = nullptr, *hc = nullptr;
+    CR(S.get(&f, 1));
+    CR(S.get(&g, m->nvar));
+    CR(S.get(&jc, m->nnzj_csc));
+    CR(S.get(&hc, m->nnzh_csc));
+    double best_step = 1e30;
+    bool best_split = false, best_direct = false;
+    for (int split = 0; split < 2; split++)
+        for (int direct = 0; direct < 2; direct++) {
+            if (direct && m->nnzj_csc != m->nnzj && m->nnzh_csc != m->nnzh) continue;
+            m->split_all = split;
+            m->csc_direct = direct;
+            if (exa_status e = eval_all_launches(m, x, y, 1.0, f, g, m->d_cbuf, m->d_jbuf, m->d_hbuf, jc, hc)) return e;
+            CR(cudaEventRecord(e0, m->stream));
+            for (int r = 0; r < 3; r++)
+                if (exa_status e = eval_all_launches(m, x, y, 1.0, f, g, m->d_cbuf, m->d_jbuf, m->d_hbuf, jc, hc)) return e;
+            CR(cudaEventRecord(e1, m->stream));
+            CR(cudaEventSynchronize(e1));
+            float ms = 0;
+            CR(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_step) {
+                best_step = ms;
+                best_split = split;
+                best_direct = direct;
+            }
+        }
+    m->split_all = best_split;
+    m->csc_direct = best_direct;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     return EXA_OK;
 }
 
@@ -892,6 +951,8 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
             pm.npar_m = d.npar;
             pm.grp = gi;
             pm.member = b;
+            pm.hcbase = m->nnzhc;
+            m->nnzhc += pm.n_inst * (i64)G.hc.size();
             for (size_t pos = 0; pos < G.pats.size(); pos++) {
                 const int p = G.pats[pos];
                 const exa::Pattern &P = m->pats[p];
@@ -949,10 +1010,16 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     CR(dalloc(m, &m->d_hcol, m->nnzh));
     CR(dalloc(m, &m->d_gvar, m->nnzg));
     CR(dalloc(m, &m->d_arow, m->naug));
+    m->use_hcomp = m->nnzhc < m->nnzh;
+    if (m->use_hcomp) {
+        CR(dalloc(m, &m->d_hcrow, m->nnzhc));
+        CR(dalloc(m, &m->d_hccol, m->nnzhc));
+    }
     if (m->ntiles[exa::M_STRUCT]) {
         ExaOut out{};
         out.status = m->d_status;
-        ExaStructOut so{m->d_jrow, m->d_jcol, m->d_hrow, m->d_hcol, m->d_gvar, m->d_arow, m->d_status};
+        ExaStructOut so{m->d_jrow, m->d_jcol, m->d_hrow, m->d_hcol, m->d_gvar, m->d_arow,
+                        m->use_hcomp ? m->d_hcrow : nullptr, m->use_hcomp ? m->d_hccol : nullptr, m->d_status};
         const double *nul = nullptr;
         double sigma = 0;
         int nt = m->ntiles[exa::M_STRUCT];
@@ -972,13 +1039,19 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     CR(dalloc(m, &m->d_gbuf, m->nnzg));
     CR(dalloc(m, &m->d_abuf, m->naug));
     CR(dalloc(m, &m->d_cbuf, m->ncon));
+    {  // objective partials: one per objective tile, sized for the smallest tile the tuner tries
+        i64 maxt = 1;
+        for (const ExaPM &pm : m->h_pms) {
+            bool obj = false;
+            for (int p : m->groups[pm.grp].pats) obj = obj || m->pats[p].kind == EXA_OBJ;
+            if (obj) maxt += (pm.n_inst + 31) / 32;
+        }
+        CR(dalloc(m, &m->d_objpart, maxt));
+    }
     if (!(o.flags & EXA_FLAG_NO_TUNE) && !o.block_threads && o.grid_factor == 0)
         if (exa_status e = autotune(m)) return e;
     if (o.grid_factor != 0)
         if (exa_status e = apply_grid(m, std::max(o.grid_factor, 0))) return e;
-    int maxt = 1;
-    for (int k = 0; k < exa::M_COUNT; k++) maxt = std::max(maxt, m->nobj[k]);
-    CR(dalloc(m, &m->d_objpart, maxt));
     CR(cudaDeviceSynchronize());
     m->create_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return EXA_OK;
@@ -1271,6 +1344,15 @@ exa_status exa_hess_csc(exa_model *m, const double *x, const double *y, double s
         o.hmap = m->d_hcoo2csc;
         return launch_eval(m, exa::M_HESS, x, y, sigma, o);
     }
+    if (m->use_hcomp) {
+        o.hess = nullptr;
+        o.hcomp = m->d_hcbuf;
+        if (exa_status e = launch_eval(m, exa::M_HESS, x, y, sigma, o)) return e;
+        k_seg_sum_warp<<<grid_of(m->nnzh_csc, 256), 256, 0, m->stream>>>(m->d_hcsegptr, m->d_hcperm, m->d_hcbuf,
+                                                                           vals_csc, (int)m->nnzh_csc);
+        CR(cudaGetLastError());
+        return EXA_OK;
+    }
     if (exa_status e = launch_eval(m, exa::M_HESS, x, y, sigma, o)) return e;
     return scatter_csc(m, m->d_hsegptr, m->d_hperm, m->d_hbuf, vals_csc, m->nnzh_csc, m->nnzh);
 }
@@ -1288,7 +1370,8 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
     o.hess = hess ? hess : m->d_hbuf;
     // a CSC without duplicates is a permutation of the COO slots: the evaluation kernel writes it
     // directly, and the COO copy is skipped when the caller did not ask for it
-    const bool jdirect = jac_csc && m->nnzj_csc == m->nnzj, hdirect = hess_csc && m->nnzh_csc == m->nnzh;
+    const bool jdirect = m->csc_direct && jac_csc && m->nnzj_csc == m->nnzj;
+    const bool hdirect = m->csc_direct && hess_csc && m->nnzh_csc == m->nnzh;
     if (jdirect) {
         o.jcsc = jac_csc;
         o.jmap = m->d_jcoo2csc;
@@ -1299,8 +1382,26 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
         o.hmap = m->d_hcoo2csc;
         if (!hess) o.hess = nullptr;
     }
+    const bool hcomp = hess_csc && !hdirect && m->use_hcomp;
+    if (hcomp) {  // the CSC sums read the group-compressed entries instead of the COO slots
+        o.hcomp = m->d_hcbuf;
+        if (!hess) o.hess = nullptr;
+    }
     Mode mode = want_h ? exa::M_ALL : exa::M_FIRST;
-    if (exa_status e = launch_eval(m, mode, x, y, sigma, o)) return e;
+    if (want_h && m->split_all) {  // first order and second order as two kernels
+        ExaOut o1 = o, o2{};
+        o1.hess = nullptr;
+        o1.hcsc = nullptr;
+        o2.hess = o.hess;
+        o2.hcsc = o.hcsc;
+        o2.hmap = o.hmap;
+        o2.hcomp = o.hcomp;
+        mode = exa::M_FIRST;
+        if (exa_status e = launch_eval(m, exa::M_FIRST, x, y, sigma, o1)) return e;
+        if (exa_status e = launch_eval(m, exa::M_HESS, x, y, sigma, o2)) return e;
+    } else if (exa_status e = launch_eval(m, mode, x, y, sigma, o)) {
+        return e;
+    }
     if (f) {
         k_obj_final<<<1, 256, 0, m->stream>>>(m->d_objpart, m->nobj[mode], f);
         CR(cudaGetLastError());
@@ -1313,7 +1414,10 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
         if (exa_status e = aug_rows(m, c)) return e;
     if (jac_csc && !jdirect)
         if (exa_status e = scatter_csc(m, m->d_jsegptr, m->d_jperm, o.jac, jac_csc, m->nnzj_csc, m->nnzj)) return e;
-    if (hess_csc && !hdirect)
+    if (hcomp)
+        k_seg_sum_warp<<<grid_of(m->nnzh_csc, 256), 256, 0, m->stream>>>(m->d_hcsegptr, m->d_hcperm, m->d_hcbuf,
+                                                                           hess_csc, (int)m->nnzh_csc);
+    else if (hess_csc && !hdirect)
         if (exa_status e = scatter_csc(m, m->d_hsegptr, m->d_hperm, o.hess, hess_csc, m->nnzh_csc, m->nnzh)) return e;
     return EXA_OK;
 }
@@ -1467,6 +1571,9 @@ exa_status exa_stat(const exa_model *m, const char *key, double *value) {
     else if (k == "eval_persist") *value = m->persist;
     else if (k == "eval_grid") *value = m->grid[exa::M_ALL];
     else if (k == "tune_ms") *value = m->tune_ms;
+    else if (k == "eval_split") *value = m->split_all;
+    else if (k == "csc_direct") *value = m->csc_direct;
+    else if (k == "nnzh_compressed") *value = (double)m->nnzhc;
     else if (k == "eval_tiles") *value = m->ntiles[exa::M_ALL];
     else if (k == "device_bytes") *value = (double)m->device_bytes;
     else if (k == "n_patterns") *value = (double)m->pats.size();

@@ -31,6 +31,7 @@
         long long hbase[16];      /* per pattern: first Hessian COO slot */                         \
         long long gbase[16];      /* per pattern: first gradient-buffer slot */                     \
         long long abase[16];      /* per pattern: first augmentation-buffer entry */                \
+        long long hcbase;         /* first slot of the group's compressed Hessian sums */           \
         int grp;                  /* group id */                                                    \
         int member;               /* batch member */                                                \
     };                                                                                              \
@@ -50,10 +51,11 @@
         const int *jmap;          /* Jacobian COO slot -> CSC position */                           \
         double *hcsc;             /* if set: Hessian CSC values written directly (no duplicates) */ \
         const int *hmap;          /* Hessian COO slot -> CSC position */                            \
+        double *hcomp;            /* if set: per-instance sums of the group's equal Hessian pairs */\
         int *status;              /* device fault word (bounds) */                                  \
     };                                                                                              \
     struct ExaStructOut {                                                                           \
-        int *jrow, *jcol, *hrow, *hcol, *gvar, *arow;                                               \
+        int *jrow, *jcol, *hrow, *hcol, *gvar, *arow, *hcrow, *hccol;                               \
         int *status;                                                                                \
     };
 
@@ -98,6 +100,10 @@ struct Group {
     std::vector<std::vector<int>> sym;      // [position][pattern symbol] -> group symbol
     std::vector<std::pair<int, int>> sym_root;  // group symbol -> (position, index root) defining it
     int nic = 0, nfc = 0;                   // member-varying constant slots in use
+    // compressed Hessian: slots of the group's patterns over the same pair of group symbols (the
+    // same (row, col) for every instance), summed per instance; each entry lists (position, slot)
+    std::vector<std::vector<std::pair<int, int>>> hc;
+    std::vector<std::pair<int, int>> hc_sym;  // group symbol pair of each compressed slot
 };
 
 // Unifies the symbols of a group's patterns: equal index expressions (columns compared as group

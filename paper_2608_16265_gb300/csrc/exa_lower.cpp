@@ -649,6 +649,21 @@ void finalize_group(Group &g, const std::vector<Pattern> &pats) {
             g.sym[pos][s] = r.first->second;
         }
     }
+    g.hc.clear();
+    g.hc_sym.clear();
+    std::map<std::pair<int, int>, int> slot;
+    for (size_t pos = 0; pos < g.pats.size(); pos++) {
+        const Pattern &p = pats[g.pats[pos]];
+        for (int j = 0; j < p.nh(); j++) {
+            int a = g.sym[pos][p.hpair[j].first], b = g.sym[pos][p.hpair[j].second];
+            auto r = slot.emplace(std::make_pair(std::min(a, b), std::max(a, b)), (int)g.hc.size());
+            if (r.second) {
+                g.hc.emplace_back();
+                g.hc_sym.push_back(r.first->first);
+            }
+            g.hc[r.first->second].push_back({(int)pos, j});
+        }
+    }
 }
 
 bool pattern_in_mode(const Pattern &p, Mode m) {
@@ -923,6 +938,16 @@ struct Emitter {
                        << "    so.hcol[pm.hbase[" << P << "] + kk * " << p.nh() << " + " << j << "] = (int)(ga > gb ? gb : ga); }\n";
                 }
             }
+            const int nhc = (int)grp.hc.size();
+            if (nhc > 0) {
+                os << "  if (so.hcrow) {\n";
+                for (int c = 0; c < nhc; c++)
+                    os << "    { const long long ga = pm.xoff + i" << grp.hc_sym[c].first << ", gb = pm.xoff + i"
+                       << grp.hc_sym[c].second << ";\n"
+                       << "      so.hcrow[pm.hcbase + kk * " << nhc << " + " << c << "] = (int)(ga > gb ? ga : gb);\n"
+                       << "      so.hccol[pm.hcbase + kk * " << nhc << " + " << c << "] = (int)(ga > gb ? gb : ga); }\n";
+                os << "  }\n";
+            }
             os << "}\n";
             return os.str();
         }
@@ -937,6 +962,20 @@ struct Emitter {
         std::map<int, std::string> name;
         body(roots, name);
         auto widen = [&](int r) { return mixed ? "exa_f2d(" + name.at(r) + ")" : name.at(r); };
+        // csc/map: optional direct CSC output (a pure permutation of the COO slots); out/slot are
+        // the COO array and the block's first slot
+        auto staged = [&](const std::string &out, const std::string &slot0, int S, const std::vector<std::string> &vals,
+                          const char *csc, const char *map) {
+            os << "  __syncwarp();\n";
+            for (int j = 0; j < S; j++) os << "  ws[lane * " << S << " + " << j << "] = " << vals[j] << ";\n";
+            os << "  __syncwarp();\n"
+               << "  { const long long q0 = " << slot0 << " + kw * " << S << ";\n"
+               << "    if (" << out << ") for (int e = lane; e < nact * " << S << "; e += 32) " << out << "[q0 + e] = ws[e];\n";
+            if (csc)
+                os << "    if (" << csc << ") for (int e = lane; e < nact * " << S << "; e += 32) "
+                   << csc << "[" << map << "[q0 + e]] = ws[e];\n";
+            os << "  }\n";
+        };
         bool objw = false;
         for (int pos : act) {
             const Pattern &p = pat(pos);
@@ -952,20 +991,6 @@ struct Emitter {
             }
             // a block of S slots per instance: stage the warp's 32 x S values, then write the warp's
             // contiguous run of nact x S values with consecutive lanes on consecutive addresses
-            // csc/map: optional direct CSC output (a pure permutation of the COO slots); out/slot are
-            // the COO array and the block's first slot
-            auto staged = [&](const std::string &out, const std::string &slot0, int S, const std::vector<std::string> &vals,
-                              const char *csc, const char *map) {
-                os << "  __syncwarp();\n";
-                for (int j = 0; j < S; j++) os << "  ws[lane * " << S << " + " << j << "] = " << vals[j] << ";\n";
-                os << "  __syncwarp();\n"
-                   << "  { const long long q0 = " << slot0 << " + kw * " << S << ";\n"
-                   << "    if (" << out << ") for (int e = lane; e < nact * " << S << "; e += 32) " << out << "[q0 + e] = ws[e];\n";
-                if (csc)
-                    os << "    if (" << csc << ") for (int e = lane; e < nact * " << S << "; e += 32) "
-                       << csc << "[" << map << "[q0 + e]] = ws[e];\n";
-                os << "  }\n";
-            };
             if (w.grad && p.nj() > 0) {
                 std::vector<std::string> vals;
                 for (int j = 0; j < p.nj(); j++) vals.push_back(widen(G.grad[p.jsym[j]]));
@@ -973,22 +998,35 @@ struct Emitter {
                 else staged("o.jac", "pm.jbase[" + P + "]", p.nj(), vals, "o.jcsc", "o.jmap");
             }
             if (w.hess) {
-                os << "  { const " << W << " w = " << (obj ? (mixed ? "exa_d2f(sigma)" : "sigma")
+                os << "  const " << W << " w" << P << " = " << (obj ? (mixed ? "exa_d2f(sigma)" : "sigma")
                                                           : (mixed ? "exa_d2f(__ldg(y + row" + P + "))" : "__ldg(y + row" + P + ")"))
                    << ";\n";
-                os << "    const " << W << " w2 = w + w;\n";
+                os << "  const " << W << " ww" << P << " = w" << P << " + w" << P << ";\n";
                 std::vector<std::string> vals;
                 for (int j = 0; j < p.nh(); j++) {
                     int a = p.hpair[j].first, b = p.hpair[j].second;
                     int r = hroots[pos][j];
                     std::string v = r >= 0 ? name.at(r) : (mixed ? "0.0f" : "0.0");
-                    std::string wt = a == b ? "w" : "(i" + std::to_string(grp.sym[pos][a]) + " == i" +
-                                                        std::to_string(grp.sym[pos][b]) + " ? w2 : w)";
-                    vals.push_back(mixed ? "exa_f2d(" + wt + " * " + v + ")" : wt + " * " + v);
+                    std::string wt = a == b ? "w" + P : "(i" + std::to_string(grp.sym[pos][a]) + " == i" +
+                                                            std::to_string(grp.sym[pos][b]) + " ? ww" + P + " : w" + P + ")";
+                    std::string hv = "hv" + P + "_" + std::to_string(j);
+                    os << "  const double " << hv << " = " << (mixed ? "exa_f2d(" + wt + " * " + v + ")" : wt + " * " + v) << ";\n";
+                    vals.push_back(hv);
                 }
                 staged("o.hess", "pm.hbase[" + P + "]", p.nh(), vals, "o.hcsc", "o.hmap");
-                os << "  }\n";
             }
+        }
+        // per-instance FP64 sums of Hessian slots that share (row, col) within the group
+        bool any_hess = false;
+        for (int pos : act) any_hess = any_hess || want[pos].hess;
+        if (any_hess && !grp.hc.empty()) {
+            std::vector<std::string> sums;
+            for (auto &members : grp.hc) {
+                std::string e;
+                for (auto &pj : members) e += (e.empty() ? "" : " + ") + ("hv" + std::to_string(pj.first) + "_" + std::to_string(pj.second));
+                sums.push_back(e);
+            }
+            staged("o.hcomp", "pm.hcbase", (int)grp.hc.size(), sums, nullptr, nullptr);
         }
         os << "}\n";
         return os.str();
@@ -1095,6 +1133,8 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
         int smax = 1;  // widest slot block staged in this kernel
         for (const Pattern &p : pats)
             if (pattern_in_mode(p, (Mode)m)) smax = std::max(smax, std::max(p.nj(), p.nh()));
+        if (m == M_HESS || m == M_ALL)
+            for (const Group &gr : groups) smax = std::max(smax, (int)gr.hc.size());
         if (m != M_STRUCT)
             src << "  __shared__ double stage[EXA_BLOCK * " << smax << "];\n"
                    "  double* __restrict__ ws = stage + (threadIdx.x & ~31u) * " << smax << ";\n";
