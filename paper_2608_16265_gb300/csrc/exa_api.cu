@@ -108,25 +108,28 @@ __global__ void k_spmv_gather(const int *__restrict__ ptr, const int *__restrict
     out[i] = s;
 }
 
-// Hv[i] = sum over lower entries (i, j) of H v_j  +  sum over lower entries (j, i), j != i, of H v_j
-__global__ void k_hprod(const int *__restrict__ rptr, const int *__restrict__ rperm,
-                        const int *__restrict__ cptr, const int *__restrict__ cperm,
-                        const int *__restrict__ hrow, const int *__restrict__ hcol,
-                        const double *__restrict__ h, const double *__restrict__ v,
-                        double *__restrict__ out, int n) {
+// Hv[i] from the lower-triangle CSC values: column i holds (r, i), r >= i, giving H_ir v_r; the
+// row-sorted permutation lists the entries (i, c), c < i, giving H_ic v_c.
+__global__ void k_hprod_csc(const int *__restrict__ colptr, const int *__restrict__ rowval,
+                            const double *__restrict__ val, const int *__restrict__ rptr,
+                            const int *__restrict__ rperm, const int *__restrict__ colof,
+                            const double *__restrict__ v, double *__restrict__ out, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double s = 0.0;
+    for (int p = colptr[i], e = colptr[i + 1]; p < e; p++) s += val[p] * v[rowval[p]];
     for (int q = rptr[i], e = rptr[i + 1]; q < e; q++) {
-        int p = rperm[q];
-        s += h[p] * v[hcol[p]];
-    }
-    for (int q = cptr[i], e = cptr[i + 1]; q < e; q++) {
-        int p = cperm[q];
-        int r = hrow[p];
-        if (r != i) s += h[p] * v[r];
+        const int p = rperm[q], c = colof[p];
+        if (c != i) s += val[p] * v[c];
     }
     out[i] = s;
+}
+
+// colof[p] = column of CSC position p
+__global__ void k_col_of(const int *__restrict__ colptr, int *colof, int ncol) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncol) return;
+    for (int p = colptr[c], e = colptr[c + 1]; p < e; p++) colof[p] = c;
 }
 
 // ---- setup kernels
@@ -224,13 +227,15 @@ struct exa_model {
     int *d_jcolptr_coo = nullptr, *d_jrperm = nullptr, *d_jrptr = nullptr;
     // Hessian: same
     int *d_hperm = nullptr, *d_hsegptr = nullptr, *d_hcolptr = nullptr, *d_hrowval = nullptr, *d_hcoo2csc = nullptr;
-    int *d_hcolptr_coo = nullptr, *d_hrperm = nullptr, *d_hrptr = nullptr;
     // compressed Hessian (per-instance sums of a group's slots with equal (row, col)): structure,
     // permutation sorted by (col, row) and segment pointers per Hessian CSC entry
     i64 nnzhc = 0;
     bool use_hcomp = false;
     int *d_hcrow = nullptr, *d_hccol = nullptr, *d_hcperm = nullptr, *d_hcsegptr = nullptr;
     double *d_hcbuf = nullptr;
+    // Hessian CSC seen by rows (products): column of each CSC entry, row-sorted permutation
+    int *d_hcolof = nullptr, *d_hcsr_perm = nullptr, *d_hcsr_ptr = nullptr;
+    double *d_hcscbuf = nullptr;
     // gradient and augmentation segments
     int *d_gperm = nullptr, *d_gptr = nullptr;
     int *d_aperm = nullptr, *d_aptr = nullptr, *d_arows = nullptr;
@@ -475,14 +480,6 @@ exa_status build_structure(exa_model *m) {
         CR(cudaGetLastError());
     }
     if (exa_status e = build_ptr(m, segkey, 32, nseg, m->nvar, &m->d_hcolptr)) return e;
-    if (exa_status e = build_ptr(m, skeys, 32, nh, m->nvar, &m->d_hcolptr_coo)) return e;
-    CR(dalloc(m, &m->d_hrperm, nh));
-    if (nh) {
-        k_keys1<<<grid_of(nh, 256), 256, 0, m->stream>>>(m->d_hrow, keys, nh);
-        CR(cudaGetLastError());
-    }
-    if (exa_status e = sort_with_perm(m, S, keys, nh, 32, &skeys, m->d_hrperm)) return e;
-    if (exa_status e = build_ptr(m, skeys, 0, nh, m->nvar, &m->d_hrptr)) return e;
 
     // ---- compressed Hessian: its (col, row)-sorted segments are the Hessian CSC entries
     if (m->use_hcomp) {
@@ -497,6 +494,24 @@ exa_status build_structure(exa_model *m) {
         if (exa_status e = segments(m, S, skeys, m->d_hcperm, nc, &nsc, &m->d_hcsegptr, &segkey, nullptr, true)) return e;
         if (nsc != m->nnzh_csc) return fail(m, EXA_E_INTERNAL, "compressed Hessian does not cover the CSC entries");
         CR(dalloc(m, &m->d_hcbuf, nc));
+    }
+
+    // ---- Hessian CSC by rows (for products)
+    {
+        const int nc = (int)m->nnzh_csc;
+        CR(dalloc(m, &m->d_hcolof, nc));
+        CR(dalloc(m, &m->d_hcsr_perm, nc));
+        CR(dalloc(m, &m->d_hcscbuf, nc));
+        if (m->nvar) {
+            k_col_of<<<grid_of(m->nvar, 256), 256, 0, m->stream>>>(m->d_hcolptr, m->d_hcolof, (int)m->nvar);
+            CR(cudaGetLastError());
+        }
+        if (nc) {
+            k_keys2<<<grid_of(nc, 256), 256, 0, m->stream>>>(m->d_hrowval, m->d_hcolof, keys, nc);
+            CR(cudaGetLastError());
+        }
+        if (exa_status e = sort_with_perm(m, S, keys, nc, 64, &skeys, m->d_hcsr_perm)) return e;
+        if (exa_status e = build_ptr(m, skeys, 32, nc, m->nvar, &m->d_hcsr_ptr)) return e;
     }
 
     // ---- gradient segments by variable
@@ -604,7 +619,7 @@ exa_status setup_kernels(exa_model *m, int block) {
                     const bool act = exa::pattern_in_mode(m->pats[p], (exa::Mode)k);
                     in = in || act;
                     part = part || (act && m->pats[p].kind == EXA_OBJ &&
-                                    (k == exa::M_OBJ || k == exa::M_ALL || k == exa::M_FIRST));
+                                    (k == exa::M_OBJ || exa::mode_all(k) || k == exa::M_FIRST));
                 }
                 if (!in) continue;
                 const ExaPM &pm = m->h_pms[(size_t)b * ng + gi];
@@ -1347,7 +1362,7 @@ exa_status exa_hess_csc(exa_model *m, const double *x, const double *y, double s
     if (m->use_hcomp) {
         o.hess = nullptr;
         o.hcomp = m->d_hcbuf;
-        if (exa_status e = launch_eval(m, exa::M_HESS, x, y, sigma, o)) return e;
+        if (exa_status e = launch_eval(m, exa::M_HESS_C, x, y, sigma, o)) return e;
         k_seg_sum_warp<<<grid_of(m->nnzh_csc, 256), 256, 0, m->stream>>>(m->d_hcsegptr, m->d_hcperm, m->d_hcbuf,
                                                                            vals_csc, (int)m->nnzh_csc);
         CR(cudaGetLastError());
@@ -1387,7 +1402,10 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
         o.hcomp = m->d_hcbuf;
         if (!hess) o.hess = nullptr;
     }
-    Mode mode = want_h ? exa::M_ALL : exa::M_FIRST;
+    // Hessian variant: COO slots, group-compressed sums for the CSC, or both
+    const bool hcoo = o.hess != nullptr;
+    Mode mode = !want_h ? exa::M_FIRST : (hcomp ? (hcoo ? exa::M_ALL_B : exa::M_ALL_C) : exa::M_ALL);
+    const Mode hmode = hcomp ? (hcoo ? exa::M_HESS_B : exa::M_HESS_C) : exa::M_HESS;
     if (want_h && m->split_all) {  // first order and second order as two kernels
         ExaOut o1 = o, o2{};
         o1.hess = nullptr;
@@ -1398,7 +1416,7 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
         o2.hcomp = o.hcomp;
         mode = exa::M_FIRST;
         if (exa_status e = launch_eval(m, exa::M_FIRST, x, y, sigma, o1)) return e;
-        if (exa_status e = launch_eval(m, exa::M_HESS, x, y, sigma, o2)) return e;
+        if (exa_status e = launch_eval(m, hmode, x, y, sigma, o2)) return e;
     } else if (exa_status e = launch_eval(m, mode, x, y, sigma, o)) {
         return e;
     }
@@ -1504,11 +1522,11 @@ exa_status exa_hprod(exa_model *m, const double *x, const double *y, double sigm
     if (!m->nvar) return EXA_OK;
     CHECK_PTRS(x, v, Hv);
     if (m->ncon && !y) return fail(m, EXA_E_INVALID, "NULL y");
-    ExaOut o{};
-    o.hess = m->d_hbuf;
-    if (exa_status e = launch_eval(m, exa::M_HESS, x, y, sigma, o)) return e;
-    k_hprod<<<grid_of(m->nvar, 256), 256, 0, m->stream>>>(m->d_hrptr, m->d_hrperm, m->d_hcolptr_coo, m->d_hperm,
-                                                           m->d_hrow, m->d_hcol, m->d_hbuf, v, Hv, (int)m->nvar);
+    // Hessian CSC values first (duplicates summed once), then the product over unique entries
+    if (m->nnzh)
+        if (exa_status e = exa_hess_csc(m, x, y, sigma, m->d_hcscbuf)) return e;
+    k_hprod_csc<<<grid_of(m->nvar, 256), 256, 0, m->stream>>>(m->d_hcolptr, m->d_hrowval, m->d_hcscbuf, m->d_hcsr_ptr,
+                                                               m->d_hcsr_perm, m->d_hcolof, v, Hv, (int)m->nvar);
     CR(cudaGetLastError());
     return EXA_OK;
 }

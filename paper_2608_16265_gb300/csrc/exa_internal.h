@@ -65,8 +65,15 @@ namespace exa {
 
 // Generated kernels, one per callback kind: values of objective / constraint patterns, first order
 // (gradient slots / Jacobian), second order (Hessian), all of them, all but second order, and the
-// structure pass that writes the COO rows and columns.
-enum Mode { M_OBJ = 0, M_CON, M_GRAD, M_JAC, M_HESS, M_ALL, M_FIRST, M_STRUCT, M_COUNT };
+// structure pass that writes the COO rows and columns.  The Hessian-producing kinds come in three
+// compile-time variants: COO slots (M_HESS, M_ALL), the group-compressed sums used for the CSC
+// (..._C), or both (..._B).
+enum Mode { M_OBJ = 0, M_CON, M_GRAD, M_JAC, M_HESS, M_ALL, M_FIRST, M_STRUCT,
+            M_HESS_C, M_HESS_B, M_ALL_C, M_ALL_B, M_COUNT };
+inline bool mode_hess(int m) { return m == M_HESS || m == M_ALL || m >= M_HESS_C; }
+inline bool mode_all(int m) { return m == M_ALL || m == M_ALL_C || m == M_ALL_B; }
+inline bool mode_hess_coo(int m) { return m == M_HESS || m == M_ALL || m == M_HESS_B || m == M_ALL_B; }
+inline bool mode_hess_comp(int m) { return m >= M_HESS_C; }
 extern const char *const kModeName[M_COUNT];
 
 struct VNode { int op, a, b; long long iv; double fv; };

@@ -33,7 +33,8 @@ namespace exa {
 #define EXA_STR2(...) #__VA_ARGS__
 #define EXA_STR(...) EXA_STR2(__VA_ARGS__)
 const char *const kDeviceStructs = EXA_STR(EXA_DEVICE_STRUCTS);
-const char *const kModeName[M_COUNT] = {"obj", "con", "grad", "jac", "hess", "all", "first", "struct"};
+const char *const kModeName[M_COUNT] = {"obj", "con", "grad", "jac", "hess", "all", "first", "struct",
+                                        "hess_c", "hess_b", "all_c", "all_b"};
 
 static bool is_unary(int op) { return op >= EXA_V_NEG && op <= EXA_V_POWI; }
 static bool is_binary(int op) { return op >= EXA_V_ADD && op <= EXA_V_POW; }
@@ -670,7 +671,7 @@ bool pattern_in_mode(const Pattern &p, Mode m) {
     switch (m) {
     case M_OBJ: case M_GRAD: return p.kind == EXA_OBJ;
     case M_CON: case M_JAC: return p.kind != EXA_OBJ;
-    case M_HESS: return p.nh() > 0;
+    case M_HESS: case M_HESS_C: case M_HESS_B: return p.nh() > 0;
     default: return true;
     }
 }
@@ -792,7 +793,8 @@ struct Emitter {
         os.str("");
         const bool mixed = opt.precision == EXA_MIXED_FP32;
         const char *W = mixed ? "float" : "double";
-        const bool all = mode == M_ALL || mode == M_FIRST;
+        const bool all = mode_all(mode) || mode == M_FIRST;
+        const bool hs_coo = mode_hess_coo(mode), hs_comp = mode_hess_comp(mode) && !grp.hc.empty();
         const bool want_struct = mode == M_STRUCT;
         std::vector<int> act;
         for (size_t pos = 0; pos < grp.pats.size(); pos++)
@@ -819,7 +821,7 @@ struct Emitter {
             Want &w = want[pos];
             w.val = (mode == M_OBJ && obj) || (mode == M_CON && !obj) || all;
             w.grad = (mode == M_GRAD && obj) || (mode == M_JAC && !obj) || all;
-            w.hess = (mode == M_HESS || mode == M_ALL) && p.nh() > 0;
+            w.hess = mode_hess(mode) && p.nh() > 0;
             w.row = !obj && (w.val || w.hess || want_struct);
             const PatternGraph &G = PG[pos];
             if (w.val) roots.push_back(G.value);
@@ -976,6 +978,10 @@ struct Emitter {
                    << csc << "[" << map << "[q0 + e]] = ws[e];\n";
             os << "  }\n";
         };
+        std::map<std::pair<int, int>, int> hc_of;  // (position, slot) -> compressed slot
+        for (size_t c = 0; c < grp.hc.size(); c++)
+            for (auto &pj : grp.hc[c]) hc_of[pj] = (int)c;
+        std::vector<char> hc_started(grp.hc.size(), 0);
         bool objw = false;
         for (int pos : act) {
             const Pattern &p = pat(pos);
@@ -1012,20 +1018,19 @@ struct Emitter {
                     std::string hv = "hv" + P + "_" + std::to_string(j);
                     os << "  const double " << hv << " = " << (mixed ? "exa_f2d(" + wt + " * " + v + ")" : wt + " * " + v) << ";\n";
                     vals.push_back(hv);
+                    if (hs_comp) {  // accumulate into the group's compressed slot (FP64, pattern order)
+                        const int c = hc_of.at({pos, j});
+                        if (hc_started[c]) os << "  hc" << c << " += " << hv << ";\n";
+                        else os << "  double hc" << c << " = " << hv << ";\n";
+                        hc_started[c] = 1;
+                    }
                 }
-                staged("o.hess", "pm.hbase[" + P + "]", p.nh(), vals, "o.hcsc", "o.hmap");
+                if (hs_coo) staged("o.hess", "pm.hbase[" + P + "]", p.nh(), vals, "o.hcsc", "o.hmap");
             }
         }
-        // per-instance FP64 sums of Hessian slots that share (row, col) within the group
-        bool any_hess = false;
-        for (int pos : act) any_hess = any_hess || want[pos].hess;
-        if (any_hess && !grp.hc.empty()) {
+        if (hs_comp) {  // per-instance FP64 sums of the Hessian slots that share (row, col) in the group
             std::vector<std::string> sums;
-            for (auto &members : grp.hc) {
-                std::string e;
-                for (auto &pj : members) e += (e.empty() ? "" : " + ") + ("hv" + std::to_string(pj.first) + "_" + std::to_string(pj.second));
-                sums.push_back(e);
-            }
+            for (size_t c = 0; c < grp.hc.size(); c++) sums.push_back(hc_started[c] ? "hc" + std::to_string(c) : "0.0");
             staged("o.hcomp", "pm.hcbase", (int)grp.hc.size(), sums, nullptr, nullptr);
         }
         os << "}\n";
@@ -1122,7 +1127,7 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
             Emitter e(pats, groups[gi], graphs[gi], pgs[gi], opt);
             src << e.function((int)gi, (Mode)m);
         }
-        const bool objred = (m == M_OBJ || m == M_ALL || m == M_FIRST);
+        const bool objred = (m == M_OBJ || mode_all(m) || m == M_FIRST);
         // Tile loop: with gridDim.x == ntiles every CTA takes one tile; a smaller (persistent) grid
         // strides over the tile list.  tl.oslot and the trip count are uniform over the CTA.
         src << "extern \"C\" __global__ void __launch_bounds__(EXA_BLOCK) exa_" << kModeName[m]
@@ -1133,7 +1138,7 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
         int smax = 1;  // widest slot block staged in this kernel
         for (const Pattern &p : pats)
             if (pattern_in_mode(p, (Mode)m)) smax = std::max(smax, std::max(p.nj(), p.nh()));
-        if (m == M_HESS || m == M_ALL)
+        if (mode_hess_comp(m))
             for (const Group &gr : groups) smax = std::max(smax, (int)gr.hc.size());
         if (m != M_STRUCT)
             src << "  __shared__ double stage[EXA_BLOCK * " << smax << "];\n"

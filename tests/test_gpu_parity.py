@@ -127,6 +127,14 @@ def test_rosenbrock_ten_points():
         check_model(wl.flat, x, y, s, o=o)
 
 
+def test_acopf_ten_points():
+    wl = synth.acopf(500, 700, 100, seed=1)
+    o = oracle.Oracle(wl.flat)
+    for seed in range(10):
+        x, y, s = synth.acopf_point(wl, seed)
+        check_model(wl.flat, x, y, s, o=o)
+
+
 def test_empty_and_degenerate_patterns():
     from paper_2608_16265_gb300.ir import Model
     m = Model()
@@ -228,6 +236,25 @@ def test_full_pde():
     wl = synth.pde(1000)
     x, y, s = synth.pde_point(wl, 0)
     check_model(wl.flat, x, y, s)
+
+
+@pytest.mark.slow
+def test_full_batch_mixed_sampled_members():
+    """The benchmark batch in mixed precision: sampled members against the FP64 oracle."""
+    B = _B()
+    wls = synth.acopf_batch(256)
+    mb = B.exa_create_batch([w.flat for w in wls], precision=B.EXA_MIXED_FP32)
+    pts = [synth.acopf_point(w, i) for i, w in enumerate(wls)]
+    x = np.concatenate([p[0] for p in pts])
+    y = np.concatenate([p[1] for p in pts])
+    out = mb.eval_all(_t(x), _t(y), 1.0, csc=False)
+    jb, hb, cb = _np(out["jac"]), _np(out["hess"]), _np(out["c"])
+    for i in (0, 17, 128, 255):
+        o = oracle.Oracle(wls[i].flat)
+        xi, yi, si = pts[i]
+        assert normwise(jb[mb.joff[i]:mb.joff[i + 1]], o.jac_coord(xi)) <= 1e-6
+        assert normwise(hb[mb.hoff[i]:mb.hoff[i + 1]], o.hess_coord(xi, yi, si)) <= 1e-6
+        assert normwise(cb[mb.coff[i]:mb.coff[i + 1]], o.cons(xi)) <= 1e-6
 
 
 @pytest.mark.slow
