@@ -76,8 +76,12 @@ enum {
     EXA_V_NEG = 10, EXA_V_ABS2, EXA_V_INV, EXA_V_EXP, EXA_V_LOG, EXA_V_SIN, EXA_V_COS,
     EXA_V_SQRT, EXA_V_TAN, EXA_V_TANH, EXA_V_ATAN,
     EXA_V_POWI = 21,  /* child a raised to the integer ival */
+    EXA_V_SINH = 22, EXA_V_COSH, EXA_V_ASIN, EXA_V_ACOS, EXA_V_LOG1P, EXA_V_EXPM1, EXA_V_LOG2,
+    EXA_V_LOG10, EXA_V_EXP2,  /* = 30; registered functions of Sec. 7.1.4 beyond the basic set */
     EXA_V_ADD = 40, EXA_V_SUB, EXA_V_MUL, EXA_V_DIV,
-    EXA_V_POW = 44    /* a ^ b for real b; a must be positive where derivatives are taken */
+    EXA_V_POW = 44,   /* a ^ b for real b; a must be positive where derivatives are taken */
+    EXA_V_ATAN2 = 45, /* atan2(a, b) */
+    EXA_V_HYPOT = 46  /* hypot(a, b) */
 };
 /* Integer index nodes (postorder within the pattern's inode array), 64-bit arithmetic. */
 enum {

@@ -42,6 +42,7 @@
  * first derivatives) and a complex-valued first-order AD gradient of the Lagrangian (for a
  * complex-step Hessian that uses only first-derivative rules).
  */
+#define _GNU_SOURCE
 #include <complex.h>
 #include <math.h>
 #include <stdint.h>
@@ -58,8 +59,9 @@
 /* opcodes of the flat IR */
 enum { OV_CONST = 0, OV_DATA = 1, OV_VAR = 2, OV_PARAM = 3,
        OV_NEG = 10, OV_ABS2, OV_INV, OV_EXP, OV_LOG, OV_SIN, OV_COS, OV_SQRT, OV_TAN, OV_TANH,
-       OV_ATAN, OV_POWI,
-       OV_ADD = 40, OV_SUB, OV_MUL, OV_DIV, OV_POW };
+       OV_ATAN, OV_POWI, OV_SINH, OV_COSH, OV_ASIN, OV_ACOS, OV_LOG1P, OV_EXPM1, OV_LOG2,
+       OV_LOG10, OV_EXP2,
+       OV_ADD = 40, OV_SUB, OV_MUL, OV_DIV, OV_POW, OV_ATAN2, OV_HYPOT };
 enum { OI_CONST = 0, OI_FIELD = 1, OI_INST = 2, OI_ADD = 10, OI_SUB = 11, OI_MUL = 12 };
 enum { OK_OBJ = 0, OK_CON = 1, OK_AUG = 2 };
 
@@ -105,8 +107,8 @@ static int set_err(orc_model *m, int code, const char *msg) {
     return code;
 }
 
-static int is_unary(int op) { return op >= OV_NEG && op <= OV_POWI; }
-static int is_binary(int op) { return op >= OV_ADD && op <= OV_POW; }
+static int is_unary(int op) { return op >= OV_NEG && op <= OV_EXP2; }
+static int is_binary(int op) { return op >= OV_ADD && op <= OV_HYPOT; }
 
 /* ------------------------------------------------------------------ construction */
 orc_model *orc_new(int64_t nvar, int64_t ncon, int64_t npar, const double *theta) {
@@ -582,6 +584,26 @@ static void forward(const orc_model *m, const opat *p, int64_t k, const double *
             h11 = (double)e * (double)(e - 1) * ipow(u, e - 2);
             break;
         }
+        case OV_SINH: v = sinh(u); d1 = cosh(u); h11 = v; break;
+        case OV_COSH: v = cosh(u); d1 = sinh(u); h11 = v; break;
+        case OV_ASIN: { double r = 1 / sqrt(1 - u * u); v = asin(u); d1 = r; h11 = u * r * r * r; break; }
+        case OV_ACOS: { double r = 1 / sqrt(1 - u * u); v = acos(u); d1 = -r; h11 = -u * r * r * r; break; }
+        case OV_LOG1P: v = log1p(u); d1 = 1 / (1 + u); h11 = -d1 * d1; break;
+        case OV_EXPM1: v = expm1(u); d1 = exp(u); h11 = d1; break;
+        case OV_LOG2: v = log2(u); d1 = 1 / (u * log(2.0)); h11 = -d1 / u; break;
+        case OV_LOG10: v = log10(u); d1 = 1 / (u * log(10.0)); h11 = -d1 / u; break;
+        case OV_EXP2: v = exp2(u); d1 = v * log(2.0); h11 = d1 * log(2.0); break;
+        case OV_ATAN2: {
+            double r = u * u + w * w;
+            v = atan2(u, w); d1 = w / r; d2 = -u / r;
+            h11 = -2 * u * w / (r * r); h12 = (u * u - w * w) / (r * r); h22 = 2 * u * w / (r * r);
+            break;
+        }
+        case OV_HYPOT: {
+            v = hypot(u, w); d1 = u / v; d2 = w / v;
+            h11 = w * w / (v * v * v); h12 = -u * w / (v * v * v); h22 = u * u / (v * v * v);
+            break;
+        }
         case OV_ADD: v = u + w; d1 = 1; d2 = 1; break;
         case OV_SUB: v = u - w; d1 = 1; d2 = -1; break;
         case OV_MUL: v = u * w; d1 = w; d2 = u; h12 = 1; break;
@@ -839,6 +861,14 @@ static cplx cipow(cplx u, int64_t n) {
     return n < 0 ? 1.0 / r : r;
 }
 
+/* atan2 continued analytically off the real axis: atan(a/b) plus the constant that selects the
+ * quadrant of the real arguments (constants do not change derivatives); b must not be 0. */
+static cplx catan2_(cplx a, cplx b) {
+    cplx r = catan(a / b);
+    if (creal(b) < 0) r += creal(a) >= 0 ? M_PI : -M_PI;
+    return r;
+}
+
 /* Value of node n of instance k in complex arithmetic (plain recursive tree walk). */
 static cplx ceval(const orc_model *m, const opat *p, int n, int64_t k, const cplx *x) {
     int op = p->vop[n];
@@ -863,6 +893,15 @@ static cplx ceval(const orc_model *m, const opat *p, int n, int64_t k, const cpl
     case OV_TANH: return ctanh(u);
     case OV_ATAN: return catan(u);
     case OV_POWI: return cipow(u, p->vi[n]);
+    case OV_SINH: return csinh(u);
+    case OV_COSH: return ccosh(u);
+    case OV_ASIN: return casin(u);
+    case OV_ACOS: return cacos(u);
+    case OV_LOG1P: return clog(1.0 + u);
+    case OV_EXPM1: return cexp(u) - 1.0;
+    case OV_LOG2: return clog(u) / log(2.0);
+    case OV_LOG10: return clog(u) / log(10.0);
+    case OV_EXP2: return cexp(u * log(2.0));
     default: break;
     }
     cplx w = ceval(m, p, p->vb[n], k, x);
@@ -871,6 +910,8 @@ static cplx ceval(const orc_model *m, const opat *p, int n, int64_t k, const cpl
     case OV_SUB: return u - w;
     case OV_MUL: return u * w;
     case OV_DIV: return u / w;
+    case OV_ATAN2: return catan2_(u, w);
+    case OV_HYPOT: return csqrt(u * u + w * w);
     default: return cexp(w * clog(u));
     }
 }
@@ -942,6 +983,17 @@ int orc_lag_grad_complex(orc_model *m, const double *xr, const double *xi, const
                 case OV_TANH: v = ctanh(u); a1 = 1.0 - v * v; break;
                 case OV_ATAN: v = catan(u); a1 = 1.0 / (1.0 + u * u); break;
                 case OV_POWI: v = cipow(u, p->vi[n]); a1 = (double)p->vi[n] * cipow(u, p->vi[n] - 1); break;
+                case OV_SINH: v = csinh(u); a1 = ccosh(u); break;
+                case OV_COSH: v = ccosh(u); a1 = csinh(u); break;
+                case OV_ASIN: v = casin(u); a1 = 1.0 / csqrt(1.0 - u * u); break;
+                case OV_ACOS: v = cacos(u); a1 = -1.0 / csqrt(1.0 - u * u); break;
+                case OV_LOG1P: v = clog(1.0 + u); a1 = 1.0 / (1.0 + u); break;
+                case OV_EXPM1: v = cexp(u) - 1.0; a1 = cexp(u); break;
+                case OV_LOG2: v = clog(u) / log(2.0); a1 = 1.0 / (u * log(2.0)); break;
+                case OV_LOG10: v = clog(u) / log(10.0); a1 = 1.0 / (u * log(10.0)); break;
+                case OV_EXP2: v = cexp(u * log(2.0)); a1 = v * log(2.0); break;
+                case OV_ATAN2: v = catan2_(u, w); a1 = w / (u * u + w * w); a2 = -u / (u * u + w * w); break;
+                case OV_HYPOT: v = csqrt(u * u + w * w); a1 = u / v; a2 = w / v; break;
                 case OV_ADD: v = u + w; a1 = 1; a2 = 1; break;
                 case OV_SUB: v = u - w; a1 = 1; a2 = -1; break;
                 case OV_MUL: v = u * w; a1 = w; a2 = u; break;

@@ -36,8 +36,8 @@ const char *const kDeviceStructs = EXA_STR(EXA_DEVICE_STRUCTS);
 const char *const kModeName[M_COUNT] = {"obj", "con", "grad", "jac", "hess", "all", "first", "struct",
                                         "hess_c", "hess_b", "all_c", "all_b"};
 
-static bool is_unary(int op) { return op >= EXA_V_NEG && op <= EXA_V_POWI; }
-static bool is_binary(int op) { return op >= EXA_V_ADD && op <= EXA_V_POW; }
+static bool is_unary(int op) { return op >= EXA_V_NEG && op <= EXA_V_EXP2; }
+static bool is_binary(int op) { return op >= EXA_V_ADD && op <= EXA_V_HYPOT; }
 static bool is_leaf(int op) { return op >= EXA_V_CONST && op <= EXA_V_PARAM; }
 
 // Is the op's second partial identically zero?  which: 1 = d2/du1^2, 2 = d2/du2^2, 3 = mixed.
@@ -260,7 +260,9 @@ enum SOp {
     S_EXP, S_LOG, S_SIN, S_COS, S_SQRT, S_TAN, S_TANH, S_ATAN, S_POW,
     S_CVT,              // convert the operand to this node's precision
     S_SINR, S_COSR,     // float sin / cos of an FP64 argument reduced in FP64
-    S_EXPR              // float exp of an FP64 argument reduced in FP64
+    S_EXPR,             // float exp of an FP64 argument reduced in FP64
+    S_SINH, S_COSH, S_ASIN, S_ACOS, S_LOG1P, S_EXPM1, S_LOG2, S_LOG10, S_EXP2,  // unary functions
+    S_ATAN2, S_HYPOT    // binary functions
 };
 enum Prec { PD = 0, PF = 1 };  // FP64, FP32
 
@@ -463,6 +465,17 @@ static void build_graph(const Pattern &p, const InputMap &im, Graph &g, PatternG
         case EXA_V_MUL: r = g.mul(dval(nd.a), dval(nd.b)); break;
         case EXA_V_DIV: r = g.div(dval(nd.a), dval(nd.b)); break;
         case EXA_V_POW: r = g.node(S_POW, PD, dval(nd.a), dval(nd.b)); break;
+        case EXA_V_SINH: r = g.fn(S_SINH, dval(nd.a)); break;
+        case EXA_V_COSH: r = g.fn(S_COSH, dval(nd.a)); break;
+        case EXA_V_ASIN: r = g.fn(S_ASIN, dval(nd.a)); break;
+        case EXA_V_ACOS: r = g.fn(S_ACOS, dval(nd.a)); break;
+        case EXA_V_LOG1P: r = g.fn(S_LOG1P, dval(nd.a)); break;
+        case EXA_V_EXPM1: r = g.fn(S_EXPM1, dval(nd.a)); break;
+        case EXA_V_LOG2: r = g.fn(S_LOG2, dval(nd.a)); break;
+        case EXA_V_LOG10: r = g.fn(S_LOG10, dval(nd.a)); break;
+        case EXA_V_EXP2: r = g.fn(S_EXP2, dval(nd.a)); break;
+        case EXA_V_ATAN2: r = g.node(S_ATAN2, PD, dval(nd.a), dval(nd.b)); break;
+        case EXA_V_HYPOT: r = g.node(S_HYPOT, PD, dval(nd.a), dval(nd.b)); break;
         }
         return dmemo[i] = r;
     };
@@ -519,6 +532,63 @@ static void build_graph(const Pattern &p, const InputMap &im, Graph &g, PatternG
             d1 = g.mul(g.lit((double)nd.iv, W), g.powi(u, nd.iv - 1));
             h11 = g.mul(g.lit((double)nd.iv * (double)(nd.iv - 1), W), g.powi(u, nd.iv - 2));
             break;
+        // exp-family functions in mixed mode: value and first derivative evaluated in FP64 from the
+        // FP64 argument and rounded to FP32 (the exp arguments are reduced in FP64)
+        case EXA_V_SINH: case EXA_V_COSH: {
+            const int o1 = nd.op == EXA_V_SINH ? S_SINH : S_COSH, o2 = nd.op == EXA_V_SINH ? S_COSH : S_SINH;
+            if (mixed) { v = g.node(S_CVT, PF, g.fn(o1, dval(nd.a))); d1 = g.node(S_CVT, PF, g.fn(o2, dval(nd.a))); }
+            else { v = g.fn(o1, u); d1 = g.fn(o2, u); }
+            h11 = v;
+            break;
+        }
+        case EXA_V_EXPM1:
+            if (mixed) { v = g.node(S_CVT, PF, g.fn(S_EXPM1, dval(nd.a))); d1 = g.fn_at(S_EXPR, PF, dval(nd.a)); }
+            else { v = g.fn(S_EXPM1, u); d1 = g.fn(S_EXP, u); }
+            h11 = d1;
+            break;
+        case EXA_V_EXP2: {
+            const int ln2 = g.lit(0.69314718055994531, W);
+            v = mixed ? g.node(S_CVT, PF, g.fn(S_EXP2, dval(nd.a))) : g.fn(S_EXP2, u);
+            d1 = g.mul(v, ln2);
+            h11 = g.mul(d1, ln2);
+            break;
+        }
+        case EXA_V_ASIN: case EXA_V_ACOS: {
+            const int r = g.div(ONE, g.fn(S_SQRT, g.sub(ONE, g.mul(u, u))));
+            v = g.fn(nd.op == EXA_V_ASIN ? S_ASIN : S_ACOS, u);
+            d1 = nd.op == EXA_V_ASIN ? r : g.neg(r);
+            h11 = g.mul(u, g.mul(d1, g.mul(r, r)));
+            break;
+        }
+        case EXA_V_LOG1P: v = g.fn(S_LOG1P, u); d1 = g.div(ONE, g.add(ONE, u)); h11 = g.neg(g.mul(d1, d1)); break;
+        case EXA_V_LOG2: case EXA_V_LOG10: {
+            const int lnb = g.lit(nd.op == EXA_V_LOG2 ? 0.69314718055994531 : 2.3025850929940457, W);
+            v = g.fn(nd.op == EXA_V_LOG2 ? S_LOG2 : S_LOG10, u);
+            d1 = g.div(ONE, g.mul(u, lnb));
+            h11 = g.neg(g.div(d1, u));
+            break;
+        }
+        case EXA_V_ATAN2: {
+            v = g.node(S_ATAN2, W, u, w);
+            const int r = g.add(g.mul(u, u), g.mul(w, w));
+            const int r2 = g.mul(r, r);
+            d1 = g.div(w, r);
+            d2 = g.neg(g.div(u, r));
+            h11 = g.neg(g.div(g.mul(TWO, g.mul(u, w)), r2));
+            h12 = g.div(g.sub(g.mul(u, u), g.mul(w, w)), r2);
+            h22 = g.div(g.mul(TWO, g.mul(u, w)), r2);
+            break;
+        }
+        case EXA_V_HYPOT: {
+            v = g.node(S_HYPOT, W, u, w);
+            const int v3 = g.mul(v, g.mul(v, v));
+            d1 = g.div(u, v);
+            d2 = g.div(w, v);
+            h11 = g.div(g.mul(w, w), v3);
+            h12 = g.neg(g.div(g.mul(u, w), v3));
+            h22 = g.div(g.mul(u, u), v3);
+            break;
+        }
         case EXA_V_ADD: v = g.add(u, w); d1 = ONE; d2 = ONE; break;
         case EXA_V_SUB: v = g.sub(u, w); d1 = ONE; d2 = g.lit(-1.0, W); break;
         case EXA_V_MUL: v = g.mul(u, w); d1 = w; d2 = u; h12 = ONE; break;
@@ -716,11 +786,18 @@ struct Emitter {
         else if (n.op >= EXA_I_ADD) { fields_of_idx(pos, n.a, f); fields_of_idx(pos, n.b, f); }
     }
 
-    static const char *fname(int op, int prec) {
-        static const char *d[] = {"exp", "log", "sin", "cos", "sqrt", "tan", "tanh", "atan"};
-        static const char *f[] = {"expf", "logf", "sinf", "cosf", "sqrtf", "tanf", "tanhf", "atanf"};
-        int k = op - S_EXP;
-        return prec == PF ? f[k] : d[k];
+    static std::string fname(int op, int prec) {
+        const char *n = "?";
+        switch (op) {
+        case S_EXP: n = "exp"; break; case S_LOG: n = "log"; break; case S_SIN: n = "sin"; break;
+        case S_COS: n = "cos"; break; case S_SQRT: n = "sqrt"; break; case S_TAN: n = "tan"; break;
+        case S_TANH: n = "tanh"; break; case S_ATAN: n = "atan"; break; case S_SINH: n = "sinh"; break;
+        case S_COSH: n = "cosh"; break; case S_ASIN: n = "asin"; break; case S_ACOS: n = "acos"; break;
+        case S_LOG1P: n = "log1p"; break; case S_EXPM1: n = "expm1"; break; case S_LOG2: n = "log2"; break;
+        case S_LOG10: n = "log10"; break; case S_EXP2: n = "exp2"; break; case S_ATAN2: n = "atan2"; break;
+        case S_HYPOT: n = "hypot"; break; case S_POW: n = "pow"; break;
+        }
+        return std::string(n) + (prec == PF ? "f" : "");
     }
     static const char *ty(int prec) { return prec == PF ? "float" : "double"; }
     static std::string in_name(const SN &s) {
@@ -761,10 +838,13 @@ struct Emitter {
             case S_SUB: os << "  const " << T << " " << t << " = " << A() << " - " << B() << ";\n"; break;
             case S_MUL: os << "  const " << T << " " << t << " = " << A() << " * " << B() << ";\n"; break;
             case S_DIV: os << "  const " << T << " " << t << " = " << A() << " / " << B() << ";\n"; break;
-            case S_POW:
-                os << "  const " << T << " " << t << " = " << (s.prec == PF ? "powf(" : "pow(") << A() << ", " << B() << ");\n";
+            case S_POW: case S_ATAN2: case S_HYPOT:
+                os << "  const " << T << " " << t << " = " << fname(s.op, s.prec) << "(" << A() << ", " << B() << ");\n";
                 break;
-            case S_CVT: os << "  const " << T << " " << t << " = (" << T << ")" << A() << ";\n"; break;
+            case S_CVT:
+                if (s.prec == PF) os << "  const float " << t << " = exa_d2f(" << A() << ");\n";
+                else os << "  const double " << t << " = exa_f2d(" << A() << ");\n";
+                break;
             case S_EXPR: os << "  const float " << t << " = exa_exp_red(" << A() << ");\n"; break;
             case S_SIN: case S_COS: case S_SINR: case S_COSR: {
                 bool red = s.op == S_SINR || s.op == S_COSR;

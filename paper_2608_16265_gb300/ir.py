@@ -28,7 +28,8 @@ import numpy as np
 # ---------------------------------------------------------------- opcodes (mirrors include/exa.h)
 V_CONST, V_DATA, V_VAR, V_PARAM = 0, 1, 2, 3
 V_NEG, V_ABS2, V_INV, V_EXP, V_LOG, V_SIN, V_COS, V_SQRT, V_TAN, V_TANH, V_ATAN, V_POWI = range(10, 22)
-V_ADD, V_SUB, V_MUL, V_DIV, V_POW = range(40, 45)
+V_SINH, V_COSH, V_ASIN, V_ACOS, V_LOG1P, V_EXPM1, V_LOG2, V_LOG10, V_EXP2 = range(22, 31)
+V_ADD, V_SUB, V_MUL, V_DIV, V_POW, V_ATAN2, V_HYPOT = range(40, 47)
 I_CONST, I_FIELD, I_INST = 0, 1, 2
 I_ADD, I_SUB, I_MUL = 10, 11, 12
 
@@ -37,8 +38,11 @@ F_I32, F_F64 = 0, 1
 
 UNARY_NAMES = {V_NEG: "neg", V_ABS2: "abs2", V_INV: "inv", V_EXP: "exp", V_LOG: "log",
                V_SIN: "sin", V_COS: "cos", V_SQRT: "sqrt", V_TAN: "tan", V_TANH: "tanh",
-               V_ATAN: "atan", V_POWI: "powi"}
-BINARY_NAMES = {V_ADD: "+", V_SUB: "-", V_MUL: "*", V_DIV: "/", V_POW: "^"}
+               V_ATAN: "atan", V_POWI: "powi", V_SINH: "sinh", V_COSH: "cosh", V_ASIN: "asin",
+               V_ACOS: "acos", V_LOG1P: "log1p", V_EXPM1: "expm1", V_LOG2: "log2", V_LOG10: "log10",
+               V_EXP2: "exp2"}
+BINARY_NAMES = {V_ADD: "+", V_SUB: "-", V_MUL: "*", V_DIV: "/", V_POW: "^", V_ATAN2: "atan2",
+                V_HYPOT: "hypot"}
 
 
 # ---------------------------------------------------------------- integer index expressions
@@ -300,6 +304,29 @@ sqrt = _unary(V_SQRT, math.sqrt)
 tan = _unary(V_TAN, math.tan)
 tanh = _unary(V_TANH, math.tanh)
 atan = _unary(V_ATAN, math.atan)
+sinh = _unary(V_SINH, math.sinh)
+cosh = _unary(V_COSH, math.cosh)
+asin = _unary(V_ASIN, math.asin)
+acos = _unary(V_ACOS, math.acos)
+log1p = _unary(V_LOG1P, math.log1p)
+expm1 = _unary(V_EXPM1, math.expm1)
+log2 = _unary(V_LOG2, math.log2)
+log10 = _unary(V_LOG10, math.log10)
+exp2 = _unary(V_EXP2, lambda v: 2.0 ** v)
+
+
+def atan2(a, b):
+    a, b = lift(a), lift(b)
+    if isinstance(a, Const) and isinstance(b, Const):
+        return Const(math.atan2(a.v, b.v))
+    return Bin(V_ATAN2, a, b)
+
+
+def hypot(a, b):
+    a, b = lift(a), lift(b)
+    if isinstance(a, Const) and isinstance(b, Const):
+        return Const(math.hypot(a.v, b.v))
+    return Bin(V_HYPOT, a, b)
 
 
 # ---------------------------------------------------------------- model containers

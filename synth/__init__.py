@@ -12,6 +12,8 @@ Families (the paper's suites are not available; these stand in for them):
   * pde(N)               distributed control of -Lap u + u^3 = c on an N x N grid, 5-point stencil
                          (a COPS-style PDE-constrained instance).
   * acopf_batch(...)     many ACOPF instances of uneven size with per-instance load multipliers.
+  * goddard(T)           Goddard rocket, trapezoidal discretisation with T steps (Eq. (rocket); a
+                         COPS-style optimal-control instance with exp and division-heavy patterns).
 Every random number comes from numpy's PCG64 (`np.random.default_rng(seed)`).
 """
 from __future__ import annotations
@@ -209,6 +211,57 @@ def acopf_batch(n_inst: int = 256, seed: int = 7, bmin: int = 200, bmax: int = 2
             for (b, l, g, s, mu) in acopf_batch_sizes(n_inst, seed, bmin, bmax)]
 
 
+# ------------------------------------------------------------------ Goddard rocket (optimal control)
+GODDARD = dict(h0=1.0, v0=0.0, m0=1.0, g0=1.0, Tc=3.5, hc=500.0, vc=620.0, mc=0.6)
+
+
+def goddard(T: int = 1000) -> Workload:
+    """Eq. (rocket) with T trapezoidal steps; variables h, v, m, tau on t = 0..T and the step dt.
+    Drag D(h, v) = Dc v^2 exp(-hc (h - h0)/h0), gravity g(h) = g0 (h0/h)^2, exhaust velocity
+    c = sqrt(g0 h0)/2, Dc = vc m0/(2 g0), final mass mf = mc m0 (a parameter).  The objective is the
+    final altitude, written as minimising -h_T."""
+    k = GODDARD
+    c = 0.5 * math.sqrt(k["g0"] * k["h0"])
+    Dc = 0.5 * k["vc"] * k["m0"] / k["g0"]
+    m = Model()
+    h = m.add_var(T + 1)
+    v = m.add_var(T + 1)
+    ms = m.add_var(T + 1)
+    tau = m.add_var(T + 1)
+    dt = m.add_var(1)
+    mf = m.add_par([k["mc"] * k["m0"]])
+
+    def accel(t):  # (tau - D)/m - g at step t
+        drag = Dc * v[t] ** 2 * exp(-k["hc"] * (h[t] - k["h0"]) / k["h0"])
+        return (tau[t] - drag) / ms[t] - k["g0"] * (k["h0"] / h[t]) ** 2
+
+    m.add_obj(lambda d: -h[T], n=1, name="final_altitude")
+    m.add_con(lambda d: h[d.k + 1] - h[d.k] - 0.5 * dt[0] * (v[d.k + 1] + v[d.k]), n=T, name="altitude")
+    m.add_con(lambda d: v[d.k + 1] - v[d.k] - 0.5 * dt[0] * (accel(d.k + 1) + accel(d.k)), n=T, name="velocity")
+    m.add_con(lambda d: ms[d.k + 1] - ms[d.k] + 0.5 * dt[0] * (tau[d.k + 1] + tau[d.k]) / c, n=T, name="mass")
+    m.add_con(lambda d: h[0] - k["h0"], n=1, name="h_initial")
+    m.add_con(lambda d: v[0] - k["v0"], n=1, name="v_initial")
+    m.add_con(lambda d: ms[0] - k["m0"], n=1, name="m_initial")
+    m.add_con(lambda d: ms[T] - mf[0], n=1, name="m_final")
+    return Workload(f"goddard_T{T}", m, m.flat(), dict(T=T))
+
+
+def goddard_point(wl: Workload, seed: int):
+    """Around the usual starting trajectory: h = 1, v = s(1 - s), m from m0 to mf, tau = Tmax/2,
+    dt = 1/T (s = t/T), each perturbed by 1 %; y ~ N(0, 1); sigma = 1."""
+    rng = np.random.default_rng(seed)
+    k = GODDARD
+    T = wl.meta["T"]
+    sgrid = np.arange(T + 1) / T
+    mfin = k["mc"] * k["m0"]
+    tmax = k["Tc"] * k["m0"] * k["g0"]
+    x = np.concatenate([np.ones(T + 1), sgrid * (1 - sgrid), (mfin - k["m0"]) * sgrid + k["m0"],
+                        np.full(T + 1, tmax / 2), [1.0 / T]])
+    x *= 1 + 0.01 * rng.standard_normal(len(x))
+    y = rng.standard_normal(wl.flat.ncon)
+    return x, y, 1.0
+
+
 # ------------------------------------------------------------------ named configurations
 def config(name: str):
     """The benchmark configurations: returns (workloads, point function)."""
@@ -222,4 +275,6 @@ def config(name: str):
         return [pde(1000)], pde_point
     if name == "acopf_batch":
         return acopf_batch(256), acopf_point
+    if name == "goddard":
+        return [goddard(100000)], goddard_point
     raise KeyError(name)

@@ -1,7 +1,8 @@
 """Shared test helpers: dense assembly of COO output and small hand-written models."""
 import numpy as np
 
-from paper_2608_16265_gb300.ir import Model, sin, cos, exp, log, sqrt, tan, tanh, atan, inv
+from paper_2608_16265_gb300.ir import (Model, sin, cos, exp, log, sqrt, tan, tanh, atan, inv, sinh, cosh,
+                                       asin, acos, log1p, expm1, log2, log10, exp2, atan2, hypot)
 
 
 def dense_jac(nrow, ncol, rows, cols, vals):
@@ -53,3 +54,20 @@ def all_ops_point(seed=1):
     x = rng.uniform(0.2, 0.9, 6)
     y = rng.standard_normal(8)
     return x, y, 0.75
+
+
+def more_ops_model(seed=0):
+    """The functions beyond the basic set (Sec. 7.1.4 registry): sinh, cosh, asin, acos, log1p,
+    expm1, log2, log10, exp2, atan2, hypot."""
+    rng = np.random.default_rng(seed)
+    m = Model()
+    x = m.add_var(6)
+    data = dict(a=np.array([0, 1, 2, 3, 4], np.int32), b=np.array([1, 2, 3, 4, 5], np.int32),
+                w=rng.uniform(0.5, 1.5, 5))
+    m.add_obj(lambda d: sinh(x[d.a]) * cosh(x[d.b]) + asin(0.5 * x[d.a]) * acos(0.3 * x[d.b])
+              + d.w * log1p(x[d.a] * x[d.b]), data=data)
+    m.add_con(lambda d: expm1(x[d.a] - x[d.b]) + log2(1 + x[d.a] ** 2) * log10(2 + x[d.b])
+              + exp2(x[d.a] * x[d.b]) + atan2(x[d.a], 1 + x[d.b]) + hypot(x[d.a], x[d.b] + 0.5), data=data)
+    m.add_con(lambda d: atan2(x[d.b] - 0.1, x[d.a]) * hypot(x[d.a] * x[d.b], 1.0) - sinh(x[d.a] * x[d.b]),
+              data=data)
+    return m

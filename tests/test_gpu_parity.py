@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import synth
-from tests.helpers import all_ops_model, all_ops_point, normwise
+from tests.helpers import all_ops_model, all_ops_point, more_ops_model, normwise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -75,10 +75,13 @@ def check_model(flat, x, y, s, block=0, tol=TOL, o=None, flags=0, precision=0, g
 
 CASES = {
     "all_ops": lambda: (all_ops_model().flat(), all_ops_point()),
+    "more_ops": lambda: (more_ops_model().flat(), (np.random.default_rng(2).uniform(0.2, 0.9, 6),
+                                                   np.random.default_rng(3).standard_normal(10), 1.3)),
     "rosenbrock_1000": lambda: (lambda w: (w.flat, synth.rosenbrock_point(w, 0)))(synth.rosenbrock(1000)),
     "acopf_small": lambda: (lambda w: (w.flat, synth.acopf_point(w, 0)))(synth.acopf(500, 700, 100, seed=1)),
     "acopf_shunts": lambda: (lambda w: (w.flat, synth.acopf_point(w, 3)))(synth.acopf(37, 61, 9, seed=4, shunts=True)),
     "pde_41": lambda: (lambda w: (w.flat, synth.pde_point(w, 2)))(synth.pde(41)),
+    "goddard_2000": lambda: (lambda w: (w.flat, synth.goddard_point(w, 2)))(synth.goddard(2000)),
 }
 
 
@@ -125,6 +128,15 @@ def test_rosenbrock_ten_points():
     for seed in range(10):
         x, y, s = synth.rosenbrock_point(wl, seed)
         check_model(wl.flat, x, y, s, o=o)
+
+
+def test_bounds_checked_kernels():
+    """With EXA_FLAG_BOUNDS_CHECK every gather index is checked on the device; valid models give the
+    same results and a clean status."""
+    B = _B()
+    flat, (x, y, s) = CASES["acopf_shunts"]()
+    m, _ = check_model(flat, x, y, s, flags=B.EXA_FLAG_BOUNDS_CHECK)
+    m.exa_check_status()
 
 
 def test_acopf_ten_points():
