@@ -93,11 +93,12 @@ FP64_PEAK_GFLOPS = 1250.0  # GB300 nominal FP64 (FMA = 2 flops); the recipe's fi
 
 
 def csrc_digest() -> str:
-    """sha256 over the library sources: ncu counters recorded for other sources are stale."""
+    """sha256 over the sources that generate the evaluation kernels (the code generator and the
+    descriptor layout): ncu counters recorded for other generated kernels are stale."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2608_16265_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in ("exa_internal.h", "exa_lower.cpp"):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()

@@ -179,6 +179,13 @@ exa_status exa_dims(const exa_model *m, int64_t *nvar, int64_t *ncon, int64_t *n
 exa_status exa_batch_offsets(const exa_model *m, int32_t *nb, int64_t *xoff, int64_t *coff,
                              int64_t *joff, int64_t *hoff);
 
+/* Replace the parameter values theta (host array of npar doubles, all batch members' parameters
+ * concatenated in member order), as the paper's parameter update does without rebuilding the model
+ * (Sec. 2.1: theta is held fixed during a solve and may change between solves).  The copy is
+ * ordered on the model's stream and the call synchronizes that stream, so the host array may be
+ * reused once the call returns. */
+exa_status exa_set_theta(exa_model *m, const double *theta, int64_t npar);
+
 /* Stream (a cudaStream_t) on which every later call on this model enqueues its work. */
 exa_status exa_set_stream(exa_model *m, void *stream);
 

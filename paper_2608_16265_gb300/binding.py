@@ -29,7 +29,7 @@ STATUS_NAMES = ["EXA_OK", "EXA_E_INVALID", "EXA_E_OOM", "EXA_E_NVRTC", "EXA_E_CU
 
 # Every function include/exa.h declares.
 EXPORTS = ["exa_create", "exa_create_batch", "exa_destroy", "exa_last_error", "exa_create_error",
-           "exa_dims", "exa_batch_offsets", "exa_set_stream", "exa_obj", "exa_obj_noalloc", "exa_grad", "exa_cons",
+           "exa_dims", "exa_batch_offsets", "exa_set_theta", "exa_set_stream", "exa_obj", "exa_obj_noalloc", "exa_grad", "exa_cons",
            "exa_jac_structure", "exa_jac_coord", "exa_hess_structure", "exa_hess_coord",
            "exa_jac_csc_structure", "exa_hess_csc_structure", "exa_jac_csc", "exa_hess_csc",
            "exa_eval_all", "exa_jprod", "exa_jtprod", "exa_hprod", "exa_check_status",
@@ -91,6 +91,7 @@ def load():
             "exa_dims": [vp, i64p, i64p, i64p, i64p, i64p, i64p],
             "exa_batch_offsets": [vp, C.POINTER(C.c_int32), i64p, i64p, i64p, i64p],
             "exa_set_stream": [vp, vp],
+            "exa_set_theta": [vp, C.POINTER(C.c_double), C.c_int64],
             "exa_obj": [vp, dp, dp],
             "exa_obj_noalloc": [vp, dp, dp],
             "exa_grad": [vp, dp, dp],
@@ -263,6 +264,10 @@ class Model:
     def exa_jtprod(self, x, w, out): self._call("exa_jtprod", _ptr(x), _ptr(w), _ptr(out))
     def exa_hprod(self, x, y, s, v, out): self._call("exa_hprod", _ptr(x), _ptr(y), float(s), _ptr(v), _ptr(out))
     def exa_check_status(self): self._call("exa_check_status")
+
+    def exa_set_theta(self, theta):
+        t = np.ascontiguousarray(theta, dtype=np.float64)
+        self._call("exa_set_theta", t.ctypes.data_as(C.POINTER(C.c_double)), len(t))
 
     # ---- allocating conveniences
     def _empty(self, n, dtype=None):

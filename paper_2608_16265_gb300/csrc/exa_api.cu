@@ -1148,6 +1148,17 @@ exa_status exa_batch_offsets(const exa_model *m, int32_t *nb, int64_t *xoff, int
     return EXA_OK;
 }
 
+exa_status exa_set_theta(exa_model *m, const double *theta, int64_t npar) {
+    if (exa_status e = check_model(m)) return e;
+    if (npar != m->npar) return fail(m, EXA_E_INVALID, "theta must have npar = " + std::to_string(m->npar) + " values");
+    if (!npar) return EXA_OK;
+    if (!theta) return fail(m, EXA_E_INVALID, "NULL theta");
+    // ordered on the model's stream; synchronized so that the caller's array is free on return
+    CR(cudaMemcpyAsync(m->d_theta, theta, sizeof(double) * npar, cudaMemcpyHostToDevice, m->stream));
+    CR(cudaStreamSynchronize(m->stream));
+    return EXA_OK;
+}
+
 exa_status exa_set_stream(exa_model *m, void *stream) {
     if (!m) return EXA_E_INVALID;
     m->stream = (cudaStream_t)stream;

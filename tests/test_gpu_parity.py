@@ -319,3 +319,20 @@ def test_eval_all_graph_replay_matches_direct_launches():
     for a, b in zip(outs["graph"], outs["direct"]):
         for k in a:
             assert torch.equal(a[k], b[k]), k
+
+
+def test_set_theta():
+    """Changing the parameters of a created model gives the results of a model built with them."""
+    B = _B()
+    flat, (x, y, s) = CASES["all_ops"]()
+    m = B.exa_create(flat)
+    new_theta = np.array([-0.4, 2.5])
+    m.exa_set_theta(new_theta)
+    flat.theta = new_theta
+    o = oracle.Oracle(flat)
+    xt, yt = _t(x), _t(y)
+    assert abs(float(m.obj(xt).item()) - o.obj(x)) <= TOL * abs(o.obj(x))
+    assert normwise(_np(m.cons(xt)), o.cons(x)) <= TOL
+    assert normwise(_np(m.hess_coord(xt, yt, s)), o.hess_coord(x, y, s)) <= TOL
+    with pytest.raises(B.ExaError):
+        m.exa_set_theta(np.zeros(3))
