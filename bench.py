@@ -33,7 +33,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "Jac+Hess nonzeros/sec (full derivative evaluation, FP64)"
+METRIC = "Jac+Hess nonzeros/sec and % of HBM roofline; FP64 vs FP32-mixed vs batched"
 UNIT = "nnz/s"
 WORKLOAD = "acopf_batch_256"
 

@@ -336,3 +336,17 @@ def test_set_theta():
     assert normwise(_np(m.hess_coord(xt, yt, s)), o.hess_coord(x, y, s)) <= TOL
     with pytest.raises(B.ExaError):
         m.exa_set_theta(np.zeros(3))
+
+
+def test_invalid_arguments_are_reported():
+    """NULL arrays and wrong sizes come back as EXA_E_INVALID with a message; nothing is launched."""
+    B = _B()
+    flat, (x, y, s) = CASES["all_ops"]()
+    m = B.exa_create(flat)
+    xt = _t(x)
+    for call in (lambda: m.exa_jac_coord(xt, None), lambda: m.exa_hess_coord(xt, None, 1.0, _t(np.zeros(m.nnzh))),
+                 lambda: m.exa_obj(None, _t(np.zeros(1))), lambda: m.exa_eval_all(None, None, 1.0)):
+        with pytest.raises(B.ExaError) as e:
+            call()
+        assert e.value.status == B.EXA_E_INVALID and "NULL" in str(e.value)
+    m.exa_check_status()
