@@ -339,6 +339,8 @@ def run_exa(args):
               "nvar": m.nvar, "ncon": m.ncon, "create_s": t_create, "generate_s": t_gen,
               "eval_regs": m.stat("eval_regs"), "eval_block": m.stat("eval_block"),
               "eval_persist": m.stat("eval_persist"), "eval_grid": m.stat("eval_grid"), "eval_tiles": m.stat("eval_tiles"),
+              "eval_min_blocks": m.stat("eval_min_blocks"), "eval_split": m.stat("eval_split"),
+              "csc_direct": m.stat("csc_direct"), "nnzh_compressed": m.stat("nnzh_compressed"),
               "device_bytes": m.stat("device_bytes")}
     if not args.no_extras:
         v = torch.randn(m.nvar, dtype=torch.float64, device=dev)

@@ -76,6 +76,35 @@ __global__ void __launch_bounds__(256) k_seg_sum_warp(const int *__restrict__ pt
     if (valid) dst[s] = acc;
 }
 
+// out[i] = sum_{q in [ptr[i], ptr[i+1])} val[perm[q]] * v[other[perm[q]]], q ascending; one warp per
+// 32 consecutive segments with the products of the warp's range gathered into shared memory by all
+// lanes first (the k_seg_sum_warp scheme).
+__global__ void __launch_bounds__(256) k_spmv_warp(const int *__restrict__ ptr, const int *__restrict__ perm,
+                                                   const double *__restrict__ val, const int *__restrict__ other,
+                                                   const double *__restrict__ v, double *__restrict__ out, int n) {
+    __shared__ double buf[8][EXA_SEG_CHUNK];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long s0 = ((long long)blockIdx.x * 8 + w) * 32;
+    if (s0 >= n) return;
+    const int s = (int)s0 + lane;
+    const bool valid = s < n;
+    const int beg = ptr[s0], end = ptr[min((long long)n, s0 + 32)];
+    const int myb = valid ? ptr[s] : end, mye = valid ? ptr[s + 1] : end;
+    double acc = 0.0;
+    for (int c0 = beg; c0 < end; c0 += EXA_SEG_CHUNK) {
+        const int c1 = min(c0 + EXA_SEG_CHUNK, end);
+        for (int e = c0 + lane; e < c1; e += 32) {
+            const int p = __ldg(perm + e);
+            buf[w][e - c0] = __ldg(val + p) * __ldg(v + __ldg(other + p));
+        }
+        __syncwarp();
+        const int qb = max(myb, c0), qe = min(mye, c1);
+        for (int q = qb; q < qe; q++) acc += buf[w][q - c0];
+        __syncwarp();
+    }
+    if (valid) out[s] = acc;
+}
+
 // dst[i] = src[perm[i]]  (CSC of a COO pattern without duplicate entries: a pure permutation)
 __global__ void k_permute(const int *__restrict__ perm, const double *__restrict__ src,
                           double *__restrict__ dst, int n) {
@@ -92,20 +121,6 @@ __global__ void k_seg_add_rows(const int *__restrict__ rows, const int *__restri
     double s = c[rows[i]];
     for (int q = ptr[i], e = ptr[i + 1]; q < e; q++) s += src[perm[q]];
     c[rows[i]] = s;
-}
-
-// out[i] = sum_{q in [ptr[i], ptr[i+1])} val[perm[q]] * v[other[perm[q]]]
-__global__ void k_spmv_gather(const int *__restrict__ ptr, const int *__restrict__ perm,
-                              const double *__restrict__ val, const int *__restrict__ other,
-                              const double *__restrict__ v, double *__restrict__ out, int n) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double s = 0.0;
-    for (int q = ptr[i], e = ptr[i + 1]; q < e; q++) {
-        int p = perm[q];
-        s += val[p] * v[other[p]];
-    }
-    out[i] = s;
 }
 
 // Hv[i] from the lower-triangle CSC values: column i holds (r, i), r >= i, giving H_ir v_r; the
@@ -206,6 +221,7 @@ struct exa_model {
     int nobj[exa::M_COUNT] = {};  // objective partial sums written by each kernel kind
     int grid[exa::M_COUNT] = {};  // CTAs launched per kernel kind (<= ntiles: persistent tile loop)
     int persist = 0;              // persistent grid factor chosen by the tuner (0: one CTA per tile)
+    int min_blocks = 0;           // launch-bounds minimum CTAs per SM chosen by the tuner
     bool split_all = false;       // exa_eval_all: first- and second-order kernels instead of one
     bool csc_direct = false;      // duplicate-free CSC written by the evaluation kernel (scatter)
     std::vector<ExaPM> h_pms;     // host copy of the group descriptors
@@ -590,11 +606,13 @@ exa_status load_patterns(const exa_model_desc &d0, exa_model *m) {
 
 // Generates, compiles and loads the kernels for `block` threads per CTA and rebuilds the tile lists
 // (member-major, then groups in declaration order; BLOCK instances per tile).
-exa_status setup_kernels(exa_model *m, int block) {
+exa_status setup_kernels(exa_model *m, int block, int min_blocks = 0) {
     m->block = block;
+    m->min_blocks = min_blocks;
     exa::CodegenOptions cg;
     cg.precision = m->precision;
     cg.block = block;
+    cg.min_blocks = min_blocks;
     cg.bounds_check = m->bounds_check;
     std::string gerr;
     std::string src = exa::generate_source(m->pats, m->groups, cg, &gerr);
@@ -701,8 +719,41 @@ exa_status autotune(exa_model *m) {
             }
         }
     }
-    if (m->block != best_block)
-        if (exa_status e = setup_kernels(m, best_block)) return e;
+    // register budget: ask for 24 or 32 resident warps per SM through __launch_bounds__ (the
+    // compiler may spill); kept only when the fused kernel gets faster
+    int best_minb = 0;
+    for (int warps : {24, 32}) {
+        const int minb = warps * 32 / best_block;
+        if (minb < 1 || minb > 32) continue;
+        if (exa_status e = setup_kernels(m, best_block, minb)) return e;
+        if (m->regs[exa::M_ALL] * best_block * minb > 65536 + 1) continue;  // bound not honoured
+        int occ = 0;
+        CR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)m->fn[exa::M_ALL], best_block, 0));
+        if (occ < minb) continue;
+        CR(S.get(&part, std::max(m->nobj[exa::M_ALL], 1)));
+        ExaOut o{};
+        o.obj_part = part;
+        o.c = m->d_cbuf;
+        o.abuf = m->d_abuf;
+        o.gbuf = m->d_gbuf;
+        o.jac = m->d_jbuf;
+        o.hess = m->d_hbuf;
+        if (exa_status e = apply_grid(m, best_factor)) return e;
+        if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
+        CR(cudaEventRecord(e0, m->stream));
+        for (int r = 0; r < 5; r++)
+            if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
+        CR(cudaEventRecord(e1, m->stream));
+        CR(cudaEventSynchronize(e1));
+        float ms = 0;
+        CR(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            best_minb = minb;
+        }
+    }
+    if (m->block != best_block || m->min_blocks != best_minb)
+        if (exa_status e = setup_kernels(m, best_block, best_minb)) return e;
     if (exa_status e = apply_grid(m, best_factor)) return e;
     m->tune_ms = best / 5.0;
     // exa_eval_all with every output: one kernel or first/second order split, CSC by a separate
@@ -1508,7 +1559,7 @@ exa_status exa_jprod(exa_model *m, const double *x, const double *v, double *Jv)
     ExaOut o{};
     o.jac = m->d_jbuf;
     if (exa_status e = launch_eval(m, exa::M_JAC, x, nullptr, 0.0, o)) return e;
-    k_spmv_gather<<<grid_of(m->ncon, 256), 256, 0, m->stream>>>(m->d_jrptr, m->d_jrperm, m->d_jbuf, m->d_jcol, v, Jv,
+    k_spmv_warp<<<grid_of(m->ncon, 256), 256, 0, m->stream>>>(m->d_jrptr, m->d_jrperm, m->d_jbuf, m->d_jcol, v, Jv,
                                                                  (int)m->ncon);
     CR(cudaGetLastError());
     return EXA_OK;
@@ -1522,7 +1573,7 @@ exa_status exa_jtprod(exa_model *m, const double *x, const double *w, double *Jt
     ExaOut o{};
     o.jac = m->d_jbuf;
     if (exa_status e = launch_eval(m, exa::M_JAC, x, nullptr, 0.0, o)) return e;
-    k_spmv_gather<<<grid_of(m->nvar, 256), 256, 0, m->stream>>>(m->d_jcolptr_coo, m->d_jperm, m->d_jbuf, m->d_jrow, w,
+    k_spmv_warp<<<grid_of(m->nvar, 256), 256, 0, m->stream>>>(m->d_jcolptr_coo, m->d_jperm, m->d_jbuf, m->d_jrow, w,
                                                                  Jtw, (int)m->nvar);
     CR(cudaGetLastError());
     return EXA_OK;
@@ -1598,6 +1649,7 @@ exa_status exa_stat(const exa_model *m, const char *key, double *value) {
     else if (k == "eval_regs_jac") *value = m->regs[exa::M_JAC];
     else if (k == "eval_block") *value = m->block;
     else if (k == "eval_persist") *value = m->persist;
+    else if (k == "eval_min_blocks") *value = m->min_blocks;
     else if (k == "eval_grid") *value = m->grid[exa::M_ALL];
     else if (k == "tune_ms") *value = m->tune_ms;
     else if (k == "eval_split") *value = m->split_all;

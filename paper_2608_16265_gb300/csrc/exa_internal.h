@@ -125,6 +125,7 @@ std::string analyse_pattern(Pattern &p);
 struct CodegenOptions {
     int precision = EXA_FP64;
     int block = 128;
+    int min_blocks = 0;  // __launch_bounds__ minimum resident CTAs per SM (0: not given)
     bool bounds_check = false;
 };
 std::string generate_source(const std::vector<Pattern> &pats, const std::vector<Group> &groups,

@@ -1181,6 +1181,8 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
     src << "// generated by exa_lower.cpp (" << (mixed ? "mixed FP32/FP64" : "FP64") << ")\n";
     src << kDeviceStructs << "\n";
     src << "#define EXA_BLOCK " << opt.block << "\n";
+    if (opt.min_blocks > 0) src << "#define EXA_BOUNDS __launch_bounds__(EXA_BLOCK, " << opt.min_blocks << ")\n";
+    else src << "#define EXA_BOUNDS __launch_bounds__(EXA_BLOCK)\n";
     if (mixed) src << kMixedHelpers;
     // one shared expression graph per group
     std::vector<Graph> graphs(groups.size());
@@ -1210,7 +1212,7 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
         const bool objred = (m == M_OBJ || mode_all(m) || m == M_FIRST);
         // Tile loop: with gridDim.x == ntiles every CTA takes one tile; a smaller (persistent) grid
         // strides over the tile list.  tl.oslot and the trip count are uniform over the CTA.
-        src << "extern \"C\" __global__ void __launch_bounds__(EXA_BLOCK) exa_" << kModeName[m]
+        src << "extern \"C\" __global__ void EXA_BOUNDS exa_" << kModeName[m]
             << "(const ExaTile* __restrict__ tiles, const int ntiles, const ExaPM* __restrict__ pms,"
                " const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ th,"
                " const double sigma, const ExaOut o, const ExaStructOut so) {\n";
