@@ -262,7 +262,11 @@ def run_exa(args):
     flats = [w.flat for w in wls]
     t_gen = time.perf_counter() - t0
     t0 = time.perf_counter()
-    m = B.exa_create_batch(flats, precision=prec, device=local)
+    pin = {}
+    if args.pin:
+        b_, mb_, gf_, fl_ = (int(v) for v in args.pin.split(","))
+        pin = dict(block=b_, min_blocks=mb_, grid_factor=gf_, flags=fl_ | B.EXA_FLAG_NO_TUNE)
+    m = B.exa_create_batch(flats, precision=prec, device=local, **pin)
     torch.cuda.synchronize()
     t_create = time.perf_counter() - t0
     dev = torch.device(f"cuda:{local}")
@@ -340,7 +344,9 @@ def run_exa(args):
               "eval_regs": m.stat("eval_regs"), "eval_block": m.stat("eval_block"),
               "eval_persist": m.stat("eval_persist"), "eval_grid": m.stat("eval_grid"), "eval_tiles": m.stat("eval_tiles"),
               "eval_min_blocks": m.stat("eval_min_blocks"), "eval_split": m.stat("eval_split"),
-              "csc_direct": m.stat("csc_direct"), "nnzh_compressed": m.stat("nnzh_compressed"),
+              "csc_direct": m.stat("csc_direct"), "hess_compressed": m.stat("hess_compressed"),
+              "nnzh_compressed": m.stat("nnzh_compressed"), "max_segment": m.stat("max_segment"),
+              "tuned_options": ",".join(str(v) for v in m.tuned_options().values()),
               "device_bytes": m.stat("device_bytes")}
     if not args.no_extras:
         v = torch.randn(m.nvar, dtype=torch.float64, device=dev)
@@ -455,6 +461,8 @@ def main(argv=None):
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--pin", default="", help="block,min_blocks,grid_factor,flags: fixed launch configuration "
+                    "(extras.tuned_options of an earlier run) instead of autotuning, for profiling runs")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

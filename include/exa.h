@@ -138,7 +138,8 @@ typedef struct {
     int32_t grid_factor;   /* evaluation grid: 0 = chosen by the autotuner (one CTA per tile when
                               tuning is off), -1 = one CTA per tile, n > 0 = persistent grid of n
                               waves of resident CTAs looping over the tiles */
-    int32_t pad;
+    int32_t min_blocks;    /* launch-bounds minimum resident CTAs per SM of the evaluation kernels
+                              (caps their registers), 0..32; 0 = none, or chosen by the autotuner */
 } exa_options;
 
 enum {
@@ -146,8 +147,15 @@ enum {
                                   the next exa_check_status return EXA_E_BOUNDS */
     EXA_FLAG_NO_TUNE = 2,      /* skip the launch-shape autotuner at creation */
     EXA_FLAG_NO_FUSE = 4,      /* evaluate every pattern in its own thread (no fused groups) */
-    EXA_FLAG_NO_GRAPH = 8      /* exa_eval_all launches its kernels directly instead of replaying a
+    EXA_FLAG_NO_GRAPH = 8,     /* exa_eval_all launches its kernels directly instead of replaying a
                                   cached CUDA graph */
+    /* The next three fix choices the autotuner otherwise makes (they apply as given when tuning is
+     * off: EXA_FLAG_NO_TUNE, or block_threads / grid_factor set).  exa_stat reports the choices. */
+    EXA_FLAG_SPLIT = 16,       /* exa_eval_all evaluates first and second order in two kernels */
+    EXA_FLAG_CSC_SCATTER = 32, /* a duplicate-free CSC is scattered by the evaluation kernel instead
+                                  of gathered from the COO values by a permutation kernel */
+    EXA_FLAG_NO_HCOMP = 64     /* the Hessian CSC is summed from the COO slots instead of from the
+                                  per-instance sums of the slots of a fused group that share an entry */
 };
 
 /* Validate the descriptor (Sec. 3.4 SIMDFunction), lower every pattern to generated device
@@ -265,8 +273,11 @@ exa_status exa_check_status(exa_model *m);
 exa_status exa_compile_check(const exa_model_desc *desc, const exa_options *opt, char *log,
                              size_t loglen);
 
-/* Named statistics (host values): "nvrtc_ms", "create_ms", "eval_regs", "eval_block",
- * "eval_tiles", "device_bytes", "n_patterns", "batch_members".  Unknown key: EXA_E_INVALID. */
+/* Named statistics (host values): "nvrtc_ms", "create_ms", "tune_ms", "eval_regs", "eval_block",
+ * "eval_regs_jac", "eval_regs_hess", "eval_tiles", "eval_grid", "eval_persist", "eval_min_blocks",
+ * "eval_split", "csc_direct",
+ * "hess_compressed", "nnzh_compressed", "max_segment", "device_bytes", "n_patterns", "batch_members".
+ * Unknown key: EXA_E_INVALID. */
 exa_status exa_stat(const exa_model *m, const char *key, double *value);
 
 #ifdef __cplusplus

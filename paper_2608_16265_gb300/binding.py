@@ -24,6 +24,7 @@ EXA_OK, EXA_E_INVALID, EXA_E_OOM, EXA_E_NVRTC, EXA_E_CUDA, EXA_E_BOUNDS, EXA_E_T
     EXA_E_UNSUPPORTED, EXA_E_INTERNAL = range(9)
 EXA_FP64, EXA_MIXED_FP32 = 0, 1
 EXA_FLAG_BOUNDS_CHECK, EXA_FLAG_NO_TUNE, EXA_FLAG_NO_FUSE, EXA_FLAG_NO_GRAPH = 1, 2, 4, 8
+EXA_FLAG_SPLIT, EXA_FLAG_CSC_SCATTER, EXA_FLAG_NO_HCOMP = 16, 32, 64
 STATUS_NAMES = ["EXA_OK", "EXA_E_INVALID", "EXA_E_OOM", "EXA_E_NVRTC", "EXA_E_CUDA", "EXA_E_BOUNDS",
                 "EXA_E_TIMEOUT", "EXA_E_UNSUPPORTED", "EXA_E_INTERNAL"]
 
@@ -66,7 +67,7 @@ class exa_model_desc(C.Structure):
 
 class exa_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("device", C.c_int32), ("block_threads", C.c_int32),
-                ("flags", C.c_int32), ("grid_factor", C.c_int32), ("pad", C.c_int32)]
+                ("flags", C.c_int32), ("grid_factor", C.c_int32), ("min_blocks", C.c_int32)]
 
 
 _lib = None
@@ -158,8 +159,8 @@ class _Desc:
                                    theta.ctypes.data_as(C.POINTER(C.c_double)), len(flat.patterns), 0, pats)
 
 
-def _opts(precision, block, flags, device, grid_factor=0):
-    return exa_options(precision, device, block, flags, grid_factor, 0)
+def _opts(precision, block, flags, device, grid_factor=0, min_blocks=0):
+    return exa_options(precision, device, block, flags, grid_factor, min_blocks)
 
 
 def _ptr(t) -> Optional[int]:
@@ -175,17 +176,17 @@ def _stream():
 
 # ------------------------------------------------------------------ ABI-named functions
 def exa_create(flat: ir.FlatModel, precision: int = EXA_FP64, block: int = 0, flags: int = 0,
-               device: int = 0, grid_factor: int = 0) -> "Model":
-    return exa_create_batch([flat], precision, block, flags, device, grid_factor)
+               device: int = 0, grid_factor: int = 0, min_blocks: int = 0) -> "Model":
+    return exa_create_batch([flat], precision, block, flags, device, grid_factor, min_blocks)
 
 
 def exa_create_batch(flats: Sequence[ir.FlatModel], precision: int = EXA_FP64, block: int = 0,
-                     flags: int = 0, device: int = 0, grid_factor: int = 0) -> "Model":
+                     flags: int = 0, device: int = 0, grid_factor: int = 0, min_blocks: int = 0) -> "Model":
     lib = load()
     descs = [_Desc(f) for f in flats]
     arr = (C.POINTER(exa_model_desc) * len(descs))(*[C.pointer(d.desc) for d in descs])
     h = C.c_void_p()
-    opt = _opts(precision, block, flags, device, grid_factor)
+    opt = _opts(precision, block, flags, device, grid_factor, min_blocks)
     rc = lib.exa_create_batch(arr, len(descs), C.byref(opt), C.byref(h))
     if rc != EXA_OK:
         raise ExaError(rc, lib.exa_create_error().decode())
@@ -236,6 +237,16 @@ class Model:
             self.destroy()
         except Exception:
             pass
+
+    def tuned_options(self) -> dict:
+        """Creation options that reproduce this model's launch configuration without tuning."""
+        flags = EXA_FLAG_NO_TUNE
+        flags |= EXA_FLAG_SPLIT if self.stat("eval_split") else 0
+        flags |= EXA_FLAG_CSC_SCATTER if self.stat("csc_direct") else 0
+        flags |= EXA_FLAG_NO_HCOMP if not self.stat("hess_compressed") else 0
+        persist = int(self.stat("eval_persist"))
+        return dict(block=int(self.stat("eval_block")), min_blocks=int(self.stat("eval_min_blocks")),
+                    grid_factor=persist if persist > 0 else -1, flags=flags)
 
     def stat(self, key: str) -> float:
         v = C.c_double()

@@ -49,6 +49,11 @@ __global__ void k_obj_final(const double *__restrict__ part, int n, double *__re
     }
 }
 
+// The gathers below are latency-bound unless each thread keeps several independent loads in
+// flight: a gather is an index load followed by a dependent value load, so EXA_ILP of them are
+// issued back to back (indices first, then values) before any result is used.
+#define EXA_ILP 8
+
 // dst[i] = sum_{q in [ptr[i], ptr[i+1])} src[perm[q]], q ascending (ascending COO index).  One warp
 // per 32 consecutive segments: the warp first gathers the values of its segments (one contiguous
 // range of sorted positions) into shared memory with every lane loading in parallel, then each lane
@@ -67,7 +72,18 @@ __global__ void __launch_bounds__(256) k_seg_sum_warp(const int *__restrict__ pt
     double acc = 0.0;
     for (int c0 = beg; c0 < end; c0 += EXA_SEG_CHUNK) {
         const int c1 = min(c0 + EXA_SEG_CHUNK, end);
-        for (int e = c0 + lane; e < c1; e += 32) buf[w][e - c0] = __ldg(src + __ldg(perm + e));
+        int p[EXA_ILP];
+#pragma unroll
+        for (int u = 0; u < EXA_ILP; u++) {
+            const int e = c0 + lane + 32 * u;
+            p[u] = e < c1 ? __ldg(perm + e) : -1;
+        }
+        double v[EXA_ILP];
+#pragma unroll
+        for (int u = 0; u < EXA_ILP; u++) v[u] = p[u] >= 0 ? __ldg(src + p[u]) : 0.0;
+#pragma unroll
+        for (int u = 0; u < EXA_ILP; u++)
+            if (p[u] >= 0) buf[w][lane + 32 * u] = v[u];
         __syncwarp();
         const int qb = max(myb, c0), qe = min(mye, c1);
         for (int q = qb; q < qe; q++) acc += buf[w][q - c0];
@@ -93,10 +109,23 @@ __global__ void __launch_bounds__(256) k_spmv_warp(const int *__restrict__ ptr, 
     double acc = 0.0;
     for (int c0 = beg; c0 < end; c0 += EXA_SEG_CHUNK) {
         const int c1 = min(c0 + EXA_SEG_CHUNK, end);
-        for (int e = c0 + lane; e < c1; e += 32) {
-            const int p = __ldg(perm + e);
-            buf[w][e - c0] = __ldg(val + p) * __ldg(v + __ldg(other + p));
+        int p[EXA_ILP], o[EXA_ILP];
+#pragma unroll
+        for (int u = 0; u < EXA_ILP; u++) {
+            const int e = c0 + lane + 32 * u;
+            p[u] = e < c1 ? __ldg(perm + e) : -1;
         }
+#pragma unroll
+        for (int u = 0; u < EXA_ILP; u++) o[u] = p[u] >= 0 ? __ldg(other + p[u]) : 0;
+        double a[EXA_ILP], b[EXA_ILP];
+#pragma unroll
+        for (int u = 0; u < EXA_ILP; u++) {
+            a[u] = p[u] >= 0 ? __ldg(val + p[u]) : 0.0;
+            b[u] = p[u] >= 0 ? __ldg(v + o[u]) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < EXA_ILP; u++)
+            if (p[u] >= 0) buf[w][lane + 32 * u] = a[u] * b[u];
         __syncwarp();
         const int qb = max(myb, c0), qe = min(mye, c1);
         for (int q = qb; q < qe; q++) acc += buf[w][q - c0];
@@ -105,11 +134,89 @@ __global__ void __launch_bounds__(256) k_spmv_warp(const int *__restrict__ ptr, 
     if (valid) out[s] = acc;
 }
 
-// dst[i] = src[perm[i]]  (CSC of a COO pattern without duplicate entries: a pure permutation)
-__global__ void k_permute(const int *__restrict__ perm, const double *__restrict__ src,
-                          double *__restrict__ dst, int n) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = src[perm[i]];
+// dst[i] = src[perm[i]]  (CSC of a COO pattern without duplicate entries: a pure permutation).
+// A block covers EXA_ILP x 256 consecutive positions; thread t takes positions t, t + 256, ... so
+// that the index loads and the stores stay coalesced.
+__global__ void __launch_bounds__(256) k_permute(const int *__restrict__ perm, const double *__restrict__ src,
+                                                 double *__restrict__ dst, long long n) {
+    const long long i0 = (long long)blockIdx.x * (256 * EXA_ILP) + threadIdx.x;
+    int p[EXA_ILP];
+#pragma unroll
+    for (int u = 0; u < EXA_ILP; u++) p[u] = i0 + 256 * u < n ? __ldg(perm + i0 + 256 * u) : -1;
+    double v[EXA_ILP];
+#pragma unroll
+    for (int u = 0; u < EXA_ILP; u++) v[u] = p[u] >= 0 ? __ldg(src + p[u]) : 0.0;
+#pragma unroll
+    for (int u = 0; u < EXA_ILP; u++)
+        if (p[u] >= 0) dst[i0 + 256 * u] = v[u];
+}
+
+// Segmented sums over short segments (at most EXA_SEG_SHORT entries each, the common case): with
+// ROWS, dst[rows[s]] += the sum of segment s; without, dst[s] = the sum.  Entries are added in
+// ascending position order starting from 0.0 (or from the current dst value), as in
+// k_seg_sum_warp / k_seg_add_rows, so the results are the same bit for bit.  Thread t of a block
+// takes the segments base + t + 256 u (u < EXA_SEGS), and the first EXA_SEG_UNROLL entries of all of
+// them are fetched with independent loads before any is added; longer segments continue in chunks.
+#define EXA_SEGS 4
+#define EXA_SEG_UNROLL 4
+#define EXA_SEG_SHORT 32
+template <bool ROWS>
+__global__ void __launch_bounds__(256) k_seg_sum_ilp(const int *__restrict__ ptr, const int *__restrict__ perm,
+                                                     const double *__restrict__ src, double *__restrict__ dst,
+                                                     const int *__restrict__ rows, long long n) {
+    const long long s0 = (long long)blockIdx.x * (256 * EXA_SEGS) + threadIdx.x;
+    int b[EXA_SEGS], e[EXA_SEGS];
+#pragma unroll
+    for (int u = 0; u < EXA_SEGS; u++) {
+        const long long s = s0 + 256 * u;
+        b[u] = s < n ? __ldg(ptr + s) : 0;
+        e[u] = s < n ? __ldg(ptr + s + 1) : 0;
+    }
+    int p[EXA_SEGS][EXA_SEG_UNROLL];
+#pragma unroll
+    for (int u = 0; u < EXA_SEGS; u++)
+#pragma unroll
+        for (int j = 0; j < EXA_SEG_UNROLL; j++) p[u][j] = b[u] + j < e[u] ? __ldg(perm + b[u] + j) : -1;
+    double v[EXA_SEGS][EXA_SEG_UNROLL];
+#pragma unroll
+    for (int u = 0; u < EXA_SEGS; u++)
+#pragma unroll
+        for (int j = 0; j < EXA_SEG_UNROLL; j++) v[u][j] = p[u][j] >= 0 ? __ldg(src + p[u][j]) : 0.0;
+    int r[EXA_SEGS];
+    double acc[EXA_SEGS];
+#pragma unroll
+    for (int u = 0; u < EXA_SEGS; u++) {
+        const long long s = s0 + 256 * u;
+        r[u] = ROWS && s < n ? __ldg(rows + s) : (int)s;
+        acc[u] = ROWS && s < n ? dst[r[u]] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < EXA_SEGS; u++) {
+        if (s0 + 256 * u >= n) continue;
+#pragma unroll
+        for (int j = 0; j < EXA_SEG_UNROLL; j++)
+            if (p[u][j] >= 0) acc[u] += v[u][j];
+        for (int q0 = b[u] + EXA_SEG_UNROLL; q0 < e[u]; q0 += EXA_SEG_UNROLL) {
+            int pp[EXA_SEG_UNROLL];
+            double vv[EXA_SEG_UNROLL];
+#pragma unroll
+            for (int j = 0; j < EXA_SEG_UNROLL; j++) pp[j] = q0 + j < e[u] ? __ldg(perm + q0 + j) : -1;
+#pragma unroll
+            for (int j = 0; j < EXA_SEG_UNROLL; j++) vv[j] = pp[j] >= 0 ? __ldg(src + pp[j]) : 0.0;
+#pragma unroll
+            for (int j = 0; j < EXA_SEG_UNROLL; j++)
+                if (pp[j] >= 0) acc[u] += vv[j];
+        }
+        dst[ROWS ? (long long)r[u] : s0 + 256 * u] = acc[u];
+    }
+}
+
+// Largest segment length of a pointer array (setup).
+__global__ void k_max_seg(const int *__restrict__ ptr, long long n, int *__restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = i < n ? ptr[i + 1] - ptr[i] : 0;
+    const int w = __reduce_max_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0 && w > 0) atomicMax(out, w);
 }
 
 // c[rows[i]] += sum of the augmentation terms of that row (rows listed once each)
@@ -235,6 +342,10 @@ struct exa_model {
     uint64_t graph_clock = 0;
     bool use_graphs = true;
     cudaStream_t cap_stream = nullptr;
+    // exa_eval_all runs its independent reductions (Jacobian CSC, Hessian CSC, the rest) on three
+    // streams forked from and joined back into the model stream
+    cudaStream_t side[2] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[2] = {};
     double *d_theta = nullptr;
     int *d_status = nullptr;
     int *d_jrow = nullptr, *d_jcol = nullptr, *d_hrow = nullptr, *d_hcol = nullptr, *d_gvar = nullptr, *d_arow = nullptr;
@@ -246,7 +357,10 @@ struct exa_model {
     // compressed Hessian (per-instance sums of a group's slots with equal (row, col)): structure,
     // permutation sorted by (col, row) and segment pointers per Hessian CSC entry
     i64 nnzhc = 0;
-    bool use_hcomp = false;
+    bool has_hcomp = false;       // group-compressed Hessian sums exist (fewer than the COO slots)
+    // longest segment of each segmented sum (picks the per-thread or the warp-cooperative kernel)
+    int maxseg_j = 0, maxseg_h = 0, maxseg_hc = 0, maxseg_g = 0, maxseg_a = 0;
+    bool use_hcomp = false;       // ... and feed the Hessian CSC (tuner choice)
     int *d_hcrow = nullptr, *d_hccol = nullptr, *d_hcperm = nullptr, *d_hcsegptr = nullptr;
     double *d_hcbuf = nullptr;
     // Hessian CSC seen by rows (products): column of each CSC entry, row-sorted permutation
@@ -302,6 +416,14 @@ void free_all(exa_model *m) {
     m->graphs.clear();
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     m->cap_stream = nullptr;
+    for (int s = 0; s < 2; s++) {
+        if (m->side[s]) cudaStreamDestroy(m->side[s]);
+        if (m->ev_join[s]) cudaEventDestroy(m->ev_join[s]);
+        m->side[s] = nullptr;
+        m->ev_join[s] = nullptr;
+    }
+    if (m->ev_fork) cudaEventDestroy(m->ev_fork);
+    m->ev_fork = nullptr;
     for (int k = 0; k < exa::M_COUNT; k++) {
         if (m->d_tiles[k]) cudaFree(m->d_tiles[k]);
         m->d_tiles[k] = nullptr;
@@ -447,6 +569,20 @@ exa_status build_ptr(exa_model *m, const unsigned long long *skeys, int shift, i
     return EXA_OK;
 }
 
+// Longest segment of ptr[0..n] (n segments).
+exa_status max_seg(exa_model *m, Scratch &S, const int *ptr, i64 n, int *out) {
+    *out = 0;
+    if (n <= 0) return EXA_OK;
+    int *d = nullptr;
+    CR(S.get(&d, 1));
+    CR(cudaMemsetAsync(d, 0, sizeof(int), m->stream));
+    k_max_seg<<<grid_of(n, 256), 256, 0, m->stream>>>(ptr, (long long)n, d);
+    CR(cudaGetLastError());
+    CR(cudaMemcpyAsync(out, d, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    CR(cudaStreamSynchronize(m->stream));
+    return EXA_OK;
+}
+
 // Per-model structure: CSC of J and H, row groupings, gradient and augmentation segments.
 exa_status build_structure(exa_model *m) {
     Scratch S{m};
@@ -498,7 +634,7 @@ exa_status build_structure(exa_model *m) {
     if (exa_status e = build_ptr(m, segkey, 32, nseg, m->nvar, &m->d_hcolptr)) return e;
 
     // ---- compressed Hessian: its (col, row)-sorted segments are the Hessian CSC entries
-    if (m->use_hcomp) {
+    if (m->has_hcomp) {
         const int nc = (int)m->nnzhc;
         unsigned long long *ck = nullptr;
         CR(S.get(&ck, nc));
@@ -553,6 +689,13 @@ exa_status build_structure(exa_model *m) {
         k_low32<<<grid_of(nseg, 256), 256, 0, m->stream>>>(segkey, m->d_arows, nseg);
         CR(cudaGetLastError());
     }
+    // longest segments: the segmented sums pick their kernel by them
+    if (exa_status e = max_seg(m, S, m->d_jsegptr, m->nnzj_csc, &m->maxseg_j)) return e;
+    if (exa_status e = max_seg(m, S, m->d_hsegptr, m->nnzh_csc, &m->maxseg_h)) return e;
+    if (m->has_hcomp)
+        if (exa_status e = max_seg(m, S, m->d_hcsegptr, m->nnzh_csc, &m->maxseg_hc)) return e;
+    if (exa_status e = max_seg(m, S, m->d_gptr, m->nvar, &m->maxseg_g)) return e;
+    if (exa_status e = max_seg(m, S, m->d_aptr, m->n_aug_rows, &m->maxseg_a)) return e;
     CR(cudaStreamSynchronize(m->stream));
     return EXA_OK;
 }
@@ -764,12 +907,14 @@ exa_status autotune(exa_model *m) {
     CR(S.get(&jc, m->nnzj_csc));
     CR(S.get(&hc, m->nnzh_csc));
     double best_step = 1e30;
-    bool best_split = false, best_direct = false;
+    bool best_split = false, best_direct = false, best_hc = m->use_hcomp;
+    for (int hcv = 0; hcv < (m->has_hcomp ? 2 : 1); hcv++)
     for (int split = 0; split < 2; split++)
         for (int direct = 0; direct < 2; direct++) {
             if (direct && m->nnzj_csc != m->nnzj && m->nnzh_csc != m->nnzh) continue;
             m->split_all = split;
             m->csc_direct = direct;
+            m->use_hcomp = hcv;
             if (exa_status e = eval_all_launches(m, x, y, 1.0, f, g, m->d_cbuf, m->d_jbuf, m->d_hbuf, jc, hc)) return e;
             CR(cudaEventRecord(e0, m->stream));
             for (int r = 0; r < 3; r++)
@@ -782,10 +927,12 @@ exa_status autotune(exa_model *m) {
                 best_step = ms;
                 best_split = split;
                 best_direct = direct;
+                best_hc = hcv;
             }
         }
     m->split_all = best_split;
     m->csc_direct = best_direct;
+    m->use_hcomp = best_hc;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return EXA_OK;
@@ -900,6 +1047,9 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     m->block = o.block_threads ? o.block_threads : 128;
     if (m->block % 32 || m->block < 32 || m->block > 1024) return fail(m, EXA_E_INVALID, "block_threads must be a multiple of 32 in [32, 1024]");
     if (o.grid_factor < -1 || o.grid_factor > 64) return fail(m, EXA_E_INVALID, "grid_factor must be in [-1, 64]");
+    if (o.min_blocks < 0 || o.min_blocks > 32) return fail(m, EXA_E_INVALID, "min_blocks must be in [0, 32]");
+    m->split_all = (o.flags & EXA_FLAG_SPLIT) != 0;
+    m->csc_direct = (o.flags & EXA_FLAG_CSC_SCATTER) != 0;
     if (nb < 1) return fail(m, EXA_E_INVALID, "empty batch");
     for (int b = 0; b < nb; b++) {
         const exa_model_desc *d = descs[b];
@@ -1067,7 +1217,7 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     CR(cudaMemcpy(m->d_pm, pms.data(), sizeof(ExaPM) * pms.size(), cudaMemcpyHostToDevice));
 
     m->h_pms = pms;
-    if (exa_status e = setup_kernels(m, m->block)) return e;
+    if (exa_status e = setup_kernels(m, m->block, o.min_blocks)) return e;
 
     // structure pass on the device
     CR(dalloc(m, &m->d_jrow, m->nnzj));
@@ -1076,8 +1226,9 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     CR(dalloc(m, &m->d_hcol, m->nnzh));
     CR(dalloc(m, &m->d_gvar, m->nnzg));
     CR(dalloc(m, &m->d_arow, m->naug));
-    m->use_hcomp = m->nnzhc < m->nnzh;
-    if (m->use_hcomp) {
+    m->has_hcomp = m->nnzhc < m->nnzh;
+    m->use_hcomp = m->has_hcomp && !(o.flags & EXA_FLAG_NO_HCOMP);
+    if (m->has_hcomp) {
         CR(dalloc(m, &m->d_hcrow, m->nnzhc));
         CR(dalloc(m, &m->d_hccol, m->nnzhc));
     }
@@ -1085,7 +1236,7 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
         ExaOut out{};
         out.status = m->d_status;
         ExaStructOut so{m->d_jrow, m->d_jcol, m->d_hrow, m->d_hcol, m->d_gvar, m->d_arow,
-                        m->use_hcomp ? m->d_hcrow : nullptr, m->use_hcomp ? m->d_hccol : nullptr, m->d_status};
+                        m->has_hcomp ? m->d_hcrow : nullptr, m->has_hcomp ? m->d_hccol : nullptr, m->d_status};
         const double *nul = nullptr;
         double sigma = 0;
         int nt = m->ntiles[exa::M_STRUCT];
@@ -1287,6 +1438,19 @@ exa_status exa_obj_noalloc(exa_model *m, const double *x, double *f) {
     return EXA_OK;
 }
 
+// dst[s] = sum over segment s of src[perm[q]] (q ascending), s < n: the per-thread kernel when every
+// segment is short, else the warp-cooperative one.
+static exa_status seg_sum(exa_model *m, const int *ptr, const int *perm, const double *src, double *dst, i64 n,
+                          int maxseg, cudaStream_t st) {
+    if (n <= 0) return EXA_OK;
+    if (maxseg <= EXA_SEG_SHORT)
+        k_seg_sum_ilp<false><<<grid_of(n, 256 * EXA_SEGS), 256, 0, st>>>(ptr, perm, src, dst, nullptr, (long long)n);
+    else
+        k_seg_sum_warp<<<grid_of(n, 256), 256, 0, st>>>(ptr, perm, src, dst, (int)n);
+    CR(cudaGetLastError());
+    return EXA_OK;
+}
+
 exa_status exa_grad(exa_model *m, const double *x, double *g) {
     if (exa_status e = check_model(m)) return e;
     CHECK_PTRS(x, g);
@@ -1294,16 +1458,19 @@ exa_status exa_grad(exa_model *m, const double *x, double *g) {
     o.gbuf = m->d_gbuf;
     if (exa_status e = launch_eval(m, exa::M_GRAD, x, nullptr, 0.0, o)) return e;
     if (m->nvar) {
-        k_seg_sum_warp<<<grid_of(m->nvar, 256), 256, 0, m->stream>>>(m->d_gptr, m->d_gperm, m->d_gbuf, g, (int)m->nvar);
-        CR(cudaGetLastError());
+        if (exa_status e = seg_sum(m, m->d_gptr, m->d_gperm, m->d_gbuf, g, m->nvar, m->maxseg_g, m->stream)) return e;
     }
     return EXA_OK;
 }
 
 static exa_status aug_rows(exa_model *m, double *c) {
     if (m->n_aug_rows) {
-        k_seg_add_rows<<<grid_of(m->n_aug_rows, 256), 256, 0, m->stream>>>(m->d_arows, m->d_aptr, m->d_aperm,
-                                                                              m->d_abuf, c, m->n_aug_rows);
+        if (m->maxseg_a <= EXA_SEG_SHORT)
+            k_seg_sum_ilp<true><<<grid_of(m->n_aug_rows, 256 * EXA_SEGS), 256, 0, m->stream>>>(
+                m->d_aptr, m->d_aperm, m->d_abuf, c, m->d_arows, (long long)m->n_aug_rows);
+        else
+            k_seg_add_rows<<<grid_of(m->n_aug_rows, 256), 256, 0, m->stream>>>(m->d_arows, m->d_aptr, m->d_aperm,
+                                                                                  m->d_abuf, c, m->n_aug_rows);
         CR(cudaGetLastError());
     }
     return EXA_OK;
@@ -1384,10 +1551,10 @@ exa_status exa_hess_csc_structure(const exa_model *mc, int32_t *colptr, int32_t 
 }
 
 static exa_status scatter_csc(exa_model *m, const int *segptr, const int *perm, const double *coo, double *csc,
-                              i64 n, i64 nnz) {
+                              i64 n, i64 nnz, int maxseg, cudaStream_t st) {
     if (!n) return EXA_OK;
-    if (n == nnz) k_permute<<<grid_of(n, 256), 256, 0, m->stream>>>(perm, coo, csc, (int)n);
-    else k_seg_sum_warp<<<grid_of(n, 256), 256, 0, m->stream>>>(segptr, perm, coo, csc, (int)n);
+    if (n != nnz) return seg_sum(m, segptr, perm, coo, csc, n, maxseg, st);
+    k_permute<<<grid_of(n, 256 * EXA_ILP), 256, 0, st>>>(perm, coo, csc, (long long)n);
     CR(cudaGetLastError());
     return EXA_OK;
 }
@@ -1405,7 +1572,7 @@ exa_status exa_jac_csc(exa_model *m, const double *x, double *vals_csc) {
         return launch_eval(m, exa::M_JAC, x, nullptr, 0.0, o);
     }
     if (exa_status e = launch_eval(m, exa::M_JAC, x, nullptr, 0.0, o)) return e;
-    return scatter_csc(m, m->d_jsegptr, m->d_jperm, m->d_jbuf, vals_csc, m->nnzj_csc, m->nnzj);
+    return scatter_csc(m, m->d_jsegptr, m->d_jperm, m->d_jbuf, vals_csc, m->nnzj_csc, m->nnzj, m->maxseg_j, m->stream);
 }
 
 exa_status exa_hess_csc(exa_model *m, const double *x, const double *y, double sigma, double *vals_csc) {
@@ -1425,13 +1592,10 @@ exa_status exa_hess_csc(exa_model *m, const double *x, const double *y, double s
         o.hess = nullptr;
         o.hcomp = m->d_hcbuf;
         if (exa_status e = launch_eval(m, exa::M_HESS_C, x, y, sigma, o)) return e;
-        k_seg_sum_warp<<<grid_of(m->nnzh_csc, 256), 256, 0, m->stream>>>(m->d_hcsegptr, m->d_hcperm, m->d_hcbuf,
-                                                                           vals_csc, (int)m->nnzh_csc);
-        CR(cudaGetLastError());
-        return EXA_OK;
+        return seg_sum(m, m->d_hcsegptr, m->d_hcperm, m->d_hcbuf, vals_csc, m->nnzh_csc, m->maxseg_hc, m->stream);
     }
     if (exa_status e = launch_eval(m, exa::M_HESS, x, y, sigma, o)) return e;
-    return scatter_csc(m, m->d_hsegptr, m->d_hperm, m->d_hbuf, vals_csc, m->nnzh_csc, m->nnzh);
+    return scatter_csc(m, m->d_hsegptr, m->d_hperm, m->d_hbuf, vals_csc, m->nnzh_csc, m->nnzh, m->maxseg_h, m->stream);
 }
 
 static exa_status eval_all_launches(exa_model *m, const double *x, const double *y, double sigma, double *f,
@@ -1482,23 +1646,43 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
     } else if (exa_status e = launch_eval(m, mode, x, y, sigma, o)) {
         return e;
     }
+    // the CSC sums are independent of each other and of the objective, gradient and constraint
+    // reductions: they run on side streams forked from the model stream (parallel graph branches)
+    const bool jside = jac_csc && !jdirect && m->nnzj_csc, hside = (hcomp || (hess_csc && !hdirect)) && m->nnzh_csc;
+    if (jside || hside) {
+        if (!m->ev_fork) CR(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
+        for (int s = 0; s < 2; s++) {
+            if (!m->side[s]) CR(cudaStreamCreateWithFlags(&m->side[s], cudaStreamNonBlocking));
+            if (!m->ev_join[s]) CR(cudaEventCreateWithFlags(&m->ev_join[s], cudaEventDisableTiming));
+        }
+        CR(cudaEventRecord(m->ev_fork, m->stream));
+    }
+    if (jside) {
+        CR(cudaStreamWaitEvent(m->side[0], m->ev_fork, 0));
+        if (exa_status e = scatter_csc(m, m->d_jsegptr, m->d_jperm, o.jac, jac_csc, m->nnzj_csc, m->nnzj, m->maxseg_j, m->side[0])) return e;
+        CR(cudaEventRecord(m->ev_join[0], m->side[0]));
+    }
+    if (hside) {
+        CR(cudaStreamWaitEvent(m->side[1], m->ev_fork, 0));
+        if (hcomp) {
+            if (exa_status e = seg_sum(m, m->d_hcsegptr, m->d_hcperm, m->d_hcbuf, hess_csc, m->nnzh_csc, m->maxseg_hc, m->side[1]))
+                return e;
+        } else if (exa_status e = scatter_csc(m, m->d_hsegptr, m->d_hperm, o.hess, hess_csc, m->nnzh_csc, m->nnzh, m->maxseg_h, m->side[1])) {
+            return e;
+        }
+        CR(cudaEventRecord(m->ev_join[1], m->side[1]));
+    }
     if (f) {
         k_obj_final<<<1, 256, 0, m->stream>>>(m->d_objpart, m->nobj[mode], f);
         CR(cudaGetLastError());
     }
     if (g && m->nvar) {
-        k_seg_sum_warp<<<grid_of(m->nvar, 256), 256, 0, m->stream>>>(m->d_gptr, m->d_gperm, m->d_gbuf, g, (int)m->nvar);
-        CR(cudaGetLastError());
+        if (exa_status e = seg_sum(m, m->d_gptr, m->d_gperm, m->d_gbuf, g, m->nvar, m->maxseg_g, m->stream)) return e;
     }
     if (c)
         if (exa_status e = aug_rows(m, c)) return e;
-    if (jac_csc && !jdirect)
-        if (exa_status e = scatter_csc(m, m->d_jsegptr, m->d_jperm, o.jac, jac_csc, m->nnzj_csc, m->nnzj)) return e;
-    if (hcomp)
-        k_seg_sum_warp<<<grid_of(m->nnzh_csc, 256), 256, 0, m->stream>>>(m->d_hcsegptr, m->d_hcperm, m->d_hcbuf,
-                                                                           hess_csc, (int)m->nnzh_csc);
-    else if (hess_csc && !hdirect)
-        if (exa_status e = scatter_csc(m, m->d_hsegptr, m->d_hperm, o.hess, hess_csc, m->nnzh_csc, m->nnzh)) return e;
+    if (jside) CR(cudaStreamWaitEvent(m->stream, m->ev_join[0], 0));
+    if (hside) CR(cudaStreamWaitEvent(m->stream, m->ev_join[1], 0));
     return EXA_OK;
 }
 
@@ -1654,6 +1838,8 @@ exa_status exa_stat(const exa_model *m, const char *key, double *value) {
     else if (k == "tune_ms") *value = m->tune_ms;
     else if (k == "eval_split") *value = m->split_all;
     else if (k == "csc_direct") *value = m->csc_direct;
+    else if (k == "hess_compressed") *value = m->use_hcomp;
+    else if (k == "max_segment") *value = std::max({m->maxseg_j, m->maxseg_h, m->maxseg_hc, m->maxseg_g, m->maxseg_a});
     else if (k == "nnzh_compressed") *value = (double)m->nnzhc;
     else if (k == "eval_tiles") *value = m->ntiles[exa::M_ALL];
     else if (k == "device_bytes") *value = (double)m->device_bytes;

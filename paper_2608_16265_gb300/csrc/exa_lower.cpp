@@ -19,6 +19,7 @@
 //     (pattern, callback), one kernel per callback over a tile list, for NVRTC.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <map>
@@ -1035,6 +1036,11 @@ struct Emitter {
         }
         for (int s : syms) os << "  const double X" << s << " = __ldg(x + pm.xoff + i" << s << ");\n";
         for (int pid : params) os << "  const double P" << pid << " = __ldg(th + pm.poff + q" << pid << ");\n";
+        // the multipliers of the constraint rows are loaded with the other inputs, so that their
+        // latency overlaps the pattern arithmetic instead of following it
+        for (int pos : act)
+            if (want[pos].hess && pat(pos).kind != EXA_OBJ)
+                os << "  const double Y" << pos << " = __ldg(y + row" << pos << ");\n";
         for (int c : fconsts) os << "  const double C" << c << " = pm.fc[" << c << "];\n";
         for (int s : fsyms) os << "  const float XF" << s << " = exa_d2f(X" << s << ");\n";
         for (int f : ffields)
@@ -1050,9 +1056,15 @@ struct Emitter {
                           const char *csc, const char *map) {
             os << "  __syncwarp();\n";
             for (int j = 0; j < S; j++) os << "  ws[lane * " << S << " + " << j << "] = " << vals[j] << ";\n";
+            // a full warp writes S x 32 consecutive values: unrolled, one address computation
             os << "  __syncwarp();\n"
                << "  { const long long q0 = " << slot0 << " + kw * " << S << ";\n"
-               << "    if (" << out << ") for (int e = lane; e < nact * " << S << "; e += 32) " << out << "[q0 + e] = ws[e];\n";
+               << "    if (" << out << ") {\n"
+               << "      if (nact == 32) { double* __restrict__ d = " << out << " + q0 + lane;\n"
+               << "        #pragma unroll\n"
+               << "        for (int j = 0; j < " << S << "; j++) d[32 * j] = ws[lane + 32 * j]; }\n"
+               << "      else for (int e = lane; e < nact * " << S << "; e += 32) " << out << "[q0 + e] = ws[e];\n"
+               << "    }\n";
             if (csc)
                 os << "    if (" << csc << ") for (int e = lane; e < nact * " << S << "; e += 32) "
                    << csc << "[" << map << "[q0 + e]] = ws[e];\n";
@@ -1085,7 +1097,7 @@ struct Emitter {
             }
             if (w.hess) {
                 os << "  const " << W << " w" << P << " = " << (obj ? (mixed ? "exa_d2f(sigma)" : "sigma")
-                                                          : (mixed ? "exa_d2f(__ldg(y + row" + P + "))" : "__ldg(y + row" + P + ")"))
+                                                          : (mixed ? "exa_d2f(Y" + P + ")" : "Y" + P))
                    << ";\n";
                 os << "  const " << W << " ww" << P << " = w" << P << " + w" << P << ";\n";
                 std::vector<std::string> vals;

@@ -29,10 +29,11 @@ def _np(t):
     return t.detach().cpu().numpy()
 
 
-def check_model(flat, x, y, s, block=0, tol=TOL, o=None, flags=0, precision=0, grid_factor=0):
+def check_model(flat, x, y, s, block=0, tol=TOL, o=None, flags=0, precision=0, grid_factor=0, min_blocks=0):
     B = _B()
     o = o or oracle.Oracle(flat)
-    m = B.exa_create(flat, block=block, flags=flags, precision=precision, grid_factor=grid_factor)
+    m = B.exa_create(flat, block=block, flags=flags, precision=precision, grid_factor=grid_factor,
+                     min_blocks=min_blocks)
     assert (m.nvar, m.ncon, m.nnzj, m.nnzh, m.nnzj_csc, m.nnzh_csc) == \
         (o.nvar, o.ncon, o.nnzj, o.nnzh, o.nnzj_csc, o.nnzh_csc)
     # structures: bit-exact
@@ -113,6 +114,43 @@ def test_autotuned_model():
     x, y, s = synth.pde_point(wl, 3)
     m, _ = check_model(wl.flat, x, y, s)
     assert m.stat("eval_block") in (64, 128, 256) and m.stat("tune_ms") > 0
+
+
+@pytest.mark.parametrize("choice", ["split", "scatter", "no_hcomp", "split+scatter+no_hcomp"])
+def test_pinned_launch_choices(choice):
+    """Every choice the tuner makes, fixed through the creation options instead, gives the same
+    results: first/second order split, the Jacobian CSC scattered by the evaluation kernel, the
+    Hessian CSC summed from the COO slots, and a register cap through min_blocks."""
+    B = _B()
+    flags = B.EXA_FLAG_NO_TUNE
+    flags |= B.EXA_FLAG_SPLIT if "split" in choice else 0
+    flags |= B.EXA_FLAG_CSC_SCATTER if "scatter" in choice else 0
+    flags |= B.EXA_FLAG_NO_HCOMP if "no_hcomp" in choice else 0
+    wl = synth.acopf(200, 300, 40, seed=8)
+    x, y, s = synth.acopf_point(wl, 2)
+    m, _ = check_model(wl.flat, x, y, s, flags=flags, block=64, min_blocks=12)
+    assert m.stat("eval_split") == ("split" in choice)
+    assert m.stat("csc_direct") == ("scatter" in choice)
+    assert m.stat("hess_compressed") == ("no_hcomp" not in choice)
+    assert m.stat("eval_min_blocks") == 12 and m.stat("eval_block") == 64
+
+
+def test_tuned_options_reproduce_the_model():
+    """tuned_options() recreates the tuner's configuration without tuning; the kernels and their
+    launch shapes are the same, so every output is the same bit for bit."""
+    B = _B()
+    wl = synth.pde(300)
+    x, y, s = synth.pde_point(wl, 2)
+    m1 = B.exa_create(wl.flat)
+    opts = m1.tuned_options()
+    m2 = B.exa_create(wl.flat, **opts)
+    for key in ("eval_block", "eval_min_blocks", "eval_persist", "eval_grid", "eval_split", "csc_direct",
+                "hess_compressed", "eval_regs"):
+        assert m1.stat(key) == m2.stat(key), key
+    xt, yt = _t(x), _t(y)
+    a1, a2 = m1.eval_all(xt, yt, s, csc=True), m2.eval_all(xt, yt, s, csc=True)
+    for k in a1:
+        assert np.array_equal(_np(a1[k]).view(np.uint64), _np(a2[k]).view(np.uint64)), k
 
 
 @pytest.mark.parametrize("block", [32, 64, 256])
