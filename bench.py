@@ -297,6 +297,17 @@ def run_exa(args):
         if pg is not None:
             pg.barrier()
 
+    if args.kernel_only:
+        # profiling mode: only the dominant call (the evaluation kernel writing J and H COO), one
+        # untimed call and then kernel_only timed calls; one JSON line with the sizes
+        kcall = lambda: m.exa_eval_all(xt, yt, sigma, jac=jac, hess=hess)
+        kcall()
+        kms = timed(kcall, args.kernel_only)
+        if rank == 0:
+            print(json.dumps({"profile": "kernel_only", "nnz_per_rank": m.nnzj + m.nnzh, "calls": args.kernel_only,
+                              "kernel_ms": kms, "precision": args.precision, "members": args.members,
+                              "tuned_options": ",".join(str(v) for v in m.tuned_options().values())}))
+        return
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -398,18 +409,15 @@ def run_exa(args):
         extras[f"{tag}_eval_regs"] = m2.stat("eval_regs")
         m2.destroy()
 
-    # end to end through the public API: pinned host x, y in; f, g, c back to pinned host
+    # end to end through the C ABI with host buffers (exa_eval_all_host): pinned host x, y in,
+    # f, g, c back to pinned host memory, every step; the derivative arrays (COO and CSC) are
+    # computed into device buffers as in the device step
     xh = torch.as_tensor(x).pin_memory()
     yh = torch.as_tensor(y).pin_memory()
     fh, gh, ch = (torch.empty(n, dtype=torch.float64).pin_memory() for n in (1, m.nvar, m.ncon))
 
     def e2e_step():
-        xt.copy_(xh, non_blocking=True)
-        yt.copy_(yh, non_blocking=True)
-        step()
-        fh.copy_(f, non_blocking=True)
-        gh.copy_(g, non_blocking=True)
-        ch.copy_(c, non_blocking=True)
+        m.exa_eval_all_host(xh, yh, sigma, f=fh, g=gh, c=ch, jac=jac, hess=hess, jac_csc=jcsc, hess_csc=hcsc)
 
     for _ in range(2):
         e2e_step()
@@ -461,6 +469,8 @@ def main(argv=None):
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--kernel-only", type=int, default=0, help="profiling mode: run only the evaluation-kernel "
+                    "call (J and H COO) this many times after one untimed call, print its sizes, exit")
     ap.add_argument("--pin", default="", help="block,min_blocks,grid_factor,flags: fixed launch configuration "
                     "(extras.tuned_options of an earlier run) instead of autotuning, for profiling runs")
     args = ap.parse_args(argv)

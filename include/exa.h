@@ -256,6 +256,16 @@ exa_status exa_eval_all(exa_model *m, const double *x, const double *y, double s
                         double *g, double *c, double *jac, double *hess, double *jac_csc,
                         double *hess_csc);
 
+/* exa_eval_all for callers whose arrays live in host memory: every argument (sizes as in
+ * exa_eval_all) may be host memory, page-locked or pageable, or device memory.  Host inputs are
+ * copied into device buffers the library owns (allocated on first use), the exa_eval_all graph is
+ * replayed on the model stream, host outputs are copied back, and the call returns when they are
+ * in host memory (the stream is synchronized).  Device arguments are used in place.  Page-locked
+ * host buffers (cudaHostAlloc / cudaHostRegister) are copied at full link speed. */
+exa_status exa_eval_all_host(exa_model *m, const double *x, const double *y, double sigma,
+                             double *f, double *g, double *c, double *jac, double *hess,
+                             double *jac_csc, double *hess_csc);
+
 /* Products at x (NLPModels jprod!/jtprod!/hprod!): Jv[ncon] = J(x) v, Jtw[nvar] = J(x)^T w,
  * Hv[nvar] = (sigma Hess f + sum y_r Hess c_r)(x) v with the Hessian's full symmetric action. */
 exa_status exa_jprod(exa_model *m, const double *x, const double *v, double *Jv);

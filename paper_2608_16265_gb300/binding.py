@@ -33,7 +33,7 @@ EXPORTS = ["exa_create", "exa_create_batch", "exa_destroy", "exa_last_error", "e
            "exa_dims", "exa_batch_offsets", "exa_set_theta", "exa_set_stream", "exa_obj", "exa_obj_noalloc", "exa_grad", "exa_cons",
            "exa_jac_structure", "exa_jac_coord", "exa_hess_structure", "exa_hess_coord",
            "exa_jac_csc_structure", "exa_hess_csc_structure", "exa_jac_csc", "exa_hess_csc",
-           "exa_eval_all", "exa_jprod", "exa_jtprod", "exa_hprod", "exa_check_status",
+           "exa_eval_all", "exa_eval_all_host", "exa_jprod", "exa_jtprod", "exa_hprod", "exa_check_status",
            "exa_compile_check", "exa_stat"]
 
 
@@ -106,6 +106,7 @@ def load():
             "exa_jac_csc": [vp, dp, dp],
             "exa_hess_csc": [vp, dp, dp, C.c_double, dp],
             "exa_eval_all": [vp, dp, dp, C.c_double, dp, dp, dp, dp, dp, dp, dp],
+            "exa_eval_all_host": [vp, dp, dp, C.c_double, dp, dp, dp, dp, dp, dp, dp],
             "exa_jprod": [vp, dp, dp, dp],
             "exa_jtprod": [vp, dp, dp, dp],
             "exa_hprod": [vp, dp, dp, C.c_double, dp, dp],
@@ -269,6 +270,15 @@ class Model:
 
     def exa_eval_all(self, x, y, s, f=None, g=None, c=None, jac=None, hess=None, jac_csc=None, hess_csc=None):
         self._call("exa_eval_all", _ptr(x), _ptr(y), float(s), _ptr(f), _ptr(g), _ptr(c), _ptr(jac),
+                   _ptr(hess), _ptr(jac_csc), _ptr(hess_csc))
+
+    def exa_eval_all_host(self, x, y, s, f=None, g=None, c=None, jac=None, hess=None, jac_csc=None, hess_csc=None):
+        """exa_eval_all with arrays in host memory (CPU tensors, preferably pinned) or on the device;
+        returns when the host outputs are filled."""
+        for t in (x, y, f, g, c, jac, hess, jac_csc, hess_csc):
+            if t is not None and not t.is_contiguous():
+                raise ValueError("exa_eval_all_host takes contiguous tensors")
+        self._call("exa_eval_all_host", _ptr(x), _ptr(y), float(s), _ptr(f), _ptr(g), _ptr(c), _ptr(jac),
                    _ptr(hess), _ptr(jac_csc), _ptr(hess_csc))
 
     def exa_jprod(self, x, v, out): self._call("exa_jprod", _ptr(x), _ptr(v), _ptr(out))

@@ -345,6 +345,8 @@ struct exa_model {
     // exa_eval_all runs its independent reductions (Jacobian CSC, Hessian CSC, the rest) on three
     // streams forked from and joined back into the model stream
     cudaStream_t side[2] = {};
+    // device buffers of exa_eval_all_host: x, y, f, g, c, jac, hess, jac_csc, hess_csc
+    double *d_host_io[9] = {};
     cudaEvent_t ev_fork = nullptr, ev_join[2] = {};
     double *d_theta = nullptr;
     int *d_status = nullptr;
@@ -1733,6 +1735,36 @@ exa_status exa_eval_all(exa_model *m, const double *x, const double *y, double s
     }
     m->graphs.push_back({key, exec, ++m->graph_clock});
     CR(cudaGraphLaunch(exec, m->stream));
+    return EXA_OK;
+}
+
+exa_status exa_eval_all_host(exa_model *m, const double *x, const double *y, double sigma, double *f, double *g,
+                             double *c, double *jac, double *hess, double *jac_csc, double *hess_csc) {
+    if (exa_status e = check_model(m)) return e;
+    CHECK_PTRS(x);
+    const bool want_h = hess || hess_csc;
+    if (want_h && m->ncon && !y) return fail(m, EXA_E_INVALID, "NULL y");
+    const i64 n[9] = {m->nvar, m->ncon, 1, m->nvar, m->ncon, m->nnzj, m->nnzh, m->nnzj_csc, m->nnzh_csc};
+    double *arg[9] = {const_cast<double *>(x), const_cast<double *>(y), f, g, c, jac, hess, jac_csc, hess_csc};
+    double *use[9] = {};
+    bool staged[9] = {};
+    for (int k = 0; k < 9; k++) {
+        if (!arg[k]) continue;
+        cudaPointerAttributes a{};
+        CR(cudaPointerGetAttributes(&a, arg[k]));
+        staged[k] = a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged;
+        if (staged[k] && !m->d_host_io[k]) CR(dalloc(m, &m->d_host_io[k], n[k]));
+        use[k] = staged[k] ? m->d_host_io[k] : arg[k];
+    }
+    for (int k = 0; k < 2; k++)
+        if (staged[k] && n[k] > 0)
+            CR(cudaMemcpyAsync(use[k], arg[k], sizeof(double) * n[k], cudaMemcpyHostToDevice, m->stream));
+    if (exa_status e = exa_eval_all(m, use[0], use[1], sigma, use[2], use[3], use[4], use[5], use[6], use[7], use[8]))
+        return e;
+    for (int k = 2; k < 9; k++)
+        if (staged[k] && n[k] > 0)
+            CR(cudaMemcpyAsync(arg[k], use[k], sizeof(double) * n[k], cudaMemcpyDeviceToHost, m->stream));
+    CR(cudaStreamSynchronize(m->stream));
     return EXA_OK;
 }
 

@@ -857,8 +857,12 @@ struct Emitter {
                         std::string cn = ci >= 0 ? "t" + std::to_string(ci) : t + "_c";
                         os << "  " << T << " " << sn << ", " << cn << ";\n";
                         if (red) os << "  exa_sincos_red(" << A() << ", &" << sn << ", &" << cn << ");\n";
-                        else os << "  " << (s.prec == PF ? "sincosf(" : "sincos(") << A() << ", &" << sn << ", &" << cn << ");\n";
+                        else os << "  " << (s.prec == PF ? "sincosf(" : "exa_sincos64(") << A() << ", &" << sn << ", &" << cn << ");\n";
                     }
+                } else if (s.prec == PD) {  // one of the pair: the other result is dead code
+                    os << "  double " << t << "_s, " << t << "_c;\n"
+                       << "  exa_sincos64(" << A() << ", &" << t << "_s, &" << t << "_c);\n"
+                       << "  const double " << t << " = " << t << (s.op == S_SIN ? "_s" : "_c") << ";\n";
                 } else {
                     os << "  const " << T << " " << t << " = " << fname(s.op, s.prec) << "(" << A() << ");\n";
                 }
@@ -1184,6 +1188,47 @@ static __device__ __forceinline__ float exa_exp_red(const double a) {
 }
 )";
 
+// FP64 sin and cos of one argument.  Cody-Waite reduction (Cody & Waite, 1980): q = rint(a 2/pi)
+// by adding and subtracting 1.5 * 2^52 in one fused multiply-add, r = a - q pi/2 with pi/2 split
+// into three doubles (P1 the double nearest pi/2, P2 the double nearest pi/2 - P1, P3 likewise;
+// computed with 400-bit arithmetic), each step a fused multiply-add, so r carries an error of about
+// one rounding for |a| < 2^20.  sin r and cos r on |r| <= pi/4 from their Taylor series,
+// (-1)^k / (2k+1)! up to r^15 and (-1)^k / (2k)! up to r^16 (truncation below 1e-16 relative),
+// by Horner's rule in r^2.  The quadrant q mod 4 (low word of the shifted q) swaps the two and
+// flips signs with integer operations, so only the reduction and the polynomials use the FP64
+// pipe.  |a| >= 2^20, infinities and NaN take the library sincos.
+static const char *kFp64Helpers = R"(
+static __device__ __forceinline__ void exa_sincos64(const double a, double* s, double* c) {
+  if (!(fabs(a) < 1048576.0)) { sincos(a, s, c); return; }
+  const double qb = fma(a, 0x1.45f306dc9c883p-1, 0x1.8p52);
+  const int n = __double2loint(qb);
+  const double q = qb - 0x1.8p52;
+  double r = fma(-q, 0x1.921fb54442d18p+0, a);
+  r = fma(-q, 0x1.1a62633145c07p-54, r);
+  r = fma(-q, -0x1.f1976b7ed8fbcp-110, r);
+  const double r2 = r * r;
+  double ps = fma(r2, -0x1.ae7f3e733b81fp-41, 0x1.6124613a86d09p-33);
+  ps = fma(r2, ps, -0x1.ae64567f544e4p-26);
+  ps = fma(r2, ps, 0x1.71de3a556c734p-19);
+  ps = fma(r2, ps, -0x1.a01a01a01a01ap-13);
+  ps = fma(r2, ps, 0x1.1111111111111p-7);
+  ps = fma(r2, ps, -0x1.5555555555555p-3);
+  const double sr = fma(r * r2, ps, r);
+  double pc = fma(r2, 0x1.ae7f3e733b81fp-45, -0x1.93974a8c07c9dp-37);
+  pc = fma(r2, pc, 0x1.1eed8eff8d898p-29);
+  pc = fma(r2, pc, -0x1.27e4fb7789f5cp-22);
+  pc = fma(r2, pc, 0x1.a01a01a01a01ap-16);
+  pc = fma(r2, pc, -0x1.6c16c16c16c17p-10);
+  pc = fma(r2, pc, 0x1.5555555555555p-5);
+  pc = fma(r2, pc, -0.5);
+  const double cr = fma(r2, pc, 1.0);
+  const double sa = (n & 1) ? cr : sr, ca = (n & 1) ? sr : cr;
+  const int fs = (n & 2) << 30, fc = ((n + 1) & 2) << 30;
+  *s = __hiloint2double(__double2hiint(sa) ^ fs, __double2loint(sa));
+  *c = __hiloint2double(__double2hiint(ca) ^ fc, __double2loint(ca));
+}
+)";
+
 }  // namespace
 
 std::string generate_source(const std::vector<Pattern> &pats, const std::vector<Group> &groups,
@@ -1196,6 +1241,7 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
     if (opt.min_blocks > 0) src << "#define EXA_BOUNDS __launch_bounds__(EXA_BLOCK, " << opt.min_blocks << ")\n";
     else src << "#define EXA_BOUNDS __launch_bounds__(EXA_BLOCK)\n";
     if (mixed) src << kMixedHelpers;
+    src << kFp64Helpers;
     // one shared expression graph per group
     std::vector<Graph> graphs(groups.size());
     std::vector<std::vector<PatternGraph>> pgs(groups.size());

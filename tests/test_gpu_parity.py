@@ -359,6 +359,37 @@ def test_eval_all_graph_replay_matches_direct_launches():
             assert torch.equal(a[k], b[k]), k
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_eval_all_host_buffers(pinned):
+    """exa_eval_all_host (host x, y in; host outputs) equals exa_eval_all on device buffers bit for
+    bit, with page-locked and with pageable host memory, with host and device arguments mixed, and
+    leaves unrequested outputs alone."""
+    B = _B()
+    wl = synth.acopf(200, 300, 40, seed=8)
+    x, y, s = synth.acopf_point(wl, 3)
+    m = B.exa_create(wl.flat)
+    sizes = (("f", 1), ("g", m.nvar), ("c", m.ncon), ("jac", m.nnzj), ("hess", m.nnzh),
+             ("jac_csc", m.nnzj_csc), ("hess_csc", m.nnzh_csc))
+    dev = {k: torch.empty(n, dtype=torch.float64, device="cuda") for k, n in sizes}
+    m.exa_eval_all(_t(x), _t(y), s, **dev)
+    pin = (lambda t: t.pin_memory()) if pinned else (lambda t: t)
+    host = {k: pin(torch.full((n,), -7.0, dtype=torch.float64)) for k, n in sizes}
+    xh, yh = pin(torch.as_tensor(x)), pin(torch.as_tensor(y))
+    for _ in range(2):  # the second call replays the cached graph
+        m.exa_eval_all_host(xh, yh, s, **host)
+        for k in host:
+            assert torch.equal(host[k], dev[k].cpu()), k
+    part = {k: pin(torch.full((n,), -7.0, dtype=torch.float64)) for k, n in sizes}
+    m.exa_eval_all_host(xh, yh, s, g=part["g"], hess_csc=part["hess_csc"])
+    assert torch.equal(part["g"], dev["g"].cpu()) and torch.equal(part["hess_csc"], dev["hess_csc"].cpu())
+    assert bool((part["c"] == -7.0).all()) and bool((part["jac"] == -7.0).all())
+    # host and device arguments mixed: device arrays are used in place
+    mix = {"g": pin(torch.full((m.nvar,), -7.0, dtype=torch.float64)),
+           "hess": torch.full((m.nnzh,), -7.0, dtype=torch.float64, device="cuda")}
+    m.exa_eval_all_host(_t(x), yh, s, **mix)
+    assert torch.equal(mix["g"], dev["g"].cpu()) and torch.equal(mix["hess"], dev["hess"])
+
+
 def test_set_theta():
     """Changing the parameters of a created model gives the results of a model built with them."""
     B = _B()
@@ -388,3 +419,34 @@ def test_invalid_arguments_are_reported():
             call()
         assert e.value.status == B.EXA_E_INVALID and "NULL" in str(e.value)
     m.exa_check_status()
+
+
+def test_fp64_sin_cos_accuracy():
+    """FP64 sin and cos of the generated code (Cody-Waite reduction, Taylor polynomials) against
+    the host C library over a sweep that includes arguments next to multiples of pi/2, signed
+    zeros, tiny and large arguments (the library path beyond 2^20): within 3 ulp of the host
+    values (6.7e-16 relative)."""
+    from paper_2608_16265_gb300 import ir
+    from paper_2608_16265_gb300.ir import Model
+    B = _B()
+    rng = np.random.default_rng(11)
+    k = np.arange(-2000, 2001)
+    near = np.concatenate([k * (np.pi / 2) + d for d in (0.0, 1e-9, -1e-12, 3e-7)])
+    vals = np.concatenate([near, rng.uniform(-4, 4, 4000), rng.uniform(-1e5, 1e5, 4000),
+                           10.0 ** rng.uniform(-30, 0, 500), -10.0 ** rng.uniform(-30, 0, 500),
+                           rng.uniform(-3e6, 3e6, 200), [0.0, -0.0, 1048575.9, 1048576.0, 2.0 ** 30]])
+    n = len(vals)
+    m = Model()
+    xv = m.add_var(n)
+    m.add_con(lambda d: ir.sin(xv[d.k]), n=n)
+    m.add_con(lambda d: ir.cos(xv[d.k]), n=n)
+    mod = B.exa_create(m.flat())
+    c = _np(mod.cons(_t(vals)))
+    for got, want in ((c[:n], np.sin(vals)), (c[n:], np.cos(vals))):
+        err = np.abs(got - want)
+        ok = err <= 6.7e-16 * np.abs(want)
+        assert ok.all(), [(v, g, w) for v, g, w in zip(vals[~ok], got[~ok], want[~ok])][:5]
+    assert np.signbit(c[n - 4]) and not np.signbit(c[n - 5])  # sin(-0) = -0, sin(+0) = +0
+    # derivatives come from the same pair: d sin = cos, d cos = -sin
+    jac = _np(mod.jac_coord(_t(vals)))
+    assert np.array_equal(jac[:n], c[n:]) and np.array_equal(jac[n:], -c[:n])
