@@ -356,7 +356,7 @@ def run_exa(args):
               "eval_persist": m.stat("eval_persist"), "eval_grid": m.stat("eval_grid"), "eval_tiles": m.stat("eval_tiles"),
               "eval_min_blocks": m.stat("eval_min_blocks"), "eval_split": m.stat("eval_split"),
               "csc_direct": m.stat("csc_direct"), "hess_compressed": m.stat("hess_compressed"),
-              "nnzh_compressed": m.stat("nnzh_compressed"), "max_segment": m.stat("max_segment"),
+              "nnzh_compressed": m.stat("nnzh_compressed"), "grad_compact": m.stat("grad_compact"),
               "tuned_options": ",".join(str(v) for v in m.tuned_options().values()),
               "device_bytes": m.stat("device_bytes")}
     if not args.no_extras:

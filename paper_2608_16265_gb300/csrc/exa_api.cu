@@ -54,22 +54,33 @@ __global__ void k_obj_final(const double *__restrict__ part, int n, double *__re
 // issued back to back (indices first, then values) before any result is used.
 #define EXA_ILP 8
 
-// dst[i] = sum_{q in [ptr[i], ptr[i+1])} src[perm[q]], q ascending (ascending COO index).  One warp
-// per 32 consecutive segments: the warp first gathers the values of its segments (one contiguous
-// range of sorted positions) into shared memory with every lane loading in parallel, then each lane
-// adds its own segment in ascending order.
+// Segmented gather-sums, no atomics: for segment s < n, the values src[perm[q]] for q in
+// [ptr[s], ptr[s+1]) are added in ascending q starting from 0.0 (ROWS: from dst[rows[s]]), and the
+// result is stored to dst[s] (ROWS: dst[rows[s]]).  One warp takes 32 x EXA_SEG_G consecutive
+// segments, whose entries are one contiguous range of sorted positions: all lanes gather that range
+// in chunks of EXA_SEG_CHUNK into shared memory (EXA_ILP independent index-then-value loads per
+// lane), then every lane adds up its own EXA_SEG_G segments from shared memory.
 #define EXA_SEG_CHUNK 256
+#define EXA_SEG_G 2
+template <bool ROWS>
 __global__ void __launch_bounds__(256) k_seg_sum_warp(const int *__restrict__ ptr, const int *__restrict__ perm,
-                                                      const double *__restrict__ src, double *__restrict__ dst, int n) {
+                                                      const double *__restrict__ src, double *__restrict__ dst,
+                                                      const int *__restrict__ rows, int n) {
     __shared__ double buf[8][EXA_SEG_CHUNK];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long s0 = ((long long)blockIdx.x * 8 + w) * 32;
+    const long long s0 = ((long long)blockIdx.x * 8 + w) * (32 * EXA_SEG_G);
     if (s0 >= n) return;
-    const int s = (int)s0 + lane;
-    const bool valid = s < n;
-    const int beg = ptr[s0], end = ptr[min((long long)n, s0 + 32)];
-    const int myb = valid ? ptr[s] : end, mye = valid ? ptr[s + 1] : end;
-    double acc = 0.0;
+    const int beg = ptr[s0], end = ptr[min((long long)n, s0 + 32 * EXA_SEG_G)];
+    int myb[EXA_SEG_G], mye[EXA_SEG_G], row[EXA_SEG_G];
+    double acc[EXA_SEG_G];
+#pragma unroll
+    for (int g = 0; g < EXA_SEG_G; g++) {
+        const long long s = s0 + 32 * g + lane;
+        myb[g] = s < n ? ptr[s] : end;
+        mye[g] = s < n ? ptr[s + 1] : end;
+        row[g] = ROWS && s < n ? rows[s] : 0;
+        acc[g] = ROWS && s < n ? dst[row[g]] : 0.0;
+    }
     for (int c0 = beg; c0 < end; c0 += EXA_SEG_CHUNK) {
         const int c1 = min(c0 + EXA_SEG_CHUNK, end);
         int p[EXA_ILP];
@@ -85,11 +96,18 @@ __global__ void __launch_bounds__(256) k_seg_sum_warp(const int *__restrict__ pt
         for (int u = 0; u < EXA_ILP; u++)
             if (p[u] >= 0) buf[w][lane + 32 * u] = v[u];
         __syncwarp();
-        const int qb = max(myb, c0), qe = min(mye, c1);
-        for (int q = qb; q < qe; q++) acc += buf[w][q - c0];
+#pragma unroll
+        for (int g = 0; g < EXA_SEG_G; g++) {
+            const int qb = max(myb[g], c0), qe = min(mye[g], c1);
+            for (int q = qb; q < qe; q++) acc[g] += buf[w][q - c0];
+        }
         __syncwarp();
     }
-    if (valid) dst[s] = acc;
+#pragma unroll
+    for (int g = 0; g < EXA_SEG_G; g++) {
+        const long long s = s0 + 32 * g + lane;
+        if (s < n) dst[ROWS ? (long long)row[g] : s] = acc[g];
+    }
 }
 
 // out[i] = sum_{q in [ptr[i], ptr[i+1])} val[perm[q]] * v[other[perm[q]]], q ascending; one warp per
@@ -149,85 +167,6 @@ __global__ void __launch_bounds__(256) k_permute(const int *__restrict__ perm, c
 #pragma unroll
     for (int u = 0; u < EXA_ILP; u++)
         if (p[u] >= 0) dst[i0 + 256 * u] = v[u];
-}
-
-// Segmented sums over short segments (at most EXA_SEG_SHORT entries each, the common case): with
-// ROWS, dst[rows[s]] += the sum of segment s; without, dst[s] = the sum.  Entries are added in
-// ascending position order starting from 0.0 (or from the current dst value), as in
-// k_seg_sum_warp / k_seg_add_rows, so the results are the same bit for bit.  Thread t of a block
-// takes the segments base + t + 256 u (u < EXA_SEGS), and the first EXA_SEG_UNROLL entries of all of
-// them are fetched with independent loads before any is added; longer segments continue in chunks.
-#define EXA_SEGS 4
-#define EXA_SEG_UNROLL 4
-#define EXA_SEG_SHORT 32
-template <bool ROWS>
-__global__ void __launch_bounds__(256) k_seg_sum_ilp(const int *__restrict__ ptr, const int *__restrict__ perm,
-                                                     const double *__restrict__ src, double *__restrict__ dst,
-                                                     const int *__restrict__ rows, long long n) {
-    const long long s0 = (long long)blockIdx.x * (256 * EXA_SEGS) + threadIdx.x;
-    int b[EXA_SEGS], e[EXA_SEGS];
-#pragma unroll
-    for (int u = 0; u < EXA_SEGS; u++) {
-        const long long s = s0 + 256 * u;
-        b[u] = s < n ? __ldg(ptr + s) : 0;
-        e[u] = s < n ? __ldg(ptr + s + 1) : 0;
-    }
-    int p[EXA_SEGS][EXA_SEG_UNROLL];
-#pragma unroll
-    for (int u = 0; u < EXA_SEGS; u++)
-#pragma unroll
-        for (int j = 0; j < EXA_SEG_UNROLL; j++) p[u][j] = b[u] + j < e[u] ? __ldg(perm + b[u] + j) : -1;
-    double v[EXA_SEGS][EXA_SEG_UNROLL];
-#pragma unroll
-    for (int u = 0; u < EXA_SEGS; u++)
-#pragma unroll
-        for (int j = 0; j < EXA_SEG_UNROLL; j++) v[u][j] = p[u][j] >= 0 ? __ldg(src + p[u][j]) : 0.0;
-    int r[EXA_SEGS];
-    double acc[EXA_SEGS];
-#pragma unroll
-    for (int u = 0; u < EXA_SEGS; u++) {
-        const long long s = s0 + 256 * u;
-        r[u] = ROWS && s < n ? __ldg(rows + s) : (int)s;
-        acc[u] = ROWS && s < n ? dst[r[u]] : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < EXA_SEGS; u++) {
-        if (s0 + 256 * u >= n) continue;
-#pragma unroll
-        for (int j = 0; j < EXA_SEG_UNROLL; j++)
-            if (p[u][j] >= 0) acc[u] += v[u][j];
-        for (int q0 = b[u] + EXA_SEG_UNROLL; q0 < e[u]; q0 += EXA_SEG_UNROLL) {
-            int pp[EXA_SEG_UNROLL];
-            double vv[EXA_SEG_UNROLL];
-#pragma unroll
-            for (int j = 0; j < EXA_SEG_UNROLL; j++) pp[j] = q0 + j < e[u] ? __ldg(perm + q0 + j) : -1;
-#pragma unroll
-            for (int j = 0; j < EXA_SEG_UNROLL; j++) vv[j] = pp[j] >= 0 ? __ldg(src + pp[j]) : 0.0;
-#pragma unroll
-            for (int j = 0; j < EXA_SEG_UNROLL; j++)
-                if (pp[j] >= 0) acc[u] += vv[j];
-        }
-        dst[ROWS ? (long long)r[u] : s0 + 256 * u] = acc[u];
-    }
-}
-
-// Largest segment length of a pointer array (setup).
-__global__ void k_max_seg(const int *__restrict__ ptr, long long n, int *__restrict__ out) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int v = i < n ? ptr[i + 1] - ptr[i] : 0;
-    const int w = __reduce_max_sync(0xffffffffu, v);
-    if ((threadIdx.x & 31) == 0 && w > 0) atomicMax(out, w);
-}
-
-// c[rows[i]] += sum of the augmentation terms of that row (rows listed once each)
-__global__ void k_seg_add_rows(const int *__restrict__ rows, const int *__restrict__ ptr,
-                               const int *__restrict__ perm, const double *__restrict__ src,
-                               double *__restrict__ c, int n) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double s = c[rows[i]];
-    for (int q = ptr[i], e = ptr[i + 1]; q < e; q++) s += src[perm[q]];
-    c[rows[i]] = s;
 }
 
 // Hv[i] from the lower-triangle CSC values: column i holds (r, i), r >= i, giving H_ir v_r; the
@@ -360,8 +299,10 @@ struct exa_model {
     // permutation sorted by (col, row) and segment pointers per Hessian CSC entry
     i64 nnzhc = 0;
     bool has_hcomp = false;       // group-compressed Hessian sums exist (fewer than the COO slots)
-    // longest segment of each segmented sum (picks the per-thread or the warp-cooperative kernel)
-    int maxseg_j = 0, maxseg_h = 0, maxseg_hc = 0, maxseg_g = 0, maxseg_a = 0;
+    // sparse gradient: zero fill plus sums over the variables that have gradient slots only
+    bool grad_compact = false;
+    int n_gseg = 0;
+    int *d_gsegptr = nullptr, *d_gsegvar = nullptr;
     bool use_hcomp = false;       // ... and feed the Hessian CSC (tuner choice)
     int *d_hcrow = nullptr, *d_hccol = nullptr, *d_hcperm = nullptr, *d_hcsegptr = nullptr;
     double *d_hcbuf = nullptr;
@@ -571,20 +512,6 @@ exa_status build_ptr(exa_model *m, const unsigned long long *skeys, int shift, i
     return EXA_OK;
 }
 
-// Longest segment of ptr[0..n] (n segments).
-exa_status max_seg(exa_model *m, Scratch &S, const int *ptr, i64 n, int *out) {
-    *out = 0;
-    if (n <= 0) return EXA_OK;
-    int *d = nullptr;
-    CR(S.get(&d, 1));
-    CR(cudaMemsetAsync(d, 0, sizeof(int), m->stream));
-    k_max_seg<<<grid_of(n, 256), 256, 0, m->stream>>>(ptr, (long long)n, d);
-    CR(cudaGetLastError());
-    CR(cudaMemcpyAsync(out, d, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
-    CR(cudaStreamSynchronize(m->stream));
-    return EXA_OK;
-}
-
 // Per-model structure: CSC of J and H, row groupings, gradient and augmentation segments.
 exa_status build_structure(exa_model *m) {
     Scratch S{m};
@@ -676,6 +603,16 @@ exa_status build_structure(exa_model *m) {
     }
     if (exa_status e = sort_with_perm(m, S, keys, ng, 32, &skeys, m->d_gperm)) return e;
     if (exa_status e = build_ptr(m, skeys, 0, ng, m->nvar, &m->d_gptr)) return e;
+    // the variables that have gradient slots, for the compact form (chosen when they are fewer than
+    // half of the variables)
+    if (exa_status e = segments(m, S, skeys, m->d_gperm, ng, &nseg, &m->d_gsegptr, &segkey, nullptr, true)) return e;
+    m->n_gseg = nseg;
+    CR(dalloc(m, &m->d_gsegvar, nseg));
+    if (nseg) {
+        k_low32<<<grid_of(nseg, 256), 256, 0, m->stream>>>(segkey, m->d_gsegvar, nseg);
+        CR(cudaGetLastError());
+    }
+    m->grad_compact = 2 * (i64)nseg < m->nvar;
 
     // ---- augmentation segments by row (only rows that receive terms)
     CR(dalloc(m, &m->d_aperm, na));
@@ -691,13 +628,6 @@ exa_status build_structure(exa_model *m) {
         k_low32<<<grid_of(nseg, 256), 256, 0, m->stream>>>(segkey, m->d_arows, nseg);
         CR(cudaGetLastError());
     }
-    // longest segments: the segmented sums pick their kernel by them
-    if (exa_status e = max_seg(m, S, m->d_jsegptr, m->nnzj_csc, &m->maxseg_j)) return e;
-    if (exa_status e = max_seg(m, S, m->d_hsegptr, m->nnzh_csc, &m->maxseg_h)) return e;
-    if (m->has_hcomp)
-        if (exa_status e = max_seg(m, S, m->d_hcsegptr, m->nnzh_csc, &m->maxseg_hc)) return e;
-    if (exa_status e = max_seg(m, S, m->d_gptr, m->nvar, &m->maxseg_g)) return e;
-    if (exa_status e = max_seg(m, S, m->d_aptr, m->n_aug_rows, &m->maxseg_a)) return e;
     CR(cudaStreamSynchronize(m->stream));
     return EXA_OK;
 }
@@ -1440,16 +1370,26 @@ exa_status exa_obj_noalloc(exa_model *m, const double *x, double *f) {
     return EXA_OK;
 }
 
-// dst[s] = sum over segment s of src[perm[q]] (q ascending), s < n: the per-thread kernel when every
-// segment is short, else the warp-cooperative one.
+// dst[s] = sum over segment s of src[perm[q]] (q ascending), s < n.
 static exa_status seg_sum(exa_model *m, const int *ptr, const int *perm, const double *src, double *dst, i64 n,
-                          int maxseg, cudaStream_t st) {
+                          cudaStream_t st) {
     if (n <= 0) return EXA_OK;
-    if (maxseg <= EXA_SEG_SHORT)
-        k_seg_sum_ilp<false><<<grid_of(n, 256 * EXA_SEGS), 256, 0, st>>>(ptr, perm, src, dst, nullptr, (long long)n);
-    else
-        k_seg_sum_warp<<<grid_of(n, 256), 256, 0, st>>>(ptr, perm, src, dst, (int)n);
+    k_seg_sum_warp<false><<<grid_of(n, 256 * EXA_SEG_G), 256, 0, st>>>(ptr, perm, src, dst, nullptr, (int)n);
     CR(cudaGetLastError());
+    return EXA_OK;
+}
+
+// Dense gradient from the gradient slots.  Compact form (most variables without a slot): zero fill,
+// then sums over the variables that have slots only.
+static exa_status grad_sum(exa_model *m, double *g, cudaStream_t st) {
+    if (!m->nvar) return EXA_OK;
+    if (!m->grad_compact) return seg_sum(m, m->d_gptr, m->d_gperm, m->d_gbuf, g, m->nvar, st);
+    CR(cudaMemsetAsync(g, 0, sizeof(double) * m->nvar, st));
+    if (m->n_gseg) {
+        k_seg_sum_warp<true><<<grid_of(m->n_gseg, 256 * EXA_SEG_G), 256, 0, st>>>(m->d_gsegptr, m->d_gperm, m->d_gbuf, g,
+                                                                                 m->d_gsegvar, m->n_gseg);
+        CR(cudaGetLastError());
+    }
     return EXA_OK;
 }
 
@@ -1460,19 +1400,15 @@ exa_status exa_grad(exa_model *m, const double *x, double *g) {
     o.gbuf = m->d_gbuf;
     if (exa_status e = launch_eval(m, exa::M_GRAD, x, nullptr, 0.0, o)) return e;
     if (m->nvar) {
-        if (exa_status e = seg_sum(m, m->d_gptr, m->d_gperm, m->d_gbuf, g, m->nvar, m->maxseg_g, m->stream)) return e;
+        if (exa_status e = grad_sum(m, g, m->stream)) return e;
     }
     return EXA_OK;
 }
 
 static exa_status aug_rows(exa_model *m, double *c) {
     if (m->n_aug_rows) {
-        if (m->maxseg_a <= EXA_SEG_SHORT)
-            k_seg_sum_ilp<true><<<grid_of(m->n_aug_rows, 256 * EXA_SEGS), 256, 0, m->stream>>>(
-                m->d_aptr, m->d_aperm, m->d_abuf, c, m->d_arows, (long long)m->n_aug_rows);
-        else
-            k_seg_add_rows<<<grid_of(m->n_aug_rows, 256), 256, 0, m->stream>>>(m->d_arows, m->d_aptr, m->d_aperm,
-                                                                                  m->d_abuf, c, m->n_aug_rows);
+        k_seg_sum_warp<true><<<grid_of(m->n_aug_rows, 256 * EXA_SEG_G), 256, 0, m->stream>>>(
+            m->d_aptr, m->d_aperm, m->d_abuf, c, m->d_arows, m->n_aug_rows);
         CR(cudaGetLastError());
     }
     return EXA_OK;
@@ -1553,9 +1489,9 @@ exa_status exa_hess_csc_structure(const exa_model *mc, int32_t *colptr, int32_t 
 }
 
 static exa_status scatter_csc(exa_model *m, const int *segptr, const int *perm, const double *coo, double *csc,
-                              i64 n, i64 nnz, int maxseg, cudaStream_t st) {
+                              i64 n, i64 nnz, cudaStream_t st) {
     if (!n) return EXA_OK;
-    if (n != nnz) return seg_sum(m, segptr, perm, coo, csc, n, maxseg, st);
+    if (n != nnz) return seg_sum(m, segptr, perm, coo, csc, n, st);
     k_permute<<<grid_of(n, 256 * EXA_ILP), 256, 0, st>>>(perm, coo, csc, (long long)n);
     CR(cudaGetLastError());
     return EXA_OK;
@@ -1574,7 +1510,7 @@ exa_status exa_jac_csc(exa_model *m, const double *x, double *vals_csc) {
         return launch_eval(m, exa::M_JAC, x, nullptr, 0.0, o);
     }
     if (exa_status e = launch_eval(m, exa::M_JAC, x, nullptr, 0.0, o)) return e;
-    return scatter_csc(m, m->d_jsegptr, m->d_jperm, m->d_jbuf, vals_csc, m->nnzj_csc, m->nnzj, m->maxseg_j, m->stream);
+    return scatter_csc(m, m->d_jsegptr, m->d_jperm, m->d_jbuf, vals_csc, m->nnzj_csc, m->nnzj, m->stream);
 }
 
 exa_status exa_hess_csc(exa_model *m, const double *x, const double *y, double sigma, double *vals_csc) {
@@ -1594,10 +1530,10 @@ exa_status exa_hess_csc(exa_model *m, const double *x, const double *y, double s
         o.hess = nullptr;
         o.hcomp = m->d_hcbuf;
         if (exa_status e = launch_eval(m, exa::M_HESS_C, x, y, sigma, o)) return e;
-        return seg_sum(m, m->d_hcsegptr, m->d_hcperm, m->d_hcbuf, vals_csc, m->nnzh_csc, m->maxseg_hc, m->stream);
+        return seg_sum(m, m->d_hcsegptr, m->d_hcperm, m->d_hcbuf, vals_csc, m->nnzh_csc, m->stream);
     }
     if (exa_status e = launch_eval(m, exa::M_HESS, x, y, sigma, o)) return e;
-    return scatter_csc(m, m->d_hsegptr, m->d_hperm, m->d_hbuf, vals_csc, m->nnzh_csc, m->nnzh, m->maxseg_h, m->stream);
+    return scatter_csc(m, m->d_hsegptr, m->d_hperm, m->d_hbuf, vals_csc, m->nnzh_csc, m->nnzh, m->stream);
 }
 
 static exa_status eval_all_launches(exa_model *m, const double *x, const double *y, double sigma, double *f,
@@ -1661,15 +1597,15 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
     }
     if (jside) {
         CR(cudaStreamWaitEvent(m->side[0], m->ev_fork, 0));
-        if (exa_status e = scatter_csc(m, m->d_jsegptr, m->d_jperm, o.jac, jac_csc, m->nnzj_csc, m->nnzj, m->maxseg_j, m->side[0])) return e;
+        if (exa_status e = scatter_csc(m, m->d_jsegptr, m->d_jperm, o.jac, jac_csc, m->nnzj_csc, m->nnzj, m->side[0])) return e;
         CR(cudaEventRecord(m->ev_join[0], m->side[0]));
     }
     if (hside) {
         CR(cudaStreamWaitEvent(m->side[1], m->ev_fork, 0));
         if (hcomp) {
-            if (exa_status e = seg_sum(m, m->d_hcsegptr, m->d_hcperm, m->d_hcbuf, hess_csc, m->nnzh_csc, m->maxseg_hc, m->side[1]))
+            if (exa_status e = seg_sum(m, m->d_hcsegptr, m->d_hcperm, m->d_hcbuf, hess_csc, m->nnzh_csc, m->side[1]))
                 return e;
-        } else if (exa_status e = scatter_csc(m, m->d_hsegptr, m->d_hperm, o.hess, hess_csc, m->nnzh_csc, m->nnzh, m->maxseg_h, m->side[1])) {
+        } else if (exa_status e = scatter_csc(m, m->d_hsegptr, m->d_hperm, o.hess, hess_csc, m->nnzh_csc, m->nnzh, m->side[1])) {
             return e;
         }
         CR(cudaEventRecord(m->ev_join[1], m->side[1]));
@@ -1679,7 +1615,7 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
         CR(cudaGetLastError());
     }
     if (g && m->nvar) {
-        if (exa_status e = seg_sum(m, m->d_gptr, m->d_gperm, m->d_gbuf, g, m->nvar, m->maxseg_g, m->stream)) return e;
+        if (exa_status e = grad_sum(m, g, m->stream)) return e;
     }
     if (c)
         if (exa_status e = aug_rows(m, c)) return e;
@@ -1871,7 +1807,7 @@ exa_status exa_stat(const exa_model *m, const char *key, double *value) {
     else if (k == "eval_split") *value = m->split_all;
     else if (k == "csc_direct") *value = m->csc_direct;
     else if (k == "hess_compressed") *value = m->use_hcomp;
-    else if (k == "max_segment") *value = std::max({m->maxseg_j, m->maxseg_h, m->maxseg_hc, m->maxseg_g, m->maxseg_a});
+    else if (k == "grad_compact") *value = m->grad_compact;
     else if (k == "nnzh_compressed") *value = (double)m->nnzhc;
     else if (k == "eval_tiles") *value = m->ntiles[exa::M_ALL];
     else if (k == "device_bytes") *value = (double)m->device_bytes;
