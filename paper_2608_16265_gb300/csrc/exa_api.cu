@@ -238,6 +238,31 @@ __global__ void k_low32(const unsigned long long *__restrict__ k, int *out, int 
     if (i < n) out[i] = (int)(k[i] & 0xffffffffULL);
 }
 
+// Two-pass segmented sums (setup): first[p] = the first entry of segment p; extra[p] = its
+// remaining entry count; multi[p] = 1 when it has any.
+__global__ void k_seg_first(const int *__restrict__ ptr, const int *__restrict__ perm, int n, int *first,
+                            int *multi, int *extra) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int b = ptr[p], c = ptr[p + 1] - b;
+    first[p] = c > 0 ? perm[b] : -1;
+    multi[p] = c > 1;
+    extra[p] = c > 1 ? c - 1 : 0;
+}
+// compacted multi-entry segments: mseg[i] = segment, mptr[i] = start of its extra entries in
+// mperm (inclusive scans midx of multi and mcum of extra)
+__global__ void k_seg_multi(const int *__restrict__ ptr, const int *__restrict__ perm, int n,
+                            const int *__restrict__ multi, const int *__restrict__ midx,
+                            const int *__restrict__ extra, const int *__restrict__ mcum, int *mseg, int *mptr,
+                            int *mperm) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n || !multi[p]) return;
+    const int i = midx[p] - 1, start = mcum[p] - extra[p];
+    mseg[i] = p;
+    mptr[i] = start;
+    for (int j = 0; j < extra[p]; j++) mperm[start + j] = perm[ptr[p] + 1 + j];
+}
+
 inline unsigned grid_of(i64 n, int b) { return (unsigned)((n + b - 1) / b); }
 
 thread_local std::string g_create_err;
@@ -245,6 +270,17 @@ thread_local std::string g_create_err;
 }  // namespace
 
 // ------------------------------------------------------------------ the model
+// A segmented sum over a sorted permutation (COO -> CSC, compressed Hessian -> CSC) in two passes:
+// a gather of every segment's first entry (k_permute over first), then the remaining entries of
+// the segments that have several, added onto the result in ascending order (k_seg_sum_warp<true>).
+// The additions and their order are those of the one-pass sum, which starts from 0.0: the results
+// are equal (bit for bit, except a one-entry segment holding -0.0, which the one-pass sum turns
+// into +0.0).  Most CSC entries have one contributor, so most of the work is a plain permutation.
+struct CscSum {
+    int n = 0, n_multi = 0;
+    int *first = nullptr, *mptr = nullptr, *mperm = nullptr, *mseg = nullptr;
+};
+
 struct exa_model {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -300,6 +336,7 @@ struct exa_model {
     i64 nnzhc = 0;
     bool has_hcomp = false;       // group-compressed Hessian sums exist (fewer than the COO slots)
     // sparse gradient: zero fill plus sums over the variables that have gradient slots only
+    CscSum sum_j, sum_h, sum_hc;  // Jacobian CSC (when it has duplicates), Hessian CSC, from compressed sums
     bool grad_compact = false;
     int n_gseg = 0;
     int *d_gsegptr = nullptr, *d_gsegvar = nullptr;
@@ -512,6 +549,35 @@ exa_status build_ptr(exa_model *m, const unsigned long long *skeys, int shift, i
     return EXA_OK;
 }
 
+exa_status build_csc_sum(exa_model *m, Scratch &S, const int *ptr, const int *perm, int n, CscSum *cs) {
+    cs->n = n;
+    CR(dalloc(m, &cs->first, n));
+    if (n <= 0) return EXA_OK;
+    int *multi = nullptr, *extra = nullptr, *midx = nullptr, *mcum = nullptr;
+    CR(S.get(&multi, n));
+    CR(S.get(&extra, n));
+    CR(S.get(&midx, n));
+    CR(S.get(&mcum, n));
+    k_seg_first<<<grid_of(n, 256), 256, 0, m->stream>>>(ptr, perm, n, cs->first, multi, extra);
+    CR(cudaGetLastError());
+    CR(exa_inclusive_sum_i32(multi, midx, n, m->stream));
+    CR(exa_inclusive_sum_i32(extra, mcum, n, m->stream));
+    int nm = 0, ne = 0;
+    CR(cudaMemcpyAsync(&nm, midx + n - 1, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    CR(cudaMemcpyAsync(&ne, mcum + n - 1, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    CR(cudaStreamSynchronize(m->stream));
+    cs->n_multi = nm;
+    CR(dalloc(m, &cs->mseg, nm));
+    CR(dalloc(m, &cs->mptr, (i64)nm + 1));
+    CR(dalloc(m, &cs->mperm, ne));
+    k_seg_multi<<<grid_of(n, 256), 256, 0, m->stream>>>(ptr, perm, n, multi, midx, extra, mcum, cs->mseg, cs->mptr,
+                                                         cs->mperm);
+    CR(cudaGetLastError());
+    CR(cudaMemcpyAsync(cs->mptr + nm, &ne, sizeof(int), cudaMemcpyHostToDevice, m->stream));
+    CR(cudaStreamSynchronize(m->stream));
+    return EXA_OK;
+}
+
 // Per-model structure: CSC of J and H, row groupings, gradient and augmentation segments.
 exa_status build_structure(exa_model *m) {
     Scratch S{m};
@@ -529,6 +595,8 @@ exa_status build_structure(exa_model *m) {
     if (exa_status e = sort_with_perm(m, S, keys, nj, 64, &skeys, m->d_jperm)) return e;
     if (exa_status e = segments(m, S, skeys, m->d_jperm, nj, &nseg, &m->d_jsegptr, &segkey, m->d_jcoo2csc, true)) return e;
     m->nnzj_csc = nseg;
+    if (nseg < nj)
+        if (exa_status e = build_csc_sum(m, S, m->d_jsegptr, m->d_jperm, nseg, &m->sum_j)) return e;
     CR(dalloc(m, &m->d_jrowval, nseg));
     if (nseg) {
         k_low32<<<grid_of(nseg, 256), 256, 0, m->stream>>>(segkey, m->d_jrowval, nseg);
@@ -555,6 +623,8 @@ exa_status build_structure(exa_model *m) {
     if (exa_status e = sort_with_perm(m, S, keys, nh, 64, &skeys, m->d_hperm)) return e;
     if (exa_status e = segments(m, S, skeys, m->d_hperm, nh, &nseg, &m->d_hsegptr, &segkey, m->d_hcoo2csc, true)) return e;
     m->nnzh_csc = nseg;
+    if (nseg < nh)
+        if (exa_status e = build_csc_sum(m, S, m->d_hsegptr, m->d_hperm, nseg, &m->sum_h)) return e;
     CR(dalloc(m, &m->d_hrowval, nseg));
     if (nseg) {
         k_low32<<<grid_of(nseg, 256), 256, 0, m->stream>>>(segkey, m->d_hrowval, nseg);
@@ -574,6 +644,7 @@ exa_status build_structure(exa_model *m) {
         int nsc = 0;
         if (exa_status e = segments(m, S, skeys, m->d_hcperm, nc, &nsc, &m->d_hcsegptr, &segkey, nullptr, true)) return e;
         if (nsc != m->nnzh_csc) return fail(m, EXA_E_INTERNAL, "compressed Hessian does not cover the CSC entries");
+        if (exa_status e = build_csc_sum(m, S, m->d_hcsegptr, m->d_hcperm, nsc, &m->sum_hc)) return e;
         CR(dalloc(m, &m->d_hcbuf, nc));
     }
 
@@ -1379,6 +1450,18 @@ static exa_status seg_sum(exa_model *m, const int *ptr, const int *perm, const d
     return EXA_OK;
 }
 
+static exa_status csc_sum(exa_model *m, const CscSum &cs, const double *src, double *dst, cudaStream_t st) {
+    if (cs.n <= 0) return EXA_OK;
+    k_permute<<<grid_of(cs.n, 256 * EXA_ILP), 256, 0, st>>>(cs.first, src, dst, (long long)cs.n);
+    CR(cudaGetLastError());
+    if (cs.n_multi) {
+        k_seg_sum_warp<true><<<grid_of(cs.n_multi, 256 * EXA_SEG_G), 256, 0, st>>>(cs.mptr, cs.mperm, src, dst, cs.mseg,
+                                                                                  cs.n_multi);
+        CR(cudaGetLastError());
+    }
+    return EXA_OK;
+}
+
 // Dense gradient from the gradient slots.  Compact form (most variables without a slot): zero fill,
 // then sums over the variables that have slots only.
 static exa_status grad_sum(exa_model *m, double *g, cudaStream_t st) {
@@ -1488,10 +1571,10 @@ exa_status exa_hess_csc_structure(const exa_model *mc, int32_t *colptr, int32_t 
     return csc_structure(m, m->nnzh, m->nnzh_csc, m->d_hcolptr, m->d_hrowval, m->d_hcoo2csc, colptr, rowval, coo2csc);
 }
 
-static exa_status scatter_csc(exa_model *m, const int *segptr, const int *perm, const double *coo, double *csc,
+static exa_status scatter_csc(exa_model *m, const CscSum &cs, const int *perm, const double *coo, double *csc,
                               i64 n, i64 nnz, cudaStream_t st) {
     if (!n) return EXA_OK;
-    if (n != nnz) return seg_sum(m, segptr, perm, coo, csc, n, st);
+    if (n != nnz) return csc_sum(m, cs, coo, csc, st);
     k_permute<<<grid_of(n, 256 * EXA_ILP), 256, 0, st>>>(perm, coo, csc, (long long)n);
     CR(cudaGetLastError());
     return EXA_OK;
@@ -1510,7 +1593,7 @@ exa_status exa_jac_csc(exa_model *m, const double *x, double *vals_csc) {
         return launch_eval(m, exa::M_JAC, x, nullptr, 0.0, o);
     }
     if (exa_status e = launch_eval(m, exa::M_JAC, x, nullptr, 0.0, o)) return e;
-    return scatter_csc(m, m->d_jsegptr, m->d_jperm, m->d_jbuf, vals_csc, m->nnzj_csc, m->nnzj, m->stream);
+    return scatter_csc(m, m->sum_j, m->d_jperm, m->d_jbuf, vals_csc, m->nnzj_csc, m->nnzj, m->stream);
 }
 
 exa_status exa_hess_csc(exa_model *m, const double *x, const double *y, double sigma, double *vals_csc) {
@@ -1530,10 +1613,10 @@ exa_status exa_hess_csc(exa_model *m, const double *x, const double *y, double s
         o.hess = nullptr;
         o.hcomp = m->d_hcbuf;
         if (exa_status e = launch_eval(m, exa::M_HESS_C, x, y, sigma, o)) return e;
-        return seg_sum(m, m->d_hcsegptr, m->d_hcperm, m->d_hcbuf, vals_csc, m->nnzh_csc, m->stream);
+        return csc_sum(m, m->sum_hc, m->d_hcbuf, vals_csc, m->stream);
     }
     if (exa_status e = launch_eval(m, exa::M_HESS, x, y, sigma, o)) return e;
-    return scatter_csc(m, m->d_hsegptr, m->d_hperm, m->d_hbuf, vals_csc, m->nnzh_csc, m->nnzh, m->stream);
+    return scatter_csc(m, m->sum_h, m->d_hperm, m->d_hbuf, vals_csc, m->nnzh_csc, m->nnzh, m->stream);
 }
 
 static exa_status eval_all_launches(exa_model *m, const double *x, const double *y, double sigma, double *f,
@@ -1597,15 +1680,15 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
     }
     if (jside) {
         CR(cudaStreamWaitEvent(m->side[0], m->ev_fork, 0));
-        if (exa_status e = scatter_csc(m, m->d_jsegptr, m->d_jperm, o.jac, jac_csc, m->nnzj_csc, m->nnzj, m->side[0])) return e;
+        if (exa_status e = scatter_csc(m, m->sum_j, m->d_jperm, o.jac, jac_csc, m->nnzj_csc, m->nnzj, m->side[0])) return e;
         CR(cudaEventRecord(m->ev_join[0], m->side[0]));
     }
     if (hside) {
         CR(cudaStreamWaitEvent(m->side[1], m->ev_fork, 0));
         if (hcomp) {
-            if (exa_status e = seg_sum(m, m->d_hcsegptr, m->d_hcperm, m->d_hcbuf, hess_csc, m->nnzh_csc, m->side[1]))
+            if (exa_status e = csc_sum(m, m->sum_hc, m->d_hcbuf, hess_csc, m->side[1]))
                 return e;
-        } else if (exa_status e = scatter_csc(m, m->d_hsegptr, m->d_hperm, o.hess, hess_csc, m->nnzh_csc, m->nnzh, m->side[1])) {
+        } else if (exa_status e = scatter_csc(m, m->sum_h, m->d_hperm, o.hess, hess_csc, m->nnzh_csc, m->nnzh, m->side[1])) {
             return e;
         }
         CR(cudaEventRecord(m->ev_join[1], m->side[1]));
