@@ -98,7 +98,7 @@ def csrc_digest() -> str:
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2608_16265_gb300", "csrc")
-    for f in ("exa_internal.h", "exa_lower.cpp"):
+    for f in ("exa_internal.h", "exa_lower.cpp", "exa_fp64_sincos.inc"):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()

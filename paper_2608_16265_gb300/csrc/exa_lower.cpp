@@ -1188,49 +1188,10 @@ static __device__ __forceinline__ float exa_exp_red(const double a) {
 }
 )";
 
-// FP64 sin and cos of one argument.  Cody-Waite reduction (Cody & Waite, 1980): q = rint(a 2/pi)
-// by adding and subtracting 1.5 * 2^52 in one fused multiply-add, r = a - q pi/2 with pi/2 split
-// into three doubles (P1 the double nearest pi/2, P2 the double nearest pi/2 - P1, P3 likewise;
-// computed with 400-bit arithmetic), each step a fused multiply-add, so r carries an error of about
-// one rounding for |a| < 2^20.  sin r and cos r on |r| <= pi/4 from their Taylor series,
-// (-1)^k / (2k+1)! up to r^15 and (-1)^k / (2k)! up to r^16 (truncation below 1e-16 relative),
-// by Horner's rule in r^2.  The quadrant q mod 4 (low word of the shifted q) swaps the two and
-// flips signs with integer operations, so only the reduction and the polynomials use the FP64
-// pipe.  For q = 0 (|a| < pi/4) r is a itself, and a zero r gives sin r = r, so sin(-0) = -0.
-// |a| >= 2^20, infinities and NaN take the library sincos.
-static const char *kFp64Helpers = R"(
-static __device__ __forceinline__ void exa_sincos64(const double a, double* s, double* c) {
-  if (!(fabs(a) < 1048576.0)) { sincos(a, s, c); return; }
-  const double qb = fma(a, 0x1.45f306dc9c883p-1, 0x1.8p52);
-  const int n = __double2loint(qb);
-  const double q = qb - 0x1.8p52;
-  double r = fma(-q, 0x1.921fb54442d18p+0, a);
-  r = fma(-q, 0x1.1a62633145c07p-54, r);
-  r = fma(-q, -0x1.f1976b7ed8fbcp-110, r);
-  if (__double_as_longlong(qb) == 0x4338000000000000LL) r = a;  // q = 0: r = a exactly
-  const double r2 = r * r;
-  double ps = fma(r2, -0x1.ae7f3e733b81fp-41, 0x1.6124613a86d09p-33);
-  ps = fma(r2, ps, -0x1.ae64567f544e4p-26);
-  ps = fma(r2, ps, 0x1.71de3a556c734p-19);
-  ps = fma(r2, ps, -0x1.a01a01a01a01ap-13);
-  ps = fma(r2, ps, 0x1.1111111111111p-7);
-  ps = fma(r2, ps, -0x1.5555555555555p-3);
-  double sr = fma(r * r2, ps, r);
-  if ((__double_as_longlong(r) & 0x7fffffffffffffffLL) == 0) sr = r;  // sin(+-0) = +-0
-  double pc = fma(r2, 0x1.ae7f3e733b81fp-45, -0x1.93974a8c07c9dp-37);
-  pc = fma(r2, pc, 0x1.1eed8eff8d898p-29);
-  pc = fma(r2, pc, -0x1.27e4fb7789f5cp-22);
-  pc = fma(r2, pc, 0x1.a01a01a01a01ap-16);
-  pc = fma(r2, pc, -0x1.6c16c16c16c17p-10);
-  pc = fma(r2, pc, 0x1.5555555555555p-5);
-  pc = fma(r2, pc, -0.5);
-  const double cr = fma(r2, pc, 1.0);
-  const double sa = (n & 1) ? cr : sr, ca = (n & 1) ? sr : cr;
-  const int fs = (n & 2) << 30, fc = ((n + 1) & 2) << 30;
-  *s = __hiloint2double(__double2hiint(sa) ^ fs, __double2loint(sa));
-  *c = __hiloint2double(__double2hiint(ca) ^ fc, __double2loint(ca));
-}
-)";
+// FP64 sin/cos helper of the generated code (its own file, so that a host test can compile it)
+static const char *kFp64Helpers =
+#include "exa_fp64_sincos.inc"
+    ;
 
 }  // namespace
 
