@@ -309,7 +309,7 @@ struct exa_model {
     std::vector<ExaPM> h_pms;     // host copy of the group descriptors
     // CUDA graphs of exa_eval_all, one per argument tuple
     struct GraphEntry {
-        std::array<const void *, 10> key;
+        std::array<const void *, 13> key;
         cudaGraphExec_t exec;
         uint64_t last_use;
     };
@@ -319,10 +319,10 @@ struct exa_model {
     cudaStream_t cap_stream = nullptr;
     // exa_eval_all runs its independent reductions (Jacobian CSC, Hessian CSC, the rest) on three
     // streams forked from and joined back into the model stream
-    cudaStream_t side[2] = {};
+    cudaStream_t side[3] = {};
     // device buffers of exa_eval_all_host: x, y, f, g, c, jac, hess, jac_csc, hess_csc
     double *d_host_io[9] = {};
-    cudaEvent_t ev_fork = nullptr, ev_join[2] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[3] = {}, ev_out[3] = {};
     double *d_theta = nullptr;
     int *d_status = nullptr;
     int *d_jrow = nullptr, *d_jcol = nullptr, *d_hrow = nullptr, *d_hcol = nullptr, *d_gvar = nullptr, *d_arow = nullptr;
@@ -361,7 +361,7 @@ struct exa_model {
 extern "C" {
 static exa_status eval_all_launches(exa_model *m, const double *x, const double *y, double sigma, double *f,
                                     double *g, double *c, double *jac, double *hess, double *jac_csc,
-                                    double *hess_csc);
+                                    double *hess_csc, double *const *host_fgc = nullptr);
 }
 
 namespace {
@@ -396,11 +396,13 @@ void free_all(exa_model *m) {
     m->graphs.clear();
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     m->cap_stream = nullptr;
-    for (int s = 0; s < 2; s++) {
+    for (int s = 0; s < 3; s++) {
         if (m->side[s]) cudaStreamDestroy(m->side[s]);
         if (m->ev_join[s]) cudaEventDestroy(m->ev_join[s]);
+        if (m->ev_out[s]) cudaEventDestroy(m->ev_out[s]);
         m->side[s] = nullptr;
         m->ev_join[s] = nullptr;
+        m->ev_out[s] = nullptr;
     }
     if (m->ev_fork) cudaEventDestroy(m->ev_fork);
     m->ev_fork = nullptr;
@@ -1621,7 +1623,7 @@ exa_status exa_hess_csc(exa_model *m, const double *x, const double *y, double s
 
 static exa_status eval_all_launches(exa_model *m, const double *x, const double *y, double sigma, double *f,
                                     double *g, double *c, double *jac, double *hess, double *jac_csc,
-                                    double *hess_csc) {
+                                    double *hess_csc, double *const *host_fgc) {
     const bool want_h = hess || hess_csc;
     ExaOut o{};
     o.obj_part = m->d_objpart;
@@ -1670,14 +1672,27 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
     // the CSC sums are independent of each other and of the objective, gradient and constraint
     // reductions: they run on side streams forked from the model stream (parallel graph branches)
     const bool jside = jac_csc && !jdirect && m->nnzj_csc, hside = (hcomp || (hess_csc && !hdirect)) && m->nnzh_csc;
-    if (jside || hside) {
+    // host copies of f, g, c (page-locked destinations) run on a third side stream as soon as each
+    // is final, overlapping the reductions that follow
+    double *const hf = host_fgc && f ? host_fgc[0] : nullptr, *const hg = host_fgc && g ? host_fgc[1] : nullptr,
+                  *const hc = host_fgc && c ? host_fgc[2] : nullptr;
+    const bool cside = hf || hg || hc;
+    if (jside || hside || cside) {
         if (!m->ev_fork) CR(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
-        for (int s = 0; s < 2; s++) {
+        for (int s = 0; s < 3; s++) {
             if (!m->side[s]) CR(cudaStreamCreateWithFlags(&m->side[s], cudaStreamNonBlocking));
             if (!m->ev_join[s]) CR(cudaEventCreateWithFlags(&m->ev_join[s], cudaEventDisableTiming));
+            if (!m->ev_out[s]) CR(cudaEventCreateWithFlags(&m->ev_out[s], cudaEventDisableTiming));
         }
         CR(cudaEventRecord(m->ev_fork, m->stream));
     }
+    // one finished output (on the model stream) copied to the host on side stream 2
+    auto to_host = [&](int slot, double *dst, const double *src, i64 n) -> exa_status {
+        CR(cudaEventRecord(m->ev_out[slot], m->stream));
+        CR(cudaStreamWaitEvent(m->side[2], m->ev_out[slot], 0));
+        CR(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToHost, m->side[2]));
+        return EXA_OK;
+    };
     if (jside) {
         CR(cudaStreamWaitEvent(m->side[0], m->ev_fork, 0));
         if (exa_status e = scatter_csc(m, m->sum_j, m->d_jperm, o.jac, jac_csc, m->nnzj_csc, m->nnzj, m->side[0])) return e;
@@ -1696,14 +1711,23 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
     if (f) {
         k_obj_final<<<1, 256, 0, m->stream>>>(m->d_objpart, m->nobj[mode], f);
         CR(cudaGetLastError());
+        if (hf)
+            if (exa_status e = to_host(0, hf, f, 1)) return e;
     }
     if (g && m->nvar) {
         if (exa_status e = grad_sum(m, g, m->stream)) return e;
+        if (hg)
+            if (exa_status e = to_host(1, hg, g, m->nvar)) return e;
     }
-    if (c)
+    if (c) {
         if (exa_status e = aug_rows(m, c)) return e;
+        if (hc && m->ncon)
+            if (exa_status e = to_host(2, hc, c, m->ncon)) return e;
+    }
+    if (cside) CR(cudaEventRecord(m->ev_join[2], m->side[2]));
     if (jside) CR(cudaStreamWaitEvent(m->stream, m->ev_join[0], 0));
     if (hside) CR(cudaStreamWaitEvent(m->stream, m->ev_join[1], 0));
+    if (cside) CR(cudaStreamWaitEvent(m->stream, m->ev_join[2], 0));
     return EXA_OK;
 }
 
@@ -1711,18 +1735,18 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
 // captured once per argument tuple on a private stream and cached (at most 4 tuples, least recently
 // used evicted).  When the model's stream is itself being captured, the launches go straight into
 // the caller's capture instead.
-exa_status exa_eval_all(exa_model *m, const double *x, const double *y, double sigma, double *f, double *g,
-                        double *c, double *jac, double *hess, double *jac_csc, double *hess_csc) {
-    if (exa_status e = check_model(m)) return e;
-    CHECK_PTRS(x);
-    if ((hess || hess_csc) && m->ncon && !y) return fail(m, EXA_E_INVALID, "NULL y");
+static exa_status eval_all_cached(exa_model *m, const double *x, const double *y, double sigma, double *f, double *g,
+                                  double *c, double *jac, double *hess, double *jac_csc, double *hess_csc,
+                                  double *const *host_fgc) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CR(cudaStreamIsCapturing(m->stream, &cs));
     if (!m->use_graphs || cs != cudaStreamCaptureStatusNone)
-        return eval_all_launches(m, x, y, sigma, f, g, c, jac, hess, jac_csc, hess_csc);
+        return eval_all_launches(m, x, y, sigma, f, g, c, jac, hess, jac_csc, hess_csc, host_fgc);
     uint64_t sb;
     std::memcpy(&sb, &sigma, 8);
-    const std::array<const void *, 10> key = {x, y, f, g, c, jac, hess, jac_csc, hess_csc, (const void *)(uintptr_t)sb};
+    const std::array<const void *, 13> key = {x, y, f, g, c, jac, hess, jac_csc, hess_csc, (const void *)(uintptr_t)sb,
+                                              host_fgc ? host_fgc[0] : nullptr, host_fgc ? host_fgc[1] : nullptr,
+                                              host_fgc ? host_fgc[2] : nullptr};
     for (auto &ge : m->graphs)
         if (ge.key == key) {
             ge.last_use = ++m->graph_clock;
@@ -1733,7 +1757,7 @@ exa_status exa_eval_all(exa_model *m, const double *x, const double *y, double s
     cudaStream_t user = m->stream;
     m->stream = m->cap_stream;
     CR(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
-    exa_status st = eval_all_launches(m, x, y, sigma, f, g, c, jac, hess, jac_csc, hess_csc);
+    exa_status st = eval_all_launches(m, x, y, sigma, f, g, c, jac, hess, jac_csc, hess_csc, host_fgc);
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamEndCapture(m->cap_stream, &graph);
     m->stream = user;
@@ -1757,6 +1781,14 @@ exa_status exa_eval_all(exa_model *m, const double *x, const double *y, double s
     return EXA_OK;
 }
 
+exa_status exa_eval_all(exa_model *m, const double *x, const double *y, double sigma, double *f, double *g,
+                        double *c, double *jac, double *hess, double *jac_csc, double *hess_csc) {
+    if (exa_status e = check_model(m)) return e;
+    CHECK_PTRS(x);
+    if ((hess || hess_csc) && m->ncon && !y) return fail(m, EXA_E_INVALID, "NULL y");
+    return eval_all_cached(m, x, y, sigma, f, g, c, jac, hess, jac_csc, hess_csc, nullptr);
+}
+
 exa_status exa_eval_all_host(exa_model *m, const double *x, const double *y, double sigma, double *f, double *g,
                              double *c, double *jac, double *hess, double *jac_csc, double *hess_csc) {
     if (exa_status e = check_model(m)) return e;
@@ -1766,22 +1798,32 @@ exa_status exa_eval_all_host(exa_model *m, const double *x, const double *y, dou
     const i64 n[9] = {m->nvar, m->ncon, 1, m->nvar, m->ncon, m->nnzj, m->nnzh, m->nnzj_csc, m->nnzh_csc};
     double *arg[9] = {const_cast<double *>(x), const_cast<double *>(y), f, g, c, jac, hess, jac_csc, hess_csc};
     double *use[9] = {};
-    bool staged[9] = {};
+    bool staged[9] = {}, pinned[9] = {};
     for (int k = 0; k < 9; k++) {
         if (!arg[k]) continue;
         cudaPointerAttributes a{};
         CR(cudaPointerGetAttributes(&a, arg[k]));
         staged[k] = a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged;
+        pinned[k] = a.type == cudaMemoryTypeHost;
         if (staged[k] && !m->d_host_io[k]) CR(dalloc(m, &m->d_host_io[k], n[k]));
         use[k] = staged[k] ? m->d_host_io[k] : arg[k];
     }
     for (int k = 0; k < 2; k++)
         if (staged[k] && n[k] > 0)
             CR(cudaMemcpyAsync(use[k], arg[k], sizeof(double) * n[k], cudaMemcpyHostToDevice, m->stream));
-    if (exa_status e = exa_eval_all(m, use[0], use[1], sigma, use[2], use[3], use[4], use[5], use[6], use[7], use[8]))
+    // page-locked f, g, c are copied back inside the evaluation (overlapping the CSC reductions)
+    double *host_fgc[3] = {};
+    bool early = false;
+    for (int k = 2; k < 5; k++)
+        if (staged[k] && pinned[k]) {
+            host_fgc[k - 2] = arg[k];
+            early = true;
+        }
+    if (exa_status e = eval_all_cached(m, use[0], use[1], sigma, use[2], use[3], use[4], use[5], use[6], use[7], use[8],
+                                       early ? host_fgc : nullptr))
         return e;
     for (int k = 2; k < 9; k++)
-        if (staged[k] && n[k] > 0)
+        if (staged[k] && n[k] > 0 && !(k < 5 && host_fgc[k - 2]))
             CR(cudaMemcpyAsync(arg[k], use[k], sizeof(double) * n[k], cudaMemcpyDeviceToHost, m->stream));
     CR(cudaStreamSynchronize(m->stream));
     return EXA_OK;
