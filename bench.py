@@ -297,6 +297,15 @@ def run_exa(args):
         if pg is not None:
             pg.barrier()
 
+    if args.steps_only:
+        # profiling mode: one untimed step, then steps_only timed steps (the launch list of a step)
+        step()
+        sms = timed(step, args.steps_only)
+        if rank == 0:
+            print(json.dumps({"profile": "steps_only", "nnz_per_rank": m.nnzj + m.nnzh, "steps": args.steps_only,
+                              "ms_per_step": sms, "precision": args.precision, "members": args.members,
+                              "tuned_options": ",".join(str(v) for v in m.tuned_options().values())}))
+        return
     if args.kernel_only:
         # profiling mode: only the dominant call (the evaluation kernel writing J and H COO), one
         # untimed call and then kernel_only timed calls; one JSON line with the sizes
@@ -408,6 +417,25 @@ def run_exa(args):
         extras[f"{tag}_kernel_hbm_frac"] = nbytes / (k2 * 1e-3) / 1e9 / peak
         extras[f"{tag}_eval_regs"] = m2.stat("eval_regs")
         m2.destroy()
+        # two-stage stochastic ACOPF (shared generator dispatch, 256 load scenarios of a 1000-bus
+        # network): the scenario axis as one more data dimension, full step in both precisions
+        import synth
+        ts = synth.two_stage_acopf(1000, 1500, 166, 256, seed=11)
+        tx, ty, tsig = synth.two_stage_point(ts, 0)
+        txt, tyt = torch.as_tensor(tx, device=dev), torch.as_tensor(ty, device=dev)
+        two = {"workload": ts.name}
+        for tname, tprec in (("fp64", B.EXA_FP64), ("mixed", B.EXA_MIXED_FP32)):
+            mt = B.exa_create(ts.flat, precision=tprec, device=local)
+            to = {k: E(n) for k, n in (("f", 1), ("g", mt.nvar), ("c", mt.ncon), ("jac", mt.nnzj), ("hess", mt.nnzh),
+                                        ("jac_csc", mt.nnzj_csc), ("hess_csc", mt.nnzh_csc))}
+            tstep = lambda: mt.exa_eval_all(txt, tyt, tsig, **to)
+            tstep()
+            tms = timed(tstep, 50)
+            two[f"{tname}_step_ms"] = tms
+            two[f"{tname}_nnz_per_s"] = (mt.nnzj + mt.nnzh) / (tms * 1e-3)
+            two["nnz"] = mt.nnzj + mt.nnzh
+            mt.destroy()
+        extras["two_stage"] = two
 
     # end to end through the C ABI with host buffers (exa_eval_all_host): pinned host x, y in,
     # f, g, c back to pinned host memory, every step; the derivative arrays (COO and CSC) are
@@ -469,6 +497,8 @@ def main(argv=None):
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--steps-only", type=int, default=0, help="profiling mode: one untimed step, then this many "
+                    "steps, print the step time, exit (no extras, no CPU baseline)")
     ap.add_argument("--kernel-only", type=int, default=0, help="profiling mode: run only the evaluation-kernel "
                     "call (J and H COO) this many times after one untimed call, print its sizes, exit")
     ap.add_argument("--pin", default="", help="block,min_blocks,grid_factor,flags: fixed launch configuration "

@@ -482,6 +482,144 @@ class Model:
                          [flatten_pattern(p) for p in self.patterns])
 
 
+
+# ---------------------------------------------------------------- two-stage models
+class ScenarioBlock(VarBlock):
+    """A block declared once per scenario: `z[j..., s]` with the scenario index last (Sec. 8.1.2,
+    the EachScenario marker).  Storage is scenario-major, `offset + s * size + rowmajor(j)`, so every
+    scenario's copy is one contiguous range."""
+
+    def __init__(self, offset: int, shape: tuple, nscen: int):
+        super().__init__(offset, shape)
+        self.nscen = nscen
+
+    def _flat_s(self, idx):
+        if not isinstance(idx, tuple):
+            idx = (idx,)
+        if len(idx) != len(self.shape) + 1:
+            raise IndexError(f"block has {len(self.shape)} dimensions plus the scenario, got {len(idx)} indices")
+        inner = self._flat(idx[:-1]) if self.shape else IConst(0)
+        return _ilift(idx[-1]) * self.size + inner + self.offset
+
+    def __getitem__(self, idx):
+        return Var(self._flat_s(idx))
+
+    def scenario_range(self, s: int) -> slice:
+        """Positions of scenario s's copy in x (or theta)."""
+        return slice(self.offset + s * self.size, self.offset + (s + 1) * self.size)
+
+
+class ScenarioParBlock(ScenarioBlock):
+    def __getitem__(self, idx):
+        return Param(self._flat_s(idx))
+
+
+@dataclass
+class ScenarioConBlock(ConBlock):
+    n_per: int = 0  # rows per scenario; scenario s owns rows [s * n_per, (s + 1) * n_per) of the block
+
+
+class TwoStageModel(Model):
+    """Two-stage builder (Sec. 8.1, Eq. (extensions) with B = 1; the TwoStageExaCore analog).
+
+    Declarations with `scenario=True` are replicated once per scenario s = 0 .. S-1 (the paper's
+    scenarios 1 .. S; the root is stage 0): variable and parameter blocks gain the scenario as last
+    index, constraint and objective patterns run over their data once per scenario, with the data
+    columns repeated and an int32 field `s` holding the scenario.  Every replicated pattern is still
+    one pattern, so it is generated and compiled once and evaluated across all scenarios in one
+    launch.  Root declarations are those of `Model`.  Stage tags: `var_stage()` / `con_stage()` give
+    0 for the root and s + 1 for scenario s."""
+
+    def __init__(self, nscen: int):
+        super().__init__()
+        if nscen < 1:
+            raise ValueError("a two-stage model needs at least one scenario")
+        self.nscen = int(nscen)
+        self._vstage: List[tuple] = []  # (start, count, stage) ranges
+        self._cstage: List[tuple] = []
+
+    def add_var(self, *shape, scenario: bool = False) -> VarBlock:
+        if not scenario:
+            b = super().add_var(*shape)
+            self._vstage.append((b.offset, b.size, 0))
+            return b
+        b = ScenarioBlock(self.nvar, tuple(int(v) for v in shape), self.nscen)
+        for s in range(self.nscen):
+            self._vstage.append((b.offset + s * b.size, b.size, s + 1))
+        self.nvar += b.size * self.nscen
+        return b
+
+    def add_par(self, values, scenario: bool = False) -> ParBlock:
+        """With scenario=True, `values` has the scenario as its last axis."""
+        if not scenario:
+            return super().add_par(values)
+        values = np.asarray(values, dtype=np.float64)
+        if values.ndim < 1 or values.shape[-1] != self.nscen:
+            raise ValueError("scenario parameter values need the scenario as last axis of length nscen")
+        b = ScenarioParBlock(len(self.theta), values.shape[:-1], self.nscen)
+        self.theta.extend(np.moveaxis(values, -1, 0).ravel().tolist())
+        return b
+
+    def _replicate(self, data: Dict[str, np.ndarray], n: Optional[int]):
+        data = dict(data or {})
+        if "s" in data:
+            raise ValueError("the data field name 's' is reserved for the scenario index")
+        names, arrs, types, n = self._table(data, n)
+        rep = {k: np.tile(a, self.nscen) for k, a in zip(names, arrs)}
+        rep["s"] = np.repeat(np.arange(self.nscen, dtype=np.int32), n)
+        return rep, n
+
+    def add_obj(self, fn, data=None, n=None, name: str = "", scenario: bool = False) -> int:
+        if not scenario:
+            return super().add_obj(fn, data, n, name)
+        rep, n = self._replicate(data, n)
+        return super().add_obj(fn, rep, n * self.nscen, name)
+
+    def add_con(self, fn, data=None, n=None, name: str = "", scenario: bool = False) -> ConBlock:
+        if not scenario:
+            blk = super().add_con(fn, data, n, name)
+            self._cstage.append((blk.row_base, blk.n_rows, 0))
+            return blk
+        rep, n = self._replicate(data, n)
+        blk = super().add_con(fn, rep, n * self.nscen, name)
+        for s in range(self.nscen):
+            self._cstage.append((blk.row_base + s * n, n, s + 1))
+        return ScenarioConBlock(blk.row_base, blk.n_rows, blk.pattern_index, n_per=n)
+
+    def add_con_aug(self, block: ConBlock, fn, data=None, n=None, name: str = "",
+                    scenario: bool = False) -> int:
+        """With scenario=True the pattern runs once per scenario and its row index (within one
+        scenario's rows of a scenario block) is moved to scenario s's rows."""
+        if not scenario:
+            return super().add_con_aug(block, fn, data, n, name)
+        if not isinstance(block, ScenarioConBlock):
+            raise ValueError("a per-scenario augmentation needs a per-scenario constraint block")
+        rep, n = self._replicate(data, n)
+
+        def shifted(d):
+            idx, val = fn(d)
+            return _ilift(idx) + d.s * block.n_per, val
+        return super().add_con_aug(block, shifted, rep, n * self.nscen, name)
+
+    def var_stage(self) -> np.ndarray:
+        out = np.zeros(self.nvar, dtype=np.int32)
+        for a, c, st in self._vstage:
+            out[a:a + c] = st
+        return out
+
+    def con_stage(self) -> np.ndarray:
+        out = np.zeros(self.ncon, dtype=np.int32)
+        for a, c, st in self._cstage:
+            out[a:a + c] = st
+        return out
+
+    def scenario_theta(self, theta: np.ndarray, block: ScenarioParBlock, s: int, values) -> np.ndarray:
+        """A copy of `theta` with scenario s's values of a per-scenario parameter block replaced
+        (the single-scenario accessor; pass the result to exa_set_theta)."""
+        out = np.array(theta, dtype=np.float64, copy=True)
+        out[block.scenario_range(s)] = np.asarray(values, dtype=np.float64).ravel()
+        return out
+
 @dataclass
 class FlatPattern:
     kind: int

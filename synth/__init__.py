@@ -14,6 +14,9 @@ Families (the paper's suites are not available; these stand in for them):
   * acopf_batch(...)     many ACOPF instances of uneven size with per-instance load multipliers.
   * goddard(T)           Goddard rocket, trapezoidal discretisation with T steps (Eq. (rocket); a
                          COPS-style optimal-control instance with exp and division-heavy patterns).
+  * two_stage_acopf(...) two-stage stochastic ACOPF (Eq. (extensions), B = 1): generator active
+                         power is the shared first stage, voltages, reactive power and flows are
+                         per scenario, and scenario loads are per-scenario parameters.
 Every random number comes from numpy's PCG64 (`np.random.default_rng(seed)`).
 """
 from __future__ import annotations
@@ -25,7 +28,7 @@ from typing import List, Optional
 import numpy as np
 
 from paper_2608_16265_gb300 import ir
-from paper_2608_16265_gb300.ir import Model, sin, cos, exp
+from paper_2608_16265_gb300.ir import Model, TwoStageModel, sin, cos, exp
 
 
 @dataclass
@@ -209,6 +212,89 @@ def acopf_batch_sizes(n_inst: int = 256, seed: int = 7, bmin: int = 200, bmax: i
 def acopf_batch(n_inst: int = 256, seed: int = 7, bmin: int = 200, bmax: int = 20000) -> List[Workload]:
     return [acopf(b, l, g, seed=s, load_mult=mu)
             for (b, l, g, s, mu) in acopf_batch_sizes(n_inst, seed, bmin, bmax)]
+
+
+# ------------------------------------------------------------------ two-stage stochastic ACOPF
+def two_stage_acopf(B: int, L: int, G: int, S: int, seed: int = 0, spread: float = 0.1) -> Workload:
+    """ACOPF of `acopf` in two stages over S load scenarios.  Root (shared) variables: pg[G].
+    Per-scenario variables: va, vm[B], qg[G], p, q[2L].  Per-scenario parameters: pd, qd[B]
+    (scenario s: the base loads times (1 + spread N(0,1)) per bus).  Objective: the root generation
+    cost plus, per scenario, (1/S) 0.01 qg^2.  Per scenario: the reference angle, the four flow
+    definitions, angle difference, two thermal limits, P and Q balances with the generator (root
+    pg, scenario qg) and arc augmentations.  Network and branch data as in `acopf`."""
+    rng = np.random.default_rng(seed)
+    br = _network(B, L, rng)
+    f, t = br[:, 0].astype(np.int32), br[:, 1].astype(np.int32)
+    r = rng.uniform(0.001, 0.05, L)
+    xx = rng.uniform(0.01, 0.3, L)
+    bc = rng.uniform(0.0, 0.05, L)
+    z2 = r * r + xx * xx
+    g, b = r / z2, -xx / z2
+    gff, bff, gft, bft = g.copy(), b + bc / 2, -g, -b.copy()
+    gtt, btt, gtf, btf = g.copy(), b + bc / 2, -g, -b.copy()
+    pd0 = rng.uniform(0.0, 1.0, B)
+    gbus = rng.integers(0, B, G).astype(np.int32)
+    c2 = rng.uniform(0.0, 0.1, G)
+    c1 = rng.uniform(1.0, 50.0, G)
+    pd = pd0[:, None] * (1.0 + spread * rng.standard_normal((B, S)))
+    qd = 0.3 * pd
+
+    m = TwoStageModel(S)
+    pg = m.add_var(G)
+    va = m.add_var(B, scenario=True)
+    vm = m.add_var(B, scenario=True)
+    qg = m.add_var(G, scenario=True)
+    p = m.add_var(2 * L, scenario=True)
+    q = m.add_var(2 * L, scenario=True)
+    PD = m.add_par(pd, scenario=True)
+    QD = m.add_par(qd, scenario=True)
+
+    gi = np.arange(G, dtype=np.int32)
+    m.add_obj(lambda d: d.c2 * pg[d.k] ** 2 + d.c1 * pg[d.k], data=dict(c2=c2, c1=c1), name="gen_cost")
+    m.add_obj(lambda d: (0.01 / S) * qg[d.g, d.s] ** 2, data=dict(g=gi), scenario=True, name="q_cost")
+    m.add_con(lambda d: va[d.ref, d.s], data=dict(ref=np.array([gbus[0]], np.int32)), scenario=True,
+              name="ref_angle")
+    brd = dict(a=np.arange(L, dtype=np.int32), f=f, t=t, gff=gff, bff=bff, gft=gft, bft=bft, gtt=gtt,
+               btt=btt, gtf=gtf, btf=btf)
+
+    def th(d, i, j):
+        return va[i, d.s] - va[j, d.s]
+
+    m.add_con(lambda d: p[d.a, d.s] - (d.gff * vm[d.f, d.s] ** 2 + vm[d.f, d.s] * vm[d.t, d.s] * (
+        d.gft * cos(th(d, d.f, d.t)) + d.bft * sin(th(d, d.f, d.t)))), data=brd, scenario=True, name="p_from")
+    m.add_con(lambda d: q[d.a, d.s] - (-d.bff * vm[d.f, d.s] ** 2 - vm[d.f, d.s] * vm[d.t, d.s] * (
+        d.bft * cos(th(d, d.f, d.t)) - d.gft * sin(th(d, d.f, d.t)))), data=brd, scenario=True, name="q_from")
+    m.add_con(lambda d: p[d.a + L, d.s] - (d.gtt * vm[d.t, d.s] ** 2 + vm[d.t, d.s] * vm[d.f, d.s] * (
+        d.gtf * cos(th(d, d.t, d.f)) + d.btf * sin(th(d, d.t, d.f)))), data=brd, scenario=True, name="p_to")
+    m.add_con(lambda d: q[d.a + L, d.s] - (-d.btt * vm[d.t, d.s] ** 2 - vm[d.t, d.s] * vm[d.f, d.s] * (
+        d.btf * cos(th(d, d.t, d.f)) - d.gtf * sin(th(d, d.t, d.f)))), data=brd, scenario=True, name="q_to")
+    m.add_con(lambda d: va[d.f, d.s] - va[d.t, d.s], data=dict(f=f, t=t), scenario=True, name="angle_diff")
+    ai = dict(a=np.arange(L, dtype=np.int32))
+    m.add_con(lambda d: p[d.a, d.s] ** 2 + q[d.a, d.s] ** 2, data=ai, scenario=True, name="thermal_from")
+    m.add_con(lambda d: p[d.a + L, d.s] ** 2 + q[d.a + L, d.s] ** 2, data=ai, scenario=True, name="thermal_to")
+    bi = dict(i=np.arange(B, dtype=np.int32))
+    cp = m.add_con(lambda d: PD[d.i, d.s], data=bi, scenario=True, name="p_balance")
+    cq = m.add_con(lambda d: QD[d.i, d.s], data=bi, scenario=True, name="q_balance")
+    m.add_con_aug(cp, lambda d: (d.bus, -pg[d.g]), data=dict(bus=gbus, g=gi), scenario=True, name="gen_p")
+    m.add_con_aug(cq, lambda d: (d.bus, -qg[d.g, d.s]), data=dict(bus=gbus, g=gi), scenario=True, name="gen_q")
+    arcs = dict(bus=np.concatenate([f, t]).astype(np.int32), a=np.arange(2 * L, dtype=np.int32))
+    m.add_con_aug(cp, lambda d: (d.bus, p[d.a, d.s]), data=arcs, scenario=True, name="arc_p")
+    m.add_con_aug(cq, lambda d: (d.bus, q[d.a, d.s]), data=arcs, scenario=True, name="arc_q")
+    meta = dict(B=B, L=L, G=G, S=S, seed=seed, spread=spread, vm=vm, pd=PD, qd=QD)
+    return Workload(f"two_stage_acopf_b{B}_l{L}_g{G}_s{S}", m, m.flat(), meta)
+
+
+def two_stage_point(wl: Workload, seed: int):
+    """vm = 1 in every scenario, everything else 0, plus 0.05 N(0,1) on every variable;
+    y ~ N(0, 1); sigma = 1."""
+    rng = np.random.default_rng(seed)
+    x = np.zeros(wl.flat.nvar)
+    vm = wl.meta["vm"]
+    for s in range(wl.meta["S"]):
+        x[vm.scenario_range(s)] = 1.0
+    x += 0.05 * rng.standard_normal(wl.flat.nvar)
+    y = rng.standard_normal(wl.flat.ncon)
+    return x, y, 1.0
 
 
 # ------------------------------------------------------------------ Goddard rocket (optimal control)

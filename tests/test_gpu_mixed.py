@@ -31,6 +31,7 @@ CASES = {
     "acopf_small": lambda: (lambda w: (w.flat, synth.acopf_point(w, 0)))(synth.acopf(500, 700, 100, seed=1)),
     "pde_41": lambda: (lambda w: (w.flat, synth.pde_point(w, 2)))(synth.pde(41)),
     "goddard_2000": lambda: (lambda w: (w.flat, synth.goddard_point(w, 2)))(synth.goddard(2000)),
+    "two_stage_acopf": lambda: (lambda w: (w.flat, synth.two_stage_point(w, 2)))(synth.two_stage_acopf(120, 180, 20, 8, seed=4)),
 }
 
 

@@ -3,6 +3,8 @@
 Bar: structures and CSC maps bit-exact; FP64 values within 1e-12 relative, normwise per output
 array.  Sizes span several tiles with ragged tails; full-size configurations are compared on
 sampled batch members or whole outputs where the oracle finishes in seconds."""
+import copy
+
 import numpy as np
 import pytest
 
@@ -83,6 +85,7 @@ CASES = {
     "acopf_shunts": lambda: (lambda w: (w.flat, synth.acopf_point(w, 3)))(synth.acopf(37, 61, 9, seed=4, shunts=True)),
     "pde_41": lambda: (lambda w: (w.flat, synth.pde_point(w, 2)))(synth.pde(41)),
     "goddard_2000": lambda: (lambda w: (w.flat, synth.goddard_point(w, 2)))(synth.goddard(2000)),
+    "two_stage_acopf": lambda: (lambda w: (w.flat, synth.two_stage_point(w, 2)))(synth.two_stage_acopf(120, 180, 20, 8, seed=4)),
 }
 
 
@@ -395,6 +398,26 @@ def test_eval_all_host_buffers(pinned):
             "hess": torch.empty(m.nnzh, dtype=torch.float64, device="cuda")}
     m.exa_eval_all(_t(x), _t(y), s, **devm)
     assert torch.equal(mix["g"], devm["g"].cpu()) and torch.equal(mix["hess"], devm["hess"])
+
+
+def test_two_stage_scenario_parameters():
+    """Replacing one scenario's loads with exa_set_theta (the builder's single-scenario accessor)
+    gives the results of a model created with those loads, bit for bit."""
+    B = _B()
+    wl = synth.two_stage_acopf(60, 90, 12, 6, seed=9)
+    x, y, s = synth.two_stage_point(wl, 1)
+    m = B.exa_create(wl.flat)
+    pd = wl.meta["pd"]
+    new = wl.model.scenario_theta(wl.flat.theta, pd, 3, np.linspace(0.1, 1.0, 60))
+    m.exa_set_theta(new)
+    flat2 = copy.copy(wl.flat)
+    flat2.theta = new
+    m2 = B.exa_create(flat2)
+    a, b = m.eval_all(_t(x), _t(y), s, csc=True), m2.eval_all(_t(x), _t(y), s, csc=True)
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+    o = oracle.Oracle(flat2)
+    assert normwise(_np(a["c"]), o.cons(x)) <= TOL
 
 
 def test_set_theta():

@@ -202,6 +202,7 @@ CASES = [
     ("acopf", lambda: (lambda w: (w.flat, synth.acopf_point(w, 1)))(synth.acopf(5, 7, 2, seed=3, shunts=True))),
     ("pde", lambda: (lambda w: (w.flat, synth.pde_point(w, 1)))(synth.pde(5))),
     ("goddard", lambda: (lambda w: (w.flat, synth.goddard_point(w, 1)))(synth.goddard(6))),
+    ("two_stage", lambda: (lambda w: (w.flat, synth.two_stage_point(w, 1)))(synth.two_stage_acopf(5, 7, 2, 3, seed=3))),
 ]
 
 
