@@ -89,7 +89,11 @@ def whole_job_rate(nnz_per_rank: int, world_size: int, ms_max: float) -> float:
     return world_size * nnz_per_rank / (ms_max * 1e-3)
 
 
-FP64_PEAK_GFLOPS = 1250.0  # GB300 nominal FP64 (FMA = 2 flops); the recipe's figure
+# GB300 FP64 pipe: 2 FP64 operations (DFMA, DMUL or DADD) per clock per SM (1/64 of the FP32 rate;
+# it is what ncu's fp64 pipe utilisation counts against), 152 SMs at the 2070 MHz maximum clock:
+# 629 G FP64 instructions/s, i.e. 1.26 TFLOP/s counting an FMA as 2 flops (the nominal 1.25).
+FP64_INST_PEAK_G = 2 * 152 * 2.070
+FP64_PEAK_GFLOPS = 2 * FP64_INST_PEAK_G
 
 
 def csrc_digest() -> str:
@@ -348,13 +352,17 @@ def run_exa(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_kind, "kernel": "exa_all (generated eval kernel)",
                 "algorithmic_bytes": nbytes, "kernel_ms": kern_ms}
-    if ctr and ctr.get("fp64_flops_per_nnz"):
-        # the FP64 pipe bounds this kernel when its FP64 rate is the larger fraction of its peak
+    if ctr and ctr.get("fp64_inst_per_nnz"):
+        # the FP64 pipe bounds this kernel when its FP64 instruction rate is the larger fraction of
+        # its peak (DMUL and DADD take a pipe slot like DFMA, so instructions, not flops, are counted)
+        ginst = ctr["fp64_inst_per_nnz"] * nnz_rank / (kern_ms * 1e-3) / 1e9
         gflops = ctr["fp64_flops_per_nnz"] * nnz_rank / (kern_ms * 1e-3) / 1e9
-        alu = {"bound": "alu", "achieved": gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
-               "frac": gflops / FP64_PEAK_GFLOPS, "traffic": traffic, "peak_source": "nominal (recipe)",
-               "kernel": roofline["kernel"], "fp64_flops": int(ctr["fp64_flops_per_nnz"] * nnz_rank),
-               "kernel_ms": kern_ms, "hbm_frac": roofline["frac"]}
+        alu = {"bound": "alu", "achieved": ginst, "peak": FP64_INST_PEAK_G, "unit": "G FP64 instructions/s",
+               "frac": ginst / FP64_INST_PEAK_G, "traffic": traffic,
+               "peak_source": "derived: 2 FP64 ops/clk/SM x 152 SMs x 2070 MHz",
+               "kernel": roofline["kernel"], "fp64_inst": int(ctr["fp64_inst_per_nnz"] * nnz_rank),
+               "fp64_gflops": gflops, "fp64_gflops_frac": gflops / FP64_PEAK_GFLOPS,
+               "kernel_ms": kern_ms, "hbm_frac": roofline["frac"], "hbm_achieved_gbs": roofline["achieved"]}
         if alu["frac"] > roofline["frac"]:
             roofline = alu
 
