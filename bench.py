@@ -268,8 +268,10 @@ def run_exa(args):
     t0 = time.perf_counter()
     pin = {}
     if args.pin:
-        b_, mb_, gf_, fl_ = (int(v) for v in args.pin.split(","))
-        pin = dict(block=b_, min_blocks=mb_, grid_factor=gf_, flags=fl_ | B.EXA_FLAG_NO_TUNE)
+        vals = [int(v) for v in args.pin.split(",")]
+        b_, mb_, gf_, fl_ = vals[:4]
+        pin = dict(block=b_, min_blocks=mb_, grid_factor=gf_, flags=fl_ | B.EXA_FLAG_NO_TUNE,
+                   chunks=vals[4] if len(vals) > 4 else 1)
     m = B.exa_create_batch(flats, precision=prec, device=local, **pin)
     torch.cuda.synchronize()
     t_create = time.perf_counter() - t0
@@ -373,6 +375,7 @@ def run_exa(args):
               "eval_persist": m.stat("eval_persist"), "eval_grid": m.stat("eval_grid"), "eval_tiles": m.stat("eval_tiles"),
               "eval_min_blocks": m.stat("eval_min_blocks"), "eval_split": m.stat("eval_split"),
               "csc_direct": m.stat("csc_direct"), "hess_compressed": m.stat("hess_compressed"),
+              "eval_chunks": m.stat("eval_chunks"),
               "nnzh_compressed": m.stat("nnzh_compressed"), "grad_compact": m.stat("grad_compact"),
               "tuned_options": ",".join(str(v) for v in m.tuned_options().values()),
               "device_bytes": m.stat("device_bytes")}
@@ -509,7 +512,7 @@ def main(argv=None):
                     "steps, print the step time, exit (no extras, no CPU baseline)")
     ap.add_argument("--kernel-only", type=int, default=0, help="profiling mode: run only the evaluation-kernel "
                     "call (J and H COO) this many times after one untimed call, print its sizes, exit")
-    ap.add_argument("--pin", default="", help="block,min_blocks,grid_factor,flags: fixed launch configuration "
+    ap.add_argument("--pin", default="", help="block,min_blocks,grid_factor,flags[,chunks]: fixed launch configuration "
                     "(extras.tuned_options of an earlier run) instead of autotuning, for profiling runs")
     args = ap.parse_args(argv)
     if args.warmup < 3:

@@ -140,6 +140,9 @@ typedef struct {
                               waves of resident CTAs looping over the tiles */
     int32_t min_blocks;    /* launch-bounds minimum resident CTAs per SM of the evaluation kernels
                               (caps their registers), 0..32; 0 = none, or chosen by the autotuner */
+    int32_t chunks;        /* exa_eval_all over this many contiguous groups of batch members, the
+                              reductions of one group overlapping the evaluation of the next,
+                              0..16; 0 = chosen by the autotuner (1 when tuning is off) */
 } exa_options;
 
 enum {
@@ -285,7 +288,7 @@ exa_status exa_compile_check(const exa_model_desc *desc, const exa_options *opt,
 
 /* Named statistics (host values): "nvrtc_ms", "create_ms", "tune_ms", "eval_regs", "eval_block",
  * "eval_regs_jac", "eval_regs_hess", "eval_tiles", "eval_grid", "eval_persist", "eval_min_blocks",
- * "eval_split", "csc_direct",
+ * "eval_split", "eval_chunks", "csc_direct",
  * "hess_compressed", "nnzh_compressed", "grad_compact", "device_bytes", "n_patterns", "batch_members".
  * Unknown key: EXA_E_INVALID. */
 exa_status exa_stat(const exa_model *m, const char *key, double *value);

@@ -263,6 +263,25 @@ __global__ void k_seg_multi(const int *__restrict__ ptr, const int *__restrict__
     for (int j = 0; j < extra[p]; j++) mperm[start + j] = perm[ptr[p] + 1 + j];
 }
 
+// out[i] = arr[idx[i]] (setup)
+__global__ void k_gather_i32(const int *__restrict__ arr, const long long *__restrict__ idx, int n, int *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = arr[idx[i]];
+}
+// out[i] = first position p in the ascending arr[0..n) with arr[p] >= key[i] (setup)
+__global__ void k_lower_bound(const int *__restrict__ arr, int n, const long long *__restrict__ key, int nk,
+                              int *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nk) return;
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = lo + (hi - lo) / 2;
+        if ((long long)arr[mid] < key[i]) lo = mid + 1;
+        else hi = mid;
+    }
+    out[i] = lo;
+}
+
 inline unsigned grid_of(i64 n, int b) { return (unsigned)((n + b - 1) / b); }
 
 thread_local std::string g_create_err;
@@ -337,6 +356,16 @@ struct exa_model {
     bool has_hcomp = false;       // group-compressed Hessian sums exist (fewer than the COO slots)
     // sparse gradient: zero fill plus sums over the variables that have gradient slots only
     CscSum sum_j, sum_h, sum_hc;  // Jacobian CSC (when it has duplicates), Hessian CSC, from compressed sums
+    // Member-chunked exa_eval_all: the members are split into nchunks contiguous groups; the
+    // evaluation of group c + 1 runs on the model stream while the reductions of group c run on a
+    // side stream.  Per member b (nb + 1 boundaries each): first tile of every kernel kind, and the
+    // first position of b's part of every reduction's output or work list.
+    int nchunks = 1;
+    bool chunks_fixed = false;  // given at creation: the tuner keeps it
+    std::vector<int> chunk_b;  // member boundaries of the chunks (nchunks + 1)
+    std::vector<int> mb_tile[exa::M_COUNT];
+    std::vector<int> mb_jcsc, mb_hcsc, mb_jmulti, mb_hmulti, mb_hcmulti, mb_gseg, mb_arow;
+    cudaEvent_t ev_chunk[16] = {};
     bool grad_compact = false;
     int n_gseg = 0;
     int *d_gsegptr = nullptr, *d_gsegvar = nullptr;
@@ -406,6 +435,10 @@ void free_all(exa_model *m) {
     }
     if (m->ev_fork) cudaEventDestroy(m->ev_fork);
     m->ev_fork = nullptr;
+    for (cudaEvent_t &e : m->ev_chunk) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
     for (int k = 0; k < exa::M_COUNT; k++) {
         if (m->d_tiles[k]) cudaFree(m->d_tiles[k]);
         m->d_tiles[k] = nullptr;
@@ -471,16 +504,21 @@ exa_status compile(exa_model *m, const std::string &src) {
     return EXA_OK;
 }
 
-exa_status launch_eval(exa_model *m, Mode mode, const double *x, const double *y, double sigma, ExaOut out) {
-    if (m->ntiles[mode] == 0) return EXA_OK;
+// The evaluation kernel of `mode` over its tiles [t0, t1) (t1 < 0: all tiles) on stream st (null:
+// the model stream).
+exa_status launch_eval(exa_model *m, Mode mode, const double *x, const double *y, double sigma, ExaOut out,
+                       int t0 = 0, int t1 = -1, cudaStream_t st = nullptr) {
+    if (t1 < 0) t1 = m->ntiles[mode];
+    if (t1 <= t0) return EXA_OK;
     out.status = m->d_status;
     ExaStructOut so{};
     so.status = m->d_status;
     const double *th = m->d_theta;
-    int nt = m->ntiles[mode];
-    void *args[] = {&m->d_tiles[mode], &nt, &m->d_pm, &x, &y, &th, &sigma, &out, &so};
-    const int grid = m->grid[mode] > 0 ? m->grid[mode] : nt;
-    CR(cudaLaunchKernel((const void *)m->fn[mode], dim3(grid), dim3(m->block), args, 0, m->stream));
+    int nt = t1 - t0;
+    const ExaTile *tiles = m->d_tiles[mode] + t0;
+    void *args[] = {&tiles, &nt, &m->d_pm, &x, &y, &th, &sigma, &out, &so};
+    const int grid = m->grid[mode] > 0 ? std::min(m->grid[mode], nt) : nt;
+    CR(cudaLaunchKernel((const void *)m->fn[mode], dim3(grid), dim3(m->block), args, 0, st ? st : m->stream));
     return EXA_OK;
 }
 
@@ -578,6 +616,71 @@ exa_status build_csc_sum(exa_model *m, Scratch &S, const int *ptr, const int *pe
     CR(cudaMemcpyAsync(cs->mptr + nm, &ne, sizeof(int), cudaMemcpyHostToDevice, m->stream));
     CR(cudaStreamSynchronize(m->stream));
     return EXA_OK;
+}
+
+// Per-member boundaries of every reduction's output and work lists (for member-chunked evaluation).
+exa_status build_member_bounds(exa_model *m) {
+    Scratch S{m};
+    const int nb = m->nb;
+    long long *key = nullptr;
+    int *out = nullptr;
+    CR(S.get(&key, nb + 1));
+    CR(S.get(&out, nb + 1));
+    std::vector<long long> k(nb + 1);
+    auto fetch = [&](std::vector<int> &dst) -> exa_status {
+        dst.assign(nb + 1, 0);
+        CR(cudaMemcpy(dst.data(), out, sizeof(int) * (nb + 1), cudaMemcpyDeviceToHost));
+        return EXA_OK;
+    };
+    auto gather = [&](const int *arr, const std::vector<i64> &idx, std::vector<int> &dst) -> exa_status {
+        for (int b = 0; b <= nb; b++) k[b] = idx[b];
+        CR(cudaMemcpy(key, k.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice));
+        k_gather_i32<<<grid_of(nb + 1, 256), 256, 0, m->stream>>>(arr, key, nb + 1, out);
+        CR(cudaGetLastError());
+        return fetch(dst);
+    };
+    auto lower = [&](const int *arr, int n, const std::vector<long long> &keys, std::vector<int> &dst) -> exa_status {
+        CR(cudaMemcpy(key, keys.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice));
+        k_lower_bound<<<grid_of(nb + 1, 256), 256, 0, m->stream>>>(arr, n, key, nb + 1, out);
+        CR(cudaGetLastError());
+        return fetch(dst);
+    };
+    auto as_ll = [&](const std::vector<int> &v) { return std::vector<long long>(v.begin(), v.end()); };
+    if (exa_status e = gather(m->d_jcolptr, m->xoff, m->mb_jcsc)) return e;
+    if (exa_status e = gather(m->d_hcolptr, m->xoff, m->mb_hcsc)) return e;
+    m->mb_jmulti.assign(nb + 1, 0);
+    m->mb_hmulti.assign(nb + 1, 0);
+    m->mb_hcmulti.assign(nb + 1, 0);
+    if (m->sum_j.n_multi)
+        if (exa_status e = lower(m->sum_j.mseg, m->sum_j.n_multi, as_ll(m->mb_jcsc), m->mb_jmulti)) return e;
+    if (m->sum_h.n_multi)
+        if (exa_status e = lower(m->sum_h.mseg, m->sum_h.n_multi, as_ll(m->mb_hcsc), m->mb_hmulti)) return e;
+    if (m->sum_hc.n_multi)
+        if (exa_status e = lower(m->sum_hc.mseg, m->sum_hc.n_multi, as_ll(m->mb_hcsc), m->mb_hcmulti)) return e;
+    m->mb_gseg.assign(nb + 1, 0);
+    if (m->n_gseg)
+        if (exa_status e = lower(m->d_gsegvar, m->n_gseg, std::vector<long long>(m->xoff.begin(), m->xoff.end()),
+                                 m->mb_gseg)) return e;
+    m->mb_arow.assign(nb + 1, 0);
+    if (m->n_aug_rows)
+        if (exa_status e = lower(m->d_arows, m->n_aug_rows, std::vector<long long>(m->coff.begin(), m->coff.end()),
+                                 m->mb_arow)) return e;
+    return EXA_OK;
+}
+
+// Member boundaries of n chunks of about equal nonzeros (n = 1: one chunk of all members).
+void set_chunks(exa_model *m, int n) {
+    const int nb = m->nb;
+    n = std::max(1, std::min(n, std::min(nb, 16)));
+    m->nchunks = n;
+    m->chunk_b.assign(1, 0);
+    const double tot = (double)(m->nnzj + m->nnzh);
+    for (int c = 1; c < n; c++) {
+        int b = m->chunk_b.back() + 1;
+        while (b < nb && (double)(m->joff[b] + m->hoff[b]) < tot * c / n) b++;
+        m->chunk_b.push_back(std::min(b, nb - (n - c)));
+    }
+    m->chunk_b.push_back(nb);
 }
 
 // Per-model structure: CSC of J and H, row groupings, gradient and augmentation segments.
@@ -778,8 +881,10 @@ exa_status setup_kernels(exa_model *m, int block, int min_blocks = 0) {
     for (int k = 0; k < exa::M_COUNT; k++) {
         std::vector<ExaTile> tiles;
         m->nobj[k] = 0;
+        m->mb_tile[k].assign(nb + 1, 0);
         for (int b = 0; b < nb; b++)
             for (int gi = 0; gi < ng; gi++) {
+                if (gi == 0) m->mb_tile[k][b] = (int)tiles.size();
                 bool in = false, part = false;
                 for (int p : m->groups[gi].pats) {
                     const bool act = exa::pattern_in_mode(m->pats[p], (exa::Mode)k);
@@ -793,6 +898,7 @@ exa_status setup_kernels(exa_model *m, int block, int min_blocks = 0) {
                     tiles.push_back({b * ng + gi, (int)s, part ? m->nobj[k]++ : -1});
             }
         m->ntiles[k] = (int)tiles.size();
+        m->mb_tile[k][nb] = m->ntiles[k];
         m->grid[k] = m->ntiles[k];
         if (m->d_tiles[k]) cudaFree(m->d_tiles[k]);
         m->d_tiles[k] = nullptr;
@@ -913,10 +1019,14 @@ exa_status autotune(exa_model *m) {
     CR(S.get(&hc, m->nnzh_csc));
     double best_step = 1e30;
     bool best_split = false, best_direct = false, best_hc = m->use_hcomp;
+    int best_chunks = m->nchunks;
+    for (int nch : {1, 4, 8, 16})
     for (int hcv = 0; hcv < (m->has_hcomp ? 2 : 1); hcv++)
     for (int split = 0; split < 2; split++)
         for (int direct = 0; direct < 2; direct++) {
             if (direct && m->nnzj_csc != m->nnzj && m->nnzh_csc != m->nnzh) continue;
+            if (nch > m->nb || (m->chunks_fixed && nch != best_chunks)) continue;
+            set_chunks(m, nch);
             m->split_all = split;
             m->csc_direct = direct;
             m->use_hcomp = hcv;
@@ -933,8 +1043,10 @@ exa_status autotune(exa_model *m) {
                 best_split = split;
                 best_direct = direct;
                 best_hc = hcv;
+                best_chunks = nch;
             }
         }
+    set_chunks(m, best_chunks);
     m->split_all = best_split;
     m->csc_direct = best_direct;
     m->use_hcomp = best_hc;
@@ -1053,6 +1165,7 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     if (m->block % 32 || m->block < 32 || m->block > 1024) return fail(m, EXA_E_INVALID, "block_threads must be a multiple of 32 in [32, 1024]");
     if (o.grid_factor < -1 || o.grid_factor > 64) return fail(m, EXA_E_INVALID, "grid_factor must be in [-1, 64]");
     if (o.min_blocks < 0 || o.min_blocks > 32) return fail(m, EXA_E_INVALID, "min_blocks must be in [0, 32]");
+    if (o.chunks < 0 || o.chunks > 16) return fail(m, EXA_E_INVALID, "chunks must be in [0, 16]");
     m->split_all = (o.flags & EXA_FLAG_SPLIT) != 0;
     m->csc_direct = (o.flags & EXA_FLAG_CSC_SCATTER) != 0;
     if (nb < 1) return fail(m, EXA_E_INVALID, "empty batch");
@@ -1254,6 +1367,9 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
         if (st) return fail(m, EXA_E_BOUNDS, "a resolved variable, parameter or row index is out of range");
     }
     if (exa_status e = build_structure(m)) return e;
+    if (exa_status e = build_member_bounds(m)) return e;
+    set_chunks(m, o.chunks ? o.chunks : 1);
+    m->chunks_fixed = o.chunks != 0;
 
     // work buffers
     CR(dalloc(m, &m->d_jbuf, m->nnzj));
@@ -1464,6 +1580,21 @@ static exa_status csc_sum(exa_model *m, const CscSum &cs, const double *src, dou
     return EXA_OK;
 }
 
+// csc_sum over CSC positions [p0, p1), whose multi-entry segments are mseg[i0 .. i1).
+static exa_status csc_sum_range(exa_model *m, const CscSum &cs, const double *src, double *dst, int p0, int p1,
+                                int i0, int i1, cudaStream_t st) {
+    if (p1 > p0) {
+        k_permute<<<grid_of(p1 - p0, 256 * EXA_ILP), 256, 0, st>>>(cs.first + p0, src, dst + p0, (long long)(p1 - p0));
+        CR(cudaGetLastError());
+    }
+    if (i1 > i0) {
+        k_seg_sum_warp<true><<<grid_of(i1 - i0, 256 * EXA_SEG_G), 256, 0, st>>>(cs.mptr + i0, cs.mperm, src, dst,
+                                                                               cs.mseg + i0, i1 - i0);
+        CR(cudaGetLastError());
+    }
+    return EXA_OK;
+}
+
 // Dense gradient from the gradient slots.  Compact form (most variables without a slot): zero fill,
 // then sums over the variables that have slots only.
 static exa_status grad_sum(exa_model *m, double *g, cudaStream_t st) {
@@ -1621,6 +1752,118 @@ exa_status exa_hess_csc(exa_model *m, const double *x, const double *y, double s
     return scatter_csc(m, m->sum_h, m->d_hperm, m->d_hbuf, vals_csc, m->nnzh_csc, m->nnzh, m->stream);
 }
 
+// exa_eval_all over member chunks: for every chunk, its evaluation kernel(s) on the model stream,
+// then, on side stream 0 once that chunk's kernel has finished, its Jacobian CSC, Hessian CSC,
+// gradient and constraint reductions over the chunk's own ranges of every output (members own
+// contiguous ranges of variables, rows, tiles and CSC positions).  The evaluation of the next chunk
+// overlaps these reductions.  The objective sum follows the last evaluation; the host copies of
+// f, g, c follow the last reduction.  Same kernels, same per-element arithmetic as one chunk.
+static exa_status eval_all_chunked(exa_model *m, const double *x, const double *y, double sigma, double *f, double *g,
+                                   double *c, double *jac_csc, double *hess_csc, double *const *host_fgc, ExaOut o,
+                                   Mode mode, Mode hmode, bool split, bool jdirect, bool hdirect, bool hcomp) {
+    if (!m->ev_fork) CR(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
+    for (int s = 0; s < 3; s++) {
+        if (!m->side[s]) CR(cudaStreamCreateWithFlags(&m->side[s], cudaStreamNonBlocking));
+        if (!m->ev_join[s]) CR(cudaEventCreateWithFlags(&m->ev_join[s], cudaEventDisableTiming));
+    }
+    for (int k = 0; k < m->nchunks; k++)
+        if (!m->ev_chunk[k]) CR(cudaEventCreateWithFlags(&m->ev_chunk[k], cudaEventDisableTiming));
+    cudaStream_t ps = m->side[0];
+    const bool jside = jac_csc && !jdirect && m->nnzj_csc;
+    const bool hside = (hcomp || (hess_csc && !hdirect)) && m->nnzh_csc;
+    ExaOut o1 = o, o2{};
+    if (split) {
+        o1.hess = nullptr;
+        o1.hcsc = nullptr;
+        o1.hcomp = nullptr;
+        o2.hess = o.hess;
+        o2.hcsc = o.hcsc;
+        o2.hmap = o.hmap;
+        o2.hcomp = o.hcomp;
+    }
+    const Mode m1 = split ? exa::M_FIRST : mode;
+    for (int k = 0; k < m->nchunks; k++) {
+        const int b0 = m->chunk_b[k], b1 = m->chunk_b[k + 1];
+        if (exa_status e = launch_eval(m, m1, x, y, sigma, split ? o1 : o, m->mb_tile[m1][b0], m->mb_tile[m1][b1]))
+            return e;
+        if (split)
+            if (exa_status e = launch_eval(m, hmode, x, y, sigma, o2, m->mb_tile[hmode][b0], m->mb_tile[hmode][b1]))
+                return e;
+        CR(cudaEventRecord(m->ev_chunk[k], m->stream));
+        CR(cudaStreamWaitEvent(ps, m->ev_chunk[k], 0));
+        if (jside) {
+            const int p0 = m->mb_jcsc[b0], p1 = m->mb_jcsc[b1];
+            if (m->nnzj_csc == m->nnzj) {
+                if (p1 > p0) {
+                    k_permute<<<grid_of(p1 - p0, 256 * EXA_ILP), 256, 0, ps>>>(m->d_jperm + p0, o.jac, jac_csc + p0,
+                                                                            (long long)(p1 - p0));
+                    CR(cudaGetLastError());
+                }
+            } else if (exa_status e = csc_sum_range(m, m->sum_j, o.jac, jac_csc, p0, p1, m->mb_jmulti[b0],
+                                                    m->mb_jmulti[b1], ps)) {
+                return e;
+            }
+        }
+        if (hside) {
+            const int p0 = m->mb_hcsc[b0], p1 = m->mb_hcsc[b1];
+            if (hcomp) {
+                if (exa_status e = csc_sum_range(m, m->sum_hc, m->d_hcbuf, hess_csc, p0, p1, m->mb_hcmulti[b0],
+                                                 m->mb_hcmulti[b1], ps))
+                    return e;
+            } else if (m->nnzh_csc == m->nnzh) {
+                if (p1 > p0) {
+                    k_permute<<<grid_of(p1 - p0, 256 * EXA_ILP), 256, 0, ps>>>(m->d_hperm + p0, o.hess, hess_csc + p0,
+                                                                            (long long)(p1 - p0));
+                    CR(cudaGetLastError());
+                }
+            } else if (exa_status e = csc_sum_range(m, m->sum_h, o.hess, hess_csc, p0, p1, m->mb_hmulti[b0],
+                                                    m->mb_hmulti[b1], ps)) {
+                return e;
+            }
+        }
+        if (g && m->nvar) {
+            const i64 v0 = m->xoff[b0], v1 = m->xoff[b1];
+            if (!m->grad_compact) {
+                if (v1 > v0) {
+                    k_seg_sum_warp<false><<<grid_of(v1 - v0, 256 * EXA_SEG_G), 256, 0, ps>>>(
+                        m->d_gptr + v0, m->d_gperm, m->d_gbuf, g + v0, nullptr, (int)(v1 - v0));
+                    CR(cudaGetLastError());
+                }
+            } else {
+                if (v1 > v0) CR(cudaMemsetAsync(g + v0, 0, sizeof(double) * (v1 - v0), ps));
+                const int s0 = m->mb_gseg[b0], s1 = m->mb_gseg[b1];
+                if (s1 > s0) {
+                    k_seg_sum_warp<true><<<grid_of(s1 - s0, 256 * EXA_SEG_G), 256, 0, ps>>>(
+                        m->d_gsegptr + s0, m->d_gperm, m->d_gbuf, g, m->d_gsegvar + s0, s1 - s0);
+                    CR(cudaGetLastError());
+                }
+            }
+        }
+        if (c) {
+            const int a0 = m->mb_arow[b0], a1 = m->mb_arow[b1];
+            if (a1 > a0) {
+                k_seg_sum_warp<true><<<grid_of(a1 - a0, 256 * EXA_SEG_G), 256, 0, ps>>>(
+                    m->d_aptr + a0, m->d_aperm, m->d_abuf, c, m->d_arows + a0, a1 - a0);
+                CR(cudaGetLastError());
+            }
+        }
+    }
+    if (f) {
+        k_obj_final<<<1, 256, 0, m->stream>>>(m->d_objpart, m->nobj[m1], f);
+        CR(cudaGetLastError());
+    }
+    CR(cudaEventRecord(m->ev_join[0], ps));
+    CR(cudaStreamWaitEvent(m->stream, m->ev_join[0], 0));
+    if (host_fgc) {
+        if (f && host_fgc[0]) CR(cudaMemcpyAsync(host_fgc[0], f, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+        if (g && host_fgc[1] && m->nvar)
+            CR(cudaMemcpyAsync(host_fgc[1], g, sizeof(double) * m->nvar, cudaMemcpyDeviceToHost, m->stream));
+        if (c && host_fgc[2] && m->ncon)
+            CR(cudaMemcpyAsync(host_fgc[2], c, sizeof(double) * m->ncon, cudaMemcpyDeviceToHost, m->stream));
+    }
+    return EXA_OK;
+}
+
 static exa_status eval_all_launches(exa_model *m, const double *x, const double *y, double sigma, double *f,
                                     double *g, double *c, double *jac, double *hess, double *jac_csc,
                                     double *hess_csc, double *const *host_fgc) {
@@ -1655,6 +1898,9 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
     const bool hcoo = o.hess != nullptr;
     Mode mode = !want_h ? exa::M_FIRST : (hcomp ? (hcoo ? exa::M_ALL_B : exa::M_ALL_C) : exa::M_ALL);
     const Mode hmode = hcomp ? (hcoo ? exa::M_HESS_B : exa::M_HESS_C) : exa::M_HESS;
+    if (m->nchunks > 1)
+        return eval_all_chunked(m, x, y, sigma, f, g, c, jac_csc, hess_csc, host_fgc, o, want_h ? mode : exa::M_FIRST,
+                                hmode, want_h && m->split_all, jdirect, hdirect, hcomp);
     if (want_h && m->split_all) {  // first order and second order as two kernels
         ExaOut o1 = o, o2{};
         o1.hess = nullptr;
@@ -1932,6 +2178,7 @@ exa_status exa_stat(const exa_model *m, const char *key, double *value) {
     else if (k == "eval_split") *value = m->split_all;
     else if (k == "csc_direct") *value = m->csc_direct;
     else if (k == "hess_compressed") *value = m->use_hcomp;
+    else if (k == "eval_chunks") *value = m->nchunks;
     else if (k == "grad_compact") *value = m->grad_compact;
     else if (k == "nnzh_compressed") *value = (double)m->nnzhc;
     else if (k == "eval_tiles") *value = m->ntiles[exa::M_ALL];

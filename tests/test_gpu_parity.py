@@ -276,6 +276,37 @@ def test_batch_matches_members():
     assert abs(f - fo) <= TOL * abs(fo)
 
 
+@pytest.mark.parametrize("chunks,extra", [(2, 0), (3, 0), (5, "split"), (4, "scatter"), (4, "no_hcomp"), (11, 0)])
+def test_member_chunks_match_one_pass(chunks, extra):
+    """exa_eval_all over member chunks (reductions of one chunk overlapping the evaluation of the
+    next) gives every output bit for bit as one pass over all members, in every kernel variant,
+    through device and host buffers; and the oracle's values."""
+    B = _B()
+    wls = synth.acopf_batch(11, seed=5, bmin=20, bmax=600)
+    flats = [w.flat for w in wls]
+    pts = [synth.acopf_point(w, i) for i, w in enumerate(wls)]
+    x = np.concatenate([p[0] for p in pts])
+    y = np.concatenate([p[1] for p in pts])
+    flags = B.EXA_FLAG_NO_TUNE
+    flags |= {"split": B.EXA_FLAG_SPLIT, "scatter": B.EXA_FLAG_CSC_SCATTER, "no_hcomp": B.EXA_FLAG_NO_HCOMP}.get(extra, 0)
+    m1 = B.exa_create_batch(flats, flags=flags, chunks=1)
+    mc = B.exa_create_batch(flats, flags=flags, chunks=chunks)
+    assert mc.stat("eval_chunks") == chunks
+    a = m1.eval_all(_t(x), _t(y), 0.8, csc=True)
+    b = mc.eval_all(_t(x), _t(y), 0.8, csc=True)
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+    host = {k: torch.empty(v.numel(), dtype=torch.float64).pin_memory() for k, v in a.items()}
+    mc.exa_eval_all_host(torch.as_tensor(x).pin_memory(), torch.as_tensor(y).pin_memory(), 0.8, **host)
+    for k in a:
+        assert torch.equal(host[k], a[k].cpu()), k
+    for i, (w, (xi, yi, si)) in enumerate(zip(wls, pts)):
+        o = oracle.Oracle(w.flat)
+        cs = slice(mc.coff[i], mc.coff[i + 1])
+        xs = slice(mc.xoff[i], mc.xoff[i + 1])
+        assert normwise(_np(b["c"])[cs], o.cons(xi)) <= TOL and normwise(_np(b["g"])[xs], o.grad(xi)) <= TOL
+
+
 # ------------------------------------------------------------------ full-size configurations
 @pytest.mark.slow
 def test_full_acopf_large():
