@@ -1752,6 +1752,15 @@ exa_status exa_hess_csc(exa_model *m, const double *x, const double *y, double s
     return scatter_csc(m, m->sum_h, m->d_hperm, m->d_hbuf, vals_csc, m->nnzh_csc, m->nnzh, m->stream);
 }
 
+// The side streams of exa_eval_all run at the highest priority, so that the reductions' CTAs are
+// scheduled as soon as an evaluation kernel's CTAs retire instead of queueing behind the next one.
+static cudaError_t side_stream(cudaStream_t *s) {
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e != cudaSuccess) return e;
+    return cudaStreamCreateWithPriority(s, cudaStreamNonBlocking, hi);
+}
+
 // exa_eval_all over member chunks: for every chunk, its evaluation kernel(s) on the model stream,
 // then, on side stream 0 once that chunk's kernel has finished, its Jacobian CSC, Hessian CSC,
 // gradient and constraint reductions over the chunk's own ranges of every output (members own
@@ -1763,7 +1772,7 @@ static exa_status eval_all_chunked(exa_model *m, const double *x, const double *
                                    Mode mode, Mode hmode, bool split, bool jdirect, bool hdirect, bool hcomp) {
     if (!m->ev_fork) CR(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
     for (int s = 0; s < 3; s++) {
-        if (!m->side[s]) CR(cudaStreamCreateWithFlags(&m->side[s], cudaStreamNonBlocking));
+        if (!m->side[s]) CR(side_stream(&m->side[s]));
         if (!m->ev_join[s]) CR(cudaEventCreateWithFlags(&m->ev_join[s], cudaEventDisableTiming));
     }
     for (int k = 0; k < m->nchunks; k++)
@@ -1926,7 +1935,7 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
     if (jside || hside || cside) {
         if (!m->ev_fork) CR(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
         for (int s = 0; s < 3; s++) {
-            if (!m->side[s]) CR(cudaStreamCreateWithFlags(&m->side[s], cudaStreamNonBlocking));
+            if (!m->side[s]) CR(side_stream(&m->side[s]));
             if (!m->ev_join[s]) CR(cudaEventCreateWithFlags(&m->ev_join[s], cudaEventDisableTiming));
             if (!m->ev_out[s]) CR(cudaEventCreateWithFlags(&m->ev_out[s], cudaEventDisableTiming));
         }
