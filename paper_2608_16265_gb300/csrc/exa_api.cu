@@ -973,12 +973,13 @@ exa_status autotune(exa_model *m) {
             }
         }
     }
-    // register budget: ask for 24 or 32 resident warps per SM through __launch_bounds__ (the
+    // register budget: ask for 20 to 32 resident warps per SM through __launch_bounds__ (the
     // compiler may spill); kept only when the fused kernel gets faster
-    int best_minb = 0;
-    for (int warps : {24, 32}) {
+    int best_minb = 0, last_minb = 0;
+    for (int warps : {20, 24, 28, 32}) {
         const int minb = warps * 32 / best_block;
-        if (minb < 1 || minb > 32) continue;
+        if (minb < 1 || minb > 32 || minb == last_minb) continue;
+        last_minb = minb;
         if (exa_status e = setup_kernels(m, best_block, minb)) return e;
         if (m->regs[exa::M_ALL] * best_block * minb > 65536 + 1) continue;  // bound not honoured
         int occ = 0;
