@@ -334,6 +334,7 @@ struct exa_model {
     };
     std::vector<GraphEntry> graphs;
     uint64_t graph_clock = 0;
+    int graph_kernels = 0;  // kernel launches in the most recently captured exa_eval_all graph
     bool use_graphs = true;
     cudaStream_t cap_stream = nullptr;
     // exa_eval_all runs its independent reductions (Jacobian CSC, Hessian CSC, the rest) on three
@@ -2022,6 +2023,19 @@ static exa_status eval_all_cached(exa_model *m, const double *x, const double *y
         return st;
     }
     if (ce != cudaSuccess) return fail(m, EXA_E_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
+    {  // kernels per replay of this graph (reported by exa_stat "graph_kernels")
+        size_t nn = 0;
+        if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn) {
+            std::vector<cudaGraphNode_t> nodes(nn);
+            int nk = 0;
+            if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+                for (cudaGraphNode_t nd : nodes) {
+                    cudaGraphNodeType ty;
+                    if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) nk++;
+                }
+            m->graph_kernels = nk;
+        }
+    }
     cudaGraphExec_t exec = nullptr;
     ce = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
@@ -2189,6 +2203,7 @@ exa_status exa_stat(const exa_model *m, const char *key, double *value) {
     else if (k == "csc_direct") *value = m->csc_direct;
     else if (k == "hess_compressed") *value = m->use_hcomp;
     else if (k == "eval_chunks") *value = m->nchunks;
+    else if (k == "graph_kernels") *value = m->graph_kernels;
     else if (k == "grad_compact") *value = m->grad_compact;
     else if (k == "nnzh_compressed") *value = (double)m->nnzhc;
     else if (k == "eval_tiles") *value = m->ntiles[exa::M_ALL];
