@@ -323,6 +323,7 @@ struct exa_model {
     int grid[exa::M_COUNT] = {};  // CTAs launched per kernel kind (<= ntiles: persistent tile loop)
     int persist = 0;              // persistent grid factor chosen by the tuner (0: one CTA per tile)
     int min_blocks = 0;           // launch-bounds minimum CTAs per SM chosen by the tuner
+    bool by_pattern = true;       // generated code emits each pattern's arithmetic next to its outputs
     bool split_all = false;       // exa_eval_all: first- and second-order kernels instead of one
     bool csc_direct = false;      // duplicate-free CSC written by the evaluation kernel (scatter)
     std::vector<ExaPM> h_pms;     // host copy of the group descriptors
@@ -866,6 +867,7 @@ exa_status setup_kernels(exa_model *m, int block, int min_blocks = 0) {
     cg.block = block;
     cg.min_blocks = min_blocks;
     cg.bounds_check = m->bounds_check;
+    cg.by_pattern = m->by_pattern;
     std::string gerr;
     std::string src = exa::generate_source(m->pats, m->groups, cg, &gerr);
     if (!gerr.empty()) return fail(m, EXA_E_INTERNAL, gerr);
@@ -1008,7 +1010,32 @@ exa_status autotune(exa_model *m) {
             best_minb = minb;
         }
     }
-    if (m->block != best_block || m->min_blocks != best_minb)
+    // emission order of the generated arithmetic: all of a group's arithmetic up front instead of
+    // per pattern next to its outputs, kept if faster
+    {
+        m->by_pattern = false;
+        if (exa_status e = setup_kernels(m, best_block, best_minb)) return e;
+        CR(S.get(&part, std::max(m->nobj[exa::M_ALL], 1)));
+        ExaOut o{};
+        o.obj_part = part;
+        o.c = m->d_cbuf;
+        o.abuf = m->d_abuf;
+        o.gbuf = m->d_gbuf;
+        o.jac = m->d_jbuf;
+        o.hess = m->d_hbuf;
+        if (exa_status e = apply_grid(m, best_factor)) return e;
+        if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
+        CR(cudaEventRecord(e0, m->stream));
+        for (int r = 0; r < 5; r++)
+            if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
+        CR(cudaEventRecord(e1, m->stream));
+        CR(cudaEventSynchronize(e1));
+        float ms = 0;
+        CR(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) best = ms;
+        else m->by_pattern = true;
+    }
+    if (m->block != best_block || m->min_blocks != best_minb || m->by_pattern)
         if (exa_status e = setup_kernels(m, best_block, best_minb)) return e;
     if (exa_status e = apply_grid(m, best_factor)) return e;
     m->tune_ms = best / 5.0;
@@ -1169,6 +1196,7 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     if (o.min_blocks < 0 || o.min_blocks > 32) return fail(m, EXA_E_INVALID, "min_blocks must be in [0, 32]");
     if (o.chunks < 0 || o.chunks > 16) return fail(m, EXA_E_INVALID, "chunks must be in [0, 16]");
     m->split_all = (o.flags & EXA_FLAG_SPLIT) != 0;
+    m->by_pattern = (o.flags & EXA_FLAG_UPFRONT) == 0;
     m->csc_direct = (o.flags & EXA_FLAG_CSC_SCATTER) != 0;
     if (nb < 1) return fail(m, EXA_E_INVALID, "empty batch");
     for (int b = 0; b < nb; b++) {
@@ -2167,6 +2195,8 @@ exa_status exa_compile_check(const exa_model_desc *desc, const exa_options *opt,
             cg.precision = o.precision;
             cg.block = o.block_threads ? o.block_threads : 128;
             cg.bounds_check = (o.flags & EXA_FLAG_BOUNDS_CHECK) != 0;
+            cg.by_pattern = (o.flags & EXA_FLAG_UPFRONT) == 0;
+            cg.min_blocks = o.min_blocks;
             std::string gerr;
             std::string src = exa::generate_source(tmp.pats, tmp.groups, cg, &gerr);
             if (!gerr.empty()) s = fail(&tmp, EXA_E_INTERNAL, gerr);
@@ -2203,6 +2233,7 @@ exa_status exa_stat(const exa_model *m, const char *key, double *value) {
     else if (k == "csc_direct") *value = m->csc_direct;
     else if (k == "hess_compressed") *value = m->use_hcomp;
     else if (k == "eval_chunks") *value = m->nchunks;
+    else if (k == "eval_upfront") *value = !m->by_pattern;
     else if (k == "graph_kernels") *value = m->graph_kernels;
     else if (k == "grad_compact") *value = m->grad_compact;
     else if (k == "nnzh_compressed") *value = (double)m->nnzhc;

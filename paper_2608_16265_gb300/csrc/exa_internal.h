@@ -127,6 +127,9 @@ struct CodegenOptions {
     int block = 128;
     int min_blocks = 0;  // __launch_bounds__ minimum resident CTAs per SM (0: not given)
     bool bounds_check = false;
+    // emit each pattern's arithmetic just before its outputs (shorter live ranges) instead of all
+    // of a group's arithmetic before the first output
+    bool by_pattern = true;
 };
 std::string generate_source(const std::vector<Pattern> &pats, const std::vector<Group> &groups,
                             const CodegenOptions &opt, std::string *err);

@@ -805,26 +805,35 @@ struct Emitter {
         return std::string(1, s.ikind) + (s.prec == PF ? "F" : "") + std::to_string(s.iid);
     }
 
-    // Emits the nodes the roots need, in creation (dependency) order; names every node.
-    void body(const std::vector<int> &roots, std::map<int, std::string> &name) {
-        std::vector<char> need(g.n.size(), 0);
-        std::function<void(int)> mark = [&](int i) {
-            if (need[i]) return;
-            need[i] = 1;
-            if (g.n[i].a >= 0) mark(g.n[i].a);
-            if (g.n[i].b >= 0) mark(g.n[i].b);
+    // Emits the nodes the roots need that `name` does not hold yet, in creation (dependency) order,
+    // and names them.  sin and cos of one argument are computed together: the pairs are found among
+    // the nodes `pair_roots` need (all of a function's roots), so a pair split between two calls
+    // is emitted whole at the first.
+    void body(const std::vector<int> &roots, std::map<int, std::string> &name,
+              const std::vector<int> *pair_roots = nullptr) {
+        auto marks = [&](const std::vector<int> &rs) {
+            std::vector<char> need(g.n.size(), 0);
+            std::function<void(int)> mark = [&](int i) {
+                if (need[i]) return;
+                need[i] = 1;
+                if (g.n[i].a >= 0) mark(g.n[i].a);
+                if (g.n[i].b >= 0) mark(g.n[i].b);
+            };
+            for (int r : rs) mark(r);
+            return need;
         };
-        for (int r : roots) mark(r);
+        const std::vector<char> need = marks(roots);
+        const std::vector<char> pneed = pair_roots ? marks(*pair_roots) : need;
         std::map<std::pair<int, int>, std::pair<int, int>> sc;  // (arg, reduced?) -> (sin+1, cos+1)
         for (size_t i = 0; i < g.n.size(); i++) {
-            if (!need[i]) continue;
+            if (!pneed[i]) continue;
             int op = g.n[i].op;
             bool red = op == S_SINR || op == S_COSR;
             if (op == S_SIN || op == S_SINR) sc[{g.n[i].a, red}].first = (int)i + 1;
             if (op == S_COS || op == S_COSR) sc[{g.n[i].a, red}].second = (int)i + 1;
         }
         for (size_t i = 0; i < g.n.size(); i++) {
-            if (!need[i]) continue;
+            if (!need[i] || name.count((int)i)) continue;
             const SN &s = g.n[i];
             const std::string t = "t" + std::to_string(i);
             const char *T = ty(s.prec);
@@ -852,13 +861,14 @@ struct Emitter {
                 auto pr = sc[{s.a, red}];
                 int si = pr.first - 1, ci = pr.second - 1;
                 if (red || (si >= 0 && ci >= 0)) {
-                    if ((int)i == (si >= 0 && ci >= 0 ? std::min(si, ci) : (int)i)) {
-                        std::string sn = si >= 0 ? "t" + std::to_string(si) : t + "_s";
-                        std::string cn = ci >= 0 ? "t" + std::to_string(ci) : t + "_c";
-                        os << "  " << T << " " << sn << ", " << cn << ";\n";
-                        if (red) os << "  exa_sincos_red(" << A() << ", &" << sn << ", &" << cn << ");\n";
-                        else os << "  " << (s.prec == PF ? "sincosf(" : "exa_sincos64(") << A() << ", &" << sn << ", &" << cn << ");\n";
-                    }
+                    // the whole pair at its first emitted member; the partner is named here too
+                    std::string sn = si >= 0 ? "t" + std::to_string(si) : t + "_s";
+                    std::string cn = ci >= 0 ? "t" + std::to_string(ci) : t + "_c";
+                    os << "  " << T << " " << sn << ", " << cn << ";\n";
+                    if (red) os << "  exa_sincos_red(" << A() << ", &" << sn << ", &" << cn << ");\n";
+                    else os << "  " << (s.prec == PF ? "sincosf(" : "exa_sincos64(") << A() << ", &" << sn << ", &" << cn << ");\n";
+                    if (si >= 0) name[si] = sn;
+                    if (ci >= 0) name[ci] = cn;
                 } else if (s.prec == PD) {  // one of the pair: the other result is dead code
                     os << "  double " << t << "_s, " << t << "_c;\n"
                        << "  exa_sincos64(" << A() << ", &" << t << "_s, &" << t << "_c);\n"
@@ -1052,7 +1062,7 @@ struct Emitter {
         for (int pid : fparams) os << "  const float PF" << pid << " = exa_d2f(P" << pid << ");\n";
         for (int c : ffconsts) os << "  const float CF" << c << " = exa_d2f(C" << c << ");\n";
         std::map<int, std::string> name;
-        body(roots, name);
+        if (!opt.by_pattern) body(roots, name);
         auto widen = [&](int r) { return mixed ? "exa_f2d(" + name.at(r) + ")" : name.at(r); };
         // csc/map: optional direct CSC output (a pure permutation of the COO slots); out/slot are
         // the COO array and the block's first slot
@@ -1085,6 +1095,13 @@ struct Emitter {
             const Want &w = want[pos];
             const std::string P = std::to_string(pos);
             const bool obj = p.kind == EXA_OBJ;
+            if (opt.by_pattern) {  // this pattern's arithmetic, right before its outputs
+                std::vector<int> mine;
+                if (w.val) mine.push_back(G.value);
+                if (w.grad) for (int sy : p.jsym) mine.push_back(G.grad[sy]);
+                for (int r : hroots[pos]) if (r >= 0) mine.push_back(r);
+                body(mine, name, &roots);
+            }
             if (w.val) {
                 const std::string v = widen(G.value);
                 if (obj) { os << "  objv " << (objw ? "+=" : "=") << " act ? " << v << " : 0.0;\n"; objw = true; }
