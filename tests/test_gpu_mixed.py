@@ -4,7 +4,7 @@ Pattern arithmetic runs in FP32; x, y and data are loaded in FP64, trig/exp argu
 and reduced in FP64, all cross-instance sums and the outputs are FP64.  Target: 1e-6 relative,
 normwise per output.  The objective scalar is the one output where cancellation between FP32 terms
 (sum of |terms| about ten times the sum) can push the error past 1e-6; its bound is 1e-5.
-The errors each case reaches are printed (pytest -s) and recorded in the design doc."""
+The errors each case reaches are printed (pytest -s)."""
 import numpy as np
 import pytest
 
