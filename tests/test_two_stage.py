@@ -117,3 +117,35 @@ def test_identical_scenarios_give_identical_blocks():
     hv = o.hess_coord(x, y, 1.0)
     for s in range(2, S + 1):
         assert np.array_equal(hv[vs[hr] == 1], hv[vs[hr] == s])
+
+
+def test_builder_rejects_misuse():
+    import pytest
+    m = TwoStageModel(3)
+    x = m.add_var(2)
+    with pytest.raises(ValueError):
+        m.add_par(np.zeros((2, 4)), scenario=True)  # last axis must be the scenario count
+    with pytest.raises(ValueError):
+        m.add_con(lambda d: x[0] + d.s, data=dict(s=np.zeros(2, np.int32)), scenario=True)  # reserved name
+    root = m.add_con(lambda d: x[d.k], n=2)
+    with pytest.raises(ValueError):
+        m.add_con_aug(root, lambda d: (0, x[1]), n=1, scenario=True)  # per-scenario term into a root block
+    with pytest.raises(ValueError):
+        TwoStageModel(0)
+    z = m.add_var(2, scenario=True)
+    with pytest.raises(IndexError):
+        z[0]  # the scenario index is required
+
+
+def test_root_and_scenario_augmentations_land_in_the_right_rows():
+    """A per-scenario augmentation term goes to its own scenario's row of a per-scenario block; the
+    oracle's constraint values show it row by row."""
+    m = TwoStageModel(3)
+    x = m.add_var(1)
+    z = m.add_var(2, scenario=True)
+    blk = m.add_con(lambda d: z[d.i, d.s], data=dict(i=np.arange(2, dtype=np.int32)), scenario=True)
+    m.add_con_aug(blk, lambda d: (1, 10.0 * x[0]), n=1, scenario=True)
+    flat = m.flat()
+    v = np.array([2.0, 1.0, 2.0, 3.0, 4.0, 5.0, 6.0])  # x, then z[:, 0], z[:, 1], z[:, 2]
+    c = oracle.Oracle(flat).cons(v)
+    assert np.array_equal(c, [1.0, 22.0, 3.0, 24.0, 5.0, 26.0])
