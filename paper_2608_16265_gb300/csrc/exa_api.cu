@@ -976,67 +976,53 @@ exa_status autotune(exa_model *m) {
             }
         }
     }
-    // register budget: ask for 20 to 32 resident warps per SM through __launch_bounds__ (the
-    // compiler may spill); kept only when the fused kernel gets faster
-    int best_minb = 0, last_minb = 0;
-    for (int warps : {20, 24, 28, 32}) {
-        const int minb = warps * 32 / best_block;
-        if (minb < 1 || minb > 32 || minb == last_minb) continue;
-        last_minb = minb;
-        if (exa_status e = setup_kernels(m, best_block, minb)) return e;
-        if (m->regs[exa::M_ALL] * best_block * minb > 65536 + 1) continue;  // bound not honoured
-        int occ = 0;
-        CR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)m->fn[exa::M_ALL], best_block, 0));
-        if (occ < minb) continue;
-        CR(S.get(&part, std::max(m->nobj[exa::M_ALL], 1)));
-        ExaOut o{};
-        o.obj_part = part;
-        o.c = m->d_cbuf;
-        o.abuf = m->d_abuf;
-        o.gbuf = m->d_gbuf;
-        o.jac = m->d_jbuf;
-        o.hess = m->d_hbuf;
-        if (exa_status e = apply_grid(m, best_factor)) return e;
-        if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
-        CR(cudaEventRecord(e0, m->stream));
-        for (int r = 0; r < 5; r++)
+    // register budget and emission order, searched together: launch bounds asking for 20 to 32
+    // resident warps per SM (the compiler may spill) or none, with each pattern's arithmetic next to
+    // its outputs or all of a group's arithmetic up front; a variant is kept only when the fused
+    // kernel gets faster (the uncapped per-pattern variant was timed above)
+    int best_minb = 0;
+    const bool init_order = m->by_pattern;
+    bool best_order = init_order;
+    for (int order = 0; order < 2; order++) {
+        const bool byp = order == 0;
+        int last_minb = -1;
+        for (int warps : {0, 20, 24, 28, 32}) {
+            const int minb = warps * 32 / best_block;
+            if (minb > 32 || minb == last_minb || (warps && minb < 1)) continue;
+            last_minb = minb;
+            if (byp == init_order && minb == 0) continue;  // the variant timed by the search above
+            m->by_pattern = byp;
+            if (exa_status e = setup_kernels(m, best_block, minb)) return e;
+            if (minb && m->regs[exa::M_ALL] * best_block * minb > 65536 + 1) continue;  // bound not honoured
+            int occ = 0;
+            CR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)m->fn[exa::M_ALL], best_block, 0));
+            if (occ < minb) continue;
+            CR(S.get(&part, std::max(m->nobj[exa::M_ALL], 1)));
+            ExaOut o{};
+            o.obj_part = part;
+            o.c = m->d_cbuf;
+            o.abuf = m->d_abuf;
+            o.gbuf = m->d_gbuf;
+            o.jac = m->d_jbuf;
+            o.hess = m->d_hbuf;
+            if (exa_status e = apply_grid(m, best_factor)) return e;
             if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
-        CR(cudaEventRecord(e1, m->stream));
-        CR(cudaEventSynchronize(e1));
-        float ms = 0;
-        CR(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-            best = ms;
-            best_minb = minb;
+            CR(cudaEventRecord(e0, m->stream));
+            for (int r = 0; r < 5; r++)
+                if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
+            CR(cudaEventRecord(e1, m->stream));
+            CR(cudaEventSynchronize(e1));
+            float ms = 0;
+            CR(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                best_minb = minb;
+                best_order = byp;
+            }
         }
     }
-    // emission order of the generated arithmetic: all of a group's arithmetic up front instead of
-    // per pattern next to its outputs, kept if faster
-    {
-        m->by_pattern = false;
-        if (exa_status e = setup_kernels(m, best_block, best_minb)) return e;
-        CR(S.get(&part, std::max(m->nobj[exa::M_ALL], 1)));
-        ExaOut o{};
-        o.obj_part = part;
-        o.c = m->d_cbuf;
-        o.abuf = m->d_abuf;
-        o.gbuf = m->d_gbuf;
-        o.jac = m->d_jbuf;
-        o.hess = m->d_hbuf;
-        if (exa_status e = apply_grid(m, best_factor)) return e;
-        if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
-        CR(cudaEventRecord(e0, m->stream));
-        for (int r = 0; r < 5; r++)
-            if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
-        CR(cudaEventRecord(e1, m->stream));
-        CR(cudaEventSynchronize(e1));
-        float ms = 0;
-        CR(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) best = ms;
-        else m->by_pattern = true;
-    }
-    if (m->block != best_block || m->min_blocks != best_minb || m->by_pattern)
-        if (exa_status e = setup_kernels(m, best_block, best_minb)) return e;
+    m->by_pattern = best_order;
+    if (exa_status e = setup_kernels(m, best_block, best_minb)) return e;
     if (exa_status e = apply_grid(m, best_factor)) return e;
     m->tune_ms = best / 5.0;
     // exa_eval_all with every output: one kernel or first/second order split, CSC by a separate

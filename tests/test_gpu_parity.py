@@ -119,16 +119,18 @@ def test_autotuned_model():
     assert m.stat("eval_block") in (64, 128, 256) and m.stat("tune_ms") > 0
 
 
-@pytest.mark.parametrize("choice", ["split", "scatter", "no_hcomp", "split+scatter+no_hcomp"])
+@pytest.mark.parametrize("choice", ["split", "scatter", "no_hcomp", "upfront", "split+scatter+no_hcomp+upfront"])
 def test_pinned_launch_choices(choice):
     """Every choice the tuner makes, fixed through the creation options instead, gives the same
     results: first/second order split, the Jacobian CSC scattered by the evaluation kernel, the
-    Hessian CSC summed from the COO slots, and a register cap through min_blocks."""
+    Hessian CSC summed from the COO slots, the up-front emission order, and a register cap through
+    min_blocks."""
     B = _B()
     flags = B.EXA_FLAG_NO_TUNE
     flags |= B.EXA_FLAG_SPLIT if "split" in choice else 0
     flags |= B.EXA_FLAG_CSC_SCATTER if "scatter" in choice else 0
     flags |= B.EXA_FLAG_NO_HCOMP if "no_hcomp" in choice else 0
+    flags |= B.EXA_FLAG_UPFRONT if "upfront" in choice else 0
     wl = synth.acopf(200, 300, 40, seed=8)
     x, y, s = synth.acopf_point(wl, 2)
     m, _ = check_model(wl.flat, x, y, s, flags=flags, block=64, min_blocks=12)
@@ -136,6 +138,7 @@ def test_pinned_launch_choices(choice):
     assert m.stat("csc_direct") == ("scatter" in choice)
     assert m.stat("hess_compressed") == ("no_hcomp" not in choice)
     assert m.stat("eval_min_blocks") == 12 and m.stat("eval_block") == 64
+    assert m.stat("eval_upfront") == ("upfront" in choice)
 
 
 def test_tuned_options_reproduce_the_model():
