@@ -19,6 +19,7 @@
 #include <set>
 #include <memory>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -478,6 +479,31 @@ exa_status nvrtc_compile(exa_model *m, const std::string &src, std::vector<char>
 // pattern trees and options (batch members, or the same model created twice) compile once.
 std::mutex g_cubin_mu;
 std::map<std::string, std::shared_ptr<std::vector<char>>> g_cubins;
+
+// Compiles the kernels of several code-generator variants into the module cache at once, one
+// thread per variant (NVRTC is thread-safe): the tuner then loads each variant from the cache.
+// Failures are left for the variant's own compile to report.
+void precompile(const exa_model *m, const std::vector<exa::CodegenOptions> &variants) {
+    std::vector<std::string> srcs;
+    for (const exa::CodegenOptions &cg : variants) {
+        std::string gerr;
+        std::string src = exa::generate_source(m->pats, m->groups, cg, &gerr);
+        if (!gerr.empty()) continue;
+        std::lock_guard<std::mutex> lk(g_cubin_mu);
+        if (!g_cubins.count(src)) srcs.push_back(std::move(src));
+    }
+    std::vector<std::thread> th;
+    for (const std::string &src : srcs)
+        th.emplace_back([&src]() {
+            exa_model scratch;
+            auto cubin = std::make_shared<std::vector<char>>();
+            if (nvrtc_compile(&scratch, src, *cubin) != EXA_OK) return;
+            std::lock_guard<std::mutex> lk(g_cubin_mu);
+            if (g_cubins.size() > 64) g_cubins.clear();
+            g_cubins[src] = cubin;
+        });
+    for (std::thread &t : th) t.join();
+}
 
 exa_status compile(exa_model *m, const std::string &src) {
     auto t0 = std::chrono::steady_clock::now();
@@ -948,6 +974,20 @@ exa_status autotune(exa_model *m) {
     double best = 1e30;
     int best_block = m->block, best_factor = 0;
     const int blocks[] = {64, 128, 256};
+    auto variant = [&](int block, int minb, bool byp) {
+        exa::CodegenOptions cg;
+        cg.precision = m->precision;
+        cg.block = block;
+        cg.min_blocks = minb;
+        cg.bounds_check = m->bounds_check;
+        cg.by_pattern = byp;
+        return cg;
+    };
+    {
+        std::vector<exa::CodegenOptions> v;
+        for (int B : blocks) v.push_back(variant(B, 0, m->by_pattern));
+        precompile(m, v);
+    }
     for (int B : blocks) {
         if (exa_status e = setup_kernels(m, B)) return e;
         CR(S.get(&part, std::max(m->nobj[exa::M_ALL], 1)));
@@ -983,6 +1023,15 @@ exa_status autotune(exa_model *m) {
     int best_minb = 0;
     const bool init_order = m->by_pattern;
     bool best_order = init_order;
+    {
+        std::vector<exa::CodegenOptions> v;
+        for (int order = 0; order < 2; order++)
+            for (int warps : {0, 20, 24, 28, 32}) {
+                const int minb = warps * 32 / best_block;
+                if (minb <= 32 && (warps == 0 || minb >= 1)) v.push_back(variant(best_block, minb, order == 0));
+            }
+        precompile(m, v);
+    }
     for (int order = 0; order < 2; order++) {
         const bool byp = order == 0;
         int last_minb = -1;
