@@ -954,9 +954,14 @@ exa_status apply_grid(exa_model *m, int factor) {
     return EXA_OK;
 }
 
-// Launch-shape autotuner: times the fused evaluation kernel (everything, at x = 1, y = 1) for
-// 64 / 128 / 256 threads per CTA and for one CTA per tile versus persistent grids of 1, 2 and 4
-// waves of resident CTAs; keeps the fastest.  Models too small to fill the GPU are not tuned.
+// Launch-shape autotuner, in three stages, each keeping the fastest variant: (1) the fused
+// evaluation kernel (everything, at x = 1, y = 1) for 64 / 128 / 256 threads per CTA and one CTA per
+// tile versus persistent grids of 1, 2 and 4 waves of resident CTAs; (2) for that shape, launch
+// bounds for 20 to 32 resident warps per SM or none, with either emission order of the generated
+// arithmetic; (3) whole exa_eval_all steps with every output: member chunks, compressed or COO
+// Hessian sums for the CSC, fused or split first/second order, CSC gathered or scattered.  The
+// code-generator variants of a stage are compiled in parallel before they are timed.  Models too
+// small to fill the GPU are not tuned.
 exa_status autotune(exa_model *m) {
     int sms = 0;
     CR(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
