@@ -21,12 +21,15 @@
  * Conventions for every call below:
  *   - Indices are 0-based (the paper's Julia code is 1-based).
  *   - Array arguments of the evaluation and structure calls are DEVICE pointers on the model's
- *     device, owned by the caller, sized from exa_dims().  Descriptor arguments of exa_create
+ *     device, owned by the caller, sized from exa_dims() (exa_eval_all_host also takes host
+ *     pointers).  Descriptor arguments of exa_create
  *     are HOST pointers; the library copies what it needs before returning.
  *   - Evaluation calls are stream-ordered and asynchronous on the model's stream (default: the
  *     legacy default stream; see exa_set_stream).  They never synchronize the device and never
- *     allocate device memory.  Inputs must stay valid and unmodified until the enqueued work has
- *     run; outputs are valid once it has run.
+ *     allocate device memory, with one exception: exa_eval_all_host, the variant for host
+ *     arrays, allocates its staging buffers on first use and returns after synchronizing the
+ *     stream.  Inputs must stay valid and unmodified until the enqueued work has run; outputs
+ *     are valid once it has run.
  *   - Results do not depend on the launch configuration except through floating-point
  *     summation order (the duplicate sums and the objective reduction are deterministic for a
  *     fixed configuration).
