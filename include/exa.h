@@ -163,8 +163,9 @@ enum {
     EXA_FLAG_NO_HCOMP = 64,    /* the Hessian CSC is summed from the COO slots instead of from the
                                   per-instance sums of the slots of a fused group that share an entry */
     EXA_FLAG_UPFRONT = 128     /* the generated code computes all of a fused group's arithmetic
-                                  before its first output instead of each pattern's arithmetic right
-                                  before that pattern's outputs (fewer live registers, the default) */
+                                  before its first output, instead of each pattern's arithmetic right
+                                  before that pattern's outputs (the default, which keeps fewer
+                                  values live) */
 };
 
 /* Validate the descriptor (Sec. 3.4 SIMDFunction), lower every pattern to generated device
