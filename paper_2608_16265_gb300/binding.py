@@ -196,11 +196,12 @@ def exa_create_batch(flats: Sequence[ir.FlatModel], precision: int = EXA_FP64, b
     return Model(h, len(descs), device)
 
 
-def exa_compile_check(flat: ir.FlatModel, precision: int = EXA_FP64, block: int = 0, flags: int = 0) -> None:
+def exa_compile_check(flat: ir.FlatModel, precision: int = EXA_FP64, block: int = 0, flags: int = 0,
+                      min_blocks: int = 0) -> None:
     lib = load()
     d = _Desc(flat)
     buf = C.create_string_buffer(8192)
-    rc = lib.exa_compile_check(C.byref(d.desc), C.byref(_opts(precision, block, flags, 0)), buf, 8192)
+    rc = lib.exa_compile_check(C.byref(d.desc), C.byref(_opts(precision, block, flags, 0, 0, min_blocks)), buf, 8192)
     if rc != EXA_OK:
         raise ExaError(rc, buf.value.decode(errors="replace"))
 

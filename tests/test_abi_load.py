@@ -39,6 +39,19 @@ def test_generated_kernels_compile(name, flat):
     binding.exa_compile_check(flat())
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("upfront", [False, True])
+def test_generated_variants_compile(precision, upfront):
+    """Every code-generator variant the tuner can pick compiles for sm_103a: both precisions, both
+    emission orders, with and without a launch-bounds register cap, on the two-stage ACOPF (all
+    pattern kinds, scenario-indexed variables, per-scenario parameters)."""
+    from paper_2608_16265_gb300 import binding
+    flat = synth.two_stage_acopf(5, 7, 2, 3, seed=1).flat
+    flags = binding.EXA_FLAG_UPFRONT if upfront else 0
+    binding.exa_compile_check(flat, precision=precision, block=128, flags=flags)
+    binding.exa_compile_check(flat, precision=precision, block=64, flags=flags, min_blocks=16)
+
+
 def test_compile_check_rejects_bad_ir():
     from paper_2608_16265_gb300 import binding, ir
     m = ir.Model()
