@@ -237,7 +237,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": steps, "warmup": warm, "ms_per_step": 1e3 * float(np.mean(times)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "members": 256, "sample": "bounded"},
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.members == 256 else f"acopf_batch_{args.members}",
+                   "members": args.members, "sample": "bounded"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"per step: batch members in seeded order until {per_step:.1f} s of "
                                    f"single-thread oracle work (obj, grad, cons, jac, hess, jac_csc, hess_csc)",
