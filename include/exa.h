@@ -288,7 +288,9 @@ exa_status exa_hprod(exa_model *m, const double *x, const double *y, double sigm
 exa_status exa_check_status(exa_model *m);
 
 /* Validate the descriptor, generate the kernels and compile them with NVRTC for sm_103a without
- * touching any device (usable on a host without a GPU).  On failure the message (NVRTC log
+ * touching any device (usable on a host without a GPU).  With the environment variable
+ * EXA_DUMP_SOURCE set to a file name, this call and exa_create write the generated CUDA source
+ * there (for reading the code a model compiles to).  On failure the message (NVRTC log
  * included) is copied, NUL-terminated, into log[0 .. loglen-1] when log is not NULL. */
 exa_status exa_compile_check(const exa_model_desc *desc, const exa_options *opt, char *log,
                              size_t loglen);
