@@ -391,7 +391,9 @@ def run_exa(args):
         extras["jtprod_ms"] = timed(lambda: m.exa_jtprod(xt, w, out_v), 5)
         extras["hprod_ms"] = timed(lambda: m.exa_hprod(xt, yt, sigma, v, out_v), 5)
         # 256 per-instance models launched one after another (the unbatched form)
-        singles = [B.exa_create(fl, precision=prec, device=local) for fl in flats]
+        # (each with the batch's tuned launch shape, fixed, so that 256 creations stay quick)
+        tuned = m.tuned_options()
+        singles = [B.exa_create(fl, precision=prec, device=local, **tuned) for fl in flats]
         xs = [torch.as_tensor(p[0], device=dev) for p in pts]
         ys = [torch.as_tensor(p[1], device=dev) for p in pts]
         outs = [(E(s.nnzj), E(s.nnzh)) for s in singles]
