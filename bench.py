@@ -89,11 +89,24 @@ def whole_job_rate(nnz_per_rank: int, world_size: int, ms_max: float) -> float:
     return world_size * nnz_per_rank / (ms_max * 1e-3)
 
 
-# GB300 FP64 pipe: 2 FP64 operations (DFMA, DMUL or DADD) per clock per SM (1/64 of the FP32 rate;
-# it is what ncu's fp64 pipe utilisation counts against), 152 SMs at the 2070 MHz maximum clock:
-# 629 G FP64 instructions/s, i.e. 1.26 TFLOP/s counting an FMA as 2 flops (the nominal 1.25).
-FP64_INST_PEAK_G = 2 * 152 * 2.070
-FP64_PEAK_GFLOPS = 2 * FP64_INST_PEAK_G
+_T0 = time.perf_counter()
+
+
+def phase(msg: str):
+    """Progress of the run on stderr (the JSON line goes to stdout)."""
+    print(f"[bench {time.perf_counter() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
+
+
+def measure_fp64_peak(B, local: int):
+    """Measured FP64 FMA rate of the device (the DFMA probe of include/exa_probe.h), with the SM
+    clock sampled while it runs.  DMUL and DADD issue on the same pipe at the same rate, so the
+    rate bounds FP64 instructions of every kind."""
+    clk = ClockSampler(local)
+    clk.start()
+    r = B.exa_probe_fp64_fma(local, 400.0)
+    clocks = clk.stop()
+    return {"g_inst_per_s": r["dfma_per_s"] / 1e9, "ms": r["ms"], "sms": r["sms"], "clocks": clocks,
+            "derived_g_inst_per_s": 2 * r["sms"] * (clocks.get("sm_max_mhz") or 2070.0) / 1e3}
 
 
 def csrc_digest() -> str:
@@ -251,6 +264,158 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+def pattern_counts(flats):
+    """Augmentation terms and objective gradient slots are written once per instance of those
+    pattern kinds (their sizes enter the algorithmic bytes)."""
+    naug = sum(p.n_inst for fl in flats for p in fl.patterns if p.kind == 2)
+    nobj = sum(p.n_inst for fl in flats for p in fl.patterns if p.kind == 0)
+    return naug, nobj
+
+
+def make_timer(torch):
+    def timed(fn, k):
+        """Milliseconds per call of fn over k calls, CUDA events on torch's current stream (the
+        stream the binding points the library at), synchronized on both sides."""
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+    return timed
+
+
+def calls_for(timed, fn, target_ms=200.0, lo=5, hi=2000):
+    """Calls that take about target_ms, from a short probe."""
+    probe = timed(fn, 3)
+    return int(min(hi, max(lo, target_ms / max(probe, 1e-3))))
+
+
+FAMILIES = (
+    # name, generator, point function, number of points (the configurations of the benchmark
+    # workload family table: Rosenbrock-type at 10 points, ACOPF 500 and 30000 buses, PDE 1000^2)
+    ("rosenbrock_n1000", lambda s: s.rosenbrock(1000), "rosenbrock_point", 10),
+    ("acopf_b500_l700_g100", lambda s: s.acopf(500, 700, 100, seed=1), "acopf_point", 1),
+    ("acopf_b30000_l45000_g5000", lambda s: s.acopf(30000, 45000, 5000, seed=2), "acopf_point", 1),
+    ("pde_n1000", lambda s: s.pde(1000), "pde_point", 1),
+)
+
+SWEEP = (
+    # larger members of the same families, whose working sets exceed the 129 MB L2 many times over
+    ("pde_n2000", lambda s: s.pde(2000), "pde_point"),
+    ("pde_n3000", lambda s: s.pde(3000), "pde_point"),
+    ("pde_n4000", lambda s: s.pde(4000), "pde_point"),
+    ("acopf_b100000_l150000_g16666", lambda s: s.acopf(100000, 150000, 16666, seed=3), "acopf_point"),
+    ("acopf_b300000_l450000_g50000", lambda s: s.acopf(300000, 450000, 50000, seed=4), "acopf_point"),
+)
+
+L2_BYTES = 129e6
+
+
+def normwise(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    nb = float(np.linalg.norm(b))
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def measure_model(B, torch, timed, flat, pts, precision, local, peak_hbm, ref=None):
+    """One model of one family in one precision: full step (every output: f, g, c, COO, CSC), the
+    evaluation kernel alone (J and H COO), the paper's two callbacks (jac_coord + hess_coord), the
+    kernel's algorithmic bytes and HBM fraction; with `ref` (oracle outputs at point 0), the
+    normwise error of every output."""
+    dev = torch.device(f"cuda:{local}")
+    t0 = time.perf_counter()
+    m = B.exa_create(flat, precision=precision, device=local)
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - t0
+    E = lambda n: torch.empty(max(int(n), 1), dtype=torch.float64, device=dev)
+    outs = dict(f=E(1), g=E(m.nvar), c=E(m.ncon), jac=E(m.nnzj), hess=E(m.nnzh), jac_csc=E(m.nnzj_csc),
+                hess_csc=E(m.nnzh_csc))
+    xb, yb = E(m.nvar), E(m.ncon)
+    step_ms, kern_ms, jh_ms, errs = [], [], [], None
+    for i, (x, y, s) in enumerate(pts):  # the same buffers for every point: one cached graph each
+        xb.copy_(torch.as_tensor(x))
+        if len(y):
+            yb.copy_(torch.as_tensor(y))
+        step = lambda: m.exa_eval_all(xb, yb, s, **outs)
+        kern = lambda: m.exa_eval_all(xb, yb, s, jac=outs["jac"], hess=outs["hess"])
+        jh = lambda: (m.exa_jac_coord(xb, outs["jac"]), m.exa_hess_coord(xb, yb, s, outs["hess"]))
+        step()
+        if i == 0 and ref is not None:
+            torch.cuda.synchronize()
+            got = {k: v.cpu().numpy()[:n] for (k, v), n in
+                   zip(outs.items(), (1, m.nvar, m.ncon, m.nnzj, m.nnzh, m.nnzj_csc, m.nnzh_csc))}
+            errs = {k: (abs(float(got["f"][0]) - ref["f"]) / max(abs(ref["f"]), 1e-300) if k == "f"
+                        else normwise(got[k], ref[k])) for k in got}
+        step_ms.append(timed(step, calls_for(timed, step)))
+        kern()
+        kern_ms.append(timed(kern, calls_for(timed, kern)))
+        jh_ms.append(timed(jh, calls_for(timed, jh)))
+    naug, nobj = pattern_counts([flat])
+    nbytes = algorithmic_bytes([flat], m.nnzj, m.nnzh, m.nvar, m.ncon, naug, nobj)
+    nnz = m.nnzj + m.nnzh
+    st, kt, jt = float(np.mean(step_ms)), float(np.mean(kern_ms)), float(np.mean(jh_ms))
+    rec = {"nnz": nnz, "step_ms": st, "step_nnz_per_s": nnz / (st * 1e-3), "kernel_ms": kt,
+           "kernel_nnz_per_s": nnz / (kt * 1e-3), "jac_plus_hess_coord_ms": jt,
+           "algorithmic_bytes": nbytes, "kernel_gbs": nbytes / (kt * 1e-3) / 1e9,
+           "kernel_hbm_frac": nbytes / (kt * 1e-3) / 1e9 / peak_hbm,
+           "l2_resident": nbytes < L2_BYTES, "create_s": create_s, "tuned_options": m.tuned_options(),
+           "eval_regs": m.stat("eval_regs")}
+    if errs is not None:
+        rec["rel_err_vs_oracle"] = errs
+    m.destroy()
+    return rec
+
+
+def family_configs(B, torch, timed, local, peak_hbm, cpu_budget, sweep=False):
+    """The benchmark workload families at 1 GPU, each in FP64 and mixed precision, with the
+    single-thread CPU oracle timed on the same inputs (a bounded number of points)."""
+    import oracle
+    import synth
+    res = {}
+    for name, mk, ptf, npts in FAMILIES:
+        phase(f"config {name}")
+        wl = mk(synth)
+        pts = [getattr(synth, ptf)(wl, s) for s in range(npts)]
+        o = oracle.Oracle(wl.flat)
+        t, n, ref = 0.0, 0, None
+        while True:  # one step's callbacks per point, points in turn, until the budget
+            x, y, s = pts[n % npts]
+            t0 = time.perf_counter()
+            r = dict(f=o.obj(x), g=o.grad(x), c=o.cons(x), jac=o.jac_coord(x), hess=o.hess_coord(x, y, s),
+                     jac_csc=o.jac_csc(x), hess_csc=o.hess_csc(x, y, s))
+            t += time.perf_counter() - t0
+            ref = ref or r
+            n += 1
+            if t >= cpu_budget or n >= 1000:
+                break
+        nnz = o.nnzj + o.nnzh
+        rec = {"nvar": o.nvar, "ncon": o.ncon, "nnzj": o.nnzj, "nnzh": o.nnzh, "nnzj_csc": o.nnzj_csc,
+               "nnzh_csc": o.nnzh_csc, "points": npts,
+               "oracle": {"nnz_per_s": nnz * n / t, "ms_per_step": 1e3 * t / n, "steps": n, "cores": 1,
+                          "kind": "oracle"}}
+        del o
+        for tag, prec in (("fp64", B.EXA_FP64), ("mixed", B.EXA_MIXED_FP32)):
+            rec[tag] = measure_model(B, torch, timed, wl.flat, pts, prec, local, peak_hbm, ref)
+            rec[tag]["vs_oracle"] = rec[tag]["step_nnz_per_s"] / rec["oracle"]["nnz_per_s"]
+        rec["note"] = ("working set below the 129 MB L2: the step is L2-resident and bound by launch "
+                       "latency, not HBM" if rec["fp64"]["l2_resident"] else "working set exceeds the L2")
+        res[name] = rec
+    sw = {}
+    if sweep:
+        for name, mk, ptf in SWEEP:
+            phase(f"sweep {name}")
+            wl = mk(synth)
+            pts = [getattr(synth, ptf)(wl, 0)]
+            sw[name] = {tag: measure_model(B, torch, timed, wl.flat, pts, prec, local, peak_hbm)
+                        for tag, prec in (("fp64", B.EXA_FP64), ("mixed", B.EXA_MIXED_FP32))}
+            del wl
+    return res, sw
+
+
 def run_exa(args):
     import torch
     ws, rank, local = dist_env()
@@ -262,11 +427,13 @@ def run_exa(args):
         pg = dist
     from paper_2608_16265_gb300 import binding as B
 
+    phase("generate batch")
     prec = B.EXA_MIXED_FP32 if args.precision == "mixed" else B.EXA_FP64
     t0 = time.perf_counter()
     wls, pts = make_batch(rank, args.members)
     flats = [w.flat for w in wls]
     t_gen = time.perf_counter() - t0
+    phase("create batch model")
     t0 = time.perf_counter()
     pin = {}
     if args.pin:
@@ -286,20 +453,10 @@ def run_exa(args):
     E = lambda n: torch.empty(n, dtype=torch.float64, device=dev)
     f, g, c = E(1), E(m.nvar), E(m.ncon)
     jac, hess, jcsc, hcsc = E(m.nnzj), E(m.nnzh), E(m.nnzj_csc), E(m.nnzh_csc)
+    timed = make_timer(torch)
 
     def step():
         m.exa_eval_all(xt, yt, sigma, f=f, g=g, c=c, jac=jac, hess=hess, jac_csc=jcsc, hess_csc=hcsc)
-
-    def timed(fn, k):
-        stream = torch.cuda.current_stream()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(k):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / k  # ms
 
     def barrier():
         if pg is not None:
@@ -325,6 +482,7 @@ def run_exa(args):
                               "kernel_ms": kms, "precision": args.precision, "members": args.members,
                               "tuned_options": ",".join(str(v) for v in m.tuned_options().values())}))
         return
+    phase("warm-up")
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -332,6 +490,7 @@ def run_exa(args):
         probe = timed(step, 3)
         args.steps = int(min(5000, max(20, 2000.0 / max(probe, 1e-3))))
         args.steps = int(reduce_max(args.steps, pg, dev))
+    phase(f"timed region: {args.steps} steps")
     barrier()
     clk = ClockSampler(local)
     clk.start()
@@ -344,31 +503,41 @@ def run_exa(args):
     nnz_rank = m.nnzj + m.nnzh
     value = whole_job_rate(nnz_rank, ws, ms)
 
+    phase("dominant kernel and callbacks")
     # dominant kernel alone: the generated evaluation kernel writing J and H (no reductions)
     kern_ms = timed(lambda: m.exa_eval_all(xt, yt, sigma, jac=jac, hess=hess), max(5, min(args.steps, 200)))
     # Jacobian + Hessian callbacks alone (exa_jac_coord + exa_hess_coord)
     jh_ms = timed(lambda: (m.exa_jac_coord(xt, jac), m.exa_hess_coord(xt, yt, sigma, hess)), max(5, min(args.steps, 200)))
-    nbytes = algorithmic_bytes(flats, m.nnzj, m.nnzh, m.nvar, m.ncon,
-                               sum(p.n_inst for fl in flats for p in fl.patterns if p.kind == 2),
-                               sum(p.n_inst for fl in flats for p in fl.patterns if p.kind == 0))
+    naug, nobj = pattern_counts(flats)
+    nbytes = algorithmic_bytes(flats, m.nnzj, m.nnzh, m.nvar, m.ncon, naug, nobj)
+    # bytes of the whole step's outputs beyond the kernel's: the dense gradient, the CSC values
+    # (each written once) and the objective
+    step_bytes = nbytes + 8 * (m.nvar + m.nnzj_csc + m.nnzh_csc + 1)
     peak, peak_kind = read_peaks()
     achieved = nbytes / (kern_ms * 1e-3) / 1e9
     ctr = read_counters(args.precision)
     traffic = int(ctr["dram_bytes_per_nnz"] * nnz_rank) if ctr else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_source": peak_kind, "kernel": "exa_all (generated eval kernel)",
-                "algorithmic_bytes": nbytes, "kernel_ms": kern_ms}
+                "traffic": traffic, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                "kernel": "exa_all (generated eval kernel)", "algorithmic_bytes": nbytes, "kernel_ms": kern_ms,
+                "step_algorithmic_bytes": step_bytes,
+                "step_hbm_frac": step_bytes / (ms * 1e-3) / 1e9 / peak}
+    phase("FP64 peak probe")
+    fp64 = measure_fp64_peak(B, local)
     if ctr and ctr.get("fp64_inst_per_nnz"):
         # the FP64 pipe bounds this kernel when its FP64 instruction rate is the larger fraction of
         # its peak (DMUL and DADD take a pipe slot like DFMA, so instructions, not flops, are counted)
+        pk = fp64["g_inst_per_s"]
         ginst = ctr["fp64_inst_per_nnz"] * nnz_rank / (kern_ms * 1e-3) / 1e9
         gflops = ctr["fp64_flops_per_nnz"] * nnz_rank / (kern_ms * 1e-3) / 1e9
-        alu = {"bound": "alu", "achieved": ginst, "peak": FP64_INST_PEAK_G, "unit": "G FP64 instructions/s",
-               "frac": ginst / FP64_INST_PEAK_G, "traffic": traffic,
-               "peak_source": "derived: 2 FP64 ops/clk/SM x 152 SMs x 2070 MHz",
+        alu = {"bound": "alu", "achieved": ginst, "peak": pk, "unit": "G FP64 instructions/s",
+               "frac": ginst / pk, "traffic": traffic,
+               "peak_source": "measured: DFMA probe (include/exa_probe.h) in this run",
                "kernel": roofline["kernel"], "fp64_inst": int(ctr["fp64_inst_per_nnz"] * nnz_rank),
-               "fp64_gflops": gflops, "fp64_gflops_frac": gflops / FP64_PEAK_GFLOPS,
-               "kernel_ms": kern_ms, "hbm_frac": roofline["frac"], "hbm_achieved_gbs": roofline["achieved"]}
+               "fp64_gflops": gflops, "fp64_gflops_frac": gflops / (2 * pk),
+               "kernel_ms": kern_ms, "hbm_frac": roofline["frac"], "hbm_achieved_gbs": roofline["achieved"],
+               "algorithmic_bytes": nbytes, "step_algorithmic_bytes": step_bytes,
+               "step_hbm_frac": roofline["step_hbm_frac"]}
         if alu["frac"] > roofline["frac"]:
             roofline = alu
 
@@ -382,8 +551,9 @@ def run_exa(args):
               "eval_chunks": m.stat("eval_chunks"),
               "nnzh_compressed": m.stat("nnzh_compressed"), "grad_compact": m.stat("grad_compact"),
               "tuned_options": ",".join(str(v) for v in m.tuned_options().values()),
-              "device_bytes": m.stat("device_bytes")}
+              "device_bytes": m.stat("device_bytes"), "fp64_peak": fp64}
     if not args.no_extras:
+        phase("extras: products")
         v = torch.randn(m.nvar, dtype=torch.float64, device=dev)
         w = torch.randn(m.ncon, dtype=torch.float64, device=dev)
         out_c, out_v = E(m.ncon), E(m.nvar)
@@ -392,6 +562,7 @@ def run_exa(args):
         extras["hprod_ms"] = timed(lambda: m.exa_hprod(xt, yt, sigma, v, out_v), 5)
         # 256 per-instance models launched one after another (the unbatched form)
         # (each with the batch's tuned launch shape, fixed, so that 256 creations stay quick)
+        phase("extras: per-instance models")
         tuned = m.tuned_options()
         singles = [B.exa_create(fl, precision=prec, device=local, **tuned) for fl in flats]
         xs = [torch.as_tensor(p[0], device=dev) for p in pts]
@@ -408,7 +579,9 @@ def run_exa(args):
         extras["sequential_per_instance_nnz_per_s"] = nnz_rank / (seq_ms * 1e-3)
         for s_ in singles:
             s_.destroy()
+        del singles, outs
         # the same batch in the other precision mode, timed the same way
+        phase("extras: other precision")
         other = B.EXA_FP64 if prec == B.EXA_MIXED_FP32 else B.EXA_MIXED_FP32
         m2 = B.exa_create_batch(flats, precision=other, device=local)
         step2 = lambda: m2.exa_eval_all(xt, yt, sigma, f=f, g=g, c=c, jac=jac, hess=hess, jac_csc=jcsc, hess_csc=hcsc)
@@ -416,8 +589,8 @@ def run_exa(args):
         ms2 = timed(step2, max(5, min(args.steps, 200)))
         k2 = timed(lambda: m2.exa_eval_all(xt, yt, sigma, jac=jac, hess=hess), max(5, min(args.steps, 200)))
         tag = "mixed" if other == B.EXA_MIXED_FP32 else "fp64"
-        # error of the mixed outputs against the FP64 outputs on the whole batch (the FP64 path
-        # itself matches the CPU oracle to 1e-12 in the parity tests)
+        # error of the mixed outputs against the FP64 outputs on the whole batch (every member of
+        # both is checked against the CPU oracle in the parity tests)
         outs = {}
         for mm in (m, m2):
             r = {k: E(n) for k, n in (("f", 1), ("g", m.nvar), ("c", m.ncon), ("jac", m.nnzj), ("hess", m.nnzh),
@@ -433,9 +606,11 @@ def run_exa(args):
         extras[f"{tag}_kernel_ms"] = k2
         extras[f"{tag}_kernel_hbm_frac"] = nbytes / (k2 * 1e-3) / 1e9 / peak
         extras[f"{tag}_eval_regs"] = m2.stat("eval_regs")
+        extras[f"{tag}_tuned_options"] = ",".join(str(v) for v in m2.tuned_options().values())
         m2.destroy()
         # two-stage stochastic ACOPF (shared generator dispatch, 256 load scenarios of a 1000-bus
         # network): the scenario axis as one more data dimension, full step in both precisions
+        phase("extras: two-stage")
         import synth
         ts = synth.two_stage_acopf(1000, 1500, 166, 256, seed=11)
         tx, ty, tsig = synth.two_stage_point(ts, 0)
@@ -453,24 +628,42 @@ def run_exa(args):
             two["nnz"] = mt.nnzj + mt.nnzh
             mt.destroy()
         extras["two_stage"] = two
+        # the workload families one by one (Rosenbrock-type, ACOPF 500 and 30000 buses, PDE 1000^2),
+        # FP64 and mixed, the CPU oracle on the same inputs beside each
+        if rank == 0:
+            extras["configs"], sweep = family_configs(B, torch, timed, local, peak, args.config_cpu_budget,
+                                                      sweep=args.sweep)
+            if sweep:
+                extras["sweep"] = sweep
 
-    # end to end through the C ABI with host buffers (exa_eval_all_host): pinned host x, y in,
-    # f, g, c back to pinned host memory, every step; the derivative arrays (COO and CSC) are
-    # computed into device buffers as in the device step
+    # End to end through the C ABI with host buffers (exa_eval_all_host), every step: x and y from
+    # pinned host memory in, every output of the step (f, g, c, Jacobian and Hessian COO and CSC
+    # values) back to pinned host memory; the call returns when they are there.
+    phase("end to end")
     xh = torch.as_tensor(x).pin_memory()
     yh = torch.as_tensor(y).pin_memory()
-    fh, gh, ch = (torch.empty(n, dtype=torch.float64).pin_memory() for n in (1, m.nvar, m.ncon))
+    PH = lambda n: torch.empty(n, dtype=torch.float64).pin_memory()
+    host = dict(f=PH(1), g=PH(m.nvar), c=PH(m.ncon), jac=PH(m.nnzj), hess=PH(m.nnzh), jac_csc=PH(m.nnzj_csc),
+                hess_csc=PH(m.nnzh_csc))
 
     def e2e_step():
-        m.exa_eval_all_host(xh, yh, sigma, f=fh, g=gh, c=ch, jac=jac, hess=hess, jac_csc=jcsc, hess_csc=hcsc)
+        m.exa_eval_all_host(xh, yh, sigma, **host)
 
     for _ in range(2):
         e2e_step()
-    e2e_ms = timed(e2e_step, max(3, min(args.steps // 2, 200)))
+    e2e_ms = timed(e2e_step, max(3, min(args.steps // 2, 100)))
     e2e_ms = reduce_max(e2e_ms, pg, dev)
+    d2h = sum(t.numel() for t in host.values()) * 8
+    # the same call with only f, g and c coming back (the derivative arrays left on the device)
+    fgc = dict(f=host["f"], g=host["g"], c=host["c"])
+    e2e_fgc = lambda: m.exa_eval_all_host(xh, yh, sigma, jac=jac, hess=hess, jac_csc=jcsc, hess_csc=hcsc, **fgc)
+    e2e_fgc()
+    extras["e2e_derivatives_on_device_ms"] = timed(e2e_fgc, max(3, min(args.steps // 2, 100)))
+    del host
 
     cpu = None
     if rank == 0 and not args.no_cpu:
+        phase("CPU baseline")
         rate, secs, used, _ = oracle_sample_rate(wls, pts, budget_s=args.cpu_budget)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{len(used)} of 256 batch members in seeded order, {secs:.1f} s of single-thread "
@@ -484,16 +677,18 @@ def run_exa(args):
         "data": "synthetic (seeded generator; paper's suites not available)",
         "config": {"workload": WORKLOAD if args.members == 256 else f"acopf_batch_{args.members}", "members": args.members, "buses": "log-uniform 200-20000",
                    "nnz_per_rank": nnz_rank, "precision": args.precision, "parallelism": f"replicas{ws}",
-                   "l2": "inputs+outputs ~2 GB per step > 129 MB L2 (no flush needed)"},
+                   "l2": "inputs+outputs ~2 GB per step > 129 MB L2 (no flush needed)",
+                   "e2e": "x, y in and every output (f, g, c, J and H in COO and CSC) out, pinned host memory"},
         "e2e": {"value": whole_job_rate(nnz_rank, ws, e2e_ms), "unit": UNIT,
                 "h2d_bytes_per_step": int(xh.numel() * 8 + yh.numel() * 8),
-                "d2h_bytes_per_step": int((1 + m.nvar + m.ncon) * 8), "ms_per_step": e2e_ms},
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "extras": extras,
     }
+    phase("done")
     if rank == 0:
         print(json.dumps(out))
     m.destroy()
@@ -513,6 +708,10 @@ def main(argv=None):
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--config-cpu-budget", type=float, default=1.5,
+                    help="seconds of single-thread oracle work per workload family in extras.configs")
+    ap.add_argument("--sweep", action="store_true", help="also measure the larger family members of the "
+                    "supplemental roofline sweep (PDE 2000^2-4000^2, ACOPF 100k and 300k buses)")
     ap.add_argument("--steps-only", type=int, default=0, help="profiling mode: one untimed step, then this many "
                     "steps, print the step time, exit (no extras, no CPU baseline)")
     ap.add_argument("--kernel-only", type=int, default=0, help="profiling mode: run only the evaluation-kernel "

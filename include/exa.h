@@ -217,12 +217,16 @@ exa_status exa_obj(exa_model *m, const double *x, double *f);
  * which loads the library holds until the process exits.  For callers that cannot allocate device
  * memory (their memory belongs to another allocator, or they run where cudaMalloc is not allowed);
  * this call allocates nothing.  The paper has no counterpart; it is an addition of this library.
- *   - Limit: at most 65536 objective tiles (EXA_E_UNSUPPORTED beyond, with the count in the
- *     message), i.e. 8,388,608 objective instances at 128 threads per tile.
- *   - The first call on a device looks up the array's device address on that device (a CUDA
- *     runtime query, no allocation); make that first call before any stream capture.
+ *   - Limit: at most 65536 objective tiles, one partial each (EXA_E_UNSUPPORTED beyond, with the
+ *     count in the message; f is then left untouched).  Tiles are counted per batch member and
+ *     fused pattern group as ceil(objective instances / block), block being the launch shape's
+ *     threads per CTA (exa_stat "eval_block"; 64 to 256 when tuned): 65536 tiles are 8,388,608
+ *     instances of one pattern at block 128, fewer when a batch has many members or groups.
+ *   - Every call looks up the array's address on the model's device (a CUDA runtime query, no
+ *     allocation).  The first call on a device may also load the library's device code there:
+ *     make that first call before any stream capture.
  *   - Every call shares the one array: calls that overlap on the same GPU race.  Nothing needs
- *     clearing between calls; each call overwrites the partials it reads. */
+ *     clearing between calls; each call overwrites every partial it reads. */
 exa_status exa_obj_noalloc(exa_model *m, const double *x, double *f);
 
 /* g[nvar] = grad f(x): each objective instance writes its own gradient slots, then a gather
@@ -271,7 +275,8 @@ exa_status exa_eval_all(exa_model *m, const double *x, const double *y, double s
  * copied into device buffers the library owns (allocated on first use), the exa_eval_all graph is
  * replayed on the model stream, host outputs are copied back, and the call returns when they are
  * in host memory (the stream is synchronized).  Device arguments are used in place.  Page-locked
- * host buffers (cudaHostAlloc / cudaHostRegister) are copied at full link speed. */
+ * host buffers (cudaHostAlloc / cudaHostRegister) are copied at full link speed, each output as
+ * soon as it is final (the COO values while the CSC sums still run); pageable ones at the end. */
 exa_status exa_eval_all_host(exa_model *m, const double *x, const double *y, double sigma,
                              double *f, double *g, double *c, double *jac, double *hess,
                              double *jac_csc, double *hess_csc);

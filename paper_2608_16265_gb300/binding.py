@@ -35,6 +35,8 @@ EXPORTS = ["exa_create", "exa_create_batch", "exa_destroy", "exa_last_error", "e
            "exa_jac_csc_structure", "exa_hess_csc_structure", "exa_jac_csc", "exa_hess_csc",
            "exa_eval_all", "exa_eval_all_host", "exa_jprod", "exa_jtprod", "exa_hprod", "exa_check_status",
            "exa_compile_check", "exa_stat"]
+# Every function include/exa_probe.h declares (measurement, not part of the evaluation path).
+PROBE_EXPORTS = ["exa_probe_fp64_fma"]
 
 
 class exa_vnode(C.Structure):
@@ -114,6 +116,8 @@ def load():
             "exa_check_status": [vp],
             "exa_compile_check": [C.POINTER(exa_model_desc), C.POINTER(exa_options), C.c_char_p, C.c_size_t],
             "exa_stat": [vp, C.c_char_p, C.POINTER(C.c_double)],
+            "exa_probe_fp64_fma": [C.c_int32, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_int32)],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -204,6 +208,17 @@ def exa_compile_check(flat: ir.FlatModel, precision: int = EXA_FP64, block: int 
     rc = lib.exa_compile_check(C.byref(d.desc), C.byref(_opts(precision, block, flags, 0, 0, min_blocks)), buf, 8192)
     if rc != EXA_OK:
         raise ExaError(rc, buf.value.decode(errors="replace"))
+
+
+def exa_probe_fp64_fma(device: int = 0, target_ms: float = 300.0) -> dict:
+    """Measured FP64 FMA rate of the device (include/exa_probe.h): DFMA instructions per second,
+    the timed kernel's milliseconds and the SM count."""
+    lib = load()
+    r, t, n = C.c_double(), C.c_double(), C.c_int32()
+    rc = lib.exa_probe_fp64_fma(device, float(target_ms), C.byref(r), C.byref(t), C.byref(n))
+    if rc != EXA_OK:
+        raise ExaError(rc, "FP64 FMA probe failed")
+    return {"dfma_per_s": r.value, "ms": t.value, "sms": n.value}
 
 
 class Model:

@@ -1,6 +1,6 @@
 """Builds libexa.so (the C-ABI library) in-tree for sm_103a.
 
-Three translation units compiled in parallel: exa_api.cu and exa_sort.cu with nvcc
+Four translation units compiled in parallel: exa_api.cu, exa_sort.cu and exa_probe.cu with nvcc
 (-gencode arch=compute_103a,code=sm_103a), exa_lower.cpp with g++; linked against the shared CUDA
 runtime and NVRTC (no libcuda link dependency, so the library also loads on hosts without a GPU
 driver).
@@ -41,7 +41,7 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = _sources() + [os.path.join(INCLUDE, "exa.h"), __file__]
+    deps = _sources() + [os.path.join(INCLUDE, h) for h in os.listdir(INCLUDE)] + [__file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
@@ -53,7 +53,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OBJDIR, exist_ok=True)
     jobs = []
     common = ["-O3", "-std=c++17", "-I", INCLUDE]
-    for f in ("exa_api.cu", "exa_sort.cu"):
+    for f in ("exa_api.cu", "exa_sort.cu", "exa_probe.cu"):
         out = os.path.join(OBJDIR, f + ".o")
         jobs.append((out, [nvcc, *ARCH, *common, "-lineinfo", "-Xcompiler", "-fPIC", "-c",
                            os.path.join(CSRC, f), "-o", out]))

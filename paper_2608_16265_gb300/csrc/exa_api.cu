@@ -330,7 +330,7 @@ struct exa_model {
     std::vector<ExaPM> h_pms;     // host copy of the group descriptors
     // CUDA graphs of exa_eval_all, one per argument tuple
     struct GraphEntry {
-        std::array<const void *, 13> key;
+        std::array<const void *, 17> key;
         cudaGraphExec_t exec;
         uint64_t last_use;
     };
@@ -393,7 +393,7 @@ struct exa_model {
 extern "C" {
 static exa_status eval_all_launches(exa_model *m, const double *x, const double *y, double sigma, double *f,
                                     double *g, double *c, double *jac, double *hess, double *jac_csc,
-                                    double *hess_csc, double *const *host_fgc = nullptr);
+                                    double *hess_csc, double *const *host_out = nullptr);
 }
 
 namespace {
@@ -1587,24 +1587,16 @@ exa_status exa_obj(exa_model *m, const double *x, double *f) {
 static __device__ __align__(256) double g_noalloc_partials[EXA_NOALLOC_MAX_PARTIALS];
 
 namespace {
-std::mutex g_noalloc_mu;
-std::map<int, double *> g_noalloc_addr;  // device ordinal -> device address of the array
-
-// The array's name is a host-side stand-in in host code; its device address must be asked for
-// once per device, with that device current.
+// The array's name is a host-side stand-in in host code, not a device address.  Its address on the
+// model's device is asked for on every call, with that device current (check_model made it so): a
+// runtime query that allocates nothing, and that stays right if the module is loaded again at
+// another address (after cudaDeviceReset, for instance).
 exa_status noalloc_partials(exa_model *m, double **out) {
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    auto it = g_noalloc_addr.find(m->device);
-    if (it != g_noalloc_addr.end()) {
-        *out = it->second;
-        return EXA_OK;
-    }
     double *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_partials);
     if (e != cudaSuccess || !p)
         return fail(m, EXA_E_CUDA, std::string("cudaGetSymbolAddress of the static objective scratch: ") +
                                        cudaGetErrorString(e));
-    g_noalloc_addr[m->device] = p;
     *out = p;
     return EXA_OK;
 }
@@ -1613,18 +1605,21 @@ exa_status noalloc_partials(exa_model *m, double **out) {
 exa_status exa_obj_noalloc(exa_model *m, const double *x, double *f) {
     if (exa_status e = check_model(m)) return e;
     CHECK_PTRS(x, f);
-    if (m->ntiles[exa::M_OBJ] > EXA_NOALLOC_MAX_PARTIALS)
+    // one partial per objective tile: tiles are counted per (batch member, fused group) as
+    // ceil(instances / block), so the limit depends on the launch shape, not on instances alone
+    const int nparts = m->nobj[exa::M_OBJ];
+    if (nparts > EXA_NOALLOC_MAX_PARTIALS)
         return fail(m, EXA_E_UNSUPPORTED,
-                    "exa_obj_noalloc: the objective needs " + std::to_string(m->ntiles[exa::M_OBJ]) +
-                        " partial sums (one per tile of " + std::to_string(m->block) +
-                        " objective instances); the static scratch holds at most " +
+                    "exa_obj_noalloc: the objective needs " + std::to_string(nparts) +
+                        " partial sums (one per objective tile of up to " + std::to_string(m->block) +
+                        " instances); the static scratch holds at most " +
                         std::to_string(EXA_NOALLOC_MAX_PARTIALS));
     double *part = nullptr;
     if (exa_status e = noalloc_partials(m, &part)) return e;
     ExaOut o{};
     o.obj_part = part;
     if (exa_status e = launch_eval(m, exa::M_OBJ, x, nullptr, 0.0, o)) return e;
-    k_obj_final<<<1, 256, 0, m->stream>>>(part, m->ntiles[exa::M_OBJ], f);
+    k_obj_final<<<1, 256, 0, m->stream>>>(part, nparts, f);
     CR(cudaGetLastError());
     return EXA_OK;
 }
@@ -1838,7 +1833,7 @@ static cudaError_t side_stream(cudaStream_t *s) {
 // overlaps these reductions.  The objective sum follows the last evaluation; the host copies of
 // f, g, c follow the last reduction.  Same kernels, same per-element arithmetic as one chunk.
 static exa_status eval_all_chunked(exa_model *m, const double *x, const double *y, double sigma, double *f, double *g,
-                                   double *c, double *jac_csc, double *hess_csc, double *const *host_fgc, ExaOut o,
+                                   double *c, double *jac_csc, double *hess_csc, double *const *host_out, ExaOut o,
                                    Mode mode, Mode hmode, bool split, bool jdirect, bool hdirect, bool hcomp) {
     if (!m->ev_fork) CR(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
     for (int s = 0; s < 3; s++) {
@@ -1933,19 +1928,19 @@ static exa_status eval_all_chunked(exa_model *m, const double *x, const double *
     }
     CR(cudaEventRecord(m->ev_join[0], ps));
     CR(cudaStreamWaitEvent(m->stream, m->ev_join[0], 0));
-    if (host_fgc) {
-        if (f && host_fgc[0]) CR(cudaMemcpyAsync(host_fgc[0], f, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
-        if (g && host_fgc[1] && m->nvar)
-            CR(cudaMemcpyAsync(host_fgc[1], g, sizeof(double) * m->nvar, cudaMemcpyDeviceToHost, m->stream));
-        if (c && host_fgc[2] && m->ncon)
-            CR(cudaMemcpyAsync(host_fgc[2], c, sizeof(double) * m->ncon, cudaMemcpyDeviceToHost, m->stream));
+    if (host_out) {  // every page-locked host output, once everything is final
+        const double *src[7] = {f, g, c, o.jac, o.hess, jac_csc, hess_csc};
+        const i64 n[7] = {1, m->nvar, m->ncon, m->nnzj, m->nnzh, m->nnzj_csc, m->nnzh_csc};
+        for (int k = 0; k < 7; k++)
+            if (host_out[k] && src[k] && n[k] > 0)
+                CR(cudaMemcpyAsync(host_out[k], src[k], sizeof(double) * n[k], cudaMemcpyDeviceToHost, m->stream));
     }
     return EXA_OK;
 }
 
 static exa_status eval_all_launches(exa_model *m, const double *x, const double *y, double sigma, double *f,
                                     double *g, double *c, double *jac, double *hess, double *jac_csc,
-                                    double *hess_csc, double *const *host_fgc) {
+                                    double *hess_csc, double *const *host_out) {
     const bool want_h = hess || hess_csc;
     ExaOut o{};
     o.obj_part = m->d_objpart;
@@ -1978,7 +1973,7 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
     Mode mode = !want_h ? exa::M_FIRST : (hcomp ? (hcoo ? exa::M_ALL_B : exa::M_ALL_C) : exa::M_ALL);
     const Mode hmode = hcomp ? (hcoo ? exa::M_HESS_B : exa::M_HESS_C) : exa::M_HESS;
     if (m->nchunks > 1)
-        return eval_all_chunked(m, x, y, sigma, f, g, c, jac_csc, hess_csc, host_fgc, o, want_h ? mode : exa::M_FIRST,
+        return eval_all_chunked(m, x, y, sigma, f, g, c, jac_csc, hess_csc, host_out, o, want_h ? mode : exa::M_FIRST,
                                 hmode, want_h && m->split_all, jdirect, hdirect, hcomp);
     if (want_h && m->split_all) {  // first order and second order as two kernels
         ExaOut o1 = o, o2{};
@@ -1997,11 +1992,14 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
     // the CSC sums are independent of each other and of the objective, gradient and constraint
     // reductions: they run on side streams forked from the model stream (parallel graph branches)
     const bool jside = jac_csc && !jdirect && m->nnzj_csc, hside = (hcomp || (hess_csc && !hdirect)) && m->nnzh_csc;
-    // host copies of f, g, c (page-locked destinations) run on a third side stream as soon as each
-    // is final, overlapping the reductions that follow
-    double *const hf = host_fgc && f ? host_fgc[0] : nullptr, *const hg = host_fgc && g ? host_fgc[1] : nullptr,
-                  *const hc = host_fgc && c ? host_fgc[2] : nullptr;
-    const bool cside = hf || hg || hc;
+    // host copies of the outputs (page-locked destinations, exa_eval_all_host) run on a third side
+    // stream as soon as each output is final, overlapping the reductions that follow: the COO values
+    // right after the evaluation kernel, f, g and c after their sums, the CSC values last
+    auto hout = [&](int k, const double *dev) -> double * { return host_out && dev ? host_out[k] : nullptr; };
+    double *const hf = hout(0, f), *const hg = hout(1, g), *const hc = hout(2, c);
+    double *const hj = jac ? hout(3, o.jac) : nullptr, *const hh = hess ? hout(4, o.hess) : nullptr;
+    double *const hjc = hout(5, jac_csc), *const hhc = hout(6, hess_csc);
+    const bool cside = hf || hg || hc || hj || hh || hjc || hhc;
     if (jside || hside || cside) {
         if (!m->ev_fork) CR(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
         for (int s = 0; s < 3; s++) {
@@ -2018,6 +2016,11 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
         CR(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToHost, m->side[2]));
         return EXA_OK;
     };
+    if (hj || hh) {  // the COO values are final once the evaluation kernel(s) ran
+        CR(cudaStreamWaitEvent(m->side[2], m->ev_fork, 0));
+        if (hj && m->nnzj) CR(cudaMemcpyAsync(hj, o.jac, sizeof(double) * m->nnzj, cudaMemcpyDeviceToHost, m->side[2]));
+        if (hh && m->nnzh) CR(cudaMemcpyAsync(hh, o.hess, sizeof(double) * m->nnzh, cudaMemcpyDeviceToHost, m->side[2]));
+    }
     if (jside) {
         CR(cudaStreamWaitEvent(m->side[0], m->ev_fork, 0));
         if (exa_status e = scatter_csc(m, m->sum_j, m->d_jperm, o.jac, jac_csc, m->nnzj_csc, m->nnzj, m->side[0])) return e;
@@ -2049,6 +2052,17 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
         if (hc && m->ncon)
             if (exa_status e = to_host(2, hc, c, m->ncon)) return e;
     }
+    // the CSC values go to the host after their reductions (side streams 0 and 1)
+    if (hjc && m->nnzj_csc) {
+        if (jside) CR(cudaStreamWaitEvent(m->side[2], m->ev_join[0], 0));
+        else CR(cudaStreamWaitEvent(m->side[2], m->ev_fork, 0));  // written by the evaluation kernel
+        CR(cudaMemcpyAsync(hjc, jac_csc, sizeof(double) * m->nnzj_csc, cudaMemcpyDeviceToHost, m->side[2]));
+    }
+    if (hhc && m->nnzh_csc) {
+        if (hside) CR(cudaStreamWaitEvent(m->side[2], m->ev_join[1], 0));
+        else CR(cudaStreamWaitEvent(m->side[2], m->ev_fork, 0));
+        CR(cudaMemcpyAsync(hhc, hess_csc, sizeof(double) * m->nnzh_csc, cudaMemcpyDeviceToHost, m->side[2]));
+    }
     if (cside) CR(cudaEventRecord(m->ev_join[2], m->side[2]));
     if (jside) CR(cudaStreamWaitEvent(m->stream, m->ev_join[0], 0));
     if (hside) CR(cudaStreamWaitEvent(m->stream, m->ev_join[1], 0));
@@ -2062,16 +2076,15 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
 // the caller's capture instead.
 static exa_status eval_all_cached(exa_model *m, const double *x, const double *y, double sigma, double *f, double *g,
                                   double *c, double *jac, double *hess, double *jac_csc, double *hess_csc,
-                                  double *const *host_fgc) {
+                                  double *const *host_out) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CR(cudaStreamIsCapturing(m->stream, &cs));
     if (!m->use_graphs || cs != cudaStreamCaptureStatusNone)
-        return eval_all_launches(m, x, y, sigma, f, g, c, jac, hess, jac_csc, hess_csc, host_fgc);
+        return eval_all_launches(m, x, y, sigma, f, g, c, jac, hess, jac_csc, hess_csc, host_out);
     uint64_t sb;
     std::memcpy(&sb, &sigma, 8);
-    const std::array<const void *, 13> key = {x, y, f, g, c, jac, hess, jac_csc, hess_csc, (const void *)(uintptr_t)sb,
-                                              host_fgc ? host_fgc[0] : nullptr, host_fgc ? host_fgc[1] : nullptr,
-                                              host_fgc ? host_fgc[2] : nullptr};
+    std::array<const void *, 17> key = {x, y, f, g, c, jac, hess, jac_csc, hess_csc, (const void *)(uintptr_t)sb};
+    for (int k = 0; k < 7; k++) key[10 + k] = host_out ? host_out[k] : nullptr;
     for (auto &ge : m->graphs)
         if (ge.key == key) {
             ge.last_use = ++m->graph_clock;
@@ -2082,7 +2095,7 @@ static exa_status eval_all_cached(exa_model *m, const double *x, const double *y
     cudaStream_t user = m->stream;
     m->stream = m->cap_stream;
     CR(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
-    exa_status st = eval_all_launches(m, x, y, sigma, f, g, c, jac, hess, jac_csc, hess_csc, host_fgc);
+    exa_status st = eval_all_launches(m, x, y, sigma, f, g, c, jac, hess, jac_csc, hess_csc, host_out);
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamEndCapture(m->cap_stream, &graph);
     m->stream = user;
@@ -2149,19 +2162,20 @@ exa_status exa_eval_all_host(exa_model *m, const double *x, const double *y, dou
     for (int k = 0; k < 2; k++)
         if (staged[k] && n[k] > 0)
             CR(cudaMemcpyAsync(use[k], arg[k], sizeof(double) * n[k], cudaMemcpyHostToDevice, m->stream));
-    // page-locked f, g, c are copied back inside the evaluation (overlapping the CSC reductions)
-    double *host_fgc[3] = {};
+    // page-locked outputs are copied back inside the evaluation, each as soon as it is final
+    // (overlapping the reductions that follow); pageable ones after it
+    double *host_out[7] = {};
     bool early = false;
-    for (int k = 2; k < 5; k++)
+    for (int k = 2; k < 9; k++)
         if (staged[k] && pinned[k]) {
-            host_fgc[k - 2] = arg[k];
+            host_out[k - 2] = arg[k];
             early = true;
         }
     if (exa_status e = eval_all_cached(m, use[0], use[1], sigma, use[2], use[3], use[4], use[5], use[6], use[7], use[8],
-                                       early ? host_fgc : nullptr))
+                                       early ? host_out : nullptr))
         return e;
     for (int k = 2; k < 9; k++)
-        if (staged[k] && n[k] > 0 && !(k < 5 && host_fgc[k - 2]))
+        if (staged[k] && n[k] > 0 && !host_out[k - 2])
             CR(cudaMemcpyAsync(arg[k], use[k], sizeof(double) * n[k], cudaMemcpyDeviceToHost, m->stream));
     CR(cudaStreamSynchronize(m->stream));
     return EXA_OK;

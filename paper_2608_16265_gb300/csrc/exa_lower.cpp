@@ -618,7 +618,11 @@ static void build_graph(const Pattern &p, const InputMap &im, Graph &g, PatternG
         if (is_binary(nd.op)) hv[i] = hv[nd.a] || hv[nd.b];
         G.val[i] = v; G.d1[i] = d1; G.d2[i] = d2; G.h11[i] = h11; G.h12[i] = h12; G.h22[i] = h22;
     }
-    G.value = G.val[nv - 1];
+    // Mixed mode: an objective term's value is evaluated in FP64 (dval).  The objective is one sum
+    // over all terms, and terms of opposite sign cancel: an FP32 rounding of each term, however
+    // exactly the terms are summed afterwards, would leave the sum with far more than FP32's
+    // relative error.  Its derivatives are per-variable outputs and stay FP32.
+    G.value = (mixed && p.kind == EXA_OBJ) ? dval(nv - 1) : G.val[nv - 1];
 
     // first-order reverse pass (adjoints), then second order by edge pushing with tangent gradients
     G.adj.assign(nv, Z);
@@ -1063,7 +1067,7 @@ struct Emitter {
         for (int c : ffconsts) os << "  const float CF" << c << " = exa_d2f(C" << c << ");\n";
         std::map<int, std::string> name;
         if (!opt.by_pattern) body(roots, name);
-        auto widen = [&](int r) { return mixed ? "exa_f2d(" + name.at(r) + ")" : name.at(r); };
+        auto widen = [&](int r) { return g.n[r].prec == PF ? "exa_f2d(" + name.at(r) + ")" : name.at(r); };
         // csc/map: optional direct CSC output (a pure permutation of the COO slots); out/slot are
         // the COO array and the block's first slot
         auto staged = [&](const std::string &out, const std::string &slot0, int S, const std::vector<std::string> &vals,

@@ -12,8 +12,8 @@ from tests.helpers import all_ops_model
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_functions():
-    src = open(os.path.join(ROOT, "include", "exa.h")).read()
+def declared_functions(header="exa.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(exa_[a-z_0-9]+)\s*\(", src)))
 
@@ -26,6 +26,17 @@ def test_exports_match_header():
     for n in names:
         assert hasattr(lib, n), n
     assert sorted(binding.EXPORTS) == names
+
+
+def test_every_header_is_exported():
+    """Every include/*.h function is exported by libexa.so and listed by the binding."""
+    from paper_2608_16265_gb300 import binding
+    lib = binding.load()
+    headers = sorted(h for h in os.listdir(os.path.join(ROOT, "include")) if h.endswith(".h"))
+    assert headers == ["exa.h", "exa_probe.h"]
+    for n in declared_functions("exa_probe.h"):
+        assert hasattr(lib, n), n
+    assert sorted(binding.PROBE_EXPORTS) == declared_functions("exa_probe.h")
 
 
 @pytest.mark.parametrize("name,flat", [

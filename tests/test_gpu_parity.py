@@ -1,8 +1,8 @@
 """GPU path (through the C ABI) against the CPU oracle on identical seeded inputs.
 
 Bar: structures and CSC maps bit-exact; FP64 values within 1e-12 relative, normwise per output
-array.  Sizes span several tiles with ragged tails; full-size configurations are compared on
-sampled batch members or whole outputs where the oracle finishes in seconds."""
+array.  Sizes span several tiles with ragged tails; full-size configurations (ACOPF 30k buses,
+PDE 1000^2, the 256-member batch) are compared whole, every output of every batch member."""
 import copy
 
 import numpy as np
@@ -245,38 +245,94 @@ def test_create_errors():
 
 
 # ------------------------------------------------------------------ batch
-def test_batch_matches_members():
+def _csc_slice(colptr, rowval, vals, c0, c1, roff):
+    """Columns [c0, c1) of a block-diagonal batch CSC as a stand-alone CSC (rows shifted by -roff)."""
+    p0, p1 = int(colptr[c0]), int(colptr[c1])
+    return colptr[c0:c1 + 1] - p0, rowval[p0:p1] - roff, vals[p0:p1], p0
+
+
+def compare_batch_members(mb, wls, pts, out, members, tol, structures=True, log=None):
+    """Every output of a batch evaluation against the oracle of each listed member, on that member's
+    slice: COO values, constraint values, gradient, and both CSC value arrays with (when
+    `structures`) their colptr/rowval/coo2csc bit-exact.  A member's variables, rows, COO slots and
+    CSC columns are contiguous ranges of the batch's (members are block-diagonal).  Returns the
+    worst normwise error per output."""
+    worst = {}
+    jcp, jrv, jmap = (_np(t) for t in mb.jac_csc_structure())
+    hcp, hrv, hmap = (_np(t) for t in mb.hess_csc_structure())
+    res = {k: _np(v) for k, v in out.items()}
+    for i in members:
+        w, (xi, yi, si) = wls[i], pts[i]
+        o = oracle.Oracle(w.flat)
+        xs, cs = slice(mb.xoff[i], mb.xoff[i + 1]), slice(mb.coff[i], mb.coff[i + 1])
+        js, hs = slice(mb.joff[i], mb.joff[i + 1]), slice(mb.hoff[i], mb.hoff[i + 1])
+        errs = {"jac": normwise(res["jac"][js], o.jac_coord(xi)),
+                "hess": normwise(res["hess"][hs], o.hess_coord(xi, yi, si)),
+                "c": normwise(res["c"][cs], o.cons(xi)), "g": normwise(res["g"][xs], o.grad(xi))}
+        jc = _csc_slice(jcp, jrv, res["jac_csc"], mb.xoff[i], mb.xoff[i + 1], mb.coff[i])
+        hc = _csc_slice(hcp, hrv, res["hess_csc"], mb.xoff[i], mb.xoff[i + 1], mb.xoff[i])
+        errs["jac_csc"] = normwise(jc[2], o.jac_csc(xi))
+        errs["hess_csc"] = normwise(hc[2], o.hess_csc(xi, yi, si))
+        if structures:
+            for (cp, rv, _, p0), (ocp, orv, omap), gmap, sl in ((jc, o.jac_csc_structure(), jmap, js),
+                                                               (hc, o.hess_csc_structure(), hmap, hs)):
+                assert np.array_equal(cp, ocp) and np.array_equal(rv, orv), f"member {i}: CSC structure"
+                assert np.array_equal(gmap[sl] - p0, omap), f"member {i}: COO->CSC map"
+        for k, e in errs.items():
+            worst[k] = max(worst.get(k, 0.0), e)
+        bad = {k: e for k, e in errs.items() if not e <= tol}
+        assert not bad, (i, bad)
+    if log is not None:
+        log.update(worst)
+    return worst
+
+
+def batch_objective(wls, pts):
+    """The batch objective from the members' oracle objectives (exactly rounded sum of them)."""
+    import math
+    return math.fsum(oracle.Oracle(w.flat).obj(p[0]) for w, p in zip(wls, pts))
+
+
+BATCH_OPTIONS = {
+    "untuned": dict(flags=2),
+    # the launch configuration the benchmark's autotuner picks for the 256-member batch
+    # (block 128, 8 CTAs per SM register cap, one CTA per tile, up-front emission, compressed
+    # Hessian sums gathered into the CSC, one member chunk)
+    "bench_tuned": dict(block=128, min_blocks=8, grid_factor=-1, flags=2 | 128, chunks=1),
+    "split_scatter": dict(flags=2 | 16 | 32),
+    "no_hcomp_chunks": dict(flags=2 | 64, chunks=3),
+}
+
+
+@pytest.mark.parametrize("opts", list(BATCH_OPTIONS))
+def test_batch_matches_members(opts):
+    """Batch outputs, member by member, against the oracle: COO, CSC (values, structure, maps),
+    c, g and f, in the launch configurations the tuner can pick."""
     B = _B()
     wls = synth.acopf_batch(6, seed=3, bmin=20, bmax=400)
     flats = [w.flat for w in wls]
-    mb = B.exa_create_batch(flats)
+    mb = B.exa_create_batch(flats, **BATCH_OPTIONS[opts])
     pts = [synth.acopf_point(w, i) for i, w in enumerate(wls)]
     x = np.concatenate([p[0] for p in pts])
     y = np.concatenate([p[1] for p in pts])
-    jb = _np(mb.jac_coord(_t(x)))
-    hb = _np(mb.hess_coord(_t(x), _t(y), 1.0))
-    cb = _np(mb.cons(_t(x)))
-    gb = _np(mb.grad(_t(x)))
-    rb, cbs = (_np(t) for t in mb.jac_structure())
+    out = mb.eval_all(_t(x), _t(y), 1.0, csc=True)
+    compare_batch_members(mb, wls, pts, out, range(len(wls)), TOL)
+    fo = batch_objective(wls, pts)
+    assert abs(float(_np(out["f"])[0]) - fo) <= TOL * abs(fo)
+    # single callbacks agree with the fused evaluation's slices
+    xt, yt = _t(x), _t(y)
+    for name, got in (("jac", mb.jac_coord(xt)), ("hess", mb.hess_coord(xt, yt, 1.0)), ("c", mb.cons(xt)),
+                      ("g", mb.grad(xt)), ("jac_csc", mb.jac_csc(xt)), ("hess_csc", mb.hess_csc(xt, yt, 1.0))):
+        assert normwise(_np(got), _np(out[name])) <= TOL, name
+    assert abs(float(_np(mb.obj(xt))[0]) - fo) <= TOL * abs(fo)
+    # the member alone gives bitwise the same COO values as its batch slice
+    jb, hb = _np(out["jac"]), _np(out["hess"])
     for i, (w, (xi, yi, si)) in enumerate(zip(wls, pts)):
-        o = oracle.Oracle(w.flat)
-        js = slice(mb.joff[i], mb.joff[i + 1])
-        hs = slice(mb.hoff[i], mb.hoff[i + 1])
-        cs = slice(mb.coff[i], mb.coff[i + 1])
-        xs = slice(mb.xoff[i], mb.xoff[i + 1])
-        r, c = o.jac_structure()
-        assert np.array_equal(rb[js] - mb.coff[i], r) and np.array_equal(cbs[js] - mb.xoff[i], c)
-        assert normwise(jb[js], o.jac_coord(xi)) <= TOL
-        assert normwise(hb[hs], o.hess_coord(xi, yi, si)) <= TOL
-        assert normwise(cb[cs], o.cons(xi)) <= TOL
-        assert normwise(gb[xs], o.grad(xi)) <= TOL
-        # the member alone gives bitwise the same COO values as its batch slice
-        mi = B.exa_create(w.flat)
-        assert np.array_equal(_np(mi.jac_coord(_t(xi))), jb[js])
-        assert np.array_equal(_np(mi.hess_coord(_t(xi), _t(yi), si)), hb[hs])
-    f = float(_np(mb.obj(_t(x)))[0])
-    fo = sum(oracle.Oracle(w.flat).obj(p[0]) for w, p in zip(wls, pts))
-    assert abs(f - fo) <= TOL * abs(fo)
+        mi = B.exa_create(w.flat, **BATCH_OPTIONS[opts])
+        assert np.array_equal(_np(mi.jac_coord(_t(xi))), _np(mb.jac_coord(xt))[mb.joff[i]:mb.joff[i + 1]])
+        assert np.array_equal(_np(mi.hess_coord(_t(xi), _t(yi), si)),
+                              _np(mb.hess_coord(xt, yt, si))[mb.hoff[i]:mb.hoff[i + 1]])
+    del jb, hb
 
 
 @pytest.mark.parametrize("chunks,extra", [(2, 0), (3, 0), (5, "split"), (4, "scatter"), (4, "no_hcomp"), (11, 0)])
@@ -325,46 +381,40 @@ def test_full_pde():
     check_model(wl.flat, x, y, s)
 
 
-@pytest.mark.slow
-def test_full_batch_mixed_sampled_members():
-    """The benchmark batch in mixed precision: sampled members against the FP64 oracle."""
+def _full_batch(precision):
     B = _B()
     wls = synth.acopf_batch(256)
-    mb = B.exa_create_batch([w.flat for w in wls], precision=B.EXA_MIXED_FP32)
+    mb = B.exa_create_batch([w.flat for w in wls], precision=precision)  # autotuned, as in the benchmark
     pts = [synth.acopf_point(w, i) for i, w in enumerate(wls)]
     x = np.concatenate([p[0] for p in pts])
     y = np.concatenate([p[1] for p in pts])
-    out = mb.eval_all(_t(x), _t(y), 1.0, csc=False)
-    jb, hb, cb = _np(out["jac"]), _np(out["hess"]), _np(out["c"])
-    for i in (0, 17, 128, 255):
-        o = oracle.Oracle(wls[i].flat)
-        xi, yi, si = pts[i]
-        assert normwise(jb[mb.joff[i]:mb.joff[i + 1]], o.jac_coord(xi)) <= 1e-6
-        assert normwise(hb[mb.hoff[i]:mb.hoff[i + 1]], o.hess_coord(xi, yi, si)) <= 1e-6
-        assert normwise(cb[mb.coff[i]:mb.coff[i + 1]], o.cons(xi)) <= 1e-6
+    out = mb.eval_all(_t(x), _t(y), 1.0, csc=True)
+    torch.cuda.synchronize()
+    return mb, wls, pts, out
 
 
 @pytest.mark.slow
-def test_full_batch_sampled_members():
-    """The 256-instance batch exactly as the benchmark creates it; members compared against the
-    oracle: the smallest, the largest and two drawn at random."""
-    B = _B()
-    wls = synth.acopf_batch(256)
-    mb = B.exa_create_batch([w.flat for w in wls])
-    pts = [synth.acopf_point(w, i) for i, w in enumerate(wls)]
-    x = np.concatenate([p[0] for p in pts])
-    y = np.concatenate([p[1] for p in pts])
-    out = mb.eval_all(_t(x), _t(y), 1.0, csc=False)
-    jb, hb, cb = _np(out["jac"]), _np(out["hess"]), _np(out["c"])
-    sizes = [w.meta["B"] for w in wls]
-    picks = {int(np.argmin(sizes)), int(np.argmax(sizes))}
-    picks |= set(np.random.default_rng(0).choice(256, 2, replace=False).tolist())
-    for i in sorted(picks):
-        o = oracle.Oracle(wls[i].flat)
-        xi, yi, si = pts[i]
-        assert normwise(jb[mb.joff[i]:mb.joff[i + 1]], o.jac_coord(xi)) <= TOL
-        assert normwise(hb[mb.hoff[i]:mb.hoff[i + 1]], o.hess_coord(xi, yi, si)) <= TOL
-        assert normwise(cb[mb.coff[i]:mb.coff[i + 1]], o.cons(xi)) <= TOL
+def test_full_batch_every_member():
+    """The 256-member benchmark batch exactly as the benchmark creates it (autotuned launch shape):
+    every output of every member against the oracle, CSC structures and maps bit-exact."""
+    mb, wls, pts, out = _full_batch(0)
+    worst = compare_batch_members(mb, wls, pts, out, range(len(wls)), TOL)
+    fo = batch_objective(wls, pts)
+    worst["f"] = abs(float(_np(out["f"])[0]) - fo) / abs(fo)
+    print("fp64 batch", mb.tuned_options(), {k: float(f"{v:.2e}") for k, v in worst.items()})
+    assert worst["f"] <= TOL
+
+
+@pytest.mark.slow
+def test_full_batch_mixed_every_member():
+    """The benchmark batch in mixed precision: every output of every member against the FP64
+    oracle within 1e-6 (the structures are those of the FP64 model)."""
+    mb, wls, pts, out = _full_batch(_B().EXA_MIXED_FP32)
+    worst = compare_batch_members(mb, wls, pts, out, range(len(wls)), 1e-6, structures=False)
+    fo = batch_objective(wls, pts)
+    worst["f"] = abs(float(_np(out["f"])[0]) - fo) / abs(fo)
+    print("mixed batch", mb.tuned_options(), {k: float(f"{v:.2e}") for k, v in worst.items()})
+    assert worst["f"] <= 1e-6
 
 
 def test_eval_all_graph_replay_matches_direct_launches():
