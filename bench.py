@@ -430,7 +430,13 @@ def run_exa(args):
     phase("generate batch")
     prec = B.EXA_MIXED_FP32 if args.precision == "mixed" else B.EXA_FP64
     t0 = time.perf_counter()
-    wls, pts = make_batch(rank, args.members)
+    if args.workload != "batch":  # profiling modes only: one model of a workload family
+        import synth
+        spec = {n: (mk, ptf) for n, mk, ptf, *_ in FAMILIES + SWEEP}[args.workload]
+        wl = spec[0](synth)
+        wls, pts = [wl], [getattr(synth, spec[1])(wl, 0)]
+    else:
+        wls, pts = make_batch(rank, args.members)
     flats = [w.flat for w in wls]
     t_gen = time.perf_counter() - t0
     phase("create batch model")
@@ -564,7 +570,11 @@ def run_exa(args):
         # (each with the batch's tuned launch shape, fixed, so that 256 creations stay quick)
         phase("extras: per-instance models")
         tuned = m.tuned_options()
-        singles = [B.exa_create(fl, precision=prec, device=local, **tuned) for fl in flats]
+        # each single model inlines its own index constants, so each is its own NVRTC compile:
+        # created from a pool of host threads (the library call releases the interpreter lock)
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(max_workers=min(32, os.cpu_count() or 1)) as ex:
+            singles = list(ex.map(lambda fl: B.exa_create(fl, precision=prec, device=local, **tuned), flats))
         xs = [torch.as_tensor(p[0], device=dev) for p in pts]
         ys = [torch.as_tensor(p[1], device=dev) for p in pts]
         outs = [(E(s.nnzj), E(s.nnzh)) for s in singles]
@@ -716,9 +726,13 @@ def main(argv=None):
                     "steps, print the step time, exit (no extras, no CPU baseline)")
     ap.add_argument("--kernel-only", type=int, default=0, help="profiling mode: run only the evaluation-kernel "
                     "call (J and H COO) this many times after one untimed call, print its sizes, exit")
+    ap.add_argument("--workload", default="batch", help="profiling modes only (--steps-only, --kernel-only): "
+                    "'batch' (the benchmark workload) or one model of a workload family, e.g. pde_n2000")
     ap.add_argument("--pin", default="", help="block,min_blocks,grid_factor,flags[,chunks]: fixed launch configuration "
                     "(extras.tuned_options of an earlier run) instead of autotuning, for profiling runs")
     args = ap.parse_args(argv)
+    if args.workload != "batch" and not (args.steps_only or args.kernel_only):
+        ap.error("--workload applies to the profiling modes (--steps-only, --kernel-only)")
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -21,7 +21,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <functional>
+#include <iterator>
 #include <map>
 #include <set>
 #include <sstream>
@@ -278,8 +280,98 @@ struct SN {
 
 class Graph {
   public:
+    typedef std::tuple<int, int, int, uint64_t> Key;
     std::vector<SN> n;
-    std::map<std::tuple<int, int, int, uint64_t>, int> memo;
+    std::map<Key, int> memo;
+    std::vector<Key> keys;  // memo key of every node, for rollback
+    // Product view of MUL nodes: (precision, sorted factor multiset) -> (node, sign), node = sign x
+    // the product of the factors (factors: the non-MUL, non-NEG leaves of the node's product tree).
+    std::map<std::pair<int, std::vector<int>>, std::pair<int, int>> prods;
+    std::vector<std::pair<int, std::vector<int>>> prod_key;  // per node: the prods entry it registered
+    bool factoring = true;
+
+    int make(const SN &s, const Key &key) {
+        n.push_back(s);
+        keys.push_back(key);
+        prod_key.emplace_back(-1, std::vector<int>());
+        const int id = (int)n.size() - 1;
+        memo[key] = id;
+        if (s.op == S_MUL) {
+            int sg = 1;
+            std::vector<int> f;
+            flat(id, sg, f);
+            std::sort(f.begin(), f.end());
+            auto pk = std::make_pair(s.prec, f);
+            if (!prods.count(pk)) {
+                prods[pk] = {id, sg};
+                prod_key[id] = pk;
+            }
+        }
+        return id;
+    }
+    // Drops every node created after `mark` (a tentative rewrite that did not pay off).
+    void rollback(size_t mark) {
+        for (size_t i = n.size(); i-- > mark;) {
+            memo.erase(keys[i]);
+            if (prod_key[i].first >= 0) prods.erase(prod_key[i]);
+        }
+        n.resize(mark);
+        keys.resize(mark);
+        prod_key.resize(mark);
+    }
+    void flat(int i, int &sg, std::vector<int> &f) const {
+        const SN &s = n[i];
+        if (s.op == S_NEG) { sg = -sg; flat(s.a, sg, f); }
+        else if (s.op == S_MUL) { flat(s.a, sg, f); flat(s.b, sg, f); }
+        else f.push_back(i);
+    }
+    bool find_prod(int prec, const std::vector<int> &f, int &node, int &sign) const {
+        if (f.size() == 1) { node = f[0]; sign = 1; return true; }
+        auto it = prods.find(std::make_pair(prec, f));
+        if (it == prods.end()) return false;
+        node = it->second.first;
+        sign = it->second.second;
+        return true;
+    }
+    // Distributive rewrite of a +- b when both are products with common factors C:
+    // C * (rest_a +- rest_b), tried only when C, rest_a and rest_b already exist as nodes, and kept
+    // only when it needs at most one new arithmetic node (the plain sum needs one): typically the
+    // rewritten form is an existing node, e.g. the second adjoints that sin and cos of one argument
+    // push to it, x1 x2 (b sin t) + x1 x2 (g cos t), are x1 x2 (g cos t + b sin t), which the primal
+    // value already computed.  Exact in real arithmetic; only the rounding differs.
+    int try_factor(int a, int b, bool subtract) {
+        if (!factoring || n[a].prec != n[b].prec) return -1;
+        const int prec = n[a].prec;
+        int sa = 1, sb = subtract ? -1 : 1;
+        std::vector<int> fa, fb, common, ra, rb;
+        flat(a, sa, fa);
+        flat(b, sb, fb);
+        if (fa.size() < 2 || fb.size() < 2) return -1;
+        std::sort(fa.begin(), fa.end());
+        std::sort(fb.begin(), fb.end());
+        std::set_intersection(fa.begin(), fa.end(), fb.begin(), fb.end(), std::back_inserter(common));
+        if (common.empty() || common.size() == fa.size() || common.size() == fb.size()) return -1;
+        std::set_difference(fa.begin(), fa.end(), common.begin(), common.end(), std::back_inserter(ra));
+        std::set_difference(fb.begin(), fb.end(), common.begin(), common.end(), std::back_inserter(rb));
+        int pc, sc, pa, sA, pb, sB;
+        if (!find_prod(prec, common, pc, sc) || !find_prod(prec, ra, pa, sA) || !find_prod(prec, rb, pb, sB)) return -1;
+        const size_t mark = n.size();
+        const bool pos_a = sa * sA > 0, pos_b = sb * sB > 0;
+        int inner;
+        if (pos_a && pos_b) inner = add(pa, pb);
+        else if (pos_a) inner = sub(pa, pb);
+        else if (pos_b) inner = sub(pb, pa);
+        else inner = neg(add(pa, pb));
+        int r = mul(pc, inner);
+        if (sc < 0) r = neg(r);
+        int cost = 0;
+        for (size_t i = mark; i < n.size(); i++) cost += n[i].op != S_NEG;
+        if (cost > 1) {
+            rollback(mark);
+            return -1;
+        }
+        return r;
+    }
 
     int lit(double v, int prec) {
         if (prec == PF) v = (double)(float)v;
@@ -288,22 +380,22 @@ class Graph {
         auto key = std::make_tuple((int)S_LIT * 2 + prec, -1, -1, bits);
         auto it = memo.find(key);
         if (it != memo.end()) return it->second;
-        n.push_back({S_LIT, prec, -1, -1, v, 0, 0});
-        return memo[key] = (int)n.size() - 1;
+        return make({S_LIT, prec, -1, -1, v, 0, 0}, key);
     }
     int input(char kind, int id, int prec) {
         auto key = std::make_tuple((int)S_IN * 2 + prec, (int)kind, id, (uint64_t)0);
         auto it = memo.find(key);
         if (it != memo.end()) return it->second;
-        n.push_back({S_IN, prec, -1, -1, 0.0, kind, id});
-        return memo[key] = (int)n.size() - 1;
+        return make({S_IN, prec, -1, -1, 0.0, kind, id}, key);
+    }
+    bool has(int op, int prec, int a, int b = -1) const {
+        return memo.count(std::make_tuple(op * 2 + prec, a, b, (uint64_t)0)) > 0;
     }
     int node(int op, int prec, int a, int b = -1) {
         auto key = std::make_tuple(op * 2 + prec, a, b, (uint64_t)0);
         auto it = memo.find(key);
         if (it != memo.end()) return it->second;
-        n.push_back({op, prec, a, b, 0.0, 0, 0});
-        return memo[key] = (int)n.size() - 1;
+        return make({op, prec, a, b, 0.0, 0, 0}, key);
     }
     int P(int i) const { return n[i].prec; }
     bool is_lit(int i) const { return n[i].op == S_LIT; }
@@ -326,6 +418,10 @@ class Graph {
         if (isneg(b)) return sub(a, n[b].a);
         if (isneg(a)) return sub(b, n[a].a);
         if (a > b) std::swap(a, b);  // a + b == b + a exactly
+        if (!has(S_ADD, P(a), a, b)) {
+            int f = try_factor(a, b, false);
+            if (f >= 0) return f;
+        }
         return node(S_ADD, P(a), a, b);
     }
     int sub(int a, int b) {
@@ -334,6 +430,10 @@ class Graph {
         if (is_lit(a) && is_lit(b)) return lit(fold(n[a].lit - n[b].lit, P(a)), P(a));
         if (isneg(b)) return add(a, n[b].a);
         if (isneg(a)) return neg(add(n[a].a, b));
+        if (!has(S_SUB, P(a), std::min(a, b), std::max(a, b))) {
+            int f = try_factor(a, b, true);
+            if (f >= 0) return f;
+        }
         if (a > b) return neg(node(S_SUB, P(a), b, a));  // a - b == -(b - a) exactly: one canonical form
         return node(S_SUB, P(a), a, b);
     }
@@ -847,10 +947,17 @@ struct Emitter {
             auto A = [&]() { return name.at(s.a); };
             auto B = [&]() { return name.at(s.b); };
             switch (s.op) {
-            case S_NEG: os << "  const " << T << " " << t << " = -" << A() << ";\n"; break;
+            case S_NEG:  // FP64: the sign bit flipped on the integer pipe
+                if (s.prec == PD) os << "  const double " << t << " = exa_neg(" << A() << ");\n";
+                else os << "  const " << T << " " << t << " = -" << A() << ";\n";
+                break;
             case S_ADD: os << "  const " << T << " " << t << " = " << A() << " + " << B() << ";\n"; break;
             case S_SUB: os << "  const " << T << " " << t << " = " << A() << " - " << B() << ";\n"; break;
-            case S_MUL: os << "  const " << T << " " << t << " = " << A() << " * " << B() << ";\n"; break;
+            case S_MUL:  // FP64 doubling: exact, on the integer pipe
+                if (s.prec == PD && (g.is(s.a, 2.0) || g.is(s.b, 2.0)))
+                    os << "  const double " << t << " = exa_twice(" << (g.is(s.a, 2.0) ? B() : A()) << ");\n";
+                else os << "  const " << T << " " << t << " = " << A() << " * " << B() << ";\n";
+                break;
             case S_DIV: os << "  const " << T << " " << t << " = " << A() << " / " << B() << ";\n"; break;
             case S_POW: case S_ATAN2: case S_HYPOT:
                 os << "  const " << T << " " << t << " = " << fname(s.op, s.prec) << "(" << A() << ", " << B() << ");\n";
@@ -1124,24 +1231,58 @@ struct Emitter {
                 os << "  const " << W << " w" << P << " = " << (obj ? (mixed ? "exa_d2f(sigma)" : "sigma")
                                                           : (mixed ? "exa_d2f(Y" + P + ")" : "Y" + P))
                    << ";\n";
-                os << "  const " << W << " ww" << P << " = w" << P << " + w" << P << ";\n";
+                // The weight multiplies each distinct second partial once: slots whose values differ
+                // only in sign share one product.
+                std::map<int, std::string> prod;
                 std::vector<std::string> vals;
+                std::string coll;  // some symbol pair of this pattern resolves to one variable
+                std::vector<std::pair<int, std::string>> doubled;
                 for (int j = 0; j < p.nh(); j++) {
-                    int a = p.hpair[j].first, b = p.hpair[j].second;
-                    int r = hroots[pos][j];
-                    std::string v = r >= 0 ? name.at(r) : (mixed ? "0.0f" : "0.0");
-                    std::string wt = a == b ? "w" + P : "(i" + std::to_string(grp.sym[pos][a]) + " == i" +
-                                                            std::to_string(grp.sym[pos][b]) + " ? ww" + P + " : w" + P + ")";
-                    std::string hv = "hv" + P + "_" + std::to_string(j);
-                    os << "  const double " << hv << " = " << (mixed ? "exa_f2d(" + wt + " * " + v + ")" : wt + " * " + v) << ";\n";
+                    const int a = p.hpair[j].first, b = p.hpair[j].second;
+                    const int r = hroots[pos][j];
+                    const std::string hv = "hv" + P + "_" + std::to_string(j);
+                    std::string v = "0.0";
+                    if (r >= 0) {
+                        const bool ng = g.n[r].op == S_NEG;
+                        const int base = ng ? g.n[r].a : r;
+                        auto it = prod.find(base);
+                        if (it == prod.end()) {
+                            const std::string pn = "hp" + P + "_" + std::to_string(prod.size());
+                            if (!mixed && g.is(base, 2.0))
+                                os << "  const double " << pn << " = exa_twice(w" << P << ");\n";
+                            else
+                                os << "  const " << W << " " << pn << " = w" << P << " * " << name.at(base) << ";\n";
+                            it = prod.emplace(base, pn).first;
+                        }
+                        v = mixed ? "exa_f2d(" + std::string(ng ? "-" : "") + it->second + ")"
+                                  : (ng ? "exa_neg(" + it->second + ")" : it->second);
+                    }
+                    os << "  double " << hv << " = " << v << ";\n";
                     vals.push_back(hv);
-                    if (hs_comp) {  // accumulate into the group's compressed slot (FP64, pattern order)
-                        const int c = hc_of.at({pos, j});
-                        if (hc_started[c]) os << "  hc" << c << " += " << hv << ";\n";
-                        else os << "  double hc" << c << " = " << hv << ";\n";
-                        hc_started[c] = 1;
+                    if (a != b) {
+                        const std::string c = "i" + std::to_string(grp.sym[pos][a]) + " == i" +
+                                              std::to_string(grp.sym[pos][b]);
+                        coll += (coll.empty() ? "" : " || ") + ("(" + c + ")");
+                        doubled.push_back({j, c});
                     }
                 }
+                // A slot pairing two different symbols that resolve to the same variable holds twice
+                // the mixed partial (2 (w h) equals (2 w) h exactly).  Rare: one warp-uniform test,
+                // the doubling only in warps that need it.
+                if (!doubled.empty()) {
+                    os << "  if (__any_sync(0xffffffffu, " << coll << ")) {\n";
+                    for (auto &dj : doubled)
+                        os << "    if (" << dj.second << ") hv" << P << "_" << dj.first << " += hv" << P << "_"
+                           << dj.first << ";\n";
+                    os << "  }\n";
+                }
+                if (hs_comp)
+                    for (int j = 0; j < p.nh(); j++) {  // the group's compressed slot (FP64, pattern order)
+                        const int c = hc_of.at({pos, j});
+                        if (hc_started[c]) os << "  hc" << c << " += " << vals[j] << ";\n";
+                        else os << "  double hc" << c << " = " << vals[j] << ";\n";
+                        hc_started[c] = 1;
+                    }
                 if (hs_coo) staged("o.hess", "pm.hbase[" + P + "]", p.nh(), vals, "o.hcsc", "o.hmap");
             }
         }
@@ -1209,6 +1350,29 @@ static __device__ __forceinline__ float exa_exp_red(const double a) {
 }
 )";
 
+// Exact FP64 operations on the integer pipe.  GB300's FP64 pipe retires two operations per clock
+// per SM, its integer pipes sixty-four: a negation or a doubling done with the bits of the value
+// costs a few integer operations instead of a slot on the binding unit.
+//   exa_neg:   IEEE negation is the sign bit flipped (NaN included).
+//   exa_twice: 2 v: a normal v below the largest binade gets its exponent increased by one; zeros
+//              and subnormals have their magnitude bits shifted left once (a carry into the exponent
+//              field gives the right normal number); the largest binade overflows to infinity with
+//              v's sign; infinities and NaN are returned unchanged.
+static const char *kExactHelpers = R"(
+static __device__ __forceinline__ double exa_neg(const double v) {
+  return __hiloint2double(__double2hiint(v) ^ (int)0x80000000u, __double2loint(v));
+}
+static __device__ __forceinline__ double exa_twice(const double v) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const unsigned e = (hi >> 20) & 0x7ffu, sg = hi & 0x80000000u;
+  unsigned nh = hi, nl = lo;
+  if (e - 1u < 0x7fdu) nh = hi + 0x100000u;
+  else if (e == 0u) { nh = sg | ((hi << 1) & 0x7fffffffu) | (lo >> 31); nl = lo << 1; }
+  else if (e == 0x7feu) { nh = sg | 0x7ff00000u; nl = 0u; }
+  return __hiloint2double((int)nh, (int)nl);
+}
+)";
+
 // FP64 sin/cos helper of the generated code (its own file, so that a host test can compile it)
 static const char *kFp64Helpers =
 #include "exa_fp64_sincos.inc"
@@ -1226,6 +1390,7 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
     if (opt.min_blocks > 0) src << "#define EXA_BOUNDS __launch_bounds__(EXA_BLOCK, " << opt.min_blocks << ")\n";
     else src << "#define EXA_BOUNDS __launch_bounds__(EXA_BLOCK)\n";
     if (mixed) src << kMixedHelpers;
+    src << kExactHelpers;
     src << kFp64Helpers;
     // one shared expression graph per group
     std::vector<Graph> graphs(groups.size());

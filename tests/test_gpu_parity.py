@@ -564,3 +564,29 @@ def test_fp64_sin_cos_accuracy():
     # derivatives come from the same pair: d sin = cos, d cos = -sin
     jac = _np(mod.jac_coord(_t(vals)))
     assert np.array_equal(jac[:n], c[n:]) and np.array_equal(jac[n:], -c[:n])
+
+
+def test_exact_integer_pipe_negation_and_doubling():
+    """FP64 negation and multiplication by 2 are done on the integer pipe in the generated code;
+    they must equal IEEE -x and 2 x bit for bit: signed zeros, subnormals (including ones whose
+    double is normal), the largest binade (overflow to infinity), infinities and NaN."""
+    from paper_2608_16265_gb300.ir import Model
+    B = _B()
+    rng = np.random.default_rng(12)
+    tiny = np.finfo(np.float64).tiny
+    specials = [0.0, -0.0, 5e-324, -5e-324, 1e-310, -2.2e-308, tiny, -tiny, tiny / 2, tiny * (1 - 2 ** -52),
+                1.0, -1.0, 8.98846567431158e307, -8.98846567431158e307, 1.7976931348623157e308,
+                4.49423283715579e307, np.inf, -np.inf, np.nan]
+    vals = np.concatenate([np.array(specials), rng.standard_normal(1000) * 10.0 ** rng.uniform(-300, 300, 1000)])
+    n = len(vals)
+    m = Model()
+    xv = m.add_var(n)
+    m.add_con(lambda d: 2 * xv[d.k], n=n)
+    m.add_con(lambda d: -xv[d.k], n=n)
+    mod = B.exa_create(m.flat())
+    c = _np(mod.cons(_t(vals)))
+    with np.errstate(over="ignore"):
+        want2, wantn = 2.0 * vals, -vals
+    for got, want in ((c[:n], want2), (c[n:], wantn)):
+        same = (got.view(np.uint64) == want.view(np.uint64)) | (np.isnan(got) & np.isnan(want))
+        assert same.all(), [(v, g, w) for v, g, w in zip(vals[~same], got[~same], want[~same])][:5]
