@@ -155,17 +155,22 @@ enum {
     EXA_FLAG_NO_FUSE = 4,      /* evaluate every pattern in its own thread (no fused groups) */
     EXA_FLAG_NO_GRAPH = 8,     /* exa_eval_all launches its kernels directly instead of replaying a
                                   cached CUDA graph */
-    /* The next four fix choices the autotuner otherwise makes (they apply as given when tuning is
+    /* The next four (and the two prefetch flags below) fix choices the autotuner otherwise makes (they apply as given when tuning is
      * off: EXA_FLAG_NO_TUNE, or block_threads / grid_factor set).  exa_stat reports the choices. */
     EXA_FLAG_SPLIT = 16,       /* exa_eval_all evaluates first and second order in two kernels */
     EXA_FLAG_CSC_SCATTER = 32, /* a duplicate-free CSC is scattered by the evaluation kernel instead
                                   of gathered from the COO values by a permutation kernel */
     EXA_FLAG_NO_HCOMP = 64,    /* the Hessian CSC is summed from the COO slots instead of from the
                                   per-instance sums of the slots of a fused group that share an entry */
-    EXA_FLAG_UPFRONT = 128     /* the generated code computes all of a fused group's arithmetic
+    EXA_FLAG_UPFRONT = 128,    /* the generated code computes all of a fused group's arithmetic
                                   before its first output, instead of each pattern's arithmetic right
                                   before that pattern's outputs (the default, which keeps fewer
                                   values live) */
+    EXA_FLAG_PF_COLUMNS = 256, /* the evaluation kernels prefetch into L2 the data columns of the
+                                  tile two tile-steps ahead (a tile-step: a CTA's next tile in a
+                                  persistent grid, else one wave of resident CTAs) */
+    EXA_FLAG_PF_GATHERS = 512  /* as EXA_FLAG_PF_COLUMNS, and every thread also prefetches the x and
+                                  y lines its instance of the next tile-step gathers */
 };
 
 /* Validate the descriptor (Sec. 3.4 SIMDFunction), lower every pattern to generated device
@@ -302,7 +307,7 @@ exa_status exa_compile_check(const exa_model_desc *desc, const exa_options *opt,
 
 /* Named statistics (host values): "nvrtc_ms", "create_ms", "tune_ms", "eval_regs", "eval_block",
  * "eval_regs_jac", "eval_regs_hess", "eval_tiles", "eval_grid", "eval_persist", "eval_min_blocks",
- * "eval_split", "eval_chunks", "eval_upfront", "graph_kernels", "csc_direct",
+ * "eval_split", "eval_chunks", "eval_upfront", "eval_prefetch", "graph_kernels", "csc_direct",
  * "hess_compressed", "nnzh_compressed", "grad_compact", "device_bytes", "n_patterns", "batch_members".
  * Unknown key: EXA_E_INVALID. */
 exa_status exa_stat(const exa_model *m, const char *key, double *value);

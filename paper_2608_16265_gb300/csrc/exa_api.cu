@@ -325,6 +325,8 @@ struct exa_model {
     int persist = 0;              // persistent grid factor chosen by the tuner (0: one CTA per tile)
     int min_blocks = 0;           // launch-bounds minimum CTAs per SM chosen by the tuner
     bool by_pattern = true;       // generated code emits each pattern's arithmetic next to its outputs
+    int prefetch = 0;             // L2 prefetch depth of the generated tile loop (CodegenOptions)
+    int pfd[exa::M_COUNT] = {};   // prefetch distance in tiles per kernel kind (0: none)
     bool split_all = false;       // exa_eval_all: first- and second-order kernels instead of one
     bool csc_direct = false;      // duplicate-free CSC written by the evaluation kernel (scatter)
     std::vector<ExaPM> h_pms;     // host copy of the group descriptors
@@ -341,10 +343,10 @@ struct exa_model {
     cudaStream_t cap_stream = nullptr;
     // exa_eval_all runs its independent reductions (Jacobian CSC, Hessian CSC, the rest) on three
     // streams forked from and joined back into the model stream
-    cudaStream_t side[3] = {};
+    cudaStream_t side[4] = {};
     // device buffers of exa_eval_all_host: x, y, f, g, c, jac, hess, jac_csc, hess_csc
     double *d_host_io[9] = {};
-    cudaEvent_t ev_fork = nullptr, ev_join[3] = {}, ev_out[3] = {};
+    cudaEvent_t ev_fork = nullptr, ev_first = nullptr, ev_join[4] = {}, ev_out[3] = {};
     double *d_theta = nullptr;
     int *d_status = nullptr;
     int *d_jrow = nullptr, *d_jcol = nullptr, *d_hrow = nullptr, *d_hcol = nullptr, *d_gvar = nullptr, *d_arow = nullptr;
@@ -428,16 +430,18 @@ void free_all(exa_model *m) {
     m->graphs.clear();
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     m->cap_stream = nullptr;
-    for (int s = 0; s < 3; s++) {
+    for (int s = 0; s < 4; s++) {
         if (m->side[s]) cudaStreamDestroy(m->side[s]);
         if (m->ev_join[s]) cudaEventDestroy(m->ev_join[s]);
-        if (m->ev_out[s]) cudaEventDestroy(m->ev_out[s]);
+        if (s < 3 && m->ev_out[s]) cudaEventDestroy(m->ev_out[s]);
         m->side[s] = nullptr;
         m->ev_join[s] = nullptr;
-        m->ev_out[s] = nullptr;
+        if (s < 3) m->ev_out[s] = nullptr;
     }
     if (m->ev_fork) cudaEventDestroy(m->ev_fork);
+    if (m->ev_first) cudaEventDestroy(m->ev_first);
     m->ev_fork = nullptr;
+    m->ev_first = nullptr;
     for (cudaEvent_t &e : m->ev_chunk) {
         if (e) cudaEventDestroy(e);
         e = nullptr;
@@ -544,7 +548,8 @@ exa_status launch_eval(exa_model *m, Mode mode, const double *x, const double *y
     const double *th = m->d_theta;
     int nt = t1 - t0;
     const ExaTile *tiles = m->d_tiles[mode] + t0;
-    void *args[] = {&tiles, &nt, &m->d_pm, &x, &y, &th, &sigma, &out, &so};
+    int pfd = m->pfd[mode];
+    void *args[] = {&tiles, &nt, &m->d_pm, &x, &y, &th, &sigma, &out, &so, &pfd};
     const int grid = m->grid[mode] > 0 ? std::min(m->grid[mode], nt) : nt;
     CR(cudaLaunchKernel((const void *)m->fn[mode], dim3(grid), dim3(m->block), args, 0, st ? st : m->stream));
     return EXA_OK;
@@ -894,6 +899,7 @@ exa_status setup_kernels(exa_model *m, int block, int min_blocks = 0) {
     cg.min_blocks = min_blocks;
     cg.bounds_check = m->bounds_check;
     cg.by_pattern = m->by_pattern;
+    cg.prefetch = m->prefetch;
     std::string gerr;
     std::string src = exa::generate_source(m->pats, m->groups, cg, &gerr);
     if (!gerr.empty()) return fail(m, EXA_E_INTERNAL, gerr);
@@ -929,6 +935,7 @@ exa_status setup_kernels(exa_model *m, int block, int min_blocks = 0) {
         m->ntiles[k] = (int)tiles.size();
         m->mb_tile[k][nb] = m->ntiles[k];
         m->grid[k] = m->ntiles[k];
+        m->pfd[k] = 0;
         if (m->d_tiles[k]) cudaFree(m->d_tiles[k]);
         m->d_tiles[k] = nullptr;
         CR(cudaMalloc((void **)&m->d_tiles[k], sizeof(ExaTile) * std::max<size_t>(tiles.size(), 1)));
@@ -939,17 +946,22 @@ exa_status setup_kernels(exa_model *m, int block, int min_blocks = 0) {
 }
 
 // Persistent grid for every kernel kind: factor x resident CTAs per SM x SMs (0: one CTA per tile).
+// Prefetch distance: a CTA's next tile in a persistent grid; with one CTA per tile, the tile that
+// starts about one wave of resident CTAs later.
 exa_status apply_grid(exa_model *m, int factor) {
     m->persist = factor;
     int sms = 0;
     CR(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
     for (int k = 0; k < exa::M_COUNT; k++) {
         m->grid[k] = m->ntiles[k];
-        if (factor <= 0 || k == exa::M_STRUCT) continue;
+        m->pfd[k] = 0;
+        if (k == exa::M_STRUCT) continue;
         int occ = 0;
         CR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)m->fn[k], m->block, 0));
-        const long long g = (long long)factor * std::max(occ, 1) * sms;
-        if (g < m->ntiles[k]) m->grid[k] = (int)g;
+        const long long wave = (long long)std::max(occ, 1) * sms;
+        const long long g = (long long)std::max(factor, 0) * wave;
+        if (factor > 0 && g < m->ntiles[k]) m->grid[k] = (int)g;
+        if (m->prefetch > 0) m->pfd[k] = (int)std::min<long long>(m->grid[k] < m->ntiles[k] ? m->grid[k] : wave, 1 << 30);
     }
     return EXA_OK;
 }
@@ -979,18 +991,19 @@ exa_status autotune(exa_model *m) {
     double best = 1e30;
     int best_block = m->block, best_factor = 0;
     const int blocks[] = {64, 128, 256};
-    auto variant = [&](int block, int minb, bool byp) {
+    auto variant = [&](int block, int minb, bool byp, int pf) {
         exa::CodegenOptions cg;
         cg.precision = m->precision;
         cg.block = block;
         cg.min_blocks = minb;
         cg.bounds_check = m->bounds_check;
         cg.by_pattern = byp;
+        cg.prefetch = pf;
         return cg;
     };
     {
         std::vector<exa::CodegenOptions> v;
-        for (int B : blocks) v.push_back(variant(B, 0, m->by_pattern));
+        for (int B : blocks) v.push_back(variant(B, 0, m->by_pattern, m->prefetch));
         precompile(m, v);
     }
     for (int B : blocks) {
@@ -1033,7 +1046,7 @@ exa_status autotune(exa_model *m) {
         for (int order = 0; order < 2; order++)
             for (int warps : {0, 20, 24, 28, 32}) {
                 const int minb = warps * 32 / best_block;
-                if (minb <= 32 && (warps == 0 || minb >= 1)) v.push_back(variant(best_block, minb, order == 0));
+                if (minb <= 32 && (warps == 0 || minb >= 1)) v.push_back(variant(best_block, minb, order == 0, m->prefetch));
             }
         precompile(m, v);
     }
@@ -1076,6 +1089,43 @@ exa_status autotune(exa_model *m) {
         }
     }
     m->by_pattern = best_order;
+    // L2 prefetch depth (staging of later tiles' inputs): none, data columns, or data columns and
+    // the next tile's x and y lines; kept when the fused kernel gets faster
+    const int init_pf = m->prefetch;
+    int best_pf = init_pf;
+    {
+        std::vector<exa::CodegenOptions> v;
+        for (int pf : {0, 1, 2})
+            if (pf != init_pf) v.push_back(variant(best_block, best_minb, best_order, pf));
+        precompile(m, v);
+    }
+    for (int pf : {0, 1, 2}) {
+        if (pf == init_pf) continue;
+        m->prefetch = pf;
+        if (exa_status e = setup_kernels(m, best_block, best_minb)) return e;
+        if (exa_status e = apply_grid(m, best_factor)) return e;
+        CR(S.get(&part, std::max(m->nobj[exa::M_ALL], 1)));
+        ExaOut o{};
+        o.obj_part = part;
+        o.c = m->d_cbuf;
+        o.abuf = m->d_abuf;
+        o.gbuf = m->d_gbuf;
+        o.jac = m->d_jbuf;
+        o.hess = m->d_hbuf;
+        if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
+        CR(cudaEventRecord(e0, m->stream));
+        for (int r = 0; r < 5; r++)
+            if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
+        CR(cudaEventRecord(e1, m->stream));
+        CR(cudaEventSynchronize(e1));
+        float ms = 0;
+        CR(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            best_pf = pf;
+        }
+    }
+    m->prefetch = best_pf;
     if (exa_status e = setup_kernels(m, best_block, best_minb)) return e;
     if (exa_status e = apply_grid(m, best_factor)) return e;
     m->tune_ms = best / 5.0;
@@ -1238,6 +1288,7 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     m->split_all = (o.flags & EXA_FLAG_SPLIT) != 0;
     m->by_pattern = (o.flags & EXA_FLAG_UPFRONT) == 0;
     m->csc_direct = (o.flags & EXA_FLAG_CSC_SCATTER) != 0;
+    m->prefetch = (o.flags & EXA_FLAG_PF_GATHERS) ? 2 : (o.flags & EXA_FLAG_PF_COLUMNS) ? 1 : 0;
     if (nb < 1) return fail(m, EXA_E_INVALID, "empty batch");
     for (int b = 0; b < nb; b++) {
         const exa_model_desc *d = descs[b];
@@ -1428,7 +1479,8 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
         const double *nul = nullptr;
         double sigma = 0;
         int nt = m->ntiles[exa::M_STRUCT];
-        void *args[] = {&m->d_tiles[exa::M_STRUCT], &nt, &m->d_pm, &nul, &nul, &m->d_theta, &sigma, &out, &so};
+        int pfd = 0;
+        void *args[] = {&m->d_tiles[exa::M_STRUCT], &nt, &m->d_pm, &nul, &nul, &m->d_theta, &sigma, &out, &so, &pfd};
         CR(cudaLaunchKernel((const void *)m->fn[exa::M_STRUCT], dim3(m->ntiles[exa::M_STRUCT]), dim3(m->block),
                             args, 0, m->stream));
         CR(cudaStreamSynchronize(m->stream));
@@ -1456,9 +1508,10 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
         }
         CR(dalloc(m, &m->d_objpart, maxt));
     }
-    if (!(o.flags & EXA_FLAG_NO_TUNE) && !o.block_threads && o.grid_factor == 0)
+    const bool tune = !(o.flags & EXA_FLAG_NO_TUNE) && !o.block_threads && o.grid_factor == 0;
+    if (tune)
         if (exa_status e = autotune(m)) return e;
-    if (o.grid_factor != 0)
+    if (!tune || o.grid_factor != 0)
         if (exa_status e = apply_grid(m, std::max(o.grid_factor, 0))) return e;
     CR(cudaDeviceSynchronize());
     m->create_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -1686,9 +1739,9 @@ exa_status exa_grad(exa_model *m, const double *x, double *g) {
     return EXA_OK;
 }
 
-static exa_status aug_rows(exa_model *m, double *c) {
+static exa_status aug_rows(exa_model *m, double *c, cudaStream_t st) {
     if (m->n_aug_rows) {
-        k_seg_sum_warp<true><<<grid_of(m->n_aug_rows, 256 * EXA_SEG_G), 256, 0, m->stream>>>(
+        k_seg_sum_warp<true><<<grid_of(m->n_aug_rows, 256 * EXA_SEG_G), 256, 0, st>>>(
             m->d_aptr, m->d_aperm, m->d_abuf, c, m->d_arows, m->n_aug_rows);
         CR(cudaGetLastError());
     }
@@ -1703,7 +1756,7 @@ exa_status exa_cons(exa_model *m, const double *x, double *c) {
     o.c = c;
     o.abuf = m->d_abuf;
     if (exa_status e = launch_eval(m, exa::M_CON, x, nullptr, 0.0, o)) return e;
-    return aug_rows(m, c);
+    return aug_rows(m, c, m->stream);
 }
 
 exa_status exa_jac_structure(const exa_model *mc, int32_t *rows, int32_t *cols) {
@@ -1975,54 +2028,67 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
     if (m->nchunks > 1)
         return eval_all_chunked(m, x, y, sigma, f, g, c, jac_csc, hess_csc, host_out, o, want_h ? mode : exa::M_FIRST,
                                 hmode, want_h && m->split_all, jdirect, hdirect, hcomp);
-    if (want_h && m->split_all) {  // first order and second order as two kernels
+    // Streams: the model stream runs the evaluation kernel(s); side 0 the Jacobian CSC, side 1 the
+    // Hessian CSC, side 2 the host copies, side 3 (split mode) the objective, gradient and
+    // constraint sums.  Each branch is forked from and joined back into the model stream (parallel
+    // branches of the captured graph).  In split mode every first-order reduction starts as soon as
+    // the first-order kernel has run, overlapping the second-order kernel: the reductions move
+    // bytes, the second-order kernel keeps the FP64 pipe busy.
+    const bool split = want_h && m->split_all;
+    const bool jside = jac_csc && !jdirect && m->nnzj_csc, hside = (hcomp || (hess_csc && !hdirect)) && m->nnzh_csc;
+    auto hout = [&](int k, const double *dev) -> double * { return host_out && dev ? host_out[k] : nullptr; };
+    double *const hf = hout(0, f), *const hg = hout(1, g), *const hc = hout(2, c);
+    double *const hj = jac ? hout(3, o.jac) : nullptr, *const hh = hess ? hout(4, o.hess) : nullptr;
+    double *const hjc = hout(5, jac_csc), *const hhc = hout(6, hess_csc);
+    const bool cside = hf || hg || hc || hj || hh || hjc || hhc;
+    const bool forked = jside || hside || cside || split;
+    if (forked) {
+        if (!m->ev_fork) CR(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
+        if (!m->ev_first) CR(cudaEventCreateWithFlags(&m->ev_first, cudaEventDisableTiming));
+        for (int s = 0; s < 4; s++) {
+            if (!m->side[s]) CR(side_stream(&m->side[s]));
+            if (!m->ev_join[s]) CR(cudaEventCreateWithFlags(&m->ev_join[s], cudaEventDisableTiming));
+        }
+        for (int s = 0; s < 3; s++)
+            if (!m->ev_out[s]) CR(cudaEventCreateWithFlags(&m->ev_out[s], cudaEventDisableTiming));
+    }
+    if (split) {  // first order and second order as two kernels
         ExaOut o1 = o, o2{};
         o1.hess = nullptr;
         o1.hcsc = nullptr;
+        o1.hcomp = nullptr;
         o2.hess = o.hess;
         o2.hcsc = o.hcsc;
         o2.hmap = o.hmap;
         o2.hcomp = o.hcomp;
         mode = exa::M_FIRST;
         if (exa_status e = launch_eval(m, exa::M_FIRST, x, y, sigma, o1)) return e;
+        CR(cudaEventRecord(m->ev_first, m->stream));
         if (exa_status e = launch_eval(m, hmode, x, y, sigma, o2)) return e;
     } else if (exa_status e = launch_eval(m, mode, x, y, sigma, o)) {
         return e;
     }
-    // the CSC sums are independent of each other and of the objective, gradient and constraint
-    // reductions: they run on side streams forked from the model stream (parallel graph branches)
-    const bool jside = jac_csc && !jdirect && m->nnzj_csc, hside = (hcomp || (hess_csc && !hdirect)) && m->nnzh_csc;
-    // host copies of the outputs (page-locked destinations, exa_eval_all_host) run on a third side
-    // stream as soon as each output is final, overlapping the reductions that follow: the COO values
-    // right after the evaluation kernel, f, g and c after their sums, the CSC values last
-    auto hout = [&](int k, const double *dev) -> double * { return host_out && dev ? host_out[k] : nullptr; };
-    double *const hf = hout(0, f), *const hg = hout(1, g), *const hc = hout(2, c);
-    double *const hj = jac ? hout(3, o.jac) : nullptr, *const hh = hess ? hout(4, o.hess) : nullptr;
-    double *const hjc = hout(5, jac_csc), *const hhc = hout(6, hess_csc);
-    const bool cside = hf || hg || hc || hj || hh || hjc || hhc;
-    if (jside || hside || cside) {
-        if (!m->ev_fork) CR(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
-        for (int s = 0; s < 3; s++) {
-            if (!m->side[s]) CR(side_stream(&m->side[s]));
-            if (!m->ev_join[s]) CR(cudaEventCreateWithFlags(&m->ev_join[s], cudaEventDisableTiming));
-            if (!m->ev_out[s]) CR(cudaEventCreateWithFlags(&m->ev_out[s], cudaEventDisableTiming));
-        }
-        CR(cudaEventRecord(m->ev_fork, m->stream));
-    }
-    // one finished output (on the model stream) copied to the host on side stream 2
+    if (forked) CR(cudaEventRecord(m->ev_fork, m->stream));
+    const cudaEvent_t first_done = split ? m->ev_first : m->ev_fork;  // first-order outputs final
+    cudaStream_t rs = split ? m->side[3] : m->stream;                  // stream of the f, g, c sums
+    if (split) CR(cudaStreamWaitEvent(rs, m->ev_first, 0));
+    // one finished output (on stream rs) copied to the host on side stream 2
     auto to_host = [&](int slot, double *dst, const double *src, i64 n) -> exa_status {
-        CR(cudaEventRecord(m->ev_out[slot], m->stream));
+        CR(cudaEventRecord(m->ev_out[slot], rs));
         CR(cudaStreamWaitEvent(m->side[2], m->ev_out[slot], 0));
         CR(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToHost, m->side[2]));
         return EXA_OK;
     };
-    if (hj || hh) {  // the COO values are final once the evaluation kernel(s) ran
+    if (hj && m->nnzj) {  // the COO values are final once their kernel ran
+        CR(cudaStreamWaitEvent(m->side[2], first_done, 0));
+        CR(cudaMemcpyAsync(hj, o.jac, sizeof(double) * m->nnzj, cudaMemcpyDeviceToHost, m->side[2]));
+    }
+    if (hh && m->nnzh) {
         CR(cudaStreamWaitEvent(m->side[2], m->ev_fork, 0));
-        if (hj && m->nnzj) CR(cudaMemcpyAsync(hj, o.jac, sizeof(double) * m->nnzj, cudaMemcpyDeviceToHost, m->side[2]));
-        if (hh && m->nnzh) CR(cudaMemcpyAsync(hh, o.hess, sizeof(double) * m->nnzh, cudaMemcpyDeviceToHost, m->side[2]));
+        CR(cudaMemcpyAsync(hh, o.hess, sizeof(double) * m->nnzh, cudaMemcpyDeviceToHost, m->side[2]));
     }
     if (jside) {
-        CR(cudaStreamWaitEvent(m->side[0], m->ev_fork, 0));
+        CR(cudaStreamWaitEvent(m->side[0], first_done, 0));
         if (exa_status e = scatter_csc(m, m->sum_j, m->d_jperm, o.jac, jac_csc, m->nnzj_csc, m->nnzj, m->side[0])) return e;
         CR(cudaEventRecord(m->ev_join[0], m->side[0]));
     }
@@ -2037,36 +2103,36 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
         CR(cudaEventRecord(m->ev_join[1], m->side[1]));
     }
     if (f) {
-        k_obj_final<<<1, 256, 0, m->stream>>>(m->d_objpart, m->nobj[mode], f);
+        k_obj_final<<<1, 256, 0, rs>>>(m->d_objpart, m->nobj[mode], f);
         CR(cudaGetLastError());
         if (hf)
             if (exa_status e = to_host(0, hf, f, 1)) return e;
     }
     if (g && m->nvar) {
-        if (exa_status e = grad_sum(m, g, m->stream)) return e;
+        if (exa_status e = grad_sum(m, g, rs)) return e;
         if (hg)
             if (exa_status e = to_host(1, hg, g, m->nvar)) return e;
     }
     if (c) {
-        if (exa_status e = aug_rows(m, c)) return e;
+        if (exa_status e = aug_rows(m, c, rs)) return e;
         if (hc && m->ncon)
             if (exa_status e = to_host(2, hc, c, m->ncon)) return e;
     }
     // the CSC values go to the host after their reductions (side streams 0 and 1)
     if (hjc && m->nnzj_csc) {
-        if (jside) CR(cudaStreamWaitEvent(m->side[2], m->ev_join[0], 0));
-        else CR(cudaStreamWaitEvent(m->side[2], m->ev_fork, 0));  // written by the evaluation kernel
+        CR(cudaStreamWaitEvent(m->side[2], jside ? m->ev_join[0] : first_done, 0));
         CR(cudaMemcpyAsync(hjc, jac_csc, sizeof(double) * m->nnzj_csc, cudaMemcpyDeviceToHost, m->side[2]));
     }
     if (hhc && m->nnzh_csc) {
-        if (hside) CR(cudaStreamWaitEvent(m->side[2], m->ev_join[1], 0));
-        else CR(cudaStreamWaitEvent(m->side[2], m->ev_fork, 0));
+        CR(cudaStreamWaitEvent(m->side[2], hside ? m->ev_join[1] : m->ev_fork, 0));
         CR(cudaMemcpyAsync(hhc, hess_csc, sizeof(double) * m->nnzh_csc, cudaMemcpyDeviceToHost, m->side[2]));
     }
     if (cside) CR(cudaEventRecord(m->ev_join[2], m->side[2]));
+    if (split) CR(cudaEventRecord(m->ev_join[3], m->side[3]));
     if (jside) CR(cudaStreamWaitEvent(m->stream, m->ev_join[0], 0));
     if (hside) CR(cudaStreamWaitEvent(m->stream, m->ev_join[1], 0));
     if (cside) CR(cudaStreamWaitEvent(m->stream, m->ev_join[2], 0));
+    if (split) CR(cudaStreamWaitEvent(m->stream, m->ev_join[3], 0));
     return EXA_OK;
 }
 
@@ -2251,6 +2317,7 @@ exa_status exa_compile_check(const exa_model_desc *desc, const exa_options *opt,
             cg.bounds_check = (o.flags & EXA_FLAG_BOUNDS_CHECK) != 0;
             cg.by_pattern = (o.flags & EXA_FLAG_UPFRONT) == 0;
             cg.min_blocks = o.min_blocks;
+            cg.prefetch = (o.flags & EXA_FLAG_PF_GATHERS) ? 2 : (o.flags & EXA_FLAG_PF_COLUMNS) ? 1 : 0;
             std::string gerr;
             std::string src = exa::generate_source(tmp.pats, tmp.groups, cg, &gerr);
             if (!gerr.empty()) s = fail(&tmp, EXA_E_INTERNAL, gerr);
@@ -2288,6 +2355,7 @@ exa_status exa_stat(const exa_model *m, const char *key, double *value) {
     else if (k == "hess_compressed") *value = m->use_hcomp;
     else if (k == "eval_chunks") *value = m->nchunks;
     else if (k == "eval_upfront") *value = !m->by_pattern;
+    else if (k == "eval_prefetch") *value = m->prefetch;
     else if (k == "graph_kernels") *value = m->graph_kernels;
     else if (k == "grad_compact") *value = m->grad_compact;
     else if (k == "nnzh_compressed") *value = (double)m->nnzhc;

@@ -130,6 +130,10 @@ struct CodegenOptions {
     // emit each pattern's arithmetic just before its outputs (shorter live ranges) instead of all
     // of a group's arithmetic before the first output
     bool by_pattern = true;
+    // L2 prefetch of later tiles' inputs in the tile loop: 0 none; 1 the data columns of the tile
+    // 2 x pfd ahead (one bulk prefetch per column); 2 also the x and y lines the tile pfd ahead
+    // gathers (pfd: a kernel argument, the CTA's next tile in a persistent grid, else one wave)
+    int prefetch = 0;
 };
 std::string generate_source(const std::vector<Pattern> &pats, const std::vector<Group> &groups,
                             const CodegenOptions &opt, std::string *err);

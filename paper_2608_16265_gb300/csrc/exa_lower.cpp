@@ -861,6 +861,7 @@ struct Emitter {
     const std::vector<PatternGraph> &PG;  // per position in the group
     const CodegenOptions &opt;
     std::ostringstream os;
+    std::string pf_text;  // prefetch functions of the last function() (opt.prefetch > 0)
 
     Emitter(const std::vector<Pattern> &p_, const Group &g_, const Graph &gr, const std::vector<PatternGraph> &pg,
             const CodegenOptions &o)
@@ -1122,6 +1123,52 @@ struct Emitter {
                        << "]) { atomicOr(o.status, 1); lrow" << pos << " = 0; }\n";
                 os << "  const long long row" << pos << " = pm.rbase[" << pos << "] + lrow" << pos << ";\n";
             }
+        }
+        pf_text.clear();
+        if (!want_struct && opt.prefetch > 0) {
+            // _pf: lane c of a warp prefetches data column c of the tile starting at `begin` into L2
+            // (one bulk prefetch per column; 16-byte aligned since begin is a multiple of the
+            // block and columns are cudaMalloc'd; the size is rounded down, so it stays in bounds)
+            std::ostringstream pf;
+            pf << "static __device__ __forceinline__ void grp" << gid << "_" << kModeName[mode]
+               << "_pf(const ExaPM& pm, const int begin) {\n"
+                  "  const long long n = pm.n_inst - begin < EXA_BLOCK ? pm.n_inst - begin : EXA_BLOCK;\n"
+                  "  const void* p = nullptr;\n  int es = 0;\n  switch (threadIdx.x & 31) {\n";
+            int lane_no = 0;
+            for (int f : all_fields)
+                pf << "    case " << lane_no++ << ": p = pm.f[" << f << "]; es = "
+                   << (grp.ftype[f] == EXA_FIELD_I32 ? 4 : 8) << "; break;\n";
+            for (int f : fcopy) pf << "    case " << lane_no++ << ": p = pm.f32[" << f << "]; es = 4; break;\n";
+            pf << "    default: return;\n  }\n"
+                  "  const unsigned bytes = (unsigned)(n * es) & ~15u;\n"
+                  "  if (bytes) asm volatile(\"cp.async.bulk.prefetch.L2.global [%0], %1;\" :: \"l\"((const char*)p + (long long)begin * es), \"r\"(bytes) : \"memory\");\n"
+                  "}\n";
+            // _pfx: the x and y lines instance k gathers, prefetched into L2 (indices were checked
+            // by the structure pass at creation, so every address is inside x or y)
+            pf << "static __device__ __forceinline__ void grp" << gid << "_" << kModeName[mode]
+               << "_pfx(const ExaPM& pm, const int k, const double* __restrict__ x, const double* __restrict__ y) {\n"
+                  "  const long long kk = k;\n";
+            std::set<int> ixf;
+            for (int sy : syms) fields_of_idx(grp.sym_root[sy].first, grp.sym_root[sy].second, ixf);
+            std::vector<int> yrows;
+            for (int pos : act)
+                if (want[pos].hess && pat(pos).kind != EXA_OBJ) {
+                    yrows.push_back(pos);
+                    if (pat(pos).kind == EXA_AUG) fields_of_idx(pos, pat(pos).row_root, ixf);
+                }
+            for (int f : ixf)
+                pf << "  const int F" << f << " = __ldg((const int*)pm.f[" << f << "] + k);\n";
+            for (int sy : syms)
+                pf << "  asm volatile(\"prefetch.global.L2 [%0];\" :: \"l\"(x + pm.xoff + "
+                   << idx_expr(grp.sym_root[sy].first, grp.sym_root[sy].second) << "));\n";
+            for (int pos : yrows) {
+                const std::string row = pat(pos).kind == EXA_CON
+                                            ? "pm.rbase[" + std::to_string(pos) + "] + kk"
+                                            : "pm.rbase[" + std::to_string(pos) + "] + " + idx_expr(pos, pat(pos).row_root);
+                pf << "  asm volatile(\"prefetch.global.L2 [%0];\" :: \"l\"(y + " << row << "));\n";
+            }
+            pf << "}\n";
+            pf_text = pf.str();
         }
         if (want_struct) {
             os << "  if (!act) return;\n";
@@ -1387,6 +1434,7 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
     src << "// generated by exa_lower.cpp (" << (mixed ? "mixed FP32/FP64" : "FP64") << ")\n";
     src << kDeviceStructs << "\n";
     src << "#define EXA_BLOCK " << opt.block << "\n";
+    src << "#define EXA_PF_DEPTH " << opt.prefetch << "\n";
     if (opt.min_blocks > 0) src << "#define EXA_BOUNDS __launch_bounds__(EXA_BLOCK, " << opt.min_blocks << ")\n";
     else src << "#define EXA_BOUNDS __launch_bounds__(EXA_BLOCK)\n";
     if (mixed) src << kMixedHelpers;
@@ -1416,6 +1464,7 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
             gl.push_back((int)gi);
             Emitter e(pats, groups[gi], graphs[gi], pgs[gi], opt);
             src << e.function((int)gi, (Mode)m);
+            src << e.pf_text;
         }
         const bool objred = (m == M_OBJ || mode_all(m) || m == M_FIRST);
         // Tile loop: with gridDim.x == ntiles every CTA takes one tile; a smaller (persistent) grid
@@ -1423,7 +1472,7 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
         src << "extern \"C\" __global__ void EXA_BOUNDS exa_" << kModeName[m]
             << "(const ExaTile* __restrict__ tiles, const int ntiles, const ExaPM* __restrict__ pms,"
                " const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ th,"
-               " const double sigma, const ExaOut o, const ExaStructOut so) {\n";
+               " const double sigma, const ExaOut o, const ExaStructOut so, const int pfd) {\n";
         if (objred) src << "  __shared__ double red[EXA_BLOCK / 32];\n";
         int smax = 1;  // widest slot block staged in this kernel
         for (const Pattern &p : pats)
@@ -1435,8 +1484,29 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
                    "  double* __restrict__ ws = stage + (threadIdx.x & ~31u) * " << smax << ";\n";
         else
             src << "  double* ws = nullptr;\n";
-        src << "  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {\n"
-               "  const ExaTile tl = tiles[t];\n"
+        src << "  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {\n";
+        if (opt.prefetch >= 1 && m != M_STRUCT) {  // data columns of the tile 2 x pfd ahead: warp 0
+            src << "  if (threadIdx.x < 32 && pfd > 0) {\n"
+                   "    const long long tp = (long long)t + 2LL * pfd;\n"
+                   "    if (tp < ntiles) {\n"
+                   "      const ExaTile tn = tiles[tp];\n"
+                   "      const ExaPM& pn = pms[tn.pm];\n"
+                   "      switch (pn.grp) {\n";
+            for (int gi : gl) src << "        case " << gi << ": grp" << gi << "_" << kModeName[m] << "_pf(pn, tn.begin); break;\n";
+            src << "        default: break;\n      }\n    }\n  }\n";
+        }
+        if (opt.prefetch >= 2 && m != M_STRUCT) {  // x and y lines of the tile pfd ahead: every thread
+            src << "  if (pfd > 0) {\n"
+                   "    const long long tq = (long long)t + pfd;\n"
+                   "    if (tq < ntiles) {\n"
+                   "      const ExaTile tn = tiles[tq];\n"
+                   "      const ExaPM& pn = pms[tn.pm];\n"
+                   "      const int kq = tn.begin + (int)threadIdx.x;\n"
+                   "      if (kq < pn.n_inst) switch (pn.grp) {\n";
+            for (int gi : gl) src << "        case " << gi << ": grp" << gi << "_" << kModeName[m] << "_pfx(pn, kq, x, y); break;\n";
+            src << "        default: break;\n      }\n    }\n  }\n";
+        }
+        src << "  const ExaTile tl = tiles[t];\n"
                "  const ExaPM& pm = pms[tl.pm];\n"
                "  const int k0 = tl.begin + (int)threadIdx.x;\n"
                "  const bool act = k0 < pm.n_inst;\n"

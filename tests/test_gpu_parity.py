@@ -102,13 +102,21 @@ def test_parity_unfused(name):
     check_model(flat, x, y, s, flags=_B().EXA_FLAG_NO_FUSE)
 
 
-@pytest.mark.parametrize("grid_factor", [1, 2])
-def test_parity_persistent_grid(grid_factor):
-    """A persistent grid (CTAs loop over the tile list) gives the same results."""
+@pytest.mark.parametrize("grid_factor,pf", [(1, 0), (2, 0), (1, 1), (1, 2), (-1, 2), (2, 2)])
+def test_parity_persistent_grid(grid_factor, pf):
+    """A persistent grid (CTAs loop over the tile list) gives the same results, with and without
+    the L2 prefetch of later tiles' data columns (pf 1) and gather lines (pf 2); one CTA per tile
+    (grid_factor -1) prefetches one wave of resident CTAs ahead."""
+    B = _B()
+    flags = {0: 0, 1: B.EXA_FLAG_PF_COLUMNS, 2: B.EXA_FLAG_PF_GATHERS}[pf]
     wl = synth.pde(600)  # ~5600 tiles of 128: more than two waves of resident CTAs
     x, y, s = synth.pde_point(wl, 1)
-    m, _ = check_model(wl.flat, x, y, s, grid_factor=grid_factor)
-    assert m.stat("eval_persist") == grid_factor and m.stat("eval_grid") < m.stat("eval_tiles")
+    m, _ = check_model(wl.flat, x, y, s, grid_factor=grid_factor, flags=flags)
+    assert m.stat("eval_prefetch") == pf
+    if grid_factor > 0:
+        assert m.stat("eval_persist") == grid_factor and m.stat("eval_grid") < m.stat("eval_tiles")
+    else:
+        assert m.stat("eval_grid") == m.stat("eval_tiles")
 
 
 def test_autotuned_model():
