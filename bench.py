@@ -58,10 +58,11 @@ def make_batch(rank: int, n_inst: int = 256):
     return wls, pts
 
 
-def algorithmic_bytes(flats, nnzj, nnzh, nvar, ncon, naug, nnzg):
+def algorithmic_bytes(flats, nnzj, nnzh, nvar, ncon, naug, nnzg, mixed=False):
     """Bytes one evaluation of every pattern must move at least: x and y read once, every data
     column read once (columns shared by several patterns count once), every COO slot, constraint
-    value, augmentation term and gradient slot written once."""
+    value, augmentation term and gradient slot written once.  In mixed precision the f64 data
+    columns count at 4 bytes per value (the kernel may read FP32 copies of them)."""
     data = 0
     for fl in flats:
         seen = set()
@@ -70,7 +71,7 @@ def algorithmic_bytes(flats, nnzj, nnzh, nvar, ncon, naug, nnzg):
                 key = f.__array_interface__["data"][0]
                 if key not in seen:
                     seen.add(key)
-                    data += f.nbytes
+                    data += f.nbytes // 2 if (mixed and f.dtype == np.float64) else f.nbytes
     return 8 * nvar + 8 * ncon + data + 8 * (nnzj + nnzh) + 8 * ncon + 8 * naug + 8 * nnzg
 
 
@@ -355,7 +356,8 @@ def measure_model(B, torch, timed, flat, pts, precision, local, peak_hbm, ref=No
         kern_ms.append(timed(kern, calls_for(timed, kern)))
         jh_ms.append(timed(jh, calls_for(timed, jh)))
     naug, nobj = pattern_counts([flat])
-    nbytes = algorithmic_bytes([flat], m.nnzj, m.nnzh, m.nvar, m.ncon, naug, nobj)
+    nbytes = algorithmic_bytes([flat], m.nnzj, m.nnzh, m.nvar, m.ncon, naug, nobj,
+                               mixed=precision == B.EXA_MIXED_FP32)
     nnz = m.nnzj + m.nnzh
     st, kt, jt = float(np.mean(step_ms)), float(np.mean(kern_ms)), float(np.mean(jh_ms))
     rec = {"nnz": nnz, "step_ms": st, "step_nnz_per_s": nnz / (st * 1e-3), "kernel_ms": kt,
@@ -515,7 +517,7 @@ def run_exa(args):
     # Jacobian + Hessian callbacks alone (exa_jac_coord + exa_hess_coord)
     jh_ms = timed(lambda: (m.exa_jac_coord(xt, jac), m.exa_hess_coord(xt, yt, sigma, hess)), max(5, min(args.steps, 200)))
     naug, nobj = pattern_counts(flats)
-    nbytes = algorithmic_bytes(flats, m.nnzj, m.nnzh, m.nvar, m.ncon, naug, nobj)
+    nbytes = algorithmic_bytes(flats, m.nnzj, m.nnzh, m.nvar, m.ncon, naug, nobj, mixed=prec == B.EXA_MIXED_FP32)
     # bytes of the whole step's outputs beyond the kernel's: the dense gradient, the CSC values
     # (each written once) and the objective
     step_bytes = nbytes + 8 * (m.nvar + m.nnzj_csc + m.nnzh_csc + 1)
@@ -530,6 +532,11 @@ def run_exa(args):
                 "step_hbm_frac": step_bytes / (ms * 1e-3) / 1e9 / peak}
     phase("FP64 peak probe")
     fp64 = measure_fp64_peak(B, local)
+    # write-only HBM rate (the evaluation kernels' traffic is mostly writes): a 4 GiB memset
+    wbuf = torch.empty(1 << 29, dtype=torch.float64, device=dev)
+    wbuf.zero_()
+    hbm_write_gbs = wbuf.numel() * 8 / (timed(lambda: wbuf.zero_(), 5) * 1e-3) / 1e9
+    del wbuf
     if ctr and ctr.get("fp64_inst_per_nnz"):
         # the FP64 pipe bounds this kernel when its FP64 instruction rate is the larger fraction of
         # its peak (DMUL and DADD take a pipe slot like DFMA, so instructions, not flops, are counted)
@@ -557,7 +564,8 @@ def run_exa(args):
               "eval_chunks": m.stat("eval_chunks"),
               "nnzh_compressed": m.stat("nnzh_compressed"), "grad_compact": m.stat("grad_compact"),
               "tuned_options": ",".join(str(v) for v in m.tuned_options().values()),
-              "device_bytes": m.stat("device_bytes"), "fp64_peak": fp64}
+              "device_bytes": m.stat("device_bytes"), "fp64_peak": fp64,
+              "hbm_write_only_gbs": hbm_write_gbs}
     if not args.no_extras:
         phase("extras: products")
         v = torch.randn(m.nvar, dtype=torch.float64, device=dev)
@@ -614,7 +622,9 @@ def run_exa(args):
         extras[f"{tag}_step_ms"] = ms2
         extras[f"{tag}_nnz_per_s"] = nnz_rank / (ms2 * 1e-3)
         extras[f"{tag}_kernel_ms"] = k2
-        extras[f"{tag}_kernel_hbm_frac"] = nbytes / (k2 * 1e-3) / 1e9 / peak
+        nbytes2 = algorithmic_bytes(flats, m.nnzj, m.nnzh, m.nvar, m.ncon, naug, nobj, mixed=tag == "mixed")
+        extras[f"{tag}_kernel_hbm_frac"] = nbytes2 / (k2 * 1e-3) / 1e9 / peak
+        extras[f"{tag}_algorithmic_bytes"] = nbytes2
         extras[f"{tag}_eval_regs"] = m2.stat("eval_regs")
         extras[f"{tag}_tuned_options"] = ",".join(str(v) for v in m2.tuned_options().values())
         m2.destroy()
@@ -664,6 +674,10 @@ def run_exa(args):
     e2e_ms = timed(e2e_step, max(3, min(args.steps // 2, 100)))
     e2e_ms = reduce_max(e2e_ms, pg, dev)
     d2h = sum(t.numel() for t in host.values()) * 8
+    h2d = int(xh.numel() * 8 + yh.numel() * 8)
+    # the host link that bounds this step, measured (include/exa_probe.h)
+    link = B.exa_probe_host_link(local, 1 << 30)
+    link_ms = 1e3 * (h2d / link["h2d_bytes_per_s"] + d2h / link["d2h_bytes_per_s"])
     # the same call with only f, g and c coming back (the derivative arrays left on the device)
     fgc = dict(f=host["f"], g=host["g"], c=host["c"])
     e2e_fgc = lambda: m.exa_eval_all_host(xh, yh, sigma, jac=jac, hess=hess, jac_csc=jcsc, hess_csc=hcsc, **fgc)
@@ -690,8 +704,10 @@ def run_exa(args):
                    "l2": "inputs+outputs ~2 GB per step > 129 MB L2 (no flush needed)",
                    "e2e": "x, y in and every output (f, g, c, J and H in COO and CSC) out, pinned host memory"},
         "e2e": {"value": whole_job_rate(nnz_rank, ws, e2e_ms), "unit": UNIT,
-                "h2d_bytes_per_step": int(xh.numel() * 8 + yh.numel() * 8),
-                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
+                "link": {"h2d_gbs": link["h2d_bytes_per_s"] / 1e9, "d2h_gbs": link["d2h_bytes_per_s"] / 1e9,
+                         "copy_ms": link_ms, "copy_frac_of_step": link_ms / e2e_ms,
+                         "how": "exa_probe_host_link: 1 GiB page-locked cudaMemcpyAsync each way, best of 3"}},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roofline,
         "cpu_baseline": cpu,

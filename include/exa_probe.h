@@ -1,10 +1,11 @@
 /*
  * exa_probe.h -- measurement probe of the GB300 derivative-evaluation library.
  *
- * Not a callback of the paper's interface: this call measures a hardware rate that bounds the
- * library's FP64 kernels, so that their roofline is stated against a measured peak rather than a
- * derived one.  The generated FP64 evaluation kernels issue DFMA, DMUL and DADD instructions, all
- * on the FP64 pipe; on GB300 that pipe, not memory bandwidth, is their binding unit.
+ * Not callbacks of the paper's interface: these calls measure hardware rates that bound the
+ * library's work, so that it is stated against measured peaks rather than derived ones.  The
+ * generated FP64 evaluation kernels issue DFMA, DMUL and DADD instructions, all on the FP64 pipe;
+ * on GB300 that pipe, not memory bandwidth, is their binding unit.  The end-to-end call with host
+ * buffers is bound by the host link.
  */
 #ifndef EXA_PROBE_H
 #define EXA_PROBE_H
@@ -27,6 +28,17 @@ extern "C" {
  * failed); the outputs are then left untouched. */
 exa_status exa_probe_fp64_fma(int32_t device, double target_ms, double *inst_per_s, double *ms,
                               int32_t *sms);
+
+/* Measures the host link of `device`: cudaMemcpyAsync between a page-locked host buffer and a
+ * device buffer of `bytes` bytes each (clamped to 64 MiB..4 GiB), one warm-up copy each way, then
+ * the best of three timed copies per direction (CUDA events).  Outputs (host pointers, any may be
+ * NULL): host-to-device and device-to-host bytes per second.  The end-to-end calls of this library
+ * (exa_eval_all_host) move their inputs and outputs over this link.  Allocates and frees both
+ * buffers; synchronizes the device.  Errors: EXA_E_INVALID (bad device ordinal), EXA_E_OOM (an
+ * allocation failed), EXA_E_CUDA (a copy or timing call failed); the outputs are then left
+ * untouched. */
+exa_status exa_probe_host_link(int32_t device, int64_t bytes, double *h2d_bytes_per_s,
+                               double *d2h_bytes_per_s);
 
 #ifdef __cplusplus
 }

@@ -37,7 +37,7 @@ EXPORTS = ["exa_create", "exa_create_batch", "exa_destroy", "exa_last_error", "e
            "exa_eval_all", "exa_eval_all_host", "exa_jprod", "exa_jtprod", "exa_hprod", "exa_check_status",
            "exa_compile_check", "exa_stat"]
 # Every function include/exa_probe.h declares (measurement, not part of the evaluation path).
-PROBE_EXPORTS = ["exa_probe_fp64_fma"]
+PROBE_EXPORTS = ["exa_probe_fp64_fma", "exa_probe_host_link"]
 
 
 class exa_vnode(C.Structure):
@@ -119,6 +119,7 @@ def load():
             "exa_stat": [vp, C.c_char_p, C.POINTER(C.c_double)],
             "exa_probe_fp64_fma": [C.c_int32, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                    C.POINTER(C.c_int32)],
+            "exa_probe_host_link": [C.c_int32, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double)],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -220,6 +221,17 @@ def exa_probe_fp64_fma(device: int = 0, target_ms: float = 300.0) -> dict:
     if rc != EXA_OK:
         raise ExaError(rc, "FP64 FMA probe failed")
     return {"dfma_per_s": r.value, "ms": t.value, "sms": n.value}
+
+
+def exa_probe_host_link(device: int = 0, nbytes: int = 1 << 30) -> dict:
+    """Measured host link of the device (include/exa_probe.h): page-locked host <-> device copy
+    rates in bytes per second."""
+    lib = load()
+    h2d, d2h = C.c_double(), C.c_double()
+    rc = lib.exa_probe_host_link(device, int(nbytes), C.byref(h2d), C.byref(d2h))
+    if rc != EXA_OK:
+        raise ExaError(rc, "host link probe failed")
+    return {"h2d_bytes_per_s": h2d.value, "d2h_bytes_per_s": d2h.value}
 
 
 class Model:

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "../../include/exa_probe.h"
 
@@ -79,5 +80,48 @@ extern "C" exa_status exa_probe_fp64_fma(int32_t device, double target_ms, doubl
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(sink);
+    return st;
+}
+
+extern "C" exa_status exa_probe_host_link(int32_t device, int64_t bytes, double *h2d_bytes_per_s,
+                                          double *d2h_bytes_per_s) {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return EXA_E_INVALID;
+    if (cudaSetDevice(device) != cudaSuccess) return EXA_E_CUDA;
+    bytes = std::min<int64_t>(4LL << 30, std::max<int64_t>(64LL << 20, bytes));
+    void *h = nullptr, *d = nullptr;
+    if (cudaHostAlloc(&h, (size_t)bytes, cudaHostAllocDefault) != cudaSuccess) return EXA_E_OOM;
+    if (cudaMalloc(&d, (size_t)bytes) != cudaSuccess) {
+        cudaFreeHost(h);
+        return EXA_E_OOM;
+    }
+    std::memset(h, 0, (size_t)bytes);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    exa_status st = EXA_OK;
+    double best[2] = {0.0, 0.0};
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = EXA_E_CUDA;
+    for (int dir = 0; dir < 2 && st == EXA_OK; dir++) {
+        void *dst = dir == 0 ? d : h;
+        const void *src = dir == 0 ? h : d;
+        const cudaMemcpyKind kind = dir == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+        for (int r = 0; r < 4 && st == EXA_OK; r++) {  // the first copy warms up
+            float t = 0.0f;
+            if (cudaEventRecord(e0) != cudaSuccess || cudaMemcpyAsync(dst, src, (size_t)bytes, kind, 0) != cudaSuccess ||
+                cudaEventRecord(e1) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+                st = EXA_E_CUDA;
+                break;
+            }
+            if (r > 0 && t > 0.0f) best[dir] = std::max(best[dir], (double)bytes / (t * 1e-3));
+        }
+    }
+    if (st == EXA_OK) {
+        if (h2d_bytes_per_s) *h2d_bytes_per_s = best[0];
+        if (d2h_bytes_per_s) *d2h_bytes_per_s = best[1];
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(d);
+    cudaFreeHost(h);
     return st;
 }

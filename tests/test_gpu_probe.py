@@ -19,3 +19,11 @@ def test_fp64_fma_probe_is_plausible():
     assert 50.0 <= a["ms"] <= 400.0
     with pytest.raises(B.ExaError):
         B.exa_probe_fp64_fma(999, 100.0)
+
+
+def test_host_link_probe_is_plausible():
+    """Both directions of the host link measure between 10 GB/s and 2 TB/s."""
+    from paper_2608_16265_gb300 import binding as B
+    r = B.exa_probe_host_link(0, 256 << 20)
+    for k in ("h2d_bytes_per_s", "d2h_bytes_per_s"):
+        assert 1e10 < r[k] < 2e12, r
