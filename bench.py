@@ -448,7 +448,7 @@ def run_exa(args):
         vals = [int(v) for v in args.pin.split(",")]
         b_, mb_, gf_, fl_ = vals[:4]
         pin = dict(block=b_, min_blocks=mb_, grid_factor=gf_, flags=fl_ | B.EXA_FLAG_NO_TUNE,
-                   chunks=vals[4] if len(vals) > 4 else 1)
+                   chunks=vals[4] if len(vals) > 4 else 1, wave_pct=vals[5] if len(vals) > 5 else 0)
     m = B.exa_create_batch(flats, precision=prec, device=local, **pin)
     torch.cuda.synchronize()
     t_create = time.perf_counter() - t0
@@ -744,7 +744,7 @@ def main(argv=None):
                     "call (J and H COO) this many times after one untimed call, print its sizes, exit")
     ap.add_argument("--workload", default="batch", help="profiling modes only (--steps-only, --kernel-only): "
                     "'batch' (the benchmark workload) or one model of a workload family, e.g. pde_n2000")
-    ap.add_argument("--pin", default="", help="block,min_blocks,grid_factor,flags[,chunks]: fixed launch configuration "
+    ap.add_argument("--pin", default="", help="block,min_blocks,grid_factor,flags[,chunks[,wave_pct]]: fixed launch configuration "
                     "(extras.tuned_options of an earlier run) instead of autotuning, for profiling runs")
     args = ap.parse_args(argv)
     if args.workload != "batch" and not (args.steps_only or args.kernel_only):

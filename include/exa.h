@@ -146,6 +146,10 @@ typedef struct {
     int32_t chunks;        /* exa_eval_all over this many contiguous groups of batch members, the
                               reductions of one group overlapping the evaluation of the next,
                               0..16; 0 = chosen by the autotuner (1 when tuning is off) */
+    int32_t wave_pct;      /* 1..99: the evaluation kernels run as a persistent grid of this
+                              percentage of one wave of resident CTAs, leaving SM room for the
+                              reductions of the previous member chunk to run beside them;
+                              0 = per grid_factor, or chosen by the autotuner */
 } exa_options;
 
 enum {
@@ -307,7 +311,7 @@ exa_status exa_compile_check(const exa_model_desc *desc, const exa_options *opt,
 
 /* Named statistics (host values): "nvrtc_ms", "create_ms", "tune_ms", "eval_regs", "eval_block",
  * "eval_regs_jac", "eval_regs_hess", "eval_tiles", "eval_grid", "eval_persist", "eval_min_blocks",
- * "eval_split", "eval_chunks", "eval_upfront", "eval_prefetch", "graph_kernels", "csc_direct",
+ * "eval_split", "eval_chunks", "eval_upfront", "eval_prefetch", "eval_wave_pct", "graph_kernels", "csc_direct",
  * "hess_compressed", "nnzh_compressed", "grad_compact", "device_bytes", "n_patterns", "batch_members".
  * Unknown key: EXA_E_INVALID. */
 exa_status exa_stat(const exa_model *m, const char *key, double *value);

@@ -71,7 +71,7 @@ class exa_model_desc(C.Structure):
 class exa_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("device", C.c_int32), ("block_threads", C.c_int32),
                 ("flags", C.c_int32), ("grid_factor", C.c_int32), ("min_blocks", C.c_int32),
-                ("chunks", C.c_int32)]
+                ("chunks", C.c_int32), ("wave_pct", C.c_int32)]
 
 
 _lib = None
@@ -167,8 +167,8 @@ class _Desc:
                                    theta.ctypes.data_as(C.POINTER(C.c_double)), len(flat.patterns), 0, pats)
 
 
-def _opts(precision, block, flags, device, grid_factor=0, min_blocks=0, chunks=0):
-    return exa_options(precision, device, block, flags, grid_factor, min_blocks, chunks)
+def _opts(precision, block, flags, device, grid_factor=0, min_blocks=0, chunks=0, wave_pct=0):
+    return exa_options(precision, device, block, flags, grid_factor, min_blocks, chunks, wave_pct)
 
 
 def _ptr(t) -> Optional[int]:
@@ -184,18 +184,19 @@ def _stream():
 
 # ------------------------------------------------------------------ ABI-named functions
 def exa_create(flat: ir.FlatModel, precision: int = EXA_FP64, block: int = 0, flags: int = 0,
-               device: int = 0, grid_factor: int = 0, min_blocks: int = 0, chunks: int = 0) -> "Model":
-    return exa_create_batch([flat], precision, block, flags, device, grid_factor, min_blocks, chunks)
+               device: int = 0, grid_factor: int = 0, min_blocks: int = 0, chunks: int = 0,
+               wave_pct: int = 0) -> "Model":
+    return exa_create_batch([flat], precision, block, flags, device, grid_factor, min_blocks, chunks, wave_pct)
 
 
 def exa_create_batch(flats: Sequence[ir.FlatModel], precision: int = EXA_FP64, block: int = 0,
                      flags: int = 0, device: int = 0, grid_factor: int = 0, min_blocks: int = 0,
-                     chunks: int = 0) -> "Model":
+                     chunks: int = 0, wave_pct: int = 0) -> "Model":
     lib = load()
     descs = [_Desc(f) for f in flats]
     arr = (C.POINTER(exa_model_desc) * len(descs))(*[C.pointer(d.desc) for d in descs])
     h = C.c_void_p()
-    opt = _opts(precision, block, flags, device, grid_factor, min_blocks, chunks)
+    opt = _opts(precision, block, flags, device, grid_factor, min_blocks, chunks, wave_pct)
     rc = lib.exa_create_batch(arr, len(descs), C.byref(opt), C.byref(h))
     if rc != EXA_OK:
         raise ExaError(rc, lib.exa_create_error().decode())
@@ -281,7 +282,8 @@ class Model:
         flags |= EXA_FLAG_PF_GATHERS if pf == 2 else EXA_FLAG_PF_COLUMNS if pf == 1 else 0
         persist = int(self.stat("eval_persist"))
         return dict(block=int(self.stat("eval_block")), min_blocks=int(self.stat("eval_min_blocks")),
-                    grid_factor=persist if persist > 0 else -1, flags=flags, chunks=int(self.stat("eval_chunks")))
+                    grid_factor=persist if persist > 0 else -1, flags=flags, chunks=int(self.stat("eval_chunks")),
+                    wave_pct=int(self.stat("eval_wave_pct")))
 
     def stat(self, key: str) -> float:
         v = C.c_double()

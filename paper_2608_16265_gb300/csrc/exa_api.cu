@@ -326,6 +326,7 @@ struct exa_model {
     int min_blocks = 0;           // launch-bounds minimum CTAs per SM chosen by the tuner
     bool by_pattern = true;       // generated code emits each pattern's arithmetic next to its outputs
     int prefetch = 0;             // L2 prefetch depth of the generated tile loop (CodegenOptions)
+    int wave_pct = 0;             // persistent evaluation grid of this % of one wave (0: off)
     int pfd[exa::M_COUNT] = {};   // prefetch distance in tiles per kernel kind (0: none)
     bool split_all = false;       // exa_eval_all: first- and second-order kernels instead of one
     bool csc_direct = false;      // duplicate-free CSC written by the evaluation kernel (scatter)
@@ -367,6 +368,7 @@ struct exa_model {
     // first position of b's part of every reduction's output or work list.
     int nchunks = 1;
     bool chunks_fixed = false;  // given at creation: the tuner keeps it
+    bool wave_fixed = false;    // wave_pct given at creation: the tuner keeps it
     std::vector<int> chunk_b;  // member boundaries of the chunks (nchunks + 1)
     std::vector<int> mb_tile[exa::M_COUNT];
     std::vector<int> mb_jcsc, mb_hcsc, mb_jmulti, mb_hmulti, mb_hcmulti, mb_gseg, mb_arow;
@@ -961,6 +963,10 @@ exa_status apply_grid(exa_model *m, int factor) {
         const long long wave = (long long)std::max(occ, 1) * sms;
         const long long g = (long long)std::max(factor, 0) * wave;
         if (factor > 0 && g < m->ntiles[k]) m->grid[k] = (int)g;
+        if (m->wave_pct > 0) {  // less than one wave: room on every SM for work on other streams
+            const long long gp = std::max<long long>(1, (wave * m->wave_pct + 99) / 100);
+            if (gp < m->ntiles[k]) m->grid[k] = (int)gp;
+        }
         if (m->prefetch > 0) m->pfd[k] = (int)std::min<long long>(m->grid[k] < m->ntiles[k] ? m->grid[k] : wave, 1 << 30);
     }
     return EXA_OK;
@@ -1138,13 +1144,19 @@ exa_status autotune(exa_model *m) {
     CR(S.get(&hc, m->nnzh_csc));
     double best_step = 1e30;
     bool best_split = false, best_direct = false, best_hc = m->use_hcomp;
-    int best_chunks = m->nchunks;
-    for (int nch : {1, 4, 8, 16})
+    int best_chunks = m->nchunks, best_wave = m->wave_pct;
+    const int init_wave = m->wave_pct;
+    for (int nch : {1, 2, 4, 8, 16})
+    for (int wave : {0, 75, 50})
     for (int hcv = 0; hcv < (m->has_hcomp ? 2 : 1); hcv++)
     for (int split = 0; split < 2; split++)
         for (int direct = 0; direct < 2; direct++) {
             if (direct && m->nnzj_csc != m->nnzj && m->nnzh_csc != m->nnzh) continue;
             if (nch > m->nb || (m->chunks_fixed && nch != best_chunks)) continue;
+            // a partial-wave grid only pays when chunks give the reductions something to overlap
+            if (m->wave_fixed ? wave != 0 : (wave && nch == 1)) continue;
+            m->wave_pct = m->wave_fixed ? init_wave : wave;
+            if (exa_status e = apply_grid(m, best_factor)) return e;
             set_chunks(m, nch);
             m->split_all = split;
             m->csc_direct = direct;
@@ -1163,8 +1175,11 @@ exa_status autotune(exa_model *m) {
                 best_direct = direct;
                 best_hc = hcv;
                 best_chunks = nch;
+                best_wave = m->wave_pct;
             }
         }
+    m->wave_pct = best_wave;
+    if (exa_status e = apply_grid(m, best_factor)) return e;
     set_chunks(m, best_chunks);
     m->split_all = best_split;
     m->csc_direct = best_direct;
@@ -1285,6 +1300,9 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     if (o.grid_factor < -1 || o.grid_factor > 64) return fail(m, EXA_E_INVALID, "grid_factor must be in [-1, 64]");
     if (o.min_blocks < 0 || o.min_blocks > 32) return fail(m, EXA_E_INVALID, "min_blocks must be in [0, 32]");
     if (o.chunks < 0 || o.chunks > 16) return fail(m, EXA_E_INVALID, "chunks must be in [0, 16]");
+    if (o.wave_pct < 0 || o.wave_pct > 99) return fail(m, EXA_E_INVALID, "wave_pct must be in [0, 99]");
+    m->wave_pct = o.wave_pct;
+    m->wave_fixed = o.wave_pct != 0;
     m->split_all = (o.flags & EXA_FLAG_SPLIT) != 0;
     m->by_pattern = (o.flags & EXA_FLAG_UPFRONT) == 0;
     m->csc_direct = (o.flags & EXA_FLAG_CSC_SCATTER) != 0;
@@ -2356,6 +2374,7 @@ exa_status exa_stat(const exa_model *m, const char *key, double *value) {
     else if (k == "eval_chunks") *value = m->nchunks;
     else if (k == "eval_upfront") *value = !m->by_pattern;
     else if (k == "eval_prefetch") *value = m->prefetch;
+    else if (k == "eval_wave_pct") *value = m->wave_pct;
     else if (k == "graph_kernels") *value = m->graph_kernels;
     else if (k == "grad_compact") *value = m->grad_compact;
     else if (k == "nnzh_compressed") *value = (double)m->nnzhc;

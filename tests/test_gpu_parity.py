@@ -31,11 +31,12 @@ def _np(t):
     return t.detach().cpu().numpy()
 
 
-def check_model(flat, x, y, s, block=0, tol=TOL, o=None, flags=0, precision=0, grid_factor=0, min_blocks=0):
+def check_model(flat, x, y, s, block=0, tol=TOL, o=None, flags=0, precision=0, grid_factor=0, min_blocks=0,
+                wave_pct=0):
     B = _B()
     o = o or oracle.Oracle(flat)
     m = B.exa_create(flat, block=block, flags=flags, precision=precision, grid_factor=grid_factor,
-                     min_blocks=min_blocks)
+                     min_blocks=min_blocks, wave_pct=wave_pct)
     assert (m.nvar, m.ncon, m.nnzj, m.nnzh, m.nnzj_csc, m.nnzh_csc) == \
         (o.nvar, o.ncon, o.nnzj, o.nnzh, o.nnzj_csc, o.nnzh_csc)
     # structures: bit-exact
@@ -102,18 +103,22 @@ def test_parity_unfused(name):
     check_model(flat, x, y, s, flags=_B().EXA_FLAG_NO_FUSE)
 
 
-@pytest.mark.parametrize("grid_factor,pf", [(1, 0), (2, 0), (1, 1), (1, 2), (-1, 2), (2, 2)])
-def test_parity_persistent_grid(grid_factor, pf):
+@pytest.mark.parametrize("grid_factor,pf,wave", [(1, 0, 0), (2, 0, 0), (1, 1, 0), (1, 2, 0), (-1, 2, 0), (2, 2, 0),
+                                                 (1, 0, 50), (1, 2, 75)])
+def test_parity_persistent_grid(grid_factor, pf, wave):
     """A persistent grid (CTAs loop over the tile list) gives the same results, with and without
     the L2 prefetch of later tiles' data columns (pf 1) and gather lines (pf 2); one CTA per tile
-    (grid_factor -1) prefetches one wave of resident CTAs ahead."""
+    (grid_factor -1) prefetches one wave of resident CTAs ahead; a grid of part of one wave
+    (wave_pct) leaves room on the SMs."""
     B = _B()
     flags = {0: 0, 1: B.EXA_FLAG_PF_COLUMNS, 2: B.EXA_FLAG_PF_GATHERS}[pf]
     wl = synth.pde(600)  # ~5600 tiles of 128: more than two waves of resident CTAs
     x, y, s = synth.pde_point(wl, 1)
-    m, _ = check_model(wl.flat, x, y, s, grid_factor=grid_factor, flags=flags)
-    assert m.stat("eval_prefetch") == pf
-    if grid_factor > 0:
+    m, _ = check_model(wl.flat, x, y, s, grid_factor=grid_factor, flags=flags, wave_pct=wave)
+    assert m.stat("eval_prefetch") == pf and m.stat("eval_wave_pct") == wave
+    if wave:
+        assert m.stat("eval_grid") < m.stat("eval_tiles")
+    elif grid_factor > 0:
         assert m.stat("eval_persist") == grid_factor and m.stat("eval_grid") < m.stat("eval_tiles")
     else:
         assert m.stat("eval_grid") == m.stat("eval_tiles")
@@ -309,6 +314,7 @@ BATCH_OPTIONS = {
     "bench_tuned": dict(block=128, min_blocks=8, grid_factor=-1, flags=2 | 128, chunks=1),
     "split_scatter": dict(flags=2 | 16 | 32),
     "no_hcomp_chunks": dict(flags=2 | 64, chunks=3),
+    "chunks_partial_wave_prefetch": dict(flags=2 | 512, chunks=4, wave_pct=50, block=32),
 }
 
 
