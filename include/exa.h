@@ -217,8 +217,9 @@ exa_status exa_set_theta(exa_model *m, const double *theta, int64_t npar);
 exa_status exa_set_stream(exa_model *m, void *stream);
 
 /* ------------------------------------------------------------------ callbacks (Sec. 2.1) */
-/* f[0] = f(x).  f: one device double.  Objective terms are reduced in FP64 in two stages
- * (per-CTA partial sums, then one ordered sum), Sec. 7.2.3. */
+/* f[0] = f(x).  f: one device double.  Objective terms are reduced in FP64 in two stages (every
+ * CTA sums the terms of all its tiles into one partial, then one ordered sum of the partials),
+ * Sec. 7.2.3. */
 exa_status exa_obj(exa_model *m, const double *x, double *f);
 
 /* f[0] = f(x), like exa_obj, but without the scratch buffer that exa_create allocates: the
@@ -226,11 +227,13 @@ exa_status exa_obj(exa_model *m, const double *x, double *f);
  * which loads the library holds until the process exits.  For callers that cannot allocate device
  * memory (their memory belongs to another allocator, or they run where cudaMalloc is not allowed);
  * this call allocates nothing.  The paper has no counterpart; it is an addition of this library.
- *   - Limit: at most 65536 objective tiles, one partial each (EXA_E_UNSUPPORTED beyond, with the
- *     count in the message; f is then left untouched).  Tiles are counted per batch member and
- *     fused pattern group as ceil(objective instances / block), block being the launch shape's
- *     threads per CTA (exa_stat "eval_block"; 64 to 256 when tuned): 65536 tiles are 8,388,608
- *     instances of one pattern at block 128, fewer when a batch has many members or groups.
+ *   - Limit: at most 65536 partial sums, one per CTA of the objective kernel's launch
+ *     (EXA_E_UNSUPPORTED beyond, with the count in the message; f is then left untouched).  With
+ *     one CTA per tile that is one per objective tile, counted per batch member and fused pattern
+ *     group as ceil(objective instances / block), block being the launch shape's threads per CTA
+ *     (exa_stat "eval_block"; 64 to 256 when tuned): 8,388,608 instances of one pattern at block
+ *     128, fewer when a batch has many members or groups; a persistent grid (exa_stat
+ *     "eval_grid") launches fewer CTAs.
  *   - Every call looks up the array's address on the model's device (a CUDA runtime query, no
  *     allocation).  The first call on a device may also load the library's device code there:
  *     make that first call before any stream capture.

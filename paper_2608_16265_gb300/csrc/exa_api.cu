@@ -320,7 +320,6 @@ struct exa_model {
     ExaPM *d_pm = nullptr;
     ExaTile *d_tiles[exa::M_COUNT] = {};
     int ntiles[exa::M_COUNT] = {};
-    int nobj[exa::M_COUNT] = {};  // objective partial sums written by each kernel kind
     int grid[exa::M_COUNT] = {};  // CTAs launched per kernel kind (<= ntiles: persistent tile loop)
     int persist = 0;              // persistent grid factor chosen by the tuner (0: one CTA per tile)
     int min_blocks = 0;           // launch-bounds minimum CTAs per SM chosen by the tuner
@@ -540,6 +539,10 @@ exa_status compile(exa_model *m, const std::string &src) {
 
 // The evaluation kernel of `mode` over its tiles [t0, t1) (t1 < 0: all tiles) on stream st (null:
 // the model stream).
+// CTAs of one launch of kernel kind `mode` over nt tiles; kinds that reduce objective terms write one
+// partial sum per CTA.
+int eval_grid(const exa_model *m, Mode mode, int nt) { return m->grid[mode] > 0 ? std::min(m->grid[mode], nt) : nt; }
+
 exa_status launch_eval(exa_model *m, Mode mode, const double *x, const double *y, double sigma, ExaOut out,
                        int t0 = 0, int t1 = -1, cudaStream_t st = nullptr) {
     if (t1 < 0) t1 = m->ntiles[mode];
@@ -552,7 +555,7 @@ exa_status launch_eval(exa_model *m, Mode mode, const double *x, const double *y
     const ExaTile *tiles = m->d_tiles[mode] + t0;
     int pfd = m->pfd[mode];
     void *args[] = {&tiles, &nt, &m->d_pm, &x, &y, &th, &sigma, &out, &so, &pfd};
-    const int grid = m->grid[mode] > 0 ? std::min(m->grid[mode], nt) : nt;
+    const int grid = eval_grid(m, mode, nt);
     CR(cudaLaunchKernel((const void *)m->fn[mode], dim3(grid), dim3(m->block), args, 0, st ? st : m->stream));
     return EXA_OK;
 }
@@ -917,22 +920,16 @@ exa_status setup_kernels(exa_model *m, int block, int min_blocks = 0) {
     const int ng = (int)m->groups.size(), nb = m->nb;
     for (int k = 0; k < exa::M_COUNT; k++) {
         std::vector<ExaTile> tiles;
-        m->nobj[k] = 0;
         m->mb_tile[k].assign(nb + 1, 0);
         for (int b = 0; b < nb; b++)
             for (int gi = 0; gi < ng; gi++) {
                 if (gi == 0) m->mb_tile[k][b] = (int)tiles.size();
-                bool in = false, part = false;
-                for (int p : m->groups[gi].pats) {
-                    const bool act = exa::pattern_in_mode(m->pats[p], (exa::Mode)k);
-                    in = in || act;
-                    part = part || (act && m->pats[p].kind == EXA_OBJ &&
-                                    (k == exa::M_OBJ || exa::mode_all(k) || k == exa::M_FIRST));
-                }
+                bool in = false;
+                for (int p : m->groups[gi].pats) in = in || exa::pattern_in_mode(m->pats[p], (exa::Mode)k);
                 if (!in) continue;
                 const ExaPM &pm = m->h_pms[(size_t)b * ng + gi];
                 for (i64 s = 0; s < pm.n_inst; s += block)
-                    tiles.push_back({b * ng + gi, (int)s, part ? m->nobj[k]++ : -1});
+                    tiles.push_back({b * ng + gi, (int)s});
             }
         m->ntiles[k] = (int)tiles.size();
         m->mb_tile[k][nb] = m->ntiles[k];
@@ -1014,7 +1011,7 @@ exa_status autotune(exa_model *m) {
     }
     for (int B : blocks) {
         if (exa_status e = setup_kernels(m, B)) return e;
-        CR(S.get(&part, std::max(m->nobj[exa::M_ALL], 1)));
+        CR(S.get(&part, std::max(m->ntiles[exa::M_ALL], 1)));
         ExaOut o{};
         o.obj_part = part;
         o.c = m->d_cbuf;
@@ -1070,7 +1067,7 @@ exa_status autotune(exa_model *m) {
             int occ = 0;
             CR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)m->fn[exa::M_ALL], best_block, 0));
             if (occ < minb) continue;
-            CR(S.get(&part, std::max(m->nobj[exa::M_ALL], 1)));
+            CR(S.get(&part, std::max(m->ntiles[exa::M_ALL], 1)));
             ExaOut o{};
             o.obj_part = part;
             o.c = m->d_cbuf;
@@ -1110,7 +1107,7 @@ exa_status autotune(exa_model *m) {
         m->prefetch = pf;
         if (exa_status e = setup_kernels(m, best_block, best_minb)) return e;
         if (exa_status e = apply_grid(m, best_factor)) return e;
-        CR(S.get(&part, std::max(m->nobj[exa::M_ALL], 1)));
+        CR(S.get(&part, std::max(m->ntiles[exa::M_ALL], 1)));
         ExaOut o{};
         o.obj_part = part;
         o.c = m->d_cbuf;
@@ -1517,13 +1514,9 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     CR(dalloc(m, &m->d_gbuf, m->nnzg));
     CR(dalloc(m, &m->d_abuf, m->naug));
     CR(dalloc(m, &m->d_cbuf, m->ncon));
-    {  // objective partials: one per objective tile, sized for the smallest tile the tuner tries
+    {  // objective partials: one per CTA, at most one per tile; sized for 32-instance tiles
         i64 maxt = 1;
-        for (const ExaPM &pm : m->h_pms) {
-            bool obj = false;
-            for (int p : m->groups[pm.grp].pats) obj = obj || m->pats[p].kind == EXA_OBJ;
-            if (obj) maxt += (pm.n_inst + 31) / 32;
-        }
+        for (const ExaPM &pm : m->h_pms) maxt += (pm.n_inst + 31) / 32;
         CR(dalloc(m, &m->d_objpart, maxt));
     }
     const bool tune = !(o.flags & EXA_FLAG_NO_TUNE) && !o.block_threads && o.grid_factor == 0;
@@ -1642,7 +1635,7 @@ exa_status exa_obj(exa_model *m, const double *x, double *f) {
     ExaOut o{};
     o.obj_part = m->d_objpart;
     if (exa_status e = launch_eval(m, exa::M_OBJ, x, nullptr, 0.0, o)) return e;
-    k_obj_final<<<1, 256, 0, m->stream>>>(m->d_objpart, m->nobj[exa::M_OBJ], f);
+    k_obj_final<<<1, 256, 0, m->stream>>>(m->d_objpart, eval_grid(m, exa::M_OBJ, m->ntiles[exa::M_OBJ]), f);
     CR(cudaGetLastError());
     return EXA_OK;
 }
@@ -1676,13 +1669,14 @@ exa_status noalloc_partials(exa_model *m, double **out) {
 exa_status exa_obj_noalloc(exa_model *m, const double *x, double *f) {
     if (exa_status e = check_model(m)) return e;
     CHECK_PTRS(x, f);
-    // one partial per objective tile: tiles are counted per (batch member, fused group) as
-    // ceil(instances / block), so the limit depends on the launch shape, not on instances alone
-    const int nparts = m->nobj[exa::M_OBJ];
+    // one partial per CTA of the objective kernel: one CTA per objective tile (ceil(instances /
+    // block) per batch member and fused group), or fewer in a persistent grid, so the limit depends
+    // on the launch shape, not on instances alone
+    const int nparts = eval_grid(m, exa::M_OBJ, m->ntiles[exa::M_OBJ]);
     if (nparts > EXA_NOALLOC_MAX_PARTIALS)
         return fail(m, EXA_E_UNSUPPORTED,
                     "exa_obj_noalloc: the objective needs " + std::to_string(nparts) +
-                        " partial sums (one per objective tile of up to " + std::to_string(m->block) +
+                        " partial sums (one per CTA of its launch, tiles of up to " + std::to_string(m->block) +
                         " instances); the static scratch holds at most " +
                         std::to_string(EXA_NOALLOC_MAX_PARTIALS));
     double *part = nullptr;
@@ -1927,10 +1921,14 @@ static exa_status eval_all_chunked(exa_model *m, const double *x, const double *
         o2.hcomp = o.hcomp;
     }
     const Mode m1 = split ? exa::M_FIRST : mode;
+    int nparts = 0;  // objective partials so far: each chunk's launch writes one per CTA after them
     for (int k = 0; k < m->nchunks; k++) {
         const int b0 = m->chunk_b[k], b1 = m->chunk_b[k + 1];
-        if (exa_status e = launch_eval(m, m1, x, y, sigma, split ? o1 : o, m->mb_tile[m1][b0], m->mb_tile[m1][b1]))
+        ExaOut oc = split ? o1 : o;
+        oc.obj_part = m->d_objpart + nparts;
+        if (exa_status e = launch_eval(m, m1, x, y, sigma, oc, m->mb_tile[m1][b0], m->mb_tile[m1][b1]))
             return e;
+        if (m->mb_tile[m1][b1] > m->mb_tile[m1][b0]) nparts += eval_grid(m, m1, m->mb_tile[m1][b1] - m->mb_tile[m1][b0]);
         if (split)
             if (exa_status e = launch_eval(m, hmode, x, y, sigma, o2, m->mb_tile[hmode][b0], m->mb_tile[hmode][b1]))
                 return e;
@@ -1994,7 +1992,7 @@ static exa_status eval_all_chunked(exa_model *m, const double *x, const double *
         }
     }
     if (f) {
-        k_obj_final<<<1, 256, 0, m->stream>>>(m->d_objpart, m->nobj[m1], f);
+        k_obj_final<<<1, 256, 0, m->stream>>>(m->d_objpart, nparts, f);
         CR(cudaGetLastError());
     }
     CR(cudaEventRecord(m->ev_join[0], ps));
@@ -2121,7 +2119,7 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
         CR(cudaEventRecord(m->ev_join[1], m->side[1]));
     }
     if (f) {
-        k_obj_final<<<1, 256, 0, rs>>>(m->d_objpart, m->nobj[mode], f);
+        k_obj_final<<<1, 256, 0, rs>>>(m->d_objpart, eval_grid(m, mode, m->ntiles[mode]), f);
         CR(cudaGetLastError());
         if (hf)
             if (exa_status e = to_host(0, hf, f, 1)) return e;

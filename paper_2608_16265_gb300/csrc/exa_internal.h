@@ -38,10 +38,9 @@
     struct ExaTile {              /* BLOCK consecutive instances of one (member, group) */          \
         int pm;                                                                                     \
         int begin;                                                                                  \
-        int oslot;                /* tiles with objective terms: index of the partial; else -1 */   \
     };                                                                                              \
     struct ExaOut {                                                                                 \
-        double *obj_part;         /* one objective partial sum per objective tile */                \
+        double *obj_part;         /* one objective partial sum per CTA of the launch */             \
         double *c;                /* constraint base values, indexed by global row */               \
         double *abuf;             /* augmentation terms */                                          \
         double *gbuf;             /* objective gradient slots */                                    \

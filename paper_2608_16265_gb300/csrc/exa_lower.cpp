@@ -1207,6 +1207,25 @@ struct Emitter {
             return os.str();
         }
         for (int s : syms) os << "  const double X" << s << " = __ldg(x + pm.xoff + i" << s << ");\n";
+        // Pairs of different symbols whose slot doubles when both resolve to one variable: their
+        // equality tests are taken once here, into one bit mask, so that the 64-bit indices are
+        // dead once the gathers are issued instead of staying live until the Hessian.
+        std::map<std::pair<int, int>, int> eqbit;
+        for (int pos : act)
+            if (want[pos].hess)
+                for (auto &pr : pat(pos).hpair)
+                    if (pr.first != pr.second) {
+                        int ga = grp.sym[pos][pr.first], gb = grp.sym[pos][pr.second];
+                        eqbit.emplace(std::make_pair(std::min(ga, gb), std::max(ga, gb)), (int)eqbit.size());
+                    }
+        const bool use_eqm = !eqbit.empty() && eqbit.size() <= 64;
+        if (use_eqm) {
+            os << "  const unsigned long long eqm = 0ull";
+            for (auto &kv : eqbit)
+                os << " | ((unsigned long long)(i" << kv.first.first << " == i" << kv.first.second << ") << " << kv.second
+                   << ")";
+            os << ";\n";
+        }
         for (int pid : params) os << "  const double P" << pid << " = __ldg(th + pm.poff + q" << pid << ");\n";
         // the multipliers of the constraint rows are loaded with the other inputs, so that their
         // latency overlaps the pattern arithmetic instead of following it
@@ -1246,7 +1265,6 @@ struct Emitter {
         for (size_t c = 0; c < grp.hc.size(); c++)
             for (auto &pj : grp.hc[c]) hc_of[pj] = (int)c;
         std::vector<char> hc_started(grp.hc.size(), 0);
-        bool objw = false;
         for (int pos : act) {
             const Pattern &p = pat(pos);
             const PatternGraph &G = PG[pos];
@@ -1262,7 +1280,7 @@ struct Emitter {
             }
             if (w.val) {
                 const std::string v = widen(G.value);
-                if (obj) { os << "  objv " << (objw ? "+=" : "=") << " act ? " << v << " : 0.0;\n"; objw = true; }
+                if (obj) os << "  if (act) objv += " << v << ";\n";  // the thread's running objective sum
                 else if (p.kind == EXA_CON) os << "  if (act) o.c[row" << P << "] = " << v << ";\n";
                 else os << "  if (act) o.abuf[pm.abase[" << P << "] + kk] = " << v << ";\n";
             }
@@ -1307,9 +1325,11 @@ struct Emitter {
                     os << "  double " << hv << " = " << v << ";\n";
                     vals.push_back(hv);
                     if (a != b) {
-                        const std::string c = "i" + std::to_string(grp.sym[pos][a]) + " == i" +
-                                              std::to_string(grp.sym[pos][b]);
-                        coll += (coll.empty() ? "" : " || ") + ("(" + c + ")");
+                        const int ga = grp.sym[pos][a], gb = grp.sym[pos][b];
+                        const std::string c =
+                            use_eqm ? "((eqm >> " + std::to_string(eqbit.at({std::min(ga, gb), std::max(ga, gb)})) + ") & 1ull)"
+                                    : "(i" + std::to_string(ga) + " == i" + std::to_string(gb) + ")";
+                        coll += (coll.empty() ? "" : " || ") + c;
                         doubled.push_back({j, c});
                     }
                 }
@@ -1468,7 +1488,7 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
         }
         const bool objred = (m == M_OBJ || mode_all(m) || m == M_FIRST);
         // Tile loop: with gridDim.x == ntiles every CTA takes one tile; a smaller (persistent) grid
-        // strides over the tile list.  tl.oslot and the trip count are uniform over the CTA.
+        // strides over the tile list.  The trip count is uniform over the CTA.
         src << "extern \"C\" __global__ void EXA_BOUNDS exa_" << kModeName[m]
             << "(const ExaTile* __restrict__ tiles, const int ntiles, const ExaPM* __restrict__ pms,"
                " const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ th,"
@@ -1484,6 +1504,7 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
                    "  double* __restrict__ ws = stage + (threadIdx.x & ~31u) * " << smax << ";\n";
         else
             src << "  double* ws = nullptr;\n";
+        src << "  double objv = 0.0;\n";
         src << "  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {\n";
         if (opt.prefetch >= 1 && m != M_STRUCT) {  // data columns of the tile 2 x pfd ahead: warp 0
             src << "  if (threadIdx.x < 32 && pfd > 0) {\n"
@@ -1511,26 +1532,26 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
                "  const int k0 = tl.begin + (int)threadIdx.x;\n"
                "  const bool act = k0 < pm.n_inst;\n"
                "  const int k = act ? k0 : (int)pm.n_inst - 1;\n"
-               "  double objv = 0.0;\n"
                "  if (__any_sync(0xffffffffu, act)) {\n"
                "    switch (pm.grp) {\n";
         for (int gi : gl)
             src << "      case " << gi << ": grp" << gi << "_" << kModeName[m] << "(pm, k, act, x, y, th, sigma, o, so, objv, ws); break;\n";
         src << "      default: break;\n    }\n  }\n";
+        src << "  }\n";
         if (objred) {
-            src << "  if (tl.oslot >= 0) {\n"
-                   "    for (int off = 16; off > 0; off >>= 1) objv += __shfl_xor_sync(0xffffffffu, objv, off);\n"
-                   "    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = objv;\n"
-                   "    __syncthreads();\n"
-                   "    if (threadIdx.x == 0) {\n"
-                   "      double s = 0.0;\n"
-                   "      for (int i = 0; i < EXA_BLOCK / 32; i++) s += red[i];\n"
-                   "      o.obj_part[tl.oslot] = s;\n"
-                   "    }\n"
-                   "    __syncthreads();\n"
+            // Every thread sums the objective terms of all its instances over the CTA's tiles (in tile
+            // order); the CTA reduces once, after its last tile, and writes one partial sum: the
+            // partials of a launch are obj_part[0 .. gridDim.x), in a fixed order for a fixed grid.
+            src << "  for (int off = 16; off > 0; off >>= 1) objv += __shfl_xor_sync(0xffffffffu, objv, off);\n"
+                   "  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = objv;\n"
+                   "  __syncthreads();\n"
+                   "  if (threadIdx.x == 0) {\n"
+                   "    double s = 0.0;\n"
+                   "    for (int i = 0; i < EXA_BLOCK / 32; i++) s += red[i];\n"
+                   "    o.obj_part[blockIdx.x] = s;\n"
                    "  }\n";
         }
-        src << "  }\n}\n";
+        src << "}\n";
     }
     return src.str();
 }
