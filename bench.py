@@ -418,6 +418,57 @@ def family_configs(B, torch, timed, local, peak_hbm, cpu_budget, sweep=False):
     return res, sw
 
 
+def compile_sweep(args):
+    """Code generation + NVRTC time and model-creation time against the number of patterns and the
+    size of their trees (the analogue of the paper's compile-time experiment, Sec. 7.4): P
+    constraint patterns over one variable array, pattern p a sum of K terms
+    c_pj sin(x[k+j] + p) x[k+j+1]^2 + exp(x[k+j] / (p+2)) with its own constants, so every pattern
+    is distinct code.  Creation is timed without the autotuner and with an empty module cache for
+    the first model of each size (the second creation of the same model reuses the compiled
+    module)."""
+    from paper_2608_16265_gb300 import binding as B
+    from paper_2608_16265_gb300.ir import Model, sin, exp
+    import torch
+    rows = []
+    for K in (4, 16):
+        for P in (1, 2, 4, 8, 16):
+            mod = Model()
+            n = 100000
+            xv = mod.add_var(n + K + 1)
+            for pidx in range(P):
+                coef = [1.0 + 0.01 * (pidx * 31 + j) for j in range(K)]
+
+                def pat(d, pidx=pidx, coef=coef):
+                    e = 0
+                    for j in range(K):
+                        e = e + coef[j] * sin(xv[d.k + j] + pidx) * xv[d.k + j + 1] ** 2 + exp(xv[d.k + j] / (pidx + 2))
+                    return e
+                mod.add_con(pat, n=n)
+            flat = mod.flat()
+            nodes = sum(len(pp.vop) for pp in flat.patterns)
+            rec = {"patterns": P, "terms_per_pattern": K, "tree_nodes_total": nodes}
+            for prec, tag in ((B.EXA_FP64, "fp64"), (B.EXA_MIXED_FP32, "mixed")):
+                t0 = time.perf_counter()
+                B.exa_compile_check(flat, precision=prec, block=128)
+                rec[f"{tag}_generate_and_nvrtc_s"] = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            m = B.exa_create(flat, flags=B.EXA_FLAG_NO_TUNE, block=128)
+            torch.cuda.synchronize()
+            rec["create_s"] = time.perf_counter() - t0
+            rec["create_nvrtc_ms"] = m.stat("nvrtc_ms")
+            m.destroy()
+            t0 = time.perf_counter()
+            m = B.exa_create(flat, flags=B.EXA_FLAG_NO_TUNE, block=128)
+            torch.cuda.synchronize()
+            rec["create_cached_s"] = time.perf_counter() - t0
+            m.destroy()
+            rows.append(rec)
+            phase(f"compile sweep {rec}")
+    print(json.dumps({"compile_sweep": rows, "cpu": platform.processor() or platform.machine(),
+                      "nproc": os.cpu_count()}))
+    return 0
+
+
 def run_exa(args):
     import torch
     ws, rank, local = dist_env()
@@ -675,6 +726,15 @@ def run_exa(args):
     e2e_ms = reduce_max(e2e_ms, pg, dev)
     d2h = sum(t.numel() for t in host.values()) * 8
     h2d = int(xh.numel() * 8 + yh.numel() * 8)
+    # the same host buffers filled by plain copies from the device outputs, one at a time: the
+    # rate the host link gives into these very buffers (their pages may sit on either host node)
+    srcs = dict(f=f, g=g, c=c, jac=jac, hess=hess, jac_csc=jcsc, hess_csc=hcsc)
+    buf_gbs = {k: host[k].numel() * 8 / (timed(lambda k=k: host[k].copy_(srcs[k], non_blocking=True), 3) * 1e-3) / 1e9
+               for k in ("jac", "hess", "jac_csc")}
+    numa = sorted(n for n in os.listdir("/sys/devices/system/node") if n.startswith("node")) \
+        if os.path.isdir("/sys/devices/system/node") else []
+    e2e_diag = {"d2h_gbs_into_e2e_buffers": buf_gbs, "buffers_pinned": all(t.is_pinned() for t in host.values()),
+                "cpu_affinity": len(os.sched_getaffinity(0)), "numa_nodes": numa}
     # the host link that bounds this step, measured (include/exa_probe.h)
     link = B.exa_probe_host_link(local, 1 << 30)
     link_ms = 1e3 * (h2d / link["h2d_bytes_per_s"] + d2h / link["d2h_bytes_per_s"])
@@ -707,7 +767,8 @@ def run_exa(args):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
                 "link": {"h2d_gbs": link["h2d_bytes_per_s"] / 1e9, "d2h_gbs": link["d2h_bytes_per_s"] / 1e9,
                          "copy_ms": link_ms, "copy_frac_of_step": link_ms / e2e_ms,
-                         "how": "exa_probe_host_link: 1 GiB page-locked cudaMemcpyAsync each way, best of 3"}},
+                         "how": "exa_probe_host_link: 1 GiB page-locked cudaMemcpyAsync each way, best of 3"},
+                "diagnostics": e2e_diag},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roofline,
         "cpu_baseline": cpu,
@@ -742,6 +803,8 @@ def main(argv=None):
                     "steps, print the step time, exit (no extras, no CPU baseline)")
     ap.add_argument("--kernel-only", type=int, default=0, help="profiling mode: run only the evaluation-kernel "
                     "call (J and H COO) this many times after one untimed call, print its sizes, exit")
+    ap.add_argument("--compile-sweep", action="store_true", help="time code generation, NVRTC and model "
+                    "creation against the number of patterns and their tree size; print one JSON line and exit")
     ap.add_argument("--workload", default="batch", help="profiling modes only (--steps-only, --kernel-only): "
                     "'batch' (the benchmark workload) or one model of a workload family, e.g. pde_n2000")
     ap.add_argument("--pin", default="", help="block,min_blocks,grid_factor,flags[,chunks[,wave_pct]]: fixed launch configuration "
@@ -753,6 +816,8 @@ def main(argv=None):
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.compile_sweep:
+        return compile_sweep(args)
     return run_exa(args)
 
 

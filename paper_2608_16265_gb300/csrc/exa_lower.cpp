@@ -1542,7 +1542,12 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
             // Every thread sums the objective terms of all its instances over the CTA's tiles (in tile
             // order); the CTA reduces once, after its last tile, and writes one partial sum: the
             // partials of a launch are obj_part[0 .. gridDim.x), in a fixed order for a fixed grid.
-            src << "  for (int off = 16; off > 0; off >>= 1) objv += __shfl_xor_sync(0xffffffffu, objv, off);\n"
+            // (a warp whose sums are all zero, e.g. one that met no objective instance, skips the
+            // shuffle tree: the test is on the bits, on the integer pipe)
+            src << "  if (__any_sync(0xffffffffu, (__double_as_longlong(objv) << 1) != 0))\n"
+                   "    for (int off = 16; off > 0; off >>= 1) objv += __shfl_xor_sync(0xffffffffu, objv, off);\n"
+                   "  else\n"
+                   "    objv = 0.0;\n"
                    "  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = objv;\n"
                    "  __syncthreads();\n"
                    "  if (threadIdx.x == 0) {\n"
