@@ -173,8 +173,17 @@ enum {
     EXA_FLAG_PF_COLUMNS = 256, /* the evaluation kernels prefetch into L2 the data columns of the
                                   tile two tile-steps ahead (a tile-step: a CTA's next tile in a
                                   persistent grid, else one wave of resident CTAs) */
-    EXA_FLAG_PF_GATHERS = 512  /* as EXA_FLAG_PF_COLUMNS, and every thread also prefetches the x and
+    EXA_FLAG_PF_GATHERS = 512, /* as EXA_FLAG_PF_COLUMNS, and every thread also prefetches the x and
                                   y lines its instance of the next tile-step gathers */
+    EXA_FLAG_LANES2 = 1024,    /* two warp sets per instance: the warps of a CTA form two sets that
+                                  evaluate the same instances, each a contiguous subset of a fused
+                                  group's patterns (fewer registers per thread); block_threads must
+                                  be a multiple of 64; excludes the prefetch flags.  The kernels
+                                  that form the compressed Hessian sums keep one set */
+    EXA_FLAG_LAZY_LOADS = 2048 /* with the default emission order: each pattern's inputs (x values,
+                                  f64 data, parameters, multipliers) are loaded just before the
+                                  arithmetic of the pattern preceding it, not all at the top of the
+                                  fused group (fewer values live); excludes EXA_FLAG_UPFRONT */
 };
 
 /* Validate the descriptor (Sec. 3.4 SIMDFunction), lower every pattern to generated device
@@ -314,7 +323,8 @@ exa_status exa_compile_check(const exa_model_desc *desc, const exa_options *opt,
 
 /* Named statistics (host values): "nvrtc_ms", "create_ms", "tune_ms", "eval_regs", "eval_block",
  * "eval_regs_jac", "eval_regs_hess", "eval_tiles", "eval_grid", "eval_persist", "eval_min_blocks",
- * "eval_split", "eval_chunks", "eval_upfront", "eval_prefetch", "eval_wave_pct", "graph_kernels", "csc_direct",
+ * "eval_split", "eval_chunks", "eval_upfront", "eval_prefetch", "eval_wave_pct", "eval_lanes", "eval_lazy",
+ * "graph_kernels", "csc_direct",
  * "hess_compressed", "nnzh_compressed", "grad_compact", "device_bytes", "n_patterns", "batch_members".
  * Unknown key: EXA_E_INVALID. */
 exa_status exa_stat(const exa_model *m, const char *key, double *value);

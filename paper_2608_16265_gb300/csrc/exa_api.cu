@@ -325,6 +325,8 @@ struct exa_model {
     int min_blocks = 0;           // launch-bounds minimum CTAs per SM chosen by the tuner
     bool by_pattern = true;       // generated code emits each pattern's arithmetic next to its outputs
     int prefetch = 0;             // L2 prefetch depth of the generated tile loop (CodegenOptions)
+    int lanes = 1;                // warp sets per instance of split groups (CodegenOptions)
+    bool lazy_loads = false;      // with by_pattern: inputs loaded one pattern ahead (CodegenOptions)
     int wave_pct = 0;             // persistent evaluation grid of this % of one wave (0: off)
     int pfd[exa::M_COUNT] = {};   // prefetch distance in tiles per kernel kind (0: none)
     bool split_all = false;       // exa_eval_all: first- and second-order kernels instead of one
@@ -904,7 +906,9 @@ exa_status setup_kernels(exa_model *m, int block, int min_blocks = 0) {
     cg.min_blocks = min_blocks;
     cg.bounds_check = m->bounds_check;
     cg.by_pattern = m->by_pattern;
-    cg.prefetch = m->prefetch;
+    cg.prefetch = m->lanes > 1 ? 0 : m->prefetch;
+    cg.lanes = m->lanes;
+    cg.lazy_loads = m->lazy_loads;
     std::string gerr;
     std::string src = exa::generate_source(m->pats, m->groups, cg, &gerr);
     if (!gerr.empty()) return fail(m, EXA_E_INTERNAL, gerr);
@@ -928,7 +932,9 @@ exa_status setup_kernels(exa_model *m, int block, int min_blocks = 0) {
                 for (int p : m->groups[gi].pats) in = in || exa::pattern_in_mode(m->pats[p], (exa::Mode)k);
                 if (!in) continue;
                 const ExaPM &pm = m->h_pms[(size_t)b * ng + gi];
-                for (i64 s = 0; s < pm.n_inst; s += block)
+                // a group split into warp sets takes block / sets instances per tile
+                const int per = block / (int)exa::group_sets(m->pats, m->groups[gi], (exa::Mode)k, m->lanes).size();
+                for (i64 s = 0; s < pm.n_inst; s += per)
                     tiles.push_back({b * ng + gi, (int)s});
             }
         m->ntiles[k] = (int)tiles.size();
@@ -994,7 +1000,7 @@ exa_status autotune(exa_model *m) {
     double best = 1e30;
     int best_block = m->block, best_factor = 0;
     const int blocks[] = {64, 128, 256};
-    auto variant = [&](int block, int minb, bool byp, int pf) {
+    auto variant = [&](int block, int minb, bool byp, int pf, bool lazy = false) {
         exa::CodegenOptions cg;
         cg.precision = m->precision;
         cg.block = block;
@@ -1002,11 +1008,12 @@ exa_status autotune(exa_model *m) {
         cg.bounds_check = m->bounds_check;
         cg.by_pattern = byp;
         cg.prefetch = pf;
+        cg.lazy_loads = lazy;
         return cg;
     };
     {
         std::vector<exa::CodegenOptions> v;
-        for (int B : blocks) v.push_back(variant(B, 0, m->by_pattern, m->prefetch));
+        for (int B : blocks) v.push_back(variant(B, 0, m->by_pattern, m->prefetch, m->lazy_loads));
         precompile(m, v);
     }
     for (int B : blocks) {
@@ -1042,26 +1049,30 @@ exa_status autotune(exa_model *m) {
     // its outputs or all of a group's arithmetic up front; a variant is kept only when the fused
     // kernel gets faster (the uncapped per-pattern variant was timed above)
     int best_minb = 0;
-    const bool init_order = m->by_pattern;
-    bool best_order = init_order;
+    // emission orders: 0 each pattern's arithmetic next to its outputs, 1 up front, 2 as 0 with
+    // each pattern's inputs loaded one pattern ahead
+    const int init_order = m->by_pattern ? (m->lazy_loads ? 2 : 0) : 1;
+    int best_order = init_order;
     {
         std::vector<exa::CodegenOptions> v;
-        for (int order = 0; order < 2; order++)
+        for (int order = 0; order < 3; order++)
             for (int warps : {0, 20, 24, 28, 32}) {
                 const int minb = warps * 32 / best_block;
-                if (minb <= 32 && (warps == 0 || minb >= 1)) v.push_back(variant(best_block, minb, order == 0, m->prefetch));
+                if (minb <= 32 && (warps == 0 || minb >= 1))
+                    v.push_back(variant(best_block, minb, order != 1, m->prefetch, order == 2));
             }
         precompile(m, v);
     }
-    for (int order = 0; order < 2; order++) {
-        const bool byp = order == 0;
+    for (int order = 0; order < 3; order++) {
+        const bool byp = order != 1;
         int last_minb = -1;
         for (int warps : {0, 20, 24, 28, 32}) {
             const int minb = warps * 32 / best_block;
             if (minb > 32 || minb == last_minb || (warps && minb < 1)) continue;
             last_minb = minb;
-            if (byp == init_order && minb == 0) continue;  // the variant timed by the search above
+            if (order == init_order && minb == 0) continue;  // the variant timed by the search above
             m->by_pattern = byp;
+            m->lazy_loads = order == 2;
             if (exa_status e = setup_kernels(m, best_block, minb)) return e;
             if (minb && m->regs[exa::M_ALL] * best_block * minb > 65536 + 1) continue;  // bound not honoured
             int occ = 0;
@@ -1087,11 +1098,12 @@ exa_status autotune(exa_model *m) {
             if (ms < best) {
                 best = ms;
                 best_minb = minb;
-                best_order = byp;
+                best_order = order;
             }
         }
     }
-    m->by_pattern = best_order;
+    m->by_pattern = best_order != 1;
+    m->lazy_loads = best_order == 2;
     // L2 prefetch depth (staging of later tiles' inputs): none, data columns, or data columns and
     // the next tile's x and y lines; kept when the fused kernel gets faster
     const int init_pf = m->prefetch;
@@ -1099,7 +1111,7 @@ exa_status autotune(exa_model *m) {
     {
         std::vector<exa::CodegenOptions> v;
         for (int pf : {0, 1, 2})
-            if (pf != init_pf) v.push_back(variant(best_block, best_minb, best_order, pf));
+            if (pf != init_pf) v.push_back(variant(best_block, best_minb, best_order != 1, pf, best_order == 2));
         precompile(m, v);
     }
     for (int pf : {0, 1, 2}) {
@@ -1129,6 +1141,59 @@ exa_status autotune(exa_model *m) {
         }
     }
     m->prefetch = best_pf;
+    // two warp sets per instance (fewer values live per thread, so a register cap allows more
+    // warps): a fresh search over the register cap, kept when the fused kernel gets faster
+    const int init_lanes = m->lanes;
+    int best_lanes = init_lanes, best_lminb = best_minb;
+    if (init_lanes == 1 && best_block % 64 == 0) {
+        std::vector<exa::CodegenOptions> v;
+        const std::vector<int> warps_l = {0, 24, 32, 40, 48};
+        for (int warps : warps_l) {
+            const int minb = warps * 32 / best_block;
+            if (minb <= 32 && (warps == 0 || minb >= 1)) {
+                exa::CodegenOptions cg = variant(best_block, minb, best_order != 1, 0, best_order == 2);
+                cg.lanes = 2;
+                v.push_back(cg);
+            }
+        }
+        precompile(m, v);
+        m->lanes = 2;
+        const int keep_pf = m->prefetch;
+        m->prefetch = 0;
+        int last_minb = -1;
+        for (int warps : warps_l) {
+            const int minb = warps * 32 / best_block;
+            if (minb > 32 || minb == last_minb || (warps && minb < 1)) continue;
+            last_minb = minb;
+            if (exa_status e = setup_kernels(m, best_block, minb)) return e;
+            if (minb && m->regs[exa::M_ALL] * best_block * minb > 65536 + 1) continue;
+            if (exa_status e = apply_grid(m, best_factor)) return e;
+            CR(S.get(&part, std::max(m->ntiles[exa::M_ALL], 1)));
+            ExaOut o{};
+            o.obj_part = part;
+            o.c = m->d_cbuf;
+            o.abuf = m->d_abuf;
+            o.gbuf = m->d_gbuf;
+            o.jac = m->d_jbuf;
+            o.hess = m->d_hbuf;
+            if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
+            CR(cudaEventRecord(e0, m->stream));
+            for (int r = 0; r < 5; r++)
+                if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
+            CR(cudaEventRecord(e1, m->stream));
+            CR(cudaEventSynchronize(e1));
+            float ms = 0;
+            CR(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                best_lanes = 2;
+                best_lminb = minb;
+            }
+        }
+        m->prefetch = best_lanes == 2 ? 0 : keep_pf;
+    }
+    m->lanes = best_lanes;
+    if (best_lanes == 2) best_minb = best_lminb;
     if (exa_status e = setup_kernels(m, best_block, best_minb)) return e;
     if (exa_status e = apply_grid(m, best_factor)) return e;
     m->tune_ms = best / 5.0;
@@ -1294,6 +1359,8 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     m->use_graphs = (o.flags & EXA_FLAG_NO_GRAPH) == 0;
     m->block = o.block_threads ? o.block_threads : 128;
     if (m->block % 32 || m->block < 32 || m->block > 1024) return fail(m, EXA_E_INVALID, "block_threads must be a multiple of 32 in [32, 1024]");
+    if ((o.flags & EXA_FLAG_LANES2) && m->block % 64)
+        return fail(m, EXA_E_INVALID, "EXA_FLAG_LANES2 needs block_threads a multiple of 64");
     if (o.grid_factor < -1 || o.grid_factor > 64) return fail(m, EXA_E_INVALID, "grid_factor must be in [-1, 64]");
     if (o.min_blocks < 0 || o.min_blocks > 32) return fail(m, EXA_E_INVALID, "min_blocks must be in [0, 32]");
     if (o.chunks < 0 || o.chunks > 16) return fail(m, EXA_E_INVALID, "chunks must be in [0, 16]");
@@ -1304,6 +1371,10 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     m->by_pattern = (o.flags & EXA_FLAG_UPFRONT) == 0;
     m->csc_direct = (o.flags & EXA_FLAG_CSC_SCATTER) != 0;
     m->prefetch = (o.flags & EXA_FLAG_PF_GATHERS) ? 2 : (o.flags & EXA_FLAG_PF_COLUMNS) ? 1 : 0;
+    m->lanes = (o.flags & EXA_FLAG_LANES2) ? 2 : 1;
+    m->lazy_loads = (o.flags & EXA_FLAG_LAZY_LOADS) != 0;
+    if (m->lazy_loads && !m->by_pattern) return fail(m, EXA_E_INVALID, "EXA_FLAG_LAZY_LOADS excludes EXA_FLAG_UPFRONT");
+    if (m->lanes > 1 && m->prefetch) return fail(m, EXA_E_INVALID, "EXA_FLAG_LANES2 excludes the prefetch flags");
     if (nb < 1) return fail(m, EXA_E_INVALID, "empty batch");
     for (int b = 0; b < nb; b++) {
         const exa_model_desc *d = descs[b];
@@ -2334,6 +2405,8 @@ exa_status exa_compile_check(const exa_model_desc *desc, const exa_options *opt,
             cg.by_pattern = (o.flags & EXA_FLAG_UPFRONT) == 0;
             cg.min_blocks = o.min_blocks;
             cg.prefetch = (o.flags & EXA_FLAG_PF_GATHERS) ? 2 : (o.flags & EXA_FLAG_PF_COLUMNS) ? 1 : 0;
+            cg.lanes = (o.flags & EXA_FLAG_LANES2) ? 2 : 1;
+            cg.lazy_loads = (o.flags & EXA_FLAG_LAZY_LOADS) != 0;
             std::string gerr;
             std::string src = exa::generate_source(tmp.pats, tmp.groups, cg, &gerr);
             if (!gerr.empty()) s = fail(&tmp, EXA_E_INTERNAL, gerr);
@@ -2372,6 +2445,8 @@ exa_status exa_stat(const exa_model *m, const char *key, double *value) {
     else if (k == "eval_chunks") *value = m->nchunks;
     else if (k == "eval_upfront") *value = !m->by_pattern;
     else if (k == "eval_prefetch") *value = m->prefetch;
+    else if (k == "eval_lanes") *value = m->lanes;
+    else if (k == "eval_lazy") *value = m->lazy_loads;
     else if (k == "eval_wave_pct") *value = m->wave_pct;
     else if (k == "graph_kernels") *value = m->graph_kernels;
     else if (k == "grad_compact") *value = m->grad_compact;

@@ -129,11 +129,22 @@ struct CodegenOptions {
     // emit each pattern's arithmetic just before its outputs (shorter live ranges) instead of all
     // of a group's arithmetic before the first output
     bool by_pattern = true;
+    // with by_pattern: load each pattern's inputs (x values, f64 data, parameters, multipliers) just
+    // before the arithmetic of the pattern preceding it, instead of all at the top of the group
+    bool lazy_loads = false;
     // L2 prefetch of later tiles' inputs in the tile loop: 0 none; 1 the data columns of the tile
     // 2 x pfd ahead (one bulk prefetch per column); 2 also the x and y lines the tile pfd ahead
     // gathers (pfd: a kernel argument, the CTA's next tile in a persistent grid, else one wave)
     int prefetch = 0;
+    // Warp sets per instance: with 2, the warps of a CTA form two sets that evaluate the same
+    // instances of a tile, each its own contiguous subset of a fused group's patterns (fewer values
+    // live per thread; shared subexpressions recomputed by both).  Kinds that form the compressed
+    // Hessian sums, and groups with a single active pattern, keep one set.  Excludes prefetch.
+    int lanes = 1;
 };
+// The warp sets of group g in kernel kind `mode` (positions in g.pats per set, in order): one set
+// with every active pattern, or `lanes` contiguous subsets of about equal outputs.
+std::vector<std::vector<int>> group_sets(const std::vector<Pattern> &pats, const Group &g, Mode mode, int lanes);
 std::string generate_source(const std::vector<Pattern> &pats, const std::vector<Group> &groups,
                             const CodegenOptions &opt, std::string *err);
 bool pattern_in_mode(const Pattern &p, Mode m);

@@ -851,6 +851,25 @@ bool pattern_in_mode(const Pattern &p, Mode m) {
     }
 }
 
+std::vector<std::vector<int>> group_sets(const std::vector<Pattern> &pats, const Group &g, Mode mode, int lanes) {
+    std::vector<int> act;
+    for (size_t pos = 0; pos < g.pats.size(); pos++)
+        if (pattern_in_mode(pats[g.pats[pos]], mode)) act.push_back((int)pos);
+    if (lanes < 2 || (int)act.size() < 2 || mode == M_STRUCT || mode_hess_comp(mode)) return {act};
+    // two contiguous subsets, the cut that best balances the outputs (values, first- and
+    // second-order slots) of the two sides
+    auto cost = [&](int pos) { const Pattern &p = pats[g.pats[pos]]; return 1 + p.nj() + p.nh(); };
+    int total = 0;
+    for (int pos : act) total += cost(pos);
+    int best_cut = 1, best = 1 << 30, left = 0;
+    for (size_t c = 1; c < act.size(); c++) {
+        left += cost(act[c - 1]);
+        const int imbalance = std::abs(2 * left - total);
+        if (imbalance < best) { best = imbalance; best_cut = (int)c; }
+    }
+    return {std::vector<int>(act.begin(), act.begin() + best_cut), std::vector<int>(act.begin() + best_cut, act.end())};
+}
+
 namespace {
 
 // ------------------------------------------------------------------ CUDA emission
@@ -996,20 +1015,18 @@ struct Emitter {
     }
 
     // One device function per (group, mode): every active pattern of the group for one instance.
-    std::string function(int gid, Mode mode) {
+    // The device function of one warp set (`act`: positions of its patterns; `suffix` names it).
+    std::string function(int gid, Mode mode, const std::vector<int> &act, const std::string &suffix = "") {
         os.str("");
         const bool mixed = opt.precision == EXA_MIXED_FP32;
         const char *W = mixed ? "float" : "double";
         const bool all = mode_all(mode) || mode == M_FIRST;
         const bool hs_coo = mode_hess_coo(mode), hs_comp = mode_hess_comp(mode) && !grp.hc.empty();
         const bool want_struct = mode == M_STRUCT;
-        std::vector<int> act;
-        for (size_t pos = 0; pos < grp.pats.size(); pos++)
-            if (pattern_in_mode(pat((int)pos), mode)) act.push_back((int)pos);
         // k is the thread's instance clamped to the last one; act says whether it is its own.  Every
         // lane of a warp runs the function so that outputs can be staged per warp in shared memory
         // (ws) and written back as contiguous, coalesced runs.
-        os << "static __device__ __forceinline__ void grp" << gid << "_" << kModeName[mode]
+        os << "static __device__ __forceinline__ void grp" << gid << "_" << kModeName[mode] << suffix
            << "(const ExaPM& pm, const int k, const bool act, const double* __restrict__ x,"
               " const double* __restrict__ y, const double* __restrict__ th, const double sigma, const ExaOut& o,"
               " const ExaStructOut& so, double& objv, double* __restrict__ ws) {\n";
@@ -1092,15 +1109,18 @@ struct Emitter {
         for (int pid : params) fields_of_idx(pid / 65536, pat(pid / 65536).v[pid % 65536].a, all_fields);
         for (int pos : act)
             if (want[pos].row && pat(pos).kind == EXA_AUG) fields_of_idx(pos, pat(pos).row_root, all_fields);
+        const bool lazy = opt.by_pattern && opt.lazy_loads && !want_struct;
         for (int f : all_fields) {
             if (grp.ftype[f] == EXA_FIELD_I32)
                 os << "  const int F" << f << " = __ldg((const int*)pm.f[" << f << "] + k);\n";
-            else
+            else if (!lazy)
                 os << "  const double F" << f << " = __ldg((const double*)pm.f[" << f << "] + k);\n";
         }
-        for (int f : dfields)
-            os << "  const double D" << f << " = " << (grp.ftype[f] == EXA_FIELD_I32 ? "(double)F" : "F") << f << ";\n";
-        for (int f : fcopy) os << "  const float DF" << f << " = __ldg(pm.f32[" << f << "] + k);\n";
+        if (!lazy) {
+            for (int f : dfields)
+                os << "  const double D" << f << " = " << (grp.ftype[f] == EXA_FIELD_I32 ? "(double)F" : "F") << f << ";\n";
+            for (int f : fcopy) os << "  const float DF" << f << " = __ldg(pm.f32[" << f << "] + k);\n";
+        }
         for (int s : idx_syms) {
             os << "  long long i" << s << " = " << idx_expr(grp.sym_root[s].first, grp.sym_root[s].second) << ";\n";
             if (opt.bounds_check || want_struct)
@@ -1206,7 +1226,8 @@ struct Emitter {
             os << "}\n";
             return os.str();
         }
-        for (int s : syms) os << "  const double X" << s << " = __ldg(x + pm.xoff + i" << s << ");\n";
+        if (!lazy)
+            for (int s : syms) os << "  const double X" << s << " = __ldg(x + pm.xoff + i" << s << ");\n";
         // Pairs of different symbols whose slot doubles when both resolve to one variable: their
         // equality tests are taken once here, into one bit mask, so that the 64-bit indices are
         // dead once the gathers are issued instead of staying live until the Hessian.
@@ -1226,18 +1247,81 @@ struct Emitter {
                    << ")";
             os << ";\n";
         }
-        for (int pid : params) os << "  const double P" << pid << " = __ldg(th + pm.poff + q" << pid << ");\n";
-        // the multipliers of the constraint rows are loaded with the other inputs, so that their
-        // latency overlaps the pattern arithmetic instead of following it
-        for (int pos : act)
-            if (want[pos].hess && pat(pos).kind != EXA_OBJ)
-                os << "  const double Y" << pos << " = __ldg(y + row" << pos << ");\n";
         for (int c : fconsts) os << "  const double C" << c << " = pm.fc[" << c << "];\n";
-        for (int s : fsyms) os << "  const float XF" << s << " = exa_d2f(X" << s << ");\n";
-        for (int f : ffields)
-            if (!fcopy.count(f)) os << "  const float DF" << f << " = (float)F" << f << ";\n";  // int32 column
-        for (int pid : fparams) os << "  const float PF" << pid << " = exa_d2f(P" << pid << ");\n";
         for (int c : ffconsts) os << "  const float CF" << c << " = exa_d2f(C" << c << ");\n";
+        // Inputs of the patterns: loads issued (`issue`) and FP32 copies formed (`ready`).  Eagerly:
+        // everything at the top.  Lazily: a pattern's loads are issued before the arithmetic of the
+        // pattern preceding it (one pattern of lookahead covers their latency), and its FP32
+        // copies are formed where its own arithmetic starts.
+        std::set<std::string> issued, readied;
+        auto issue_in = [&](const SN &sn) {
+            const std::string key = std::string(1, sn.ikind) + std::to_string(sn.iid);
+            if (!issued.insert(key).second) return;
+            switch (sn.ikind) {
+            case 'X': os << "  const double X" << sn.iid << " = __ldg(x + pm.xoff + i" << sn.iid << ");\n"; break;
+            case 'P': os << "  const double P" << sn.iid << " = __ldg(th + pm.poff + q" << sn.iid << ");\n"; break;
+            case 'D':
+                if (grp.ftype[sn.iid] == EXA_FIELD_F64) {
+                    if (dfields.count(sn.iid) || (sn.prec == PD))
+                        os << "  const double F" << sn.iid << " = __ldg((const double*)pm.f[" << sn.iid << "] + k);\n"
+                           << "  const double D" << sn.iid << " = F" << sn.iid << ";\n";
+                    if (fcopy.count(sn.iid)) os << "  const float DF" << sn.iid << " = __ldg(pm.f32[" << sn.iid << "] + k);\n";
+                }
+                break;
+            default: break;
+            }
+        };
+        auto ready_in = [&](const SN &sn) {
+            const std::string key = std::string(1, sn.ikind) + std::to_string(sn.iid) + (sn.prec == PF ? "f" : "d");
+            if (!readied.insert(key).second) return;
+            if (sn.ikind == 'X' && sn.prec == PF) os << "  const float XF" << sn.iid << " = exa_d2f(X" << sn.iid << ");\n";
+            if (sn.ikind == 'P' && sn.prec == PF) os << "  const float PF" << sn.iid << " = exa_d2f(P" << sn.iid << ");\n";
+            if (sn.ikind == 'D' && grp.ftype[sn.iid] == EXA_FIELD_I32) {
+                if (sn.prec == PF) os << "  const float DF" << sn.iid << " = (float)F" << sn.iid << ";\n";
+                else os << "  const double D" << sn.iid << " = (double)F" << sn.iid << ";\n";
+            }
+        };
+        // inputs of every pattern, from its roots
+        std::map<int, std::vector<int>> pin;  // position -> S_IN nodes
+        {
+            for (int pos : act) {
+                std::vector<int> rs;
+                const PatternGraph &G = PG[pos];
+                if (want[pos].val) rs.push_back(G.value);
+                if (want[pos].grad) for (int sy : pat(pos).jsym) rs.push_back(G.grad[sy]);
+                for (int r : hroots[pos]) if (r >= 0) rs.push_back(r);
+                std::vector<char> seen(g.n.size(), 0);
+                std::function<void(int)> walk = [&](int i) {
+                    if (seen[i]) return;
+                    seen[i] = 1;
+                    if (g.n[i].op == S_IN && g.n[i].ikind != 'C') pin[pos].push_back(i);
+                    if (g.n[i].a >= 0) walk(g.n[i].a);
+                    if (g.n[i].b >= 0) walk(g.n[i].b);
+                };
+                for (int r : rs) walk(r);
+            }
+        }
+        auto issue_pattern = [&](int pos) {
+            for (int i : pin[pos]) issue_in(g.n[i]);
+            if (want[pos].hess && pat(pos).kind != EXA_OBJ && issued.insert("Y" + std::to_string(pos)).second)
+                os << "  const double Y" << pos << " = __ldg(y + row" << pos << ");\n";
+        };
+        auto ready_pattern = [&](int pos) { for (int i : pin[pos]) ready_in(g.n[i]); };
+        if (!lazy) {
+            for (int pid : params) os << "  const double P" << pid << " = __ldg(th + pm.poff + q" << pid << ");\n";
+            // the multipliers of the constraint rows are loaded with the other inputs, so that their
+            // latency overlaps the pattern arithmetic instead of following it
+            for (int pos : act)
+                if (want[pos].hess && pat(pos).kind != EXA_OBJ)
+                    os << "  const double Y" << pos << " = __ldg(y + row" << pos << ");\n";
+            for (int s : fsyms) os << "  const float XF" << s << " = exa_d2f(X" << s << ");\n";
+            for (int f : ffields)
+                if (!fcopy.count(f)) os << "  const float DF" << f << " = (float)F" << f << ";\n";  // int32 column
+            for (int pid : fparams) os << "  const float PF" << pid << " = exa_d2f(P" << pid << ");\n";
+        } else if (!act.empty()) {
+            issue_pattern(act[0]);
+            if (act.size() > 1) issue_pattern(act[1]);
+        }
         std::map<int, std::string> name;
         if (!opt.by_pattern) body(roots, name);
         auto widen = [&](int r) { return g.n[r].prec == PF ? "exa_f2d(" + name.at(r) + ")" : name.at(r); };
@@ -1271,6 +1355,11 @@ struct Emitter {
             const Want &w = want[pos];
             const std::string P = std::to_string(pos);
             const bool obj = p.kind == EXA_OBJ;
+            if (lazy) {  // this pattern's FP32 copies; the next pattern's loads
+                const size_t j = std::find(act.begin(), act.end(), pos) - act.begin();
+                ready_pattern(pos);
+                if (j + 2 <= act.size() && j + 1 < act.size()) issue_pattern(act[j + 1]);
+            }
             if (opt.by_pattern) {  // this pattern's arithmetic, right before its outputs
                 std::vector<int> mine;
                 if (w.val) mine.push_back(G.value);
@@ -1448,13 +1537,16 @@ static const char *kFp64Helpers =
 }  // namespace
 
 std::string generate_source(const std::vector<Pattern> &pats, const std::vector<Group> &groups,
-                            const CodegenOptions &opt, std::string *err) {
+                            const CodegenOptions &opt_in, std::string *err) {
+    CodegenOptions opt = opt_in;
+    if (opt.lanes > 1) opt.prefetch = 0;  // one or the other
     std::ostringstream src;
     const bool mixed = opt.precision == EXA_MIXED_FP32;
     src << "// generated by exa_lower.cpp (" << (mixed ? "mixed FP32/FP64" : "FP64") << ")\n";
     src << kDeviceStructs << "\n";
     src << "#define EXA_BLOCK " << opt.block << "\n";
     src << "#define EXA_PF_DEPTH " << opt.prefetch << "\n";
+    src << "#define EXA_LANES " << opt.lanes << "\n";
     if (opt.min_blocks > 0) src << "#define EXA_BOUNDS __launch_bounds__(EXA_BLOCK, " << opt.min_blocks << ")\n";
     else src << "#define EXA_BOUNDS __launch_bounds__(EXA_BLOCK)\n";
     if (mixed) src << kMixedHelpers;
@@ -1477,14 +1569,22 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
     }
     for (int m = 0; m < M_COUNT; m++) {
         std::vector<int> gl;
+        std::map<int, int> nsets;  // group -> warp sets (> 1 only when split)
         for (size_t gi = 0; gi < groups.size(); gi++) {
             bool any = false;
             for (int pid : groups[gi].pats) any = any || pattern_in_mode(pats[pid], (Mode)m);
             if (!any) continue;
             gl.push_back((int)gi);
             Emitter e(pats, groups[gi], graphs[gi], pgs[gi], opt);
-            src << e.function((int)gi, (Mode)m);
-            src << e.pf_text;
+            const std::vector<std::vector<int>> sets = group_sets(pats, groups[gi], (Mode)m, opt.lanes);
+            if (sets.size() == 1) {
+                src << e.function((int)gi, (Mode)m, sets[0]);
+                src << e.pf_text;
+            } else {
+                nsets[(int)gi] = (int)sets.size();
+                for (size_t si = 0; si < sets.size(); si++)
+                    src << e.function((int)gi, (Mode)m, sets[si], "_s" + std::to_string(si));
+            }
         }
         const bool objred = (m == M_OBJ || mode_all(m) || m == M_FIRST);
         // Tile loop: with gridDim.x == ntiles every CTA takes one tile; a smaller (persistent) grid
@@ -1528,14 +1628,36 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
             src << "        default: break;\n      }\n    }\n  }\n";
         }
         src << "  const ExaTile tl = tiles[t];\n"
-               "  const ExaPM& pm = pms[tl.pm];\n"
-               "  const int k0 = tl.begin + (int)threadIdx.x;\n"
-               "  const bool act = k0 < pm.n_inst;\n"
+               "  const ExaPM& pm = pms[tl.pm];\n";
+        if (nsets.empty()) {
+            src << "  const int k0 = tl.begin + (int)threadIdx.x;\n";
+        } else {
+            // split groups: warp set `ws_set` of EXA_BLOCK / nset threads takes the tile's instances
+            // for its subset of the group's patterns (sets are whole warps: EXA_BLOCK / 2 is a
+            // multiple of 32)
+            src << "  int nset = 1;\n  switch (pm.grp) {\n";
+            for (auto &kv : nsets) src << "    case " << kv.first << ": nset = " << kv.second << "; break;\n";
+            src << "    default: break;\n  }\n"
+                   "  const int per = EXA_BLOCK / nset;\n"
+                   "  const int ws_set = (int)threadIdx.x / per;\n"
+                   "  const int k0 = tl.begin + (int)threadIdx.x - ws_set * per;\n";
+        }
+        src << "  const bool act = k0 < pm.n_inst;\n"
                "  const int k = act ? k0 : (int)pm.n_inst - 1;\n"
                "  if (__any_sync(0xffffffffu, act)) {\n"
                "    switch (pm.grp) {\n";
-        for (int gi : gl)
-            src << "      case " << gi << ": grp" << gi << "_" << kModeName[m] << "(pm, k, act, x, y, th, sigma, o, so, objv, ws); break;\n";
+        for (int gi : gl) {
+            auto it = nsets.find(gi);
+            if (it == nsets.end()) {
+                src << "      case " << gi << ": grp" << gi << "_" << kModeName[m] << "(pm, k, act, x, y, th, sigma, o, so, objv, ws); break;\n";
+            } else {
+                src << "      case " << gi << ":\n";
+                for (int si = 0; si < it->second; si++)
+                    src << "        " << (si ? "else " : "") << "if (ws_set == " << si << ") grp" << gi << "_" << kModeName[m]
+                        << "_s" << si << "(pm, k, act, x, y, th, sigma, o, so, objv, ws);\n";
+                src << "        break;\n";
+            }
+        }
         src << "      default: break;\n    }\n  }\n";
         src << "  }\n";
         if (objred) {

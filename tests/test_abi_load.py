@@ -54,7 +54,8 @@ def test_generated_kernels_compile(name, flat):
 @pytest.mark.parametrize("upfront", [False, True])
 def test_generated_variants_compile(precision, upfront):
     """Every code-generator variant the tuner can pick compiles for sm_103a: both precisions, both
-    emission orders, with and without a launch-bounds register cap, both L2 prefetch depths, on the
+    emission orders, with and without a launch-bounds register cap, both L2 prefetch depths, two
+    warp sets per instance, inputs loaded one pattern ahead, on the
     two-stage ACOPF (all pattern kinds, scenario-indexed variables, per-scenario parameters)."""
     from paper_2608_16265_gb300 import binding
     flat = synth.two_stage_acopf(5, 7, 2, 3, seed=1).flat
@@ -63,6 +64,10 @@ def test_generated_variants_compile(precision, upfront):
     binding.exa_compile_check(flat, precision=precision, block=64, flags=flags, min_blocks=16)
     for pf in (binding.EXA_FLAG_PF_COLUMNS, binding.EXA_FLAG_PF_GATHERS):  # L2 prefetch variants
         binding.exa_compile_check(flat, precision=precision, block=128, flags=flags | pf)
+    binding.exa_compile_check(flat, precision=precision, block=128, flags=flags | binding.EXA_FLAG_LANES2)
+    if not upfront:
+        binding.exa_compile_check(flat, precision=precision, block=64, min_blocks=12,
+                                  flags=flags | binding.EXA_FLAG_LAZY_LOADS)
 
 
 def test_compile_check_rejects_bad_ir():

@@ -132,18 +132,20 @@ def test_autotuned_model():
     assert m.stat("eval_block") in (64, 128, 256) and m.stat("tune_ms") > 0
 
 
-@pytest.mark.parametrize("choice", ["split", "scatter", "no_hcomp", "upfront", "split+scatter+no_hcomp+upfront"])
+@pytest.mark.parametrize("choice", ["split", "scatter", "no_hcomp", "upfront", "split+scatter+no_hcomp+upfront",
+                                    "lanes2", "lanes2+split+no_hcomp"])
 def test_pinned_launch_choices(choice):
     """Every choice the tuner makes, fixed through the creation options instead, gives the same
     results: first/second order split, the Jacobian CSC scattered by the evaluation kernel, the
-    Hessian CSC summed from the COO slots, the up-front emission order, and a register cap through
-    min_blocks."""
+    Hessian CSC summed from the COO slots, the up-front emission order, two warp sets per instance,
+    and a register cap through min_blocks."""
     B = _B()
     flags = B.EXA_FLAG_NO_TUNE
     flags |= B.EXA_FLAG_SPLIT if "split" in choice else 0
     flags |= B.EXA_FLAG_CSC_SCATTER if "scatter" in choice else 0
     flags |= B.EXA_FLAG_NO_HCOMP if "no_hcomp" in choice else 0
     flags |= B.EXA_FLAG_UPFRONT if "upfront" in choice else 0
+    flags |= B.EXA_FLAG_LANES2 if "lanes2" in choice else 0
     wl = synth.acopf(200, 300, 40, seed=8)
     x, y, s = synth.acopf_point(wl, 2)
     m, _ = check_model(wl.flat, x, y, s, flags=flags, block=64, min_blocks=12)
@@ -152,6 +154,37 @@ def test_pinned_launch_choices(choice):
     assert m.stat("hess_compressed") == ("no_hcomp" not in choice)
     assert m.stat("eval_min_blocks") == 12 and m.stat("eval_block") == 64
     assert m.stat("eval_upfront") == ("upfront" in choice)
+    assert m.stat("eval_lanes") == (2 if "lanes2" in choice else 1)
+
+
+@pytest.mark.parametrize("name", ["all_ops", "more_ops", "acopf_shunts", "pde_41", "goddard_2000", "two_stage_acopf"])
+def test_parity_lazy_loads(name):
+    """Each pattern's inputs loaded one pattern ahead instead of at the top of the fused group (the
+    third emission order the tuner searches) on every workload kind, with a register cap."""
+    B = _B()
+    flat, (x, y, s) = CASES[name]()
+    m, _ = check_model(flat, x, y, s, flags=B.EXA_FLAG_NO_TUNE | B.EXA_FLAG_LAZY_LOADS, block=64, min_blocks=12)
+    assert m.stat("eval_lazy") == 1
+
+
+@pytest.mark.parametrize("name", ["all_ops", "more_ops", "acopf_shunts", "pde_41", "goddard_2000", "two_stage_acopf"])
+def test_parity_two_warp_sets(name):
+    """Two warp sets per instance (each a contiguous subset of a fused group's patterns) on every
+    workload kind in FP64 (the mixed-precision tests cover the other precision), with a persistent
+    grid."""
+    B = _B()
+    flat, (x, y, s) = CASES[name]()
+    check_model(flat, x, y, s, flags=B.EXA_FLAG_NO_TUNE | B.EXA_FLAG_LANES2, block=128, grid_factor=1)
+
+
+def test_option_conflicts_are_rejected():
+    B = _B()
+    flat, _ = CASES["all_ops"]()
+    for kw in (dict(block=32, flags=B.EXA_FLAG_LANES2), dict(block=64, flags=B.EXA_FLAG_LANES2 | B.EXA_FLAG_PF_COLUMNS),
+               dict(block=64, flags=B.EXA_FLAG_LAZY_LOADS | B.EXA_FLAG_UPFRONT)):
+        with pytest.raises(B.ExaError) as e:
+            B.exa_create(flat, **kw)
+        assert e.value.status == B.EXA_E_INVALID
 
 
 def test_tuned_options_reproduce_the_model():
@@ -315,6 +348,7 @@ BATCH_OPTIONS = {
     "split_scatter": dict(flags=2 | 16 | 32),
     "no_hcomp_chunks": dict(flags=2 | 64, chunks=3),
     "chunks_partial_wave_prefetch": dict(flags=2 | 512, chunks=4, wave_pct=50, block=32),
+    "two_warp_sets_split": dict(flags=2 | 1024 | 16, block=128, chunks=2),
 }
 
 
