@@ -15,6 +15,7 @@
 #include <chrono>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <set>
 #include <memory>
@@ -997,6 +998,24 @@ exa_status autotune(exa_model *m) {
     cudaEvent_t e0, e1;
     CR(cudaEventCreate(&e0));
     CR(cudaEventCreate(&e1));
+    // one warm call, then the best of three rounds of `reps` calls (milliseconds per round): the
+    // rounds make the choice between nearly equal variants less sensitive to a noisy round
+    auto time_rounds = [&](const std::function<exa_status()> &call, int reps, float *best_ms) -> exa_status {
+        if (exa_status e = call()) return e;
+        float bm = 1e30f;
+        for (int round = 0; round < 3; round++) {
+            CR(cudaEventRecord(e0, m->stream));
+            for (int r = 0; r < reps; r++)
+                if (exa_status e = call()) return e;
+            CR(cudaEventRecord(e1, m->stream));
+            CR(cudaEventSynchronize(e1));
+            float ms = 0;
+            CR(cudaEventElapsedTime(&ms, e0, e1));
+            bm = std::min(bm, ms);
+        }
+        *best_ms = bm;
+        return EXA_OK;
+    };
     double best = 1e30;
     int best_block = m->block, best_factor = 0;
     const int blocks[] = {64, 128, 256};
@@ -1029,14 +1048,8 @@ exa_status autotune(exa_model *m) {
         for (int factor : {0, 1, 2, 4}) {
             if (exa_status e = apply_grid(m, factor)) return e;
             if (factor > 0 && m->grid[exa::M_ALL] == m->ntiles[exa::M_ALL]) continue;
-            if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
-            CR(cudaEventRecord(e0, m->stream));
-            for (int r = 0; r < 5; r++)
-                if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
-            CR(cudaEventRecord(e1, m->stream));
-            CR(cudaEventSynchronize(e1));
             float ms = 0;
-            CR(cudaEventElapsedTime(&ms, e0, e1));
+            if (exa_status e = time_rounds([&]() { return launch_eval(m, exa::M_ALL, x, y, 1.0, o); }, 5, &ms)) return e;
             if (ms < best) {
                 best = ms;
                 best_block = B;
@@ -1087,14 +1100,8 @@ exa_status autotune(exa_model *m) {
             o.jac = m->d_jbuf;
             o.hess = m->d_hbuf;
             if (exa_status e = apply_grid(m, best_factor)) return e;
-            if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
-            CR(cudaEventRecord(e0, m->stream));
-            for (int r = 0; r < 5; r++)
-                if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
-            CR(cudaEventRecord(e1, m->stream));
-            CR(cudaEventSynchronize(e1));
             float ms = 0;
-            CR(cudaEventElapsedTime(&ms, e0, e1));
+            if (exa_status e = time_rounds([&]() { return launch_eval(m, exa::M_ALL, x, y, 1.0, o); }, 5, &ms)) return e;
             if (ms < best) {
                 best = ms;
                 best_minb = minb;
@@ -1127,14 +1134,8 @@ exa_status autotune(exa_model *m) {
         o.gbuf = m->d_gbuf;
         o.jac = m->d_jbuf;
         o.hess = m->d_hbuf;
-        if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
-        CR(cudaEventRecord(e0, m->stream));
-        for (int r = 0; r < 5; r++)
-            if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
-        CR(cudaEventRecord(e1, m->stream));
-        CR(cudaEventSynchronize(e1));
         float ms = 0;
-        CR(cudaEventElapsedTime(&ms, e0, e1));
+        if (exa_status e = time_rounds([&]() { return launch_eval(m, exa::M_ALL, x, y, 1.0, o); }, 5, &ms)) return e;
         if (ms < best) {
             best = ms;
             best_pf = pf;
@@ -1176,14 +1177,8 @@ exa_status autotune(exa_model *m) {
             o.gbuf = m->d_gbuf;
             o.jac = m->d_jbuf;
             o.hess = m->d_hbuf;
-            if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
-            CR(cudaEventRecord(e0, m->stream));
-            for (int r = 0; r < 5; r++)
-                if (exa_status e = launch_eval(m, exa::M_ALL, x, y, 1.0, o)) return e;
-            CR(cudaEventRecord(e1, m->stream));
-            CR(cudaEventSynchronize(e1));
             float ms = 0;
-            CR(cudaEventElapsedTime(&ms, e0, e1));
+            if (exa_status e = time_rounds([&]() { return launch_eval(m, exa::M_ALL, x, y, 1.0, o); }, 5, &ms)) return e;
             if (ms < best) {
                 best = ms;
                 best_lanes = 2;
@@ -1223,14 +1218,10 @@ exa_status autotune(exa_model *m) {
             m->split_all = split;
             m->csc_direct = direct;
             m->use_hcomp = hcv;
-            if (exa_status e = eval_all_launches(m, x, y, 1.0, f, g, m->d_cbuf, m->d_jbuf, m->d_hbuf, jc, hc)) return e;
-            CR(cudaEventRecord(e0, m->stream));
-            for (int r = 0; r < 3; r++)
-                if (exa_status e = eval_all_launches(m, x, y, 1.0, f, g, m->d_cbuf, m->d_jbuf, m->d_hbuf, jc, hc)) return e;
-            CR(cudaEventRecord(e1, m->stream));
-            CR(cudaEventSynchronize(e1));
             float ms = 0;
-            CR(cudaEventElapsedTime(&ms, e0, e1));
+            if (exa_status e = time_rounds([&]() { return eval_all_launches(m, x, y, 1.0, f, g, m->d_cbuf, m->d_jbuf, m->d_hbuf, jc, hc); },
+                                           3, &ms))
+                return e;
             if (ms < best_step) {
                 best_step = ms;
                 best_split = split;
@@ -1246,6 +1237,39 @@ exa_status autotune(exa_model *m) {
     m->split_all = best_split;
     m->csc_direct = best_direct;
     m->use_hcomp = best_hc;
+    // the register cap was chosen for the fused kernel; when the step runs first and second order
+    // as two kernels, the cap is searched again with whole steps (the variants are compiled)
+    if (best_split && m->lanes == 1) {
+        int split_minb = m->min_blocks;
+        for (int warps : {0, 20, 24, 28, 32}) {
+            const int minb = warps * 32 / best_block;
+            if (minb > 32 || (warps && minb < 1) || minb == m->min_blocks) continue;
+            const int keep = m->min_blocks;
+            if (exa_status e = setup_kernels(m, best_block, minb)) return e;
+            int occ = 0;
+            CR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)m->fn[exa::M_FIRST], best_block, 0));
+            if (minb && occ < minb) {
+                if (exa_status e = setup_kernels(m, best_block, keep)) return e;
+                if (exa_status e = apply_grid(m, best_factor)) return e;
+                continue;
+            }
+            if (exa_status e = apply_grid(m, best_factor)) return e;
+            float ms = 0;
+            if (exa_status e = time_rounds([&]() { return eval_all_launches(m, x, y, 1.0, f, g, m->d_cbuf, m->d_jbuf, m->d_hbuf, jc, hc); },
+                                           3, &ms))
+                return e;
+            if (ms < best_step) {
+                best_step = ms;
+                split_minb = minb;
+            }
+            if (exa_status e = setup_kernels(m, best_block, keep)) return e;
+            if (exa_status e = apply_grid(m, best_factor)) return e;
+        }
+        if (split_minb != m->min_blocks) {
+            if (exa_status e = setup_kernels(m, best_block, split_minb)) return e;
+            if (exa_status e = apply_grid(m, best_factor)) return e;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return EXA_OK;
