@@ -420,7 +420,7 @@ def family_configs(B, torch, timed, local, peak_hbm, cpu_budget, sweep=False):
 
 def compile_sweep(args):
     """Code generation + NVRTC time and model-creation time against the number of patterns and the
-    size of their trees (the analogue of the paper's compile-time experiment, Sec. 7.4): P
+    size of their trees (the analogue of the paper's experiment in its section on model compilation time): P
     constraint patterns over one variable array, pattern p a sum of K terms
     c_pj sin(x[k+j] + p) x[k+j+1]^2 + exp(x[k+j] / (p+2)) with its own constants, so every pattern
     is distinct code.  Creation is timed without the autotuner and with an empty module cache for

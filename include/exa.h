@@ -295,9 +295,9 @@ exa_status exa_eval_all(exa_model *m, const double *x, const double *y, double s
  * exa_eval_all) may be host memory, page-locked or pageable, or device memory.  Host inputs are
  * copied into device buffers the library owns (allocated on first use), the exa_eval_all graph is
  * replayed on the model stream, host outputs are copied back, and the call returns when they are
- * in host memory (the stream is synchronized).  Device arguments are used in place.  Page-locked
- * host buffers (cudaHostAlloc / cudaHostRegister) are copied at full link speed, each output as
- * soon as it is final (the COO values while the CSC sums still run); pageable ones at the end. */
+ * in host memory (the stream is synchronized).  Device arguments are used in place.  The host
+ * outputs are copied back one after another on the model stream once the evaluation graph has run;
+ * page-locked host buffers (cudaHostAlloc / cudaHostRegister) are copied at full link speed. */
 exa_status exa_eval_all_host(exa_model *m, const double *x, const double *y, double sigma,
                              double *f, double *g, double *c, double *jac, double *hess,
                              double *jac_csc, double *hess_csc);

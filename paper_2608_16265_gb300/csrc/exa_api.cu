@@ -335,7 +335,7 @@ struct exa_model {
     std::vector<ExaPM> h_pms;     // host copy of the group descriptors
     // CUDA graphs of exa_eval_all, one per argument tuple
     struct GraphEntry {
-        std::array<const void *, 17> key;
+        std::array<const void *, 10> key;
         cudaGraphExec_t exec;
         uint64_t last_use;
     };
@@ -344,12 +344,13 @@ struct exa_model {
     int graph_kernels = 0;  // kernel launches in the most recently captured exa_eval_all graph
     bool use_graphs = true;
     cudaStream_t cap_stream = nullptr;
-    // exa_eval_all runs its independent reductions (Jacobian CSC, Hessian CSC, the rest) on three
-    // streams forked from and joined back into the model stream
+    // exa_eval_all runs its independent reductions on side streams forked from and joined back into
+    // the model stream: 0 the Jacobian CSC (and member chunks' reductions), 1 the Hessian CSC, 3 the
+    // split mode's first-order sums (2 is not used)
     cudaStream_t side[4] = {};
     // device buffers of exa_eval_all_host: x, y, f, g, c, jac, hess, jac_csc, hess_csc
     double *d_host_io[9] = {};
-    cudaEvent_t ev_fork = nullptr, ev_first = nullptr, ev_join[4] = {}, ev_out[3] = {};
+    cudaEvent_t ev_fork = nullptr, ev_first = nullptr, ev_join[4] = {};
     double *d_theta = nullptr;
     int *d_status = nullptr;
     int *d_jrow = nullptr, *d_jcol = nullptr, *d_hrow = nullptr, *d_hcol = nullptr, *d_gvar = nullptr, *d_arow = nullptr;
@@ -399,7 +400,7 @@ struct exa_model {
 extern "C" {
 static exa_status eval_all_launches(exa_model *m, const double *x, const double *y, double sigma, double *f,
                                     double *g, double *c, double *jac, double *hess, double *jac_csc,
-                                    double *hess_csc, double *const *host_out = nullptr);
+                                    double *hess_csc);
 }
 
 namespace {
@@ -437,10 +438,8 @@ void free_all(exa_model *m) {
     for (int s = 0; s < 4; s++) {
         if (m->side[s]) cudaStreamDestroy(m->side[s]);
         if (m->ev_join[s]) cudaEventDestroy(m->ev_join[s]);
-        if (s < 3 && m->ev_out[s]) cudaEventDestroy(m->ev_out[s]);
         m->side[s] = nullptr;
         m->ev_join[s] = nullptr;
-        if (s < 3) m->ev_out[s] = nullptr;
     }
     if (m->ev_fork) cudaEventDestroy(m->ev_fork);
     if (m->ev_first) cudaEventDestroy(m->ev_first);
@@ -1993,7 +1992,7 @@ static cudaError_t side_stream(cudaStream_t *s) {
 // overlaps these reductions.  The objective sum follows the last evaluation; the host copies of
 // f, g, c follow the last reduction.  Same kernels, same per-element arithmetic as one chunk.
 static exa_status eval_all_chunked(exa_model *m, const double *x, const double *y, double sigma, double *f, double *g,
-                                   double *c, double *jac_csc, double *hess_csc, double *const *host_out, ExaOut o,
+                                   double *c, double *jac_csc, double *hess_csc, ExaOut o,
                                    Mode mode, Mode hmode, bool split, bool jdirect, bool hdirect, bool hcomp) {
     if (!m->ev_fork) CR(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
     for (int s = 0; s < 3; s++) {
@@ -2092,19 +2091,12 @@ static exa_status eval_all_chunked(exa_model *m, const double *x, const double *
     }
     CR(cudaEventRecord(m->ev_join[0], ps));
     CR(cudaStreamWaitEvent(m->stream, m->ev_join[0], 0));
-    if (host_out) {  // every page-locked host output, once everything is final
-        const double *src[7] = {f, g, c, o.jac, o.hess, jac_csc, hess_csc};
-        const i64 n[7] = {1, m->nvar, m->ncon, m->nnzj, m->nnzh, m->nnzj_csc, m->nnzh_csc};
-        for (int k = 0; k < 7; k++)
-            if (host_out[k] && src[k] && n[k] > 0)
-                CR(cudaMemcpyAsync(host_out[k], src[k], sizeof(double) * n[k], cudaMemcpyDeviceToHost, m->stream));
-    }
     return EXA_OK;
 }
 
 static exa_status eval_all_launches(exa_model *m, const double *x, const double *y, double sigma, double *f,
                                     double *g, double *c, double *jac, double *hess, double *jac_csc,
-                                    double *hess_csc, double *const *host_out) {
+                                    double *hess_csc) {
     const bool want_h = hess || hess_csc;
     ExaOut o{};
     o.obj_part = m->d_objpart;
@@ -2137,22 +2129,17 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
     Mode mode = !want_h ? exa::M_FIRST : (hcomp ? (hcoo ? exa::M_ALL_B : exa::M_ALL_C) : exa::M_ALL);
     const Mode hmode = hcomp ? (hcoo ? exa::M_HESS_B : exa::M_HESS_C) : exa::M_HESS;
     if (m->nchunks > 1)
-        return eval_all_chunked(m, x, y, sigma, f, g, c, jac_csc, hess_csc, host_out, o, want_h ? mode : exa::M_FIRST,
+        return eval_all_chunked(m, x, y, sigma, f, g, c, jac_csc, hess_csc, o, want_h ? mode : exa::M_FIRST,
                                 hmode, want_h && m->split_all, jdirect, hdirect, hcomp);
     // Streams: the model stream runs the evaluation kernel(s); side 0 the Jacobian CSC, side 1 the
-    // Hessian CSC, side 2 the host copies, side 3 (split mode) the objective, gradient and
-    // constraint sums.  Each branch is forked from and joined back into the model stream (parallel
-    // branches of the captured graph).  In split mode every first-order reduction starts as soon as
-    // the first-order kernel has run, overlapping the second-order kernel: the reductions move
-    // bytes, the second-order kernel keeps the FP64 pipe busy.
+    // Hessian CSC, side 3 (split mode) the objective, gradient and constraint sums.  Each branch is
+    // forked from and joined back into the model stream (parallel branches of the captured graph).
+    // In split mode every first-order reduction starts as soon as the first-order kernel has run,
+    // overlapping the second-order kernel: the reductions move bytes, the second-order kernel keeps
+    // the FP64 pipe busy.
     const bool split = want_h && m->split_all;
     const bool jside = jac_csc && !jdirect && m->nnzj_csc, hside = (hcomp || (hess_csc && !hdirect)) && m->nnzh_csc;
-    auto hout = [&](int k, const double *dev) -> double * { return host_out && dev ? host_out[k] : nullptr; };
-    double *const hf = hout(0, f), *const hg = hout(1, g), *const hc = hout(2, c);
-    double *const hj = jac ? hout(3, o.jac) : nullptr, *const hh = hess ? hout(4, o.hess) : nullptr;
-    double *const hjc = hout(5, jac_csc), *const hhc = hout(6, hess_csc);
-    const bool cside = hf || hg || hc || hj || hh || hjc || hhc;
-    const bool forked = jside || hside || cside || split;
+    const bool forked = jside || hside || split;
     if (forked) {
         if (!m->ev_fork) CR(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
         if (!m->ev_first) CR(cudaEventCreateWithFlags(&m->ev_first, cudaEventDisableTiming));
@@ -2160,8 +2147,6 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
             if (!m->side[s]) CR(side_stream(&m->side[s]));
             if (!m->ev_join[s]) CR(cudaEventCreateWithFlags(&m->ev_join[s], cudaEventDisableTiming));
         }
-        for (int s = 0; s < 3; s++)
-            if (!m->ev_out[s]) CR(cudaEventCreateWithFlags(&m->ev_out[s], cudaEventDisableTiming));
     }
     if (split) {  // first order and second order as two kernels
         ExaOut o1 = o, o2{};
@@ -2183,21 +2168,6 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
     const cudaEvent_t first_done = split ? m->ev_first : m->ev_fork;  // first-order outputs final
     cudaStream_t rs = split ? m->side[3] : m->stream;                  // stream of the f, g, c sums
     if (split) CR(cudaStreamWaitEvent(rs, m->ev_first, 0));
-    // one finished output (on stream rs) copied to the host on side stream 2
-    auto to_host = [&](int slot, double *dst, const double *src, i64 n) -> exa_status {
-        CR(cudaEventRecord(m->ev_out[slot], rs));
-        CR(cudaStreamWaitEvent(m->side[2], m->ev_out[slot], 0));
-        CR(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToHost, m->side[2]));
-        return EXA_OK;
-    };
-    if (hj && m->nnzj) {  // the COO values are final once their kernel ran
-        CR(cudaStreamWaitEvent(m->side[2], first_done, 0));
-        CR(cudaMemcpyAsync(hj, o.jac, sizeof(double) * m->nnzj, cudaMemcpyDeviceToHost, m->side[2]));
-    }
-    if (hh && m->nnzh) {
-        CR(cudaStreamWaitEvent(m->side[2], m->ev_fork, 0));
-        CR(cudaMemcpyAsync(hh, o.hess, sizeof(double) * m->nnzh, cudaMemcpyDeviceToHost, m->side[2]));
-    }
     if (jside) {
         CR(cudaStreamWaitEvent(m->side[0], first_done, 0));
         if (exa_status e = scatter_csc(m, m->sum_j, m->d_jperm, o.jac, jac_csc, m->nnzj_csc, m->nnzj, m->side[0])) return e;
@@ -2216,33 +2186,14 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
     if (f) {
         k_obj_final<<<1, 256, 0, rs>>>(m->d_objpart, eval_grid(m, mode, m->ntiles[mode]), f);
         CR(cudaGetLastError());
-        if (hf)
-            if (exa_status e = to_host(0, hf, f, 1)) return e;
     }
-    if (g && m->nvar) {
+    if (g && m->nvar)
         if (exa_status e = grad_sum(m, g, rs)) return e;
-        if (hg)
-            if (exa_status e = to_host(1, hg, g, m->nvar)) return e;
-    }
-    if (c) {
+    if (c)
         if (exa_status e = aug_rows(m, c, rs)) return e;
-        if (hc && m->ncon)
-            if (exa_status e = to_host(2, hc, c, m->ncon)) return e;
-    }
-    // the CSC values go to the host after their reductions (side streams 0 and 1)
-    if (hjc && m->nnzj_csc) {
-        CR(cudaStreamWaitEvent(m->side[2], jside ? m->ev_join[0] : first_done, 0));
-        CR(cudaMemcpyAsync(hjc, jac_csc, sizeof(double) * m->nnzj_csc, cudaMemcpyDeviceToHost, m->side[2]));
-    }
-    if (hhc && m->nnzh_csc) {
-        CR(cudaStreamWaitEvent(m->side[2], hside ? m->ev_join[1] : m->ev_fork, 0));
-        CR(cudaMemcpyAsync(hhc, hess_csc, sizeof(double) * m->nnzh_csc, cudaMemcpyDeviceToHost, m->side[2]));
-    }
-    if (cside) CR(cudaEventRecord(m->ev_join[2], m->side[2]));
     if (split) CR(cudaEventRecord(m->ev_join[3], m->side[3]));
     if (jside) CR(cudaStreamWaitEvent(m->stream, m->ev_join[0], 0));
     if (hside) CR(cudaStreamWaitEvent(m->stream, m->ev_join[1], 0));
-    if (cside) CR(cudaStreamWaitEvent(m->stream, m->ev_join[2], 0));
     if (split) CR(cudaStreamWaitEvent(m->stream, m->ev_join[3], 0));
     return EXA_OK;
 }
@@ -2252,16 +2203,14 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
 // used evicted).  When the model's stream is itself being captured, the launches go straight into
 // the caller's capture instead.
 static exa_status eval_all_cached(exa_model *m, const double *x, const double *y, double sigma, double *f, double *g,
-                                  double *c, double *jac, double *hess, double *jac_csc, double *hess_csc,
-                                  double *const *host_out) {
+                                  double *c, double *jac, double *hess, double *jac_csc, double *hess_csc) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CR(cudaStreamIsCapturing(m->stream, &cs));
     if (!m->use_graphs || cs != cudaStreamCaptureStatusNone)
-        return eval_all_launches(m, x, y, sigma, f, g, c, jac, hess, jac_csc, hess_csc, host_out);
+        return eval_all_launches(m, x, y, sigma, f, g, c, jac, hess, jac_csc, hess_csc);
     uint64_t sb;
     std::memcpy(&sb, &sigma, 8);
-    std::array<const void *, 17> key = {x, y, f, g, c, jac, hess, jac_csc, hess_csc, (const void *)(uintptr_t)sb};
-    for (int k = 0; k < 7; k++) key[10 + k] = host_out ? host_out[k] : nullptr;
+    const std::array<const void *, 10> key = {x, y, f, g, c, jac, hess, jac_csc, hess_csc, (const void *)(uintptr_t)sb};
     for (auto &ge : m->graphs)
         if (ge.key == key) {
             ge.last_use = ++m->graph_clock;
@@ -2272,7 +2221,7 @@ static exa_status eval_all_cached(exa_model *m, const double *x, const double *y
     cudaStream_t user = m->stream;
     m->stream = m->cap_stream;
     CR(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
-    exa_status st = eval_all_launches(m, x, y, sigma, f, g, c, jac, hess, jac_csc, hess_csc, host_out);
+    exa_status st = eval_all_launches(m, x, y, sigma, f, g, c, jac, hess, jac_csc, hess_csc);
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamEndCapture(m->cap_stream, &graph);
     m->stream = user;
@@ -2314,7 +2263,7 @@ exa_status exa_eval_all(exa_model *m, const double *x, const double *y, double s
     if (exa_status e = check_model(m)) return e;
     CHECK_PTRS(x);
     if ((hess || hess_csc) && m->ncon && !y) return fail(m, EXA_E_INVALID, "NULL y");
-    return eval_all_cached(m, x, y, sigma, f, g, c, jac, hess, jac_csc, hess_csc, nullptr);
+    return eval_all_cached(m, x, y, sigma, f, g, c, jac, hess, jac_csc, hess_csc);
 }
 
 exa_status exa_eval_all_host(exa_model *m, const double *x, const double *y, double sigma, double *f, double *g,
@@ -2326,33 +2275,25 @@ exa_status exa_eval_all_host(exa_model *m, const double *x, const double *y, dou
     const i64 n[9] = {m->nvar, m->ncon, 1, m->nvar, m->ncon, m->nnzj, m->nnzh, m->nnzj_csc, m->nnzh_csc};
     double *arg[9] = {const_cast<double *>(x), const_cast<double *>(y), f, g, c, jac, hess, jac_csc, hess_csc};
     double *use[9] = {};
-    bool staged[9] = {}, pinned[9] = {};
+    bool staged[9] = {};
     for (int k = 0; k < 9; k++) {
         if (!arg[k]) continue;
         cudaPointerAttributes a{};
         CR(cudaPointerGetAttributes(&a, arg[k]));
         staged[k] = a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged;
-        pinned[k] = a.type == cudaMemoryTypeHost;
         if (staged[k] && !m->d_host_io[k]) CR(dalloc(m, &m->d_host_io[k], n[k]));
         use[k] = staged[k] ? m->d_host_io[k] : arg[k];
     }
     for (int k = 0; k < 2; k++)
         if (staged[k] && n[k] > 0)
             CR(cudaMemcpyAsync(use[k], arg[k], sizeof(double) * n[k], cudaMemcpyHostToDevice, m->stream));
-    // page-locked outputs are copied back inside the evaluation, each as soon as it is final
-    // (overlapping the reductions that follow); pageable ones after it
-    double *host_out[7] = {};
-    bool early = false;
-    for (int k = 2; k < 9; k++)
-        if (staged[k] && pinned[k]) {
-            host_out[k - 2] = arg[k];
-            early = true;
-        }
-    if (exa_status e = eval_all_cached(m, use[0], use[1], sigma, use[2], use[3], use[4], use[5], use[6], use[7], use[8],
-                                       early ? host_out : nullptr))
+    // the device-only graph, then every host output copied back on the model stream in turn (plain
+    // stream-ordered copies: copies issued from a side stream inside the graph, overlapping the
+    // reductions, ran at half the link rate on some boxes while these ran at full rate)
+    if (exa_status e = eval_all_cached(m, use[0], use[1], sigma, use[2], use[3], use[4], use[5], use[6], use[7], use[8]))
         return e;
     for (int k = 2; k < 9; k++)
-        if (staged[k] && n[k] > 0 && !host_out[k - 2])
+        if (staged[k] && n[k] > 0)
             CR(cudaMemcpyAsync(arg[k], use[k], sizeof(double) * n[k], cudaMemcpyDeviceToHost, m->stream));
     CR(cudaStreamSynchronize(m->stream));
     return EXA_OK;
