@@ -36,8 +36,9 @@ typedef long long i64;
 // ------------------------------------------------------------------ static kernels
 namespace {
 
-// f[0] = sum of the per-CTA objective partials in a fixed order (deterministic).
-__global__ void k_obj_final(const double *__restrict__ part, int n, double *__restrict__ f) {
+// f[0] = sum of the per-CTA objective partials in a fixed order (deterministic for a given n and
+// block size; launched with one CTA of 1024 threads, so 32 warp sums are added by thread 0).
+__global__ void __launch_bounds__(1024) k_obj_final(const double *__restrict__ part, int n, double *__restrict__ f) {
     double s = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
@@ -1729,7 +1730,7 @@ exa_status exa_obj(exa_model *m, const double *x, double *f) {
     ExaOut o{};
     o.obj_part = m->d_objpart;
     if (exa_status e = launch_eval(m, exa::M_OBJ, x, nullptr, 0.0, o)) return e;
-    k_obj_final<<<1, 256, 0, m->stream>>>(m->d_objpart, eval_grid(m, exa::M_OBJ, m->ntiles[exa::M_OBJ]), f);
+    k_obj_final<<<1, 1024, 0, m->stream>>>(m->d_objpart, eval_grid(m, exa::M_OBJ, m->ntiles[exa::M_OBJ]), f);
     CR(cudaGetLastError());
     return EXA_OK;
 }
@@ -1778,7 +1779,7 @@ exa_status exa_obj_noalloc(exa_model *m, const double *x, double *f) {
     ExaOut o{};
     o.obj_part = part;
     if (exa_status e = launch_eval(m, exa::M_OBJ, x, nullptr, 0.0, o)) return e;
-    k_obj_final<<<1, 256, 0, m->stream>>>(part, nparts, f);
+    k_obj_final<<<1, 1024, 0, m->stream>>>(part, nparts, f);
     CR(cudaGetLastError());
     return EXA_OK;
 }
@@ -2086,7 +2087,7 @@ static exa_status eval_all_chunked(exa_model *m, const double *x, const double *
         }
     }
     if (f) {
-        k_obj_final<<<1, 256, 0, m->stream>>>(m->d_objpart, nparts, f);
+        k_obj_final<<<1, 1024, 0, m->stream>>>(m->d_objpart, nparts, f);
         CR(cudaGetLastError());
     }
     CR(cudaEventRecord(m->ev_join[0], ps));
@@ -2184,7 +2185,7 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
         CR(cudaEventRecord(m->ev_join[1], m->side[1]));
     }
     if (f) {
-        k_obj_final<<<1, 256, 0, rs>>>(m->d_objpart, eval_grid(m, mode, m->ntiles[mode]), f);
+        k_obj_final<<<1, 1024, 0, rs>>>(m->d_objpart, eval_grid(m, mode, m->ntiles[mode]), f);
         CR(cudaGetLastError());
     }
     if (g && m->nvar)
