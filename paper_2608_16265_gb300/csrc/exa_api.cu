@@ -11,6 +11,7 @@
 #include <nvrtc.h>
 
 #include <algorithm>
+#include <cmath>
 #include <array>
 #include <chrono>
 #include <cstdio>
@@ -977,7 +978,7 @@ exa_status apply_grid(exa_model *m, int factor) {
 }
 
 // Launch-shape autotuner, in three stages, each keeping the fastest variant: (1) the fused
-// evaluation kernel (everything, at x = 1, y = 1) for 64 / 128 / 256 threads per CTA and one CTA per
+// evaluation kernel (everything, at varied inputs of unit size) for 64 / 128 / 256 threads per CTA and one CTA per
 // tile versus persistent grids of 1, 2 and 4 waves of resident CTAs; (2) for that shape, launch
 // bounds for 20 to 32 resident warps per SM or none, with either emission order of the generated
 // arithmetic; (3) whole exa_eval_all steps with every output: member chunks, compressed or COO
@@ -992,9 +993,15 @@ exa_status autotune(exa_model *m) {
     double *x = nullptr, *y = nullptr, *part = nullptr;
     CR(S.get(&x, m->nvar));
     CR(S.get(&y, m->ncon));
-    std::vector<double> ones((size_t)std::max(m->nvar, m->ncon), 1.0);
-    CR(cudaMemcpy(x, ones.data(), sizeof(double) * m->nvar, cudaMemcpyHostToDevice));
-    if (m->ncon) CR(cudaMemcpy(y, ones.data(), sizeof(double) * m->ncon, cudaMemcpyHostToDevice));
+    // tuning inputs: deterministic, varied and of unit size (x in [0.9, 1.1], y in [-1, 1], from
+    // golden-ratio sequences), so that angle differences, products and derivatives are nonzero
+    // as at a real iterate (constant inputs would make many of them exactly zero, which takes other
+    // branches in the exact conversions of the mixed mode)
+    std::vector<double> hv((size_t)std::max<i64>(std::max(m->nvar, m->ncon), 1));
+    for (size_t i = 0; i < hv.size(); i++) hv[i] = 0.9 + 0.2 * std::fmod(0.6180339887498949 * (double)(i + 1), 1.0);
+    CR(cudaMemcpy(x, hv.data(), sizeof(double) * m->nvar, cudaMemcpyHostToDevice));
+    for (size_t i = 0; i < hv.size(); i++) hv[i] = -1.0 + 2.0 * std::fmod(0.7548776662466927 * (double)(i + 1), 1.0);
+    if (m->ncon) CR(cudaMemcpy(y, hv.data(), sizeof(double) * m->ncon, cudaMemcpyHostToDevice));
     cudaEvent_t e0, e1;
     CR(cudaEventCreate(&e0));
     CR(cudaEventCreate(&e1));
