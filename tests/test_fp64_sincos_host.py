@@ -1,9 +1,14 @@
 """The FP64 sin/cos helper of the generated kernels (csrc/exa_fp64_sincos.inc: Cody-Waite
-reduction, Taylor polynomials) compiled for the host with shims for the CUDA bit-cast intrinsics
+reduction, minimax polynomials) compiled for the host with shims for the CUDA bit-cast intrinsics
 and checked against the host C library: within 1 ulp over a sweep of arguments next to multiples
 of pi/2, tiny, large and signed-zero arguments.  Host fma is correctly rounded like the device's,
-so the host build computes the same values as the kernels."""
+so the host build computes the same values as the kernels.  The polynomial coefficients in the
+helper are the ones the Remez script beside it (csrc/gen_sincos_minimax.py) derives, and that script's
+error bound for them is checked independently of the script: the rounded polynomials are compared
+with mpmath's sin and cos on a grid that the script does not use."""
 import os
+import re
+import sys
 import shutil
 import subprocess
 
@@ -71,3 +76,34 @@ def test_fp64_sincos_helper_against_libm(tmp_path):
     assert n > 50000
     assert worst <= 2.3e-16, worst  # 1 ulp relative
     assert sb0 == 1 and sb1 == 0 and c0 == 1.0 and c1 == 1.0
+
+
+def test_sincos_coefficients_are_the_remez_ones():
+    mp = pytest.importorskip("mpmath")
+    sys.path.insert(0, os.path.dirname(INC))
+    try:
+        import gen_sincos_minimax as gen
+    finally:
+        sys.path.pop(0)
+    s_coef, c_coef = gen.derive()
+    text = open(INC).read()
+    lits = [float.fromhex(v) for v in re.findall(r"-?0x1\.[0-9a-f]+p[-+]?\d+", text)]
+    # every derived coefficient appears in the helper, sin in S(z) and cos in C(z)
+    for a in s_coef + c_coef:
+        assert a in lits, a.hex()
+    # independent check of the bound: relative error of the rounded polynomials against mpmath on
+    # a grid offset from the script's, in 50-digit arithmetic
+    mp.mp.dps = 50
+    worst_s = worst_c = mp.mpf(0)
+    for i in range(1, 1501):
+        r = (mp.pi / 4) * (mp.mpf(i) - mp.mpf("0.37")) / 1500
+        z = r * r
+        ps = mp.mpf(0)
+        for a in reversed(s_coef):
+            ps = ps * z + mp.mpf(a)
+        pc = mp.mpf(0)
+        for a in reversed(c_coef):
+            pc = pc * z + mp.mpf(a)
+        worst_s = max(worst_s, abs((r + r * z * ps) / mp.sin(r) - 1))
+        worst_c = max(worst_c, abs((1 - z / 2 + z * z * pc) / mp.cos(r) - 1))
+    assert worst_s < 2.0 ** -55 and worst_c < 2.0 ** -55, (float(worst_s), float(worst_c))

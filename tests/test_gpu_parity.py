@@ -584,7 +584,7 @@ def test_invalid_arguments_are_reported():
 
 
 def test_fp64_sin_cos_accuracy():
-    """FP64 sin and cos of the generated code (Cody-Waite reduction, Taylor polynomials) against
+    """FP64 sin and cos of the generated code (Cody-Waite reduction, minimax polynomials) against
     the host C library over a sweep that includes arguments next to multiples of pi/2, signed
     zeros, tiny and large arguments (the library path beyond 2^20): within 3 ulp of the host
     values (6.7e-16 relative)."""
