@@ -180,10 +180,16 @@ enum {
                                   group's patterns (fewer registers per thread); block_threads must
                                   be a multiple of 64; excludes the prefetch flags.  The kernels
                                   that form the compressed Hessian sums keep one set */
-    EXA_FLAG_LAZY_LOADS = 2048 /* with the default emission order: each pattern's inputs (x values,
+    EXA_FLAG_LAZY_LOADS = 2048, /* with the default emission order: each pattern's inputs (x values,
                                   f64 data, parameters, multipliers) are loaded just before the
                                   arithmetic of the pattern preceding it, not all at the top of the
                                   fused group (fewer values live); excludes EXA_FLAG_UPFRONT */
+    EXA_FLAG_STAGE_SMEM = 4096 /* staging depth 1: the tile loop copies the inputs of the CTA's next
+                                  tile (data columns, x values indexed by the instance alone,
+                                  constraint multipliers) into shared memory with cp.async while the
+                                  current tile computes from a second buffer; gathers through data
+                                  fields still load from global memory.  Excludes EXA_FLAG_LANES2 and
+                                  the prefetch flags; ignored with EXA_FLAG_BOUNDS_CHECK */
 };
 
 /* Validate the descriptor (Sec. 3.4 SIMDFunction), lower every pattern to generated device

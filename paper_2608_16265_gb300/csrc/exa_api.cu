@@ -330,6 +330,8 @@ struct exa_model {
     int prefetch = 0;             // L2 prefetch depth of the generated tile loop (CodegenOptions)
     int lanes = 1;                // warp sets per instance of split groups (CodegenOptions)
     bool lazy_loads = false;      // with by_pattern: inputs loaded one pattern ahead (CodegenOptions)
+    int stage = 0;                // inputs of the next tile staged in shared memory (CodegenOptions)
+    int dsmem[exa::M_COUNT] = {}; // dynamic shared memory of each kernel kind (bytes)
     int wave_pct = 0;             // persistent evaluation grid of this % of one wave (0: off)
     int pfd[exa::M_COUNT] = {};   // prefetch distance in tiles per kernel kind (0: none)
     bool split_all = false;       // exa_eval_all: first- and second-order kernels instead of one
@@ -534,6 +536,8 @@ exa_status compile(exa_model *m, const std::string &src) {
     for (int k = 0; k < exa::M_COUNT; k++) {
         std::string name = std::string("exa_") + exa::kModeName[k];
         CR(cudaLibraryGetKernel(&m->fn[k], m->lib, name.c_str()));
+        if (m->dsmem[k] > 0)
+            CR(cudaFuncSetAttribute((const void *)m->fn[k], cudaFuncAttributeMaxDynamicSharedMemorySize, m->dsmem[k]));
         cudaFuncAttributes attr;
         CR(cudaFuncGetAttributes(&attr, (const void *)m->fn[k]));
         m->regs[k] = attr.numRegs;
@@ -560,7 +564,8 @@ exa_status launch_eval(exa_model *m, Mode mode, const double *x, const double *y
     int pfd = m->pfd[mode];
     void *args[] = {&tiles, &nt, &m->d_pm, &x, &y, &th, &sigma, &out, &so, &pfd};
     const int grid = eval_grid(m, mode, nt);
-    CR(cudaLaunchKernel((const void *)m->fn[mode], dim3(grid), dim3(m->block), args, 0, st ? st : m->stream));
+    CR(cudaLaunchKernel((const void *)m->fn[mode], dim3(grid), dim3(m->block), args, (size_t)m->dsmem[mode],
+                        st ? st : m->stream));
     return EXA_OK;
 }
 
@@ -911,8 +916,9 @@ exa_status setup_kernels(exa_model *m, int block, int min_blocks = 0) {
     cg.prefetch = m->lanes > 1 ? 0 : m->prefetch;
     cg.lanes = m->lanes;
     cg.lazy_loads = m->lazy_loads;
+    cg.stage = m->stage;
     std::string gerr;
-    std::string src = exa::generate_source(m->pats, m->groups, cg, &gerr);
+    std::string src = exa::generate_source(m->pats, m->groups, cg, &gerr, m->dsmem);
     if (!gerr.empty()) return fail(m, EXA_E_INTERNAL, gerr);
     if (getenv("EXA_DUMP_SOURCE")) {
         FILE *fp = fopen(getenv("EXA_DUMP_SOURCE"), "w");
@@ -964,7 +970,7 @@ exa_status apply_grid(exa_model *m, int factor) {
         m->pfd[k] = 0;
         if (k == exa::M_STRUCT) continue;
         int occ = 0;
-        CR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)m->fn[k], m->block, 0));
+        CR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)m->fn[k], m->block, (size_t)m->dsmem[k]));
         const long long wave = (long long)std::max(occ, 1) * sms;
         const long long g = (long long)std::max(factor, 0) * wave;
         if (factor > 0 && g < m->ntiles[k]) m->grid[k] = (int)g;
@@ -977,11 +983,13 @@ exa_status apply_grid(exa_model *m, int factor) {
     return EXA_OK;
 }
 
-// Launch-shape autotuner, in three stages, each keeping the fastest variant: (1) the fused
-// evaluation kernel (everything, at varied inputs of unit size) for 64 / 128 / 256 threads per CTA and one CTA per
-// tile versus persistent grids of 1, 2 and 4 waves of resident CTAs; (2) for that shape, launch
-// bounds for 20 to 32 resident warps per SM or none, with either emission order of the generated
-// arithmetic; (3) whole exa_eval_all steps with every output: member chunks, compressed or COO
+// Launch-shape autotuner, in stages, each keeping the fastest variant: (1) the fused evaluation
+// kernel (everything, at varied inputs of unit size) for 64 / 128 / 256 threads per CTA and one CTA
+// per tile versus persistent grids of 1, 2 and 4 waves of resident CTAs; (2) for that shape, launch
+// bounds for 20 to 32 resident warps per SM or none, with each of the three emission orders of the
+// generated arithmetic; (3) L2 prefetch depth; (4) two warp sets per instance; (5) shared-memory
+// staging of the next tile's inputs, with its own register cap and grid search; (6) whole
+// exa_eval_all steps with every output: member chunks and partial waves, compressed or COO
 // Hessian sums for the CSC, fused or split first/second order, CSC gathered or scattered.  The
 // code-generator variants of a stage are compiled in parallel before they are timed.  Models too
 // small to fill the GPU are not tuned.
@@ -1096,7 +1104,8 @@ exa_status autotune(exa_model *m) {
             if (exa_status e = setup_kernels(m, best_block, minb)) return e;
             if (minb && m->regs[exa::M_ALL] * best_block * minb > 65536 + 1) continue;  // bound not honoured
             int occ = 0;
-            CR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)m->fn[exa::M_ALL], best_block, 0));
+            CR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)m->fn[exa::M_ALL], best_block,
+                                                             (size_t)m->dsmem[exa::M_ALL]));
             if (occ < minb) continue;
             CR(S.get(&part, std::max(m->ntiles[exa::M_ALL], 1)));
             ExaOut o{};
@@ -1196,6 +1205,62 @@ exa_status autotune(exa_model *m) {
     }
     m->lanes = best_lanes;
     if (best_lanes == 2) best_minb = best_lminb;
+    // staging depth 1 (the next tile's inputs copied into shared memory while the current tile
+    // computes): the two buffers bound occupancy below what a register cap would, so the variant
+    // has no cap; the persistent grid (which the staging needs: a CTA with one tile has nothing to
+    // overlap) is searched afresh; kept when the fused kernel gets faster
+    const int init_stage = m->stage;
+    int best_stage = init_stage, best_sminb = best_minb, best_sfactor = best_factor;
+    if (init_stage == 0 && m->lanes == 1 && !m->bounds_check) {
+        const std::vector<int> warps_s = {0};
+        std::vector<exa::CodegenOptions> v;
+        for (int warps : warps_s) {
+            const int minb = warps * 32 / best_block;
+            if (minb <= 32 && (warps == 0 || minb >= 1)) {
+                exa::CodegenOptions cg = variant(best_block, minb, best_order != 1, 0, best_order == 2);
+                cg.stage = 1;
+                v.push_back(cg);
+            }
+        }
+        precompile(m, v);
+        m->stage = 1;
+        const int keep_pf = m->prefetch;
+        m->prefetch = 0;
+        int last_minb = -1;
+        for (int warps : warps_s) {
+            const int minb = warps * 32 / best_block;
+            if (minb > 32 || minb == last_minb || (warps && minb < 1)) continue;
+            last_minb = minb;
+            if (exa_status e = setup_kernels(m, best_block, minb)) return e;
+            if (minb && m->regs[exa::M_ALL] * best_block * minb > 65536 + 1) continue;
+            CR(S.get(&part, std::max(m->ntiles[exa::M_ALL], 1)));
+            ExaOut o{};
+            o.obj_part = part;
+            o.c = m->d_cbuf;
+            o.abuf = m->d_abuf;
+            o.gbuf = m->d_gbuf;
+            o.jac = m->d_jbuf;
+            o.hess = m->d_hbuf;
+            for (int factor : {1, 2, 4}) {
+                if (exa_status e = apply_grid(m, factor)) return e;
+                if (m->grid[exa::M_ALL] == m->ntiles[exa::M_ALL] && factor > 1) continue;
+                float ms = 0;
+                if (exa_status e = time_rounds([&]() { return launch_eval(m, exa::M_ALL, x, y, 1.0, o); }, 5, &ms)) return e;
+                if (ms < best) {
+                    best = ms;
+                    best_stage = 1;
+                    best_sminb = minb;
+                    best_sfactor = factor;
+                }
+            }
+        }
+        m->prefetch = best_stage ? 0 : keep_pf;
+    }
+    m->stage = best_stage;
+    if (best_stage && !init_stage) {
+        best_minb = best_sminb;
+        best_factor = best_sfactor;
+    }
     if (exa_status e = setup_kernels(m, best_block, best_minb)) return e;
     if (exa_status e = apply_grid(m, best_factor)) return e;
     m->tune_ms = best / 5.0;
@@ -1254,7 +1319,8 @@ exa_status autotune(exa_model *m) {
             const int keep = m->min_blocks;
             if (exa_status e = setup_kernels(m, best_block, minb)) return e;
             int occ = 0;
-            CR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)m->fn[exa::M_FIRST], best_block, 0));
+            CR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)m->fn[exa::M_FIRST], best_block,
+                                                             (size_t)m->dsmem[exa::M_FIRST]));
             if (minb && occ < minb) {
                 if (exa_status e = setup_kernels(m, best_block, keep)) return e;
                 if (exa_status e = apply_grid(m, best_factor)) return e;
@@ -1404,8 +1470,11 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     m->prefetch = (o.flags & EXA_FLAG_PF_GATHERS) ? 2 : (o.flags & EXA_FLAG_PF_COLUMNS) ? 1 : 0;
     m->lanes = (o.flags & EXA_FLAG_LANES2) ? 2 : 1;
     m->lazy_loads = (o.flags & EXA_FLAG_LAZY_LOADS) != 0;
+    m->stage = (o.flags & EXA_FLAG_STAGE_SMEM) != 0 && !m->bounds_check;
     if (m->lazy_loads && !m->by_pattern) return fail(m, EXA_E_INVALID, "EXA_FLAG_LAZY_LOADS excludes EXA_FLAG_UPFRONT");
     if (m->lanes > 1 && m->prefetch) return fail(m, EXA_E_INVALID, "EXA_FLAG_LANES2 excludes the prefetch flags");
+    if ((o.flags & EXA_FLAG_STAGE_SMEM) && (m->lanes > 1 || m->prefetch))
+        return fail(m, EXA_E_INVALID, "EXA_FLAG_STAGE_SMEM excludes EXA_FLAG_LANES2 and the prefetch flags");
     if (nb < 1) return fail(m, EXA_E_INVALID, "empty batch");
     for (int b = 0; b < nb; b++) {
         const exa_model_desc *d = descs[b];
@@ -2380,6 +2449,7 @@ exa_status exa_compile_check(const exa_model_desc *desc, const exa_options *opt,
             cg.prefetch = (o.flags & EXA_FLAG_PF_GATHERS) ? 2 : (o.flags & EXA_FLAG_PF_COLUMNS) ? 1 : 0;
             cg.lanes = (o.flags & EXA_FLAG_LANES2) ? 2 : 1;
             cg.lazy_loads = (o.flags & EXA_FLAG_LAZY_LOADS) != 0;
+            cg.stage = (o.flags & EXA_FLAG_STAGE_SMEM) != 0;
             std::string gerr;
             std::string src = exa::generate_source(tmp.pats, tmp.groups, cg, &gerr);
             if (!gerr.empty()) s = fail(&tmp, EXA_E_INTERNAL, gerr);
@@ -2420,6 +2490,8 @@ exa_status exa_stat(const exa_model *m, const char *key, double *value) {
     else if (k == "eval_prefetch") *value = m->prefetch;
     else if (k == "eval_lanes") *value = m->lanes;
     else if (k == "eval_lazy") *value = m->lazy_loads;
+    else if (k == "eval_stage") *value = m->stage;
+    else if (k == "eval_dsmem") *value = m->dsmem[exa::M_ALL];
     else if (k == "eval_wave_pct") *value = m->wave_pct;
     else if (k == "graph_kernels") *value = m->graph_kernels;
     else if (k == "grad_compact") *value = m->grad_compact;

@@ -141,12 +141,18 @@ struct CodegenOptions {
     // live per thread; shared subexpressions recomputed by both).  Kinds that form the compressed
     // Hessian sums, and groups with a single active pattern, keep one set.  Excludes prefetch.
     int lanes = 1;
+    // Shared-memory staging of inputs (1: on): the persistent tile loop copies the data columns,
+    // the x values indexed by the instance alone and the constraint multipliers of the CTA's next
+    // tile into a second buffer of per-thread slots (cp.async) while the current tile computes from
+    // the first.  Excludes prefetch, warp sets and bounds checking.
+    int stage = 0;
 };
 // The warp sets of group g in kernel kind `mode` (positions in g.pats per set, in order): one set
 // with every active pattern, or `lanes` contiguous subsets of about equal outputs.
 std::vector<std::vector<int>> group_sets(const std::vector<Pattern> &pats, const Group &g, Mode mode, int lanes);
+// dsmem (optional, M_COUNT entries): the dynamic shared memory each kernel kind needs, in bytes.
 std::string generate_source(const std::vector<Pattern> &pats, const std::vector<Group> &groups,
-                            const CodegenOptions &opt, std::string *err);
+                            const CodegenOptions &opt, std::string *err, int *dsmem = nullptr);
 bool pattern_in_mode(const Pattern &p, Mode m);
 
 extern const char *const kDeviceStructs;

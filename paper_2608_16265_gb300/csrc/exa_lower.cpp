@@ -881,6 +881,11 @@ struct Emitter {
     const CodegenOptions &opt;
     std::ostringstream os;
     std::string pf_text;  // prefetch functions of the last function() (opt.prefetch > 0)
+    // shared-memory staging (opt.stage): the last function()'s stage function and its 8- and
+    // 4-byte slot counts per thread
+    std::string st_text;
+    int n_st8 = 0, n_st4 = 0;
+    int st_budget = 0;  // bytes of staged slots one thread may have per buffer (later inputs load from global memory)
 
     Emitter(const std::vector<Pattern> &p_, const Group &g_, const Graph &gr, const std::vector<PatternGraph> &pg,
             const CodegenOptions &o)
@@ -1023,13 +1028,17 @@ struct Emitter {
         const bool all = mode_all(mode) || mode == M_FIRST;
         const bool hs_coo = mode_hess_coo(mode), hs_comp = mode_hess_comp(mode) && !grp.hc.empty();
         const bool want_struct = mode == M_STRUCT;
+        // inputs staged in shared memory by the tile loop (s8 / s4: this thread's column of 8- and
+        // 4-byte slots of the current buffer, slot j at [j * EXA_BLOCK])
+        const bool in_smem = opt.stage && !want_struct && suffix.empty();
         // k is the thread's instance clamped to the last one; act says whether it is its own.  Every
         // lane of a warp runs the function so that outputs can be staged per warp in shared memory
         // (ws) and written back as contiguous, coalesced runs.
         os << "static __device__ __forceinline__ void grp" << gid << "_" << kModeName[mode] << suffix
            << "(const ExaPM& pm, const int k, const bool act, const double* __restrict__ x,"
               " const double* __restrict__ y, const double* __restrict__ th, const double sigma, const ExaOut& o,"
-              " const ExaStructOut& so, double& objv, double* __restrict__ ws) {\n";
+              " const ExaStructOut& so, double& objv, double* __restrict__ ws"
+           << (in_smem ? ", const double* __restrict__ s8, const int* __restrict__ s4" : "") << ") {\n";
         os << "  const long long kk = k;\n";
         if (!want_struct)
             os << "  const int lane = threadIdx.x & 31;\n"
@@ -1110,16 +1119,77 @@ struct Emitter {
         for (int pos : act)
             if (want[pos].row && pat(pos).kind == EXA_AUG) fields_of_idx(pos, pat(pos).row_root, all_fields);
         const bool lazy = opt.by_pattern && opt.lazy_loads && !want_struct;
+        // Staged inputs: every data column, the FP32 column copies, the x values whose index is
+        // the instance plus constants, and the multipliers of constraint rows; the tile loop copies
+        // them for the CTA's next tile (cp.async) while this tile computes.  Gathers through data
+        // fields are loaded here from global memory, their index fields coming from shared memory.
+        std::map<std::string, int> st8, st4;
+        std::vector<std::string> st_src8, st_src4;
+        if (in_smem) {
+            int bytes = 0;
+            auto add = [&](std::map<std::string, int> &mp, std::vector<std::string> &src, const std::string &key,
+                           const std::string &addr) {
+                const int b = &mp == &st8 ? 8 : 4;
+                if (mp.count(key) || bytes + b > st_budget) return;
+                bytes += b;
+                mp.emplace(key, (int)src.size());
+                src.push_back(addr);
+            };
+            for (int f : all_fields) {
+                const std::string F = std::to_string(f);
+                if (grp.ftype[f] == EXA_FIELD_I32) add(st4, st_src4, "F" + F, "(const int*)pm.f[" + F + "] + k");
+                else add(st8, st_src8, "F" + F, "(const double*)pm.f[" + F + "] + k");
+            }
+            for (int f : fcopy) add(st4, st_src4, "DF" + std::to_string(f), "pm.f32[" + std::to_string(f) + "] + k");
+            for (int sy : syms) {
+                std::set<int> fs;
+                fields_of_idx(grp.sym_root[sy].first, grp.sym_root[sy].second, fs);
+                if (fs.empty())
+                    add(st8, st_src8, "X" + std::to_string(sy),
+                        "x + pm.xoff + " + idx_expr(grp.sym_root[sy].first, grp.sym_root[sy].second));
+            }
+            for (int pos : act)
+                if (want[pos].hess && pat(pos).kind == EXA_CON)
+                    add(st8, st_src8, "Y" + std::to_string(pos), "y + pm.rbase[" + std::to_string(pos) + "] + kk");
+        }
+        // the load of one input: its shared-memory slot when staged, else global memory
+        auto ld = [&](const std::string &key, const std::string &global) -> std::string {
+            auto i8 = st8.find(key);
+            if (i8 != st8.end()) return "s8[" + std::to_string(i8->second) + " * EXA_BLOCK]";
+            auto i4 = st4.find(key);
+            if (i4 != st4.end())
+                return key[0] == 'D' ? "__int_as_float(s4[" + std::to_string(i4->second) + " * EXA_BLOCK])"
+                                     : "s4[" + std::to_string(i4->second) + " * EXA_BLOCK]";
+            return "__ldg(" + global + ")";
+        };
+        st_text.clear();
+        n_st8 = (int)st_src8.size();
+        n_st4 = (int)st_src4.size();
+        if (in_smem && (n_st8 + n_st4) > 0) {
+            std::ostringstream st;
+            st << "static __device__ __forceinline__ void grp" << gid << "_" << kModeName[mode]
+               << "_st(const ExaPM& pm, const int k, const double* __restrict__ x, const double* __restrict__ y,"
+                  " const unsigned d8, const unsigned d4) {\n"
+                  "  const long long kk = k;\n";
+            for (size_t j = 0; j < st_src8.size(); j++)
+                st << "  exa_cp_async8(d8 + " << j << "u * (EXA_BLOCK * 8u), " << st_src8[j] << ");\n";
+            for (size_t j = 0; j < st_src4.size(); j++)
+                st << "  exa_cp_async4(d4 + " << j << "u * (EXA_BLOCK * 4u), " << st_src4[j] << ");\n";
+            st << "}\n";
+            st_text = st.str();
+        }
         for (int f : all_fields) {
+            const std::string F = std::to_string(f);
             if (grp.ftype[f] == EXA_FIELD_I32)
-                os << "  const int F" << f << " = __ldg((const int*)pm.f[" << f << "] + k);\n";
+                os << "  const int F" << f << " = " << ld("F" + F, "(const int*)pm.f[" + F + "] + k") << ";\n";
             else if (!lazy)
-                os << "  const double F" << f << " = __ldg((const double*)pm.f[" << f << "] + k);\n";
+                os << "  const double F" << f << " = " << ld("F" + F, "(const double*)pm.f[" + F + "] + k") << ";\n";
         }
         if (!lazy) {
             for (int f : dfields)
                 os << "  const double D" << f << " = " << (grp.ftype[f] == EXA_FIELD_I32 ? "(double)F" : "F") << f << ";\n";
-            for (int f : fcopy) os << "  const float DF" << f << " = __ldg(pm.f32[" << f << "] + k);\n";
+            for (int f : fcopy)
+                os << "  const float DF" << f << " = " << ld("DF" + std::to_string(f), "pm.f32[" + std::to_string(f) + "] + k") << ";\n";
         }
         for (int s : idx_syms) {
             os << "  long long i" << s << " = " << idx_expr(grp.sym_root[s].first, grp.sym_root[s].second) << ";\n";
@@ -1227,7 +1297,8 @@ struct Emitter {
             return os.str();
         }
         if (!lazy)
-            for (int s : syms) os << "  const double X" << s << " = __ldg(x + pm.xoff + i" << s << ");\n";
+            for (int s : syms)
+                os << "  const double X" << s << " = " << ld("X" + std::to_string(s), "x + pm.xoff + i" + std::to_string(s)) << ";\n";
         // Pairs of different symbols whose slot doubles when both resolve to one variable: their
         // equality tests are taken once here, into one bit mask, so that the 64-bit indices are
         // dead once the gathers are issued instead of staying live until the Hessian.
@@ -1258,14 +1329,19 @@ struct Emitter {
             const std::string key = std::string(1, sn.ikind) + std::to_string(sn.iid);
             if (!issued.insert(key).second) return;
             switch (sn.ikind) {
-            case 'X': os << "  const double X" << sn.iid << " = __ldg(x + pm.xoff + i" << sn.iid << ");\n"; break;
+            case 'X':
+                os << "  const double X" << sn.iid << " = " << ld("X" + std::to_string(sn.iid), "x + pm.xoff + i" + std::to_string(sn.iid)) << ";\n";
+                break;
             case 'P': os << "  const double P" << sn.iid << " = __ldg(th + pm.poff + q" << sn.iid << ");\n"; break;
             case 'D':
                 if (grp.ftype[sn.iid] == EXA_FIELD_F64) {
                     if (dfields.count(sn.iid) || (sn.prec == PD))
-                        os << "  const double F" << sn.iid << " = __ldg((const double*)pm.f[" << sn.iid << "] + k);\n"
+                        os << "  const double F" << sn.iid << " = "
+                           << ld("F" + std::to_string(sn.iid), "(const double*)pm.f[" + std::to_string(sn.iid) + "] + k") << ";\n"
                            << "  const double D" << sn.iid << " = F" << sn.iid << ";\n";
-                    if (fcopy.count(sn.iid)) os << "  const float DF" << sn.iid << " = __ldg(pm.f32[" << sn.iid << "] + k);\n";
+                    if (fcopy.count(sn.iid))
+                        os << "  const float DF" << sn.iid << " = "
+                           << ld("DF" + std::to_string(sn.iid), "pm.f32[" + std::to_string(sn.iid) + "] + k") << ";\n";
                 }
                 break;
             default: break;
@@ -1304,7 +1380,7 @@ struct Emitter {
         auto issue_pattern = [&](int pos) {
             for (int i : pin[pos]) issue_in(g.n[i]);
             if (want[pos].hess && pat(pos).kind != EXA_OBJ && issued.insert("Y" + std::to_string(pos)).second)
-                os << "  const double Y" << pos << " = __ldg(y + row" << pos << ");\n";
+                os << "  const double Y" << pos << " = " << ld("Y" + std::to_string(pos), "y + row" + std::to_string(pos)) << ";\n";
         };
         auto ready_pattern = [&](int pos) { for (int i : pin[pos]) ready_in(g.n[i]); };
         if (!lazy) {
@@ -1313,7 +1389,7 @@ struct Emitter {
             // latency overlaps the pattern arithmetic instead of following it
             for (int pos : act)
                 if (want[pos].hess && pat(pos).kind != EXA_OBJ)
-                    os << "  const double Y" << pos << " = __ldg(y + row" << pos << ");\n";
+                    os << "  const double Y" << pos << " = " << ld("Y" + std::to_string(pos), "y + row" + std::to_string(pos)) << ";\n";
             for (int s : fsyms) os << "  const float XF" << s << " = exa_d2f(X" << s << ");\n";
             for (int f : ffields)
                 if (!fcopy.count(f)) os << "  const float DF" << f << " = (float)F" << f << ";\n";  // int32 column
@@ -1537,9 +1613,16 @@ static const char *kFp64Helpers =
 }  // namespace
 
 std::string generate_source(const std::vector<Pattern> &pats, const std::vector<Group> &groups,
-                            const CodegenOptions &opt_in, std::string *err) {
+                            const CodegenOptions &opt_in, std::string *err, int *dsmem) {
     CodegenOptions opt = opt_in;
     if (opt.lanes > 1) opt.prefetch = 0;  // one or the other
+    if (opt.stage) {  // staging excludes L2 prefetch, warp sets and the bounds-checked indices
+        opt.prefetch = 0;
+        opt.lanes = 1;
+        if (opt.bounds_check) opt.stage = 0;
+    }
+    if (dsmem)
+        for (int m = 0; m < M_COUNT; m++) dsmem[m] = 0;
     std::ostringstream src;
     const bool mixed = opt.precision == EXA_MIXED_FP32;
     src << "// generated by exa_lower.cpp (" << (mixed ? "mixed FP32/FP64" : "FP64") << ")\n";
@@ -1552,6 +1635,16 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
     if (mixed) src << kMixedHelpers;
     src << kExactHelpers;
     src << kFp64Helpers;
+    if (opt.stage)
+        src << "// cp.async of one 8- or 4-byte input into a shared-memory slot (both addresses aligned to\n"
+               "// the size: data columns, x and y are arrays of that element size)\n"
+               "static __device__ __forceinline__ void exa_cp_async8(const unsigned d, const void* s) {\n"
+               "  asm volatile(\"cp.async.ca.shared.global [%0], [%1], 8;\" :: \"r\"(d), \"l\"(s) : \"memory\");\n"
+               "}\n"
+               "static __device__ __forceinline__ void exa_cp_async4(const unsigned d, const void* s) {\n"
+               "  asm volatile(\"cp.async.ca.shared.global [%0], [%1], 4;\" :: \"r\"(d), \"l\"(s) : \"memory\");\n"
+               "}\n"
+               "extern __shared__ __align__(16) unsigned char exa_dsm[];\n";
     // one shared expression graph per group
     std::vector<Graph> graphs(groups.size());
     std::vector<std::vector<PatternGraph>> pgs(groups.size());
@@ -1570,16 +1663,32 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
     for (int m = 0; m < M_COUNT; m++) {
         std::vector<int> gl;
         std::map<int, int> nsets;  // group -> warp sets (> 1 only when split)
+        int S8 = 0, S4 = 0;        // staged slots per thread (largest over the kernel's groups)
+        std::vector<int> gst;      // groups with a stage function
+        int smax = 1;  // widest slot block staged per warp for the coalesced output writes (ws)
+        for (const Pattern &p : pats)
+            if (pattern_in_mode(p, (Mode)m)) smax = std::max(smax, std::max(p.nj(), p.nh()));
+        if (mode_hess_comp(m))
+            for (const Group &gr : groups) smax = std::max(smax, (int)gr.hc.size());
+        // staged input slots: two buffers within 160 KB of shared memory per CTA beside ws
+        const int st_budget = opt.stage ? std::max(0, (160 * 1024 - opt.block * smax * 8) / (2 * opt.block)) & ~7 : 0;
         for (size_t gi = 0; gi < groups.size(); gi++) {
             bool any = false;
             for (int pid : groups[gi].pats) any = any || pattern_in_mode(pats[pid], (Mode)m);
             if (!any) continue;
             gl.push_back((int)gi);
             Emitter e(pats, groups[gi], graphs[gi], pgs[gi], opt);
+            e.st_budget = st_budget;
             const std::vector<std::vector<int>> sets = group_sets(pats, groups[gi], (Mode)m, opt.lanes);
             if (sets.size() == 1) {
                 src << e.function((int)gi, (Mode)m, sets[0]);
                 src << e.pf_text;
+                if (!e.st_text.empty()) {
+                    src << e.st_text;
+                    gst.push_back((int)gi);
+                    S8 = std::max(S8, e.n_st8);
+                    S4 = std::max(S4, e.n_st4);
+                }
             } else {
                 nsets[(int)gi] = (int)sets.size();
                 for (size_t si = 0; si < sets.size(); si++)
@@ -1587,6 +1696,23 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
             }
         }
         const bool objred = (m == M_OBJ || mode_all(m) || m == M_FIRST);
+        const bool stk = opt.stage && m != M_STRUCT && !gst.empty();  // staged tile loop
+        if (stk) {
+            // the staged inputs of tile t, instance clamped like the tile loop's, into the slot
+            // columns at shared addresses d8 / d4
+            src << "static __device__ __forceinline__ void exa_st_" << kModeName[m]
+                << "(const ExaTile* __restrict__ tiles, const ExaPM* __restrict__ pms, const long long t,"
+                   " const double* __restrict__ x, const double* __restrict__ y, const unsigned d8, const unsigned d4) {\n"
+                   "  const ExaTile tl = tiles[t];\n"
+                   "  const ExaPM& pm = pms[tl.pm];\n"
+                   "  const int k0 = tl.begin + (int)threadIdx.x;\n"
+                   "  const int k = k0 < pm.n_inst ? k0 : (int)pm.n_inst - 1;\n"
+                   "  switch (pm.grp) {\n";
+            for (int gi : gst)
+                src << "    case " << gi << ": grp" << gi << "_" << kModeName[m] << "_st(pm, k, x, y, d8, d4); break;\n";
+            src << "    default: break;\n  }\n}\n";
+            if (dsmem) dsmem[m] = 2 * opt.block * (8 * S8 + 4 * S4);
+        }
         // Tile loop: with gridDim.x == ntiles every CTA takes one tile; a smaller (persistent) grid
         // strides over the tile list.  The trip count is uniform over the CTA.
         src << "extern \"C\" __global__ void EXA_BOUNDS exa_" << kModeName[m]
@@ -1594,18 +1720,36 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
                " const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ th,"
                " const double sigma, const ExaOut o, const ExaStructOut so, const int pfd) {\n";
         if (objred) src << "  __shared__ double red[EXA_BLOCK / 32];\n";
-        int smax = 1;  // widest slot block staged in this kernel
-        for (const Pattern &p : pats)
-            if (pattern_in_mode(p, (Mode)m)) smax = std::max(smax, std::max(p.nj(), p.nh()));
-        if (mode_hess_comp(m))
-            for (const Group &gr : groups) smax = std::max(smax, (int)gr.hc.size());
         if (m != M_STRUCT)
             src << "  __shared__ double stage[EXA_BLOCK * " << smax << "];\n"
                    "  double* __restrict__ ws = stage + (threadIdx.x & ~31u) * " << smax << ";\n";
         else
             src << "  double* ws = nullptr;\n";
         src << "  double objv = 0.0;\n";
+        if (stk) {
+            // Two buffers of per-thread slot columns: while tile t computes from one, the CTA's next
+            // tile is copied into the other (each thread copies and later reads only its own
+            // slots, so the per-thread cp.async group wait is the only synchronisation).
+            src << "  double* const sd8 = (double*)exa_dsm;                              // [2][" << S8 << "][EXA_BLOCK]\n"
+                   "  int* const sd4 = (int*)(exa_dsm + 2 * " << S8 << " * EXA_BLOCK * 8);  // [2][" << S4 << "][EXA_BLOCK]\n"
+                   "  const unsigned sa8 = (unsigned)__cvta_generic_to_shared(sd8 + threadIdx.x);\n"
+                   "  const unsigned sa4 = (unsigned)__cvta_generic_to_shared(sd4 + threadIdx.x);\n"
+                   "  int sbuf = 0;\n"
+                   "  if ((int)blockIdx.x < ntiles) exa_st_" << kModeName[m] << "(tiles, pms, blockIdx.x, x, y, sa8, sa4);\n"
+                   "  asm volatile(\"cp.async.commit_group;\" ::: \"memory\");\n";
+        }
         src << "  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {\n";
+        if (stk) {
+            src << "  {\n"
+                   "    const long long tn = (long long)t + gridDim.x;\n"
+                   "    if (tn < ntiles) exa_st_" << kModeName[m] << "(tiles, pms, tn, x, y, sa8 + (unsigned)(sbuf ^ 1) * (" << S8
+                << "u * EXA_BLOCK * 8u), sa4 + (unsigned)(sbuf ^ 1) * (" << S4 << "u * EXA_BLOCK * 4u));\n"
+                   "    asm volatile(\"cp.async.commit_group;\" ::: \"memory\");\n"
+                   "    asm volatile(\"cp.async.wait_group 1;\" ::: \"memory\");\n"
+                   "  }\n"
+                   "  const double* __restrict__ s8 = sd8 + sbuf * (" << S8 << " * EXA_BLOCK) + threadIdx.x;\n"
+                   "  const int* __restrict__ s4 = sd4 + sbuf * (" << S4 << " * EXA_BLOCK) + threadIdx.x;\n";
+        }
         if (opt.prefetch >= 1 && m != M_STRUCT) {  // data columns of the tile 2 x pfd ahead: warp 0
             src << "  if (threadIdx.x < 32 && pfd > 0) {\n"
                    "    const long long tp = (long long)t + 2LL * pfd;\n"
@@ -1649,7 +1793,8 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
         for (int gi : gl) {
             auto it = nsets.find(gi);
             if (it == nsets.end()) {
-                src << "      case " << gi << ": grp" << gi << "_" << kModeName[m] << "(pm, k, act, x, y, th, sigma, o, so, objv, ws); break;\n";
+                src << "      case " << gi << ": grp" << gi << "_" << kModeName[m] << "(pm, k, act, x, y, th, sigma, o, so, objv, ws"
+                    << (opt.stage && m != M_STRUCT ? (stk ? ", s8, s4" : ", nullptr, nullptr") : "") << "); break;\n";
             } else {
                 src << "      case " << gi << ":\n";
                 for (int si = 0; si < it->second; si++)
@@ -1659,7 +1804,9 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
             }
         }
         src << "      default: break;\n    }\n  }\n";
+        if (stk) src << "  sbuf ^= 1;\n";
         src << "  }\n";
+        if (stk) src << "  asm volatile(\"cp.async.wait_group 0;\" ::: \"memory\");  // nothing in flight at exit\n";
         if (objred) {
             // Every thread sums the objective terms of all its instances over the CTA's tiles (in tile
             // order); the CTA reduces once, after its last tile, and writes one partial sum: the

@@ -34,14 +34,16 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("variant", ["tuned", "lanes2", "lazy"])
+@pytest.mark.parametrize("variant", ["tuned", "lanes2", "lazy", "stage"])
 @pytest.mark.parametrize("name", list(CASES))
 def test_mixed_parity(name, variant):
     from paper_2608_16265_gb300 import binding as B
     flat, (x, y, s) = CASES[name]()
     o = oracle.Oracle(flat)
     extra = {"tuned": {}, "lanes2": dict(flags=B.EXA_FLAG_NO_TUNE | B.EXA_FLAG_LANES2, block=128),
-             "lazy": dict(flags=B.EXA_FLAG_NO_TUNE | B.EXA_FLAG_LAZY_LOADS, block=128, min_blocks=8)}[variant]
+             "lazy": dict(flags=B.EXA_FLAG_NO_TUNE | B.EXA_FLAG_LAZY_LOADS, block=128, min_blocks=8),
+             "stage": dict(flags=B.EXA_FLAG_NO_TUNE | B.EXA_FLAG_STAGE_SMEM | B.EXA_FLAG_LAZY_LOADS, block=64,
+                           grid_factor=2)}[variant]
     m = B.exa_create(flat, precision=B.EXA_MIXED_FP32, **extra)
     out = m.eval_all(_t(x), _t(y if len(y) else np.zeros(1)), s, csc=True)
     ref = dict(g=o.grad(x), c=o.cons(x), jac=o.jac_coord(x), hess=o.hess_coord(x, y, s),

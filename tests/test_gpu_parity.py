@@ -133,12 +133,12 @@ def test_autotuned_model():
 
 
 @pytest.mark.parametrize("choice", ["split", "scatter", "no_hcomp", "upfront", "split+scatter+no_hcomp+upfront",
-                                    "lanes2", "lanes2+split+no_hcomp"])
+                                    "lanes2", "lanes2+split+no_hcomp", "stage", "stage+split+no_hcomp+upfront"])
 def test_pinned_launch_choices(choice):
     """Every choice the tuner makes, fixed through the creation options instead, gives the same
     results: first/second order split, the Jacobian CSC scattered by the evaluation kernel, the
     Hessian CSC summed from the COO slots, the up-front emission order, two warp sets per instance,
-    and a register cap through min_blocks."""
+    inputs staged in shared memory, and a register cap through min_blocks."""
     B = _B()
     flags = B.EXA_FLAG_NO_TUNE
     flags |= B.EXA_FLAG_SPLIT if "split" in choice else 0
@@ -146,6 +146,7 @@ def test_pinned_launch_choices(choice):
     flags |= B.EXA_FLAG_NO_HCOMP if "no_hcomp" in choice else 0
     flags |= B.EXA_FLAG_UPFRONT if "upfront" in choice else 0
     flags |= B.EXA_FLAG_LANES2 if "lanes2" in choice else 0
+    flags |= B.EXA_FLAG_STAGE_SMEM if "stage" in choice else 0
     wl = synth.acopf(200, 300, 40, seed=8)
     x, y, s = synth.acopf_point(wl, 2)
     m, _ = check_model(wl.flat, x, y, s, flags=flags, block=64, min_blocks=12)
@@ -155,6 +156,7 @@ def test_pinned_launch_choices(choice):
     assert m.stat("eval_min_blocks") == 12 and m.stat("eval_block") == 64
     assert m.stat("eval_upfront") == ("upfront" in choice)
     assert m.stat("eval_lanes") == (2 if "lanes2" in choice else 1)
+    assert m.stat("eval_stage") == ("stage" in choice)
 
 
 @pytest.mark.parametrize("name", ["all_ops", "more_ops", "acopf_shunts", "pde_41", "goddard_2000", "two_stage_acopf"])
@@ -177,11 +179,26 @@ def test_parity_two_warp_sets(name):
     check_model(flat, x, y, s, flags=B.EXA_FLAG_NO_TUNE | B.EXA_FLAG_LANES2, block=128, grid_factor=1)
 
 
+@pytest.mark.parametrize("name", ["all_ops", "more_ops", "acopf_shunts", "pde_41", "goddard_2000", "two_stage_acopf"])
+@pytest.mark.parametrize("order", ["eager", "lazy"])
+def test_parity_smem_staging(name, order):
+    """The next tile's inputs staged in shared memory by cp.async (double-buffered persistent tile
+    loop) on every workload kind, with the gathers loaded eagerly or one pattern ahead; a persistent
+    grid of two waves so that every CTA runs several tiles, with a ragged last tile per pattern."""
+    B = _B()
+    flat, (x, y, s) = CASES[name]()
+    flags = B.EXA_FLAG_NO_TUNE | B.EXA_FLAG_STAGE_SMEM | (B.EXA_FLAG_LAZY_LOADS if order == "lazy" else 0)
+    m, _ = check_model(flat, x, y, s, flags=flags, block=64, grid_factor=2)
+    assert m.stat("eval_stage") == 1 and m.stat("eval_dsmem") > 0
+
+
 def test_option_conflicts_are_rejected():
     B = _B()
     flat, _ = CASES["all_ops"]()
     for kw in (dict(block=32, flags=B.EXA_FLAG_LANES2), dict(block=64, flags=B.EXA_FLAG_LANES2 | B.EXA_FLAG_PF_COLUMNS),
-               dict(block=64, flags=B.EXA_FLAG_LAZY_LOADS | B.EXA_FLAG_UPFRONT)):
+               dict(block=64, flags=B.EXA_FLAG_LAZY_LOADS | B.EXA_FLAG_UPFRONT),
+               dict(block=64, flags=B.EXA_FLAG_STAGE_SMEM | B.EXA_FLAG_LANES2),
+               dict(block=64, flags=B.EXA_FLAG_STAGE_SMEM | B.EXA_FLAG_PF_GATHERS)):
         with pytest.raises(B.ExaError) as e:
             B.exa_create(flat, **kw)
         assert e.value.status == B.EXA_E_INVALID
@@ -349,6 +366,7 @@ BATCH_OPTIONS = {
     "no_hcomp_chunks": dict(flags=2 | 64, chunks=3),
     "chunks_partial_wave_prefetch": dict(flags=2 | 512, chunks=4, wave_pct=50, block=32),
     "two_warp_sets_split": dict(flags=2 | 1024 | 16, block=128, chunks=2),
+    "smem_staging_lazy_chunks": dict(flags=2 | 4096 | 2048, block=64, grid_factor=2, chunks=3),
 }
 
 
