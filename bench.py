@@ -743,6 +743,15 @@ def run_exa(args):
     e2e_fgc = lambda: m.exa_eval_all_host(xh, yh, sigma, jac=jac, hess=hess, jac_csc=jcsc, hess_csc=hcsc, **fgc)
     e2e_fgc()
     extras["e2e_derivatives_on_device_ms"] = timed(e2e_fgc, max(3, min(args.steps // 2, 100)))
+    # the same step without the member-chunk pipeline of exa_eval_all_host (all inputs in, the
+    # graph, then all outputs back), on a model created with the same launch configuration
+    opts = m.tuned_options()
+    opts["flags"] |= B.EXA_FLAG_HOST_SERIAL
+    ms_serial = B.exa_create_batch(flats, precision=prec, device=local, **opts)
+    e2e_serial = lambda: ms_serial.exa_eval_all_host(xh, yh, sigma, **host)
+    e2e_serial()
+    extras["e2e_serial_ms"] = timed(e2e_serial, max(3, min(args.steps // 2, 100)))
+    ms_serial.destroy()
     del host
 
     cpu = None
@@ -767,6 +776,7 @@ def run_exa(args):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
                 "link": {"h2d_gbs": link["h2d_bytes_per_s"] / 1e9, "d2h_gbs": link["d2h_bytes_per_s"] / 1e9,
                          "copy_ms": link_ms, "copy_frac_of_step": link_ms / e2e_ms,
+                         "h2d_ms": 1e3 * h2d / link["h2d_bytes_per_s"], "d2h_ms": 1e3 * d2h / link["d2h_bytes_per_s"],
                          "how": "exa_probe_host_link: 1 GiB page-locked cudaMemcpyAsync each way, best of 3"},
                 "diagnostics": e2e_diag},
         "gpu_launches": launches_per_step * args.steps,

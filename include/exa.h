@@ -184,6 +184,8 @@ enum {
                                   f64 data, parameters, multipliers) are loaded just before the
                                   arithmetic of the pattern preceding it, not all at the top of the
                                   fused group (fewer values live); excludes EXA_FLAG_UPFRONT */
+    EXA_FLAG_HOST_SERIAL = 8192, /* exa_eval_all_host on a batch: no member-chunk pipeline (inputs,
+                                  graph, outputs one after another on the model stream) */
     EXA_FLAG_STAGE_SMEM = 4096 /* staging depth 1: the tile loop copies the inputs of the CTA's next
                                   tile (data columns, x values indexed by the instance alone,
                                   constraint multipliers) into shared memory with cp.async while the
@@ -301,9 +303,15 @@ exa_status exa_eval_all(exa_model *m, const double *x, const double *y, double s
  * exa_eval_all) may be host memory, page-locked or pageable, or device memory.  Host inputs are
  * copied into device buffers the library owns (allocated on first use), the exa_eval_all graph is
  * replayed on the model stream, host outputs are copied back, and the call returns when they are
- * in host memory (the stream is synchronized).  Device arguments are used in place.  The host
- * outputs are copied back one after another on the model stream once the evaluation graph has run;
- * page-locked host buffers (cudaHostAlloc / cudaHostRegister) are copied at full link speed. */
+ * in host memory (the stream is synchronized).  Device arguments are used in place.  For a batch
+ * of two or more members the call is pipelined over up to 8 member chunks of about equal
+ * nonzeros: the chunks' inputs are copied in on a stream of their own, chunk k is evaluated
+ * (directly launched, not from the graph) once its inputs are in, and its outputs (every output
+ * of a member is a contiguous range) are copied back on another stream as soon as its reductions
+ * have run, overlapping the copies of later chunks; the objective follows the last chunk.  Single
+ * models, EXA_FLAG_HOST_SERIAL, and calls while the model stream is being captured copy all inputs,
+ * replay the graph and then copy the outputs back one after another on the model stream.
+ * Page-locked host buffers (cudaHostAlloc / cudaHostRegister) are copied at full link speed. */
 exa_status exa_eval_all_host(exa_model *m, const double *x, const double *y, double sigma,
                              double *f, double *g, double *c, double *jac, double *hess,
                              double *jac_csc, double *hess_csc);

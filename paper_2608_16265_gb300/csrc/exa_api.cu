@@ -380,6 +380,13 @@ struct exa_model {
     std::vector<int> mb_tile[exa::M_COUNT];
     std::vector<int> mb_jcsc, mb_hcsc, mb_jmulti, mb_hmulti, mb_hcmulti, mb_gseg, mb_arow;
     cudaEvent_t ev_chunk[16] = {};
+    // Hooks of eval_all_chunked, called before chunk k's evaluation is enqueued and after its
+    // reductions are (the host-buffer pipeline of exa_eval_all_host); empty otherwise.
+    std::function<exa_status(int)> pre_chunk, post_chunk;
+    // exa_eval_all_host pipeline: copy streams and per-chunk events (inputs in, outputs final)
+    bool host_serial = false;
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t ev_in[16] = {}, ev_out[16] = {}, ev_hstart = nullptr, ev_hdone = nullptr;
     bool grad_compact = false;
     int n_gseg = 0;
     int *d_gsegptr = nullptr, *d_gsegvar = nullptr;
@@ -452,6 +459,19 @@ void free_all(exa_model *m) {
     for (cudaEvent_t &e : m->ev_chunk) {
         if (e) cudaEventDestroy(e);
         e = nullptr;
+    }
+    for (cudaEvent_t *e : {&m->ev_hstart, &m->ev_hdone}) {
+        if (*e) cudaEventDestroy(*e);
+        *e = nullptr;
+    }
+    for (int k = 0; k < 16; k++)
+        for (cudaEvent_t *e : {&m->ev_in[k], &m->ev_out[k]}) {
+            if (*e) cudaEventDestroy(*e);
+            *e = nullptr;
+        }
+    for (cudaStream_t *st : {&m->h2d, &m->d2h}) {
+        if (*st) cudaStreamDestroy(*st);
+        *st = nullptr;
     }
     for (int k = 0; k < exa::M_COUNT; k++) {
         if (m->d_tiles[k]) cudaFree(m->d_tiles[k]);
@@ -1471,6 +1491,7 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     m->lanes = (o.flags & EXA_FLAG_LANES2) ? 2 : 1;
     m->lazy_loads = (o.flags & EXA_FLAG_LAZY_LOADS) != 0;
     m->stage = (o.flags & EXA_FLAG_STAGE_SMEM) != 0 && !m->bounds_check;
+    m->host_serial = (o.flags & EXA_FLAG_HOST_SERIAL) != 0;
     if (m->lazy_loads && !m->by_pattern) return fail(m, EXA_E_INVALID, "EXA_FLAG_LAZY_LOADS excludes EXA_FLAG_UPFRONT");
     if (m->lanes > 1 && m->prefetch) return fail(m, EXA_E_INVALID, "EXA_FLAG_LANES2 excludes the prefetch flags");
     if ((o.flags & EXA_FLAG_STAGE_SMEM) && (m->lanes > 1 || m->prefetch))
@@ -2095,6 +2116,8 @@ static exa_status eval_all_chunked(exa_model *m, const double *x, const double *
     int nparts = 0;  // objective partials so far: each chunk's launch writes one per CTA after them
     for (int k = 0; k < m->nchunks; k++) {
         const int b0 = m->chunk_b[k], b1 = m->chunk_b[k + 1];
+        if (m->pre_chunk)
+            if (exa_status e = m->pre_chunk(k)) return e;
         ExaOut oc = split ? o1 : o;
         oc.obj_part = m->d_objpart + nparts;
         if (exa_status e = launch_eval(m, m1, x, y, sigma, oc, m->mb_tile[m1][b0], m->mb_tile[m1][b1]))
@@ -2161,6 +2184,8 @@ static exa_status eval_all_chunked(exa_model *m, const double *x, const double *
                 CR(cudaGetLastError());
             }
         }
+        if (m->post_chunk)
+            if (exa_status e = m->post_chunk(k)) return e;
     }
     if (f) {
         k_obj_final<<<1, 1024, 0, m->stream>>>(m->d_objpart, nparts, f);
@@ -2353,6 +2378,7 @@ exa_status exa_eval_all_host(exa_model *m, const double *x, const double *y, dou
     double *arg[9] = {const_cast<double *>(x), const_cast<double *>(y), f, g, c, jac, hess, jac_csc, hess_csc};
     double *use[9] = {};
     bool staged[9] = {};
+    bool any_out = false;
     for (int k = 0; k < 9; k++) {
         if (!arg[k]) continue;
         cudaPointerAttributes a{};
@@ -2360,19 +2386,111 @@ exa_status exa_eval_all_host(exa_model *m, const double *x, const double *y, dou
         staged[k] = a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged;
         if (staged[k] && !m->d_host_io[k]) CR(dalloc(m, &m->d_host_io[k], n[k]));
         use[k] = staged[k] ? m->d_host_io[k] : arg[k];
+        if (k >= 2) any_out = any_out || staged[k];
     }
-    for (int k = 0; k < 2; k++)
-        if (staged[k] && n[k] > 0)
-            CR(cudaMemcpyAsync(use[k], arg[k], sizeof(double) * n[k], cudaMemcpyHostToDevice, m->stream));
-    // the device-only graph, then every host output copied back on the model stream in turn (plain
-    // stream-ordered copies: copies issued from a side stream inside the graph, overlapping the
-    // reductions, ran at half the link rate on some boxes while these ran at full rate)
-    if (exa_status e = eval_all_cached(m, use[0], use[1], sigma, use[2], use[3], use[4], use[5], use[6], use[7], use[8]))
-        return e;
-    for (int k = 2; k < 9; k++)
-        if (staged[k] && n[k] > 0)
-            CR(cudaMemcpyAsync(arg[k], use[k], sizeof(double) * n[k], cudaMemcpyDeviceToHost, m->stream));
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CR(cudaStreamIsCapturing(m->stream, &cs));
+    const int K = std::min(m->nb, 8);
+    if (m->host_serial || K < 2 || !any_out || cs != cudaStreamCaptureStatusNone) {
+        for (int k = 0; k < 2; k++)
+            if (staged[k] && n[k] > 0)
+                CR(cudaMemcpyAsync(use[k], arg[k], sizeof(double) * n[k], cudaMemcpyHostToDevice, m->stream));
+        // the device-only graph, then every host output copied back on the model stream in turn
+        if (exa_status e = eval_all_cached(m, use[0], use[1], sigma, use[2], use[3], use[4], use[5], use[6], use[7], use[8]))
+            return e;
+        for (int k = 2; k < 9; k++)
+            if (staged[k] && n[k] > 0)
+                CR(cudaMemcpyAsync(arg[k], use[k], sizeof(double) * n[k], cudaMemcpyDeviceToHost, m->stream));
+        CR(cudaStreamSynchronize(m->stream));
+        return EXA_OK;
+    }
+    // Batch pipeline over K member chunks (members are independent and their x, y, c, g, COO and CSC
+    // entries are contiguous ranges): one stream copies every chunk's x and y in, the evaluation and
+    // reductions of chunk k start when its inputs are there, and a second stream copies chunk k's
+    // outputs back as soon as its reductions have run, so the link carries chunk k's outputs while
+    // later chunks are still being copied in and evaluated.
+    if (!m->h2d) CR(cudaStreamCreateWithFlags(&m->h2d, cudaStreamNonBlocking));
+    if (!m->d2h) CR(cudaStreamCreateWithFlags(&m->d2h, cudaStreamNonBlocking));
+    for (cudaEvent_t *e : {&m->ev_hstart, &m->ev_hdone})
+        if (!*e) CR(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    for (int k = 0; k < K; k++)
+        for (cudaEvent_t *e : {&m->ev_in[k], &m->ev_out[k]})
+            if (!*e) CR(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    const int keep_chunks = m->nchunks;
+    const std::vector<int> keep_b = m->chunk_b;
+    set_chunks(m, K);
+    const int nk = m->nchunks;
+    // copies start after earlier work on the model stream
+    CR(cudaEventRecord(m->ev_hstart, m->stream));
+    CR(cudaStreamWaitEvent(m->h2d, m->ev_hstart, 0));
+    CR(cudaStreamWaitEvent(m->d2h, m->ev_hstart, 0));
+    // element ranges of chunk k: x and g over variables, y and c over rows, then the COO and CSC
+    auto range = [&](int k, int which, i64 *lo, i64 *hi) {
+        const int b0 = m->chunk_b[k], b1 = m->chunk_b[k + 1];
+        switch (which) {
+        case 0: case 3: *lo = m->xoff[b0]; *hi = m->xoff[b1]; break;
+        case 1: case 4: *lo = m->coff[b0]; *hi = m->coff[b1]; break;
+        case 5: *lo = m->joff[b0]; *hi = m->joff[b1]; break;
+        case 6: *lo = m->hoff[b0]; *hi = m->hoff[b1]; break;
+        case 7: *lo = m->mb_jcsc[b0]; *hi = m->mb_jcsc[b1]; break;
+        case 8: *lo = m->mb_hcsc[b0]; *hi = m->mb_hcsc[b1]; break;
+        default: *lo = *hi = 0; break;
+        }
+    };
+    exa_status st = EXA_OK;
+    for (int k = 0; k < nk && st == EXA_OK; k++) {
+        for (int a = 0; a < 2; a++) {
+            if (!staged[a]) continue;
+            i64 lo, hi;
+            range(k, a, &lo, &hi);
+            if (hi > lo) {
+                cudaError_t e = cudaMemcpyAsync(use[a] + lo, arg[a] + lo, sizeof(double) * (hi - lo), cudaMemcpyHostToDevice, m->h2d);
+                if (e != cudaSuccess) st = fail(m, EXA_E_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+            }
+        }
+        if (st == EXA_OK) {
+            cudaError_t e = cudaEventRecord(m->ev_in[k], m->h2d);
+            if (e != cudaSuccess) st = fail(m, EXA_E_CUDA, std::string("cudaEventRecord: ") + cudaGetErrorString(e));
+        }
+    }
+    m->pre_chunk = [&](int k) -> exa_status {
+        CR(cudaStreamWaitEvent(m->stream, m->ev_in[k], 0));
+        return EXA_OK;
+    };
+    m->post_chunk = [&](int k) -> exa_status {
+        // chunk k's reductions ran on side stream 0 after its evaluation kernel
+        CR(cudaEventRecord(m->ev_out[k], m->side[0]));
+        CR(cudaStreamWaitEvent(m->d2h, m->ev_out[k], 0));
+        for (int a = 3; a < 9; a++) {
+            if (!staged[a]) continue;
+            i64 lo, hi;
+            range(k, a, &lo, &hi);
+            if (hi > lo)
+                CR(cudaMemcpyAsync(arg[a] + lo, use[a] + lo, sizeof(double) * (hi - lo), cudaMemcpyDeviceToHost, m->d2h));
+        }
+        return EXA_OK;
+    };
+    if (st == EXA_OK)
+        st = eval_all_launches(m, use[0], use[1], sigma, use[2], use[3], use[4], use[5], use[6], use[7], use[8]);
+    m->pre_chunk = nullptr;
+    m->post_chunk = nullptr;
+    m->nchunks = keep_chunks;
+    m->chunk_b = keep_b;
+    if (st != EXA_OK) {
+        cudaStreamSynchronize(m->h2d);
+        cudaStreamSynchronize(m->d2h);
+        cudaStreamSynchronize(m->stream);
+        return st;
+    }
+    // the objective after every chunk, then wait for the last copies
+    if (staged[2]) {
+        CR(cudaEventRecord(m->ev_hdone, m->stream));
+        CR(cudaStreamWaitEvent(m->d2h, m->ev_hdone, 0));
+        CR(cudaMemcpyAsync(arg[2], use[2], sizeof(double), cudaMemcpyDeviceToHost, m->d2h));
+    }
+    CR(cudaStreamSynchronize(m->d2h));
     CR(cudaStreamSynchronize(m->stream));
+    CR(cudaStreamSynchronize(m->h2d));
     return EXA_OK;
 }
 

@@ -550,6 +550,58 @@ def test_eval_all_host_buffers(pinned):
     assert torch.equal(mix["g"], devm["g"].cpu()) and torch.equal(mix["hess"], devm["hess"])
 
 
+@pytest.mark.parametrize("opts", ["untuned", "bench_tuned", "two_warp_sets_split", "no_hcomp_chunks"])
+def test_eval_all_host_batch_pipeline(opts):
+    """exa_eval_all_host on a batch (the member-chunk pipeline: inputs copied in per chunk, each
+    chunk evaluated once its inputs are in, its outputs copied back after its reductions) against
+    the oracle member by member, and bit for bit against exa_eval_all on device buffers for every
+    output except the objective, whose per-chunk partial sums are added in another order (1e-12);
+    EXA_FLAG_HOST_SERIAL gives the graph path's results bit for bit.  Pageable inputs, a host/device
+    mix and an output subset go through the pipeline too."""
+    B = _B()
+    wls = synth.acopf_batch(11, seed=5, bmin=20, bmax=300)
+    flats = [w.flat for w in wls]
+    kw = BATCH_OPTIONS[opts]
+    mb = B.exa_create_batch(flats, **kw)
+    pts = [synth.acopf_point(w, i) for i, w in enumerate(wls)]
+    x = np.concatenate([p[0] for p in pts])
+    y = np.concatenate([p[1] for p in pts])
+    sizes = (("f", 1), ("g", mb.nvar), ("c", mb.ncon), ("jac", mb.nnzj), ("hess", mb.nnzh),
+             ("jac_csc", mb.nnzj_csc), ("hess_csc", mb.nnzh_csc))
+    dev = {k: torch.empty(n, dtype=torch.float64, device="cuda") for k, n in sizes}
+    mb.exa_eval_all(_t(x), _t(y), 1.0, **dev)
+    host = {k: torch.full((n,), -7.0, dtype=torch.float64).pin_memory() for k, n in sizes}
+    xh, yh = torch.as_tensor(x).pin_memory(), torch.as_tensor(y).pin_memory()
+    for _ in range(2):
+        mb.exa_eval_all_host(xh, yh, 1.0, **host)
+        for k in host:
+            if k == "f":
+                assert abs(float(host["f"][0]) - float(dev["f"][0])) <= 1e-12 * abs(float(dev["f"][0]))
+            else:
+                assert torch.equal(host[k], dev[k].cpu()), k
+    out = {k: v.cuda() for k, v in host.items()}
+    compare_batch_members(mb, wls, pts, out, range(len(wls)), TOL)
+    fo = batch_objective(wls, pts)
+    assert abs(float(host["f"][0]) - fo) <= TOL * abs(fo)
+    # the serial path (all inputs, graph, all outputs) equals the device call bit for bit
+    kw_s = dict(kw)
+    kw_s["flags"] = kw.get("flags", 0) | B.EXA_FLAG_HOST_SERIAL
+    ms = B.exa_create_batch(flats, **kw_s)
+    ser = {k: torch.full((n,), -7.0, dtype=torch.float64).pin_memory() for k, n in sizes}
+    ms.exa_eval_all_host(xh, yh, 1.0, **ser)
+    for k in ser:
+        assert torch.equal(ser[k], dev[k].cpu()), k
+    # pageable inputs, x on the device, and a subset of host outputs (the rest untouched)
+    part = {"g": torch.full((mb.nvar,), -7.0, dtype=torch.float64),
+            "hess_csc": torch.full((mb.nnzh_csc,), -7.0, dtype=torch.float64),
+            "jac": torch.full((mb.nnzj,), -7.0, dtype=torch.float64, device="cuda")}
+    mb.exa_eval_all_host(_t(x), torch.as_tensor(y), 1.0, **part)
+    devp = {k: torch.empty(v.numel(), dtype=torch.float64, device="cuda") for k, v in part.items()}
+    mb.exa_eval_all(_t(x), _t(y), 1.0, **devp)
+    for k in part:
+        assert torch.equal(part[k].cpu(), devp[k].cpu()), k
+
+
 def test_two_stage_scenario_parameters():
     """Replacing one scenario's loads with exa_set_theta (the builder's single-scenario accessor)
     gives the results of a model created with those loads, bit for bit."""
