@@ -122,18 +122,44 @@ def csrc_digest() -> str:
     return h.hexdigest()
 
 
-def read_counters(precision: str):
-    """Per-nonzero DRAM bytes and FP64 flops of the evaluation kernel from the committed ncu
-    capture (profiles/eval_kernel_counters.json), or None when the sources changed since."""
+def read_counters(precision: str, kernel: str):
+    """Per-nonzero DRAM bytes and FP64 instructions of the evaluation kernel(s) `kernel` (e.g.
+    "exa_all_b") from the committed ncu capture (profiles/eval_kernel_counters.json, key
+    "<precision>:<kernel>"), or None when there is none or the sources changed since."""
     try:
         with open(os.path.join(ROOT, "profiles", "eval_kernel_counters.json")) as fh:
             d = json.load(fh)
-        e = d[precision]
+        e = d[f"{precision}:{kernel}"]
         if e.get("csrc_sha256") != csrc_digest():
             return None
         return e
     except Exception:
         return None
+
+
+# the generated kernel(s) an exa_eval_all step with every output runs (exa_stat "eval_kernel_kind")
+KERNEL_KINDS = {0: "exa_all", 1: "exa_all_b", 2: "exa_first+exa_hess", 3: "exa_first+exa_hess_b"}
+
+
+def step_kernel(m, nbytes):
+    """Name and algorithmic bytes of the evaluation kernel(s) of the model's full step: the COO
+    kernel's bytes plus, when the step forms the compressed Hessian sums, their writes."""
+    kind = int(m.stat("eval_kernel_kind"))
+    extra = 8 * int(m.stat("nnzh_compressed")) if kind in (1, 3) else 0
+    return KERNEL_KINDS[kind], nbytes + extra
+
+
+def live_kernel_ms(m, step, n):
+    """The step's evaluation kernel(s) timed live: the library records CUDA events on the model
+    stream right before and after them in every exa_eval_all step (inside its cached graph); the
+    mean over n steps, each read after its step."""
+    v = []
+    for _ in range(n):
+        step()
+        t = m.stat("eval_kernel_ms")
+        if t > 0:
+            v.append(t)
+    return float(np.mean(v)) if v else float("nan")
 
 
 def read_peaks():
@@ -336,7 +362,7 @@ def measure_model(B, torch, timed, flat, pts, precision, local, peak_hbm, ref=No
     outs = dict(f=E(1), g=E(m.nvar), c=E(m.ncon), jac=E(m.nnzj), hess=E(m.nnzh), jac_csc=E(m.nnzj_csc),
                 hess_csc=E(m.nnzh_csc))
     xb, yb = E(m.nvar), E(m.ncon)
-    step_ms, kern_ms, jh_ms, errs = [], [], [], None
+    step_ms, kern_ms, coo_ms, jh_ms, errs = [], [], [], [], None
     for i, (x, y, s) in enumerate(pts):  # the same buffers for every point: one cached graph each
         xb.copy_(torch.as_tensor(x))
         if len(y):
@@ -352,18 +378,22 @@ def measure_model(B, torch, timed, flat, pts, precision, local, peak_hbm, ref=No
             errs = {k: (abs(float(got["f"][0]) - ref["f"]) / max(abs(ref["f"]), 1e-300) if k == "f"
                         else normwise(got[k], ref[k])) for k in got}
         step_ms.append(timed(step, calls_for(timed, step)))
+        kern_ms.append(live_kernel_ms(m, step, 20))
         kern()
-        kern_ms.append(timed(kern, calls_for(timed, kern)))
+        coo_ms.append(timed(kern, calls_for(timed, kern)))
         jh_ms.append(timed(jh, calls_for(timed, jh)))
     naug, nobj = pattern_counts([flat])
     nbytes = algorithmic_bytes([flat], m.nnzj, m.nnzh, m.nvar, m.ncon, naug, nobj,
                                mixed=precision == B.EXA_MIXED_FP32)
     nnz = m.nnzj + m.nnzh
+    kname, kbytes = step_kernel(m, nbytes)
     st, kt, jt = float(np.mean(step_ms)), float(np.mean(kern_ms)), float(np.mean(jh_ms))
-    rec = {"nnz": nnz, "step_ms": st, "step_nnz_per_s": nnz / (st * 1e-3), "kernel_ms": kt,
+    ct = float(np.mean(coo_ms))
+    rec = {"nnz": nnz, "step_ms": st, "step_nnz_per_s": nnz / (st * 1e-3), "kernel": kname, "kernel_ms": kt,
            "kernel_nnz_per_s": nnz / (kt * 1e-3), "jac_plus_hess_coord_ms": jt,
-           "algorithmic_bytes": nbytes, "kernel_gbs": nbytes / (kt * 1e-3) / 1e9,
-           "kernel_hbm_frac": nbytes / (kt * 1e-3) / 1e9 / peak_hbm,
+           "algorithmic_bytes": kbytes, "kernel_gbs": kbytes / (kt * 1e-3) / 1e9,
+           "kernel_hbm_frac": kbytes / (kt * 1e-3) / 1e9 / peak_hbm,
+           "coo_kernel_ms": ct, "coo_kernel_hbm_frac": nbytes / (ct * 1e-3) / 1e9 / peak_hbm,
            "l2_resident": nbytes < L2_BYTES, "create_s": create_s, "tuned_options": m.tuned_options(),
            "eval_regs": m.stat("eval_regs")}
     if errs is not None:
@@ -563,8 +593,14 @@ def run_exa(args):
     value = whole_job_rate(nnz_rank, ws, ms)
 
     phase("dominant kernel and callbacks")
-    # dominant kernel alone: the generated evaluation kernel writing J and H (no reductions)
-    kern_ms = timed(lambda: m.exa_eval_all(xt, yt, sigma, jac=jac, hess=hess), max(5, min(args.steps, 200)))
+    # the dominant kernel, live: the step's evaluation kernel(s) between the CUDA events the library
+    # records around them in every step (the last timed step's pair, then more steps read one by one)
+    last_ms = m.stat("eval_kernel_ms")
+    kern_ms = live_kernel_ms(m, step, max(5, min(args.steps, 100)))
+    if last_ms > 0:
+        kern_ms = (kern_ms * max(5, min(args.steps, 100)) + last_ms) / (max(5, min(args.steps, 100)) + 1)
+    # the COO-only variant alone (exa_eval_all writing J and H, no compressed sums, no reductions)
+    coo_ms = timed(lambda: m.exa_eval_all(xt, yt, sigma, jac=jac, hess=hess), max(5, min(args.steps, 200)))
     # Jacobian + Hessian callbacks alone (exa_jac_coord + exa_hess_coord)
     jh_ms = timed(lambda: (m.exa_jac_coord(xt, jac), m.exa_hess_coord(xt, yt, sigma, hess)), max(5, min(args.steps, 200)))
     naug, nobj = pattern_counts(flats)
@@ -573,14 +609,18 @@ def run_exa(args):
     # (each written once) and the objective
     step_bytes = nbytes + 8 * (m.nvar + m.nnzj_csc + m.nnzh_csc + 1)
     peak, peak_kind = read_peaks()
-    achieved = nbytes / (kern_ms * 1e-3) / 1e9
-    ctr = read_counters(args.precision)
+    kname, kbytes = step_kernel(m, nbytes)
+    achieved = kbytes / (kern_ms * 1e-3) / 1e9
+    ctr = read_counters(args.precision, kname)
     traffic = int(ctr["dram_bytes_per_nnz"] * nnz_rank) if ctr else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
-                "kernel": "exa_all (generated eval kernel)", "algorithmic_bytes": nbytes, "kernel_ms": kern_ms,
+                "kernel": f"{kname} (generated evaluation kernel of the step)", "algorithmic_bytes": kbytes,
+                "kernel_ms": kern_ms, "kernel_timing": "CUDA events around the kernel inside the step's graph",
                 "step_algorithmic_bytes": step_bytes,
-                "step_hbm_frac": step_bytes / (ms * 1e-3) / 1e9 / peak}
+                "step_hbm_frac": step_bytes / (ms * 1e-3) / 1e9 / peak,
+                "coo_only_kernel_ms": coo_ms, "coo_only_algorithmic_bytes": nbytes,
+                "coo_only_hbm_frac": nbytes / (coo_ms * 1e-3) / 1e9 / peak}
     phase("FP64 peak probe")
     fp64 = measure_fp64_peak(B, local)
     # write-only HBM rate (the evaluation kernels' traffic is mostly writes): a 4 GiB memset
@@ -599,9 +639,11 @@ def run_exa(args):
                "peak_source": "measured: DFMA probe (include/exa_probe.h) in this run",
                "kernel": roofline["kernel"], "fp64_inst": int(ctr["fp64_inst_per_nnz"] * nnz_rank),
                "fp64_gflops": gflops, "fp64_gflops_frac": gflops / (2 * pk),
-               "kernel_ms": kern_ms, "hbm_frac": roofline["frac"], "hbm_achieved_gbs": roofline["achieved"],
-               "algorithmic_bytes": nbytes, "step_algorithmic_bytes": step_bytes,
-               "step_hbm_frac": roofline["step_hbm_frac"]}
+               "kernel_ms": kern_ms, "kernel_timing": roofline["kernel_timing"], "hbm_frac": roofline["frac"],
+               "hbm_achieved_gbs": roofline["achieved"], "algorithmic_bytes": kbytes,
+               "step_algorithmic_bytes": step_bytes, "step_hbm_frac": roofline["step_hbm_frac"],
+               "coo_only_kernel_ms": coo_ms, "coo_only_algorithmic_bytes": nbytes,
+               "coo_only_hbm_frac": roofline["coo_only_hbm_frac"]}
         if alu["frac"] > roofline["frac"]:
             roofline = alu
 
@@ -656,7 +698,8 @@ def run_exa(args):
         step2 = lambda: m2.exa_eval_all(xt, yt, sigma, f=f, g=g, c=c, jac=jac, hess=hess, jac_csc=jcsc, hess_csc=hcsc)
         step2()
         ms2 = timed(step2, max(5, min(args.steps, 200)))
-        k2 = timed(lambda: m2.exa_eval_all(xt, yt, sigma, jac=jac, hess=hess), max(5, min(args.steps, 200)))
+        k2 = live_kernel_ms(m2, step2, max(5, min(args.steps, 100)))
+        k2coo = timed(lambda: m2.exa_eval_all(xt, yt, sigma, jac=jac, hess=hess), max(5, min(args.steps, 200)))
         tag = "mixed" if other == B.EXA_MIXED_FP32 else "fp64"
         # error of the mixed outputs against the FP64 outputs on the whole batch (every member of
         # both is checked against the CPU oracle in the parity tests)
@@ -672,10 +715,14 @@ def run_exa(args):
         del outs, ref, mix
         extras[f"{tag}_step_ms"] = ms2
         extras[f"{tag}_nnz_per_s"] = nnz_rank / (ms2 * 1e-3)
-        extras[f"{tag}_kernel_ms"] = k2
         nbytes2 = algorithmic_bytes(flats, m.nnzj, m.nnzh, m.nvar, m.ncon, naug, nobj, mixed=tag == "mixed")
-        extras[f"{tag}_kernel_hbm_frac"] = nbytes2 / (k2 * 1e-3) / 1e9 / peak
-        extras[f"{tag}_algorithmic_bytes"] = nbytes2
+        kname2, kbytes2 = step_kernel(m2, nbytes2)
+        extras[f"{tag}_kernel"] = kname2
+        extras[f"{tag}_kernel_ms"] = k2
+        extras[f"{tag}_kernel_hbm_frac"] = kbytes2 / (k2 * 1e-3) / 1e9 / peak
+        extras[f"{tag}_algorithmic_bytes"] = kbytes2
+        extras[f"{tag}_coo_kernel_ms"] = k2coo
+        extras[f"{tag}_coo_kernel_hbm_frac"] = nbytes2 / (k2coo * 1e-3) / 1e9 / peak
         extras[f"{tag}_eval_regs"] = m2.stat("eval_regs")
         extras[f"{tag}_tuned_options"] = ",".join(str(v) for v in m2.tuned_options().values())
         m2.destroy()

@@ -338,8 +338,14 @@ exa_status exa_compile_check(const exa_model_desc *desc, const exa_options *opt,
 /* Named statistics (host values): "nvrtc_ms", "create_ms", "tune_ms", "eval_regs", "eval_block",
  * "eval_regs_jac", "eval_regs_hess", "eval_tiles", "eval_grid", "eval_persist", "eval_min_blocks",
  * "eval_split", "eval_chunks", "eval_upfront", "eval_prefetch", "eval_wave_pct", "eval_lanes", "eval_lazy",
- * "graph_kernels", "csc_direct",
+ * "eval_stage", "eval_dsmem", "graph_kernels", "csc_direct",
  * "hess_compressed", "nnzh_compressed", "grad_compact", "device_bytes", "n_patterns", "batch_members".
+ * "eval_kernel_ms": milliseconds between CUDA events recorded on the model stream right before and
+ * right after the evaluation kernel(s) of the latest exa_eval_all call (also inside its cached
+ * graphs; member chunks: the first chunk's launch to the last chunk's); waits for the second event;
+ * -1 when no call has recorded them.  "eval_kernel_kind": the generated kernel(s) an exa_eval_all
+ * call with every output runs: 0 exa_all, 1 exa_all_b (COO and compressed Hessian sums),
+ * 2 exa_first + exa_hess, 3 exa_first + exa_hess_b.
  * Unknown key: EXA_E_INVALID. */
 exa_status exa_stat(const exa_model *m, const char *key, double *value);
 

@@ -387,6 +387,10 @@ struct exa_model {
     bool host_serial = false;
     cudaStream_t h2d = nullptr, d2h = nullptr;
     cudaEvent_t ev_in[16] = {}, ev_out[16] = {}, ev_hstart = nullptr, ev_hdone = nullptr;
+    // timing events around the evaluation kernel(s) of the latest exa_eval_all step (recorded into
+    // the cached graphs too); exa_stat "eval_kernel_ms" reads them
+    cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;
+    bool ev_k_valid = false;
     bool grad_compact = false;
     int n_gseg = 0;
     int *d_gsegptr = nullptr, *d_gsegvar = nullptr;
@@ -460,10 +464,11 @@ void free_all(exa_model *m) {
         if (e) cudaEventDestroy(e);
         e = nullptr;
     }
-    for (cudaEvent_t *e : {&m->ev_hstart, &m->ev_hdone}) {
+    for (cudaEvent_t *e : {&m->ev_hstart, &m->ev_hdone, &m->ev_k0, &m->ev_k1}) {
         if (*e) cudaEventDestroy(*e);
         *e = nullptr;
     }
+    m->ev_k_valid = false;
     for (int k = 0; k < 16; k++)
         for (cudaEvent_t *e : {&m->ev_in[k], &m->ev_out[k]}) {
             if (*e) cudaEventDestroy(*e);
@@ -2089,6 +2094,20 @@ static cudaError_t side_stream(cudaStream_t *s) {
 // contiguous ranges of variables, rows, tiles and CSC positions).  The evaluation of the next chunk
 // overlaps these reductions.  The objective sum follows the last evaluation; the host copies of
 // f, g, c follow the last reduction.  Same kernels, same per-element arithmetic as one chunk.
+// Records timing event ev (ev_k0 or ev_k1) on the model stream: plainly, or as an event-record node
+// while this library captures its own graph; not inside a capture the caller is making.
+static exa_status record_eval_event(exa_model *m, cudaEvent_t *ev) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CR(cudaStreamIsCapturing(m->stream, &cs));
+    const bool own_capture = cs != cudaStreamCaptureStatusNone && m->stream == m->cap_stream;
+    if (cs != cudaStreamCaptureStatusNone && !own_capture) return EXA_OK;
+    if (!*ev) CR(cudaEventCreate(ev));
+    if (own_capture) CR(cudaEventRecordWithFlags(*ev, m->stream, cudaEventRecordExternal));
+    else CR(cudaEventRecord(*ev, m->stream));
+    if (ev == &m->ev_k1) m->ev_k_valid = true;
+    return EXA_OK;
+}
+
 static exa_status eval_all_chunked(exa_model *m, const double *x, const double *y, double sigma, double *f, double *g,
                                    double *c, double *jac_csc, double *hess_csc, ExaOut o,
                                    Mode mode, Mode hmode, bool split, bool jdirect, bool hdirect, bool hcomp) {
@@ -2120,12 +2139,16 @@ static exa_status eval_all_chunked(exa_model *m, const double *x, const double *
             if (exa_status e = m->pre_chunk(k)) return e;
         ExaOut oc = split ? o1 : o;
         oc.obj_part = m->d_objpart + nparts;
+        if (k == 0)
+            if (exa_status e = record_eval_event(m, &m->ev_k0)) return e;
         if (exa_status e = launch_eval(m, m1, x, y, sigma, oc, m->mb_tile[m1][b0], m->mb_tile[m1][b1]))
             return e;
         if (m->mb_tile[m1][b1] > m->mb_tile[m1][b0]) nparts += eval_grid(m, m1, m->mb_tile[m1][b1] - m->mb_tile[m1][b0]);
         if (split)
             if (exa_status e = launch_eval(m, hmode, x, y, sigma, o2, m->mb_tile[hmode][b0], m->mb_tile[hmode][b1]))
                 return e;
+        if (k == m->nchunks - 1)
+            if (exa_status e = record_eval_event(m, &m->ev_k1)) return e;
         CR(cudaEventRecord(m->ev_chunk[k], m->stream));
         CR(cudaStreamWaitEvent(ps, m->ev_chunk[k], 0));
         if (jside) {
@@ -2260,12 +2283,15 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
         o2.hmap = o.hmap;
         o2.hcomp = o.hcomp;
         mode = exa::M_FIRST;
+        if (exa_status e = record_eval_event(m, &m->ev_k0)) return e;
         if (exa_status e = launch_eval(m, exa::M_FIRST, x, y, sigma, o1)) return e;
         CR(cudaEventRecord(m->ev_first, m->stream));
         if (exa_status e = launch_eval(m, hmode, x, y, sigma, o2)) return e;
-    } else if (exa_status e = launch_eval(m, mode, x, y, sigma, o)) {
-        return e;
+    } else {
+        if (exa_status e = record_eval_event(m, &m->ev_k0)) return e;
+        if (exa_status e = launch_eval(m, mode, x, y, sigma, o)) return e;
     }
+    if (exa_status e = record_eval_event(m, &m->ev_k1)) return e;
     if (forked) CR(cudaEventRecord(m->ev_fork, m->stream));
     const cudaEvent_t first_done = split ? m->ev_first : m->ev_fork;  // first-order outputs final
     cudaStream_t rs = split ? m->side[3] : m->stream;                  // stream of the f, g, c sums
@@ -2609,6 +2635,19 @@ exa_status exa_stat(const exa_model *m, const char *key, double *value) {
     else if (k == "eval_lanes") *value = m->lanes;
     else if (k == "eval_lazy") *value = m->lazy_loads;
     else if (k == "eval_stage") *value = m->stage;
+    else if (k == "eval_kernel_ms") {  // evaluation kernel(s) of the latest exa_eval_all step
+        float ms = -1.0f;
+        if (!m->ev_k_valid || cudaEventSynchronize(m->ev_k1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, m->ev_k0, m->ev_k1) != cudaSuccess)
+            ms = -1.0f;
+        *value = ms;
+    }
+    else if (k == "eval_kernel_kind") {  // which generated kernel(s) the exa_eval_all step with every output runs
+        // 0 exa_all, 1 exa_all_b (COO and compressed Hessian sums), 2 exa_first + exa_hess,
+        // 3 exa_first + exa_hess_b
+        const bool hc = m->use_hcomp && !(m->csc_direct && m->nnzh_csc == m->nnzh);
+        *value = (m->split_all ? 2 : 0) + (hc ? 1 : 0);
+    }
     else if (k == "eval_dsmem") *value = m->dsmem[exa::M_ALL];
     else if (k == "eval_wave_pct") *value = m->wave_pct;
     else if (k == "graph_kernels") *value = m->graph_kernels;

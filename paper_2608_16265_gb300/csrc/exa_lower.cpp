@@ -1425,6 +1425,49 @@ struct Emitter {
         for (size_t c = 0; c < grp.hc.size(); c++)
             for (auto &pj : grp.hc[c]) hc_of[pj] = (int)c;
         std::vector<char> hc_started(grp.hc.size(), 0);
+        // Compressed sums, from the slots' products before any doubling.  Each sum is a sequence of
+        // terms (pattern, product node, sign; a slot whose two different symbols are one group
+        // symbol always holds twice its product).  Two sums whose sequences agree up to one overall
+        // sign are equal up to that sign, bit for bit (same operands added in the same order), so
+        // the later one is the earlier one negated or copied: the angle-difference patterns of power
+        // flow give h(tf,tf) = h(tt,tt) = -h(tf,tt), and likewise for their mixed partials.  A sum
+        // over two different symbols is doubled afterwards, as a whole, where they resolve to one
+        // variable (2 a + 2 b = 2 (a + b) exactly).
+        std::vector<int> hc_dup(grp.hc.size(), -1), hc_dsign(grp.hc.size(), 1);
+        std::vector<std::vector<char>> hc_twice(grp.hc.size());  // per term of hc[c]: always doubled
+        if (hs_comp) {
+            std::map<std::vector<long long>, std::pair<int, int>> seen;  // normalised terms -> (sum, sign)
+            for (size_t c = 0; c < grp.hc.size(); c++) {
+                std::vector<long long> key;
+                int first_sign = 0;
+                hc_twice[c].assign(grp.hc[c].size(), 0);
+                for (size_t t = 0; t < grp.hc[c].size(); t++) {
+                    const int pos = grp.hc[c][t].first, j = grp.hc[c][t].second;
+                    if (std::find(act.begin(), act.end(), pos) == act.end() || !want[pos].hess) continue;
+                    const Pattern &p = pat(pos);
+                    const int a = p.hpair[j].first, b = p.hpair[j].second;
+                    const bool twice = a != b && grp.sym[pos][a] == grp.sym[pos][b];
+                    hc_twice[c][t] = twice;
+                    const int r = hroots[pos][j];
+                    int base = -1, sign = 1;
+                    if (r >= 0) {
+                        const bool ng = g.n[r].op == S_NEG;
+                        base = ng ? g.n[r].a : r;
+                        sign = ng ? -1 : 1;
+                    }
+                    if (!first_sign) first_sign = sign;
+                    key.push_back(((long long)pos << 40) ^ ((long long)(base + 1) << 2) ^ (twice ? 2 : 0) ^
+                                  (sign * first_sign < 0 ? 1 : 0));
+                }
+                if (key.empty()) continue;
+                auto it = seen.find(key);
+                if (it == seen.end()) seen.emplace(key, std::make_pair((int)c, first_sign));
+                else {
+                    hc_dup[c] = it->second.first;
+                    hc_dsign[c] = first_sign * it->second.second;
+                }
+            }
+        }
         for (int pos : act) {
             const Pattern &p = pat(pos);
             const PatternGraph &G = PG[pos];
@@ -1498,6 +1541,17 @@ struct Emitter {
                         doubled.push_back({j, c});
                     }
                 }
+                if (hs_comp)  // the group's compressed sums (FP64, pattern order), before the doubling
+                    for (int j = 0; j < p.nh(); j++) {
+                        const int c = hc_of.at({pos, j});
+                        if (hc_dup[c] >= 0) continue;  // equal up to sign to an earlier sum
+                        size_t t = 0;
+                        while (grp.hc[c][t] != std::make_pair(pos, j)) t++;
+                        const std::string term = hc_twice[c][t] ? "exa_twice(" + vals[j] + ")" : vals[j];
+                        if (hc_started[c]) os << "  hc" << c << " += " << term << ";\n";
+                        else os << "  double hc" << c << " = " << term << ";\n";
+                        hc_started[c] = 1;
+                    }
                 // A slot pairing two different symbols that resolve to the same variable holds twice
                 // the mixed partial (2 (w h) equals (2 w) h exactly).  Rare: one warp-uniform test,
                 // the doubling only in warps that need it.
@@ -1508,17 +1562,34 @@ struct Emitter {
                            << dj.first << ";\n";
                     os << "  }\n";
                 }
-                if (hs_comp)
-                    for (int j = 0; j < p.nh(); j++) {  // the group's compressed slot (FP64, pattern order)
-                        const int c = hc_of.at({pos, j});
-                        if (hc_started[c]) os << "  hc" << c << " += " << vals[j] << ";\n";
-                        else os << "  double hc" << c << " = " << vals[j] << ";\n";
-                        hc_started[c] = 1;
-                    }
                 if (hs_coo) staged("o.hess", "pm.hbase[" + P + "]", p.nh(), vals, "o.hcsc", "o.hmap");
             }
         }
         if (hs_comp) {  // per-instance FP64 sums of the Hessian slots that share (row, col) in the group
+            for (size_t c = 0; c < grp.hc.size(); c++)
+                if (hc_dup[c] >= 0 && hc_started[hc_dup[c]]) {
+                    const std::string src = "hc" + std::to_string(hc_dup[c]);
+                    os << "  double hc" << c << " = " << (hc_dsign[c] < 0 ? "exa_neg(" + src + ")" : src) << ";\n";
+                    hc_started[c] = 1;
+                }
+            // sums over two different symbols that resolve to one variable: doubled as a whole
+            std::string any;
+            std::vector<std::pair<size_t, std::string>> dbl;
+            for (size_t c = 0; c < grp.hc.size(); c++) {
+                const int ga = grp.hc_sym[c].first, gb = grp.hc_sym[c].second;
+                if (!hc_started[c] || ga == gb) continue;
+                auto eb = eqbit.find({std::min(ga, gb), std::max(ga, gb)});
+                const std::string cond = use_eqm && eb != eqbit.end()
+                                             ? "((eqm >> " + std::to_string(eb->second) + ") & 1ull)"
+                                             : "(i" + std::to_string(ga) + " == i" + std::to_string(gb) + ")";
+                any += (any.empty() ? "" : " || ") + cond;
+                dbl.push_back({c, cond});
+            }
+            if (!dbl.empty()) {
+                os << "  if (__any_sync(0xffffffffu, " << any << ")) {\n";
+                for (auto &d : dbl) os << "    if (" << d.second << ") hc" << d.first << " += hc" << d.first << ";\n";
+                os << "  }\n";
+            }
             std::vector<std::string> sums;
             for (size_t c = 0; c < grp.hc.size(); c++) sums.push_back(hc_started[c] ? "hc" + std::to_string(c) : "0.0");
             staged("o.hcomp", "pm.hcbase", (int)grp.hc.size(), sums, nullptr, nullptr);

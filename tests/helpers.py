@@ -49,6 +49,39 @@ def all_ops_model(seed=0):
     return m
 
 
+def flow_collision_model(seed=0):
+    """The four polar branch-flow patterns of ACOPF on one data array (one fused group, so the
+    Hessian CSC can come from per-branch compressed sums) on a network with self-loops (from bus =
+    to bus) and a parallel branch: Hessian slots over two different symbols that resolve to one
+    variable, and compressed sums whose terms agree up to sign (h(tf,tf) = h(tt,tt) = -h(tf,tt))."""
+    rng = np.random.default_rng(seed)
+    nb = 5
+    m = Model()
+    va = m.add_var(nb)
+    vm = m.add_var(nb)
+    f = np.array([0, 1, 2, 2, 3, 4, 4, 0], np.int32)
+    t = np.array([1, 2, 2, 3, 0, 4, 1, 1], np.int32)  # self-loops at buses 2 and 4; 0-1 twice
+    nl = len(f)
+    br = dict(f=f, t=t, g=rng.uniform(0.5, 2.0, nl), b=rng.uniform(-3.0, -1.0, nl), gs=rng.uniform(0.0, 0.1, nl))
+    m.add_con(lambda d: d.gs * vm[d.f] ** 2 + vm[d.f] * vm[d.t] * (
+        d.g * cos(va[d.f] - va[d.t]) + d.b * sin(va[d.f] - va[d.t])), data=br)
+    m.add_con(lambda d: -d.gs * vm[d.f] ** 2 - vm[d.f] * vm[d.t] * (
+        d.b * cos(va[d.f] - va[d.t]) - d.g * sin(va[d.f] - va[d.t])), data=br)
+    m.add_con(lambda d: d.gs * vm[d.t] ** 2 + vm[d.t] * vm[d.f] * (
+        d.g * cos(va[d.t] - va[d.f]) + d.b * sin(va[d.t] - va[d.f])), data=br)
+    m.add_con(lambda d: -d.gs * vm[d.t] ** 2 - vm[d.t] * vm[d.f] * (
+        d.b * cos(va[d.t] - va[d.f]) - d.g * sin(va[d.t] - va[d.f])), data=br)
+    m.add_obj(lambda d: (vm[d.k] - 1.0) ** 2, n=nb)
+    return m
+
+
+def flow_collision_point(seed=1):
+    rng = np.random.default_rng(seed)
+    x = np.concatenate([rng.uniform(-0.3, 0.3, 5), rng.uniform(0.9, 1.1, 5)])
+    y = rng.standard_normal(32)
+    return x, y, 0.5
+
+
 def all_ops_point(seed=1):
     rng = np.random.default_rng(seed)
     x = rng.uniform(0.2, 0.9, 6)

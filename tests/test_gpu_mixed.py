@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import synth
-from tests.helpers import all_ops_model, all_ops_point, more_ops_model, normwise
+from tests.helpers import all_ops_model, all_ops_point, flow_collision_model, flow_collision_point, more_ops_model, normwise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -24,6 +24,7 @@ def _t(a):
 
 CASES = {
     "all_ops": lambda: (all_ops_model().flat(), all_ops_point()),
+    "flow_collisions": lambda: (flow_collision_model().flat(), flow_collision_point()),
     "more_ops": lambda: (more_ops_model().flat(), (np.random.default_rng(2).uniform(0.2, 0.9, 6),
                                                    np.random.default_rng(3).standard_normal(10), 1.3)),
     "rosenbrock_1000": lambda: (lambda w: (w.flat, synth.rosenbrock_point(w, 0)))(synth.rosenbrock(1000)),

@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import synth
-from tests.helpers import all_ops_model, all_ops_point, more_ops_model, normwise
+from tests.helpers import all_ops_model, all_ops_point, flow_collision_model, flow_collision_point, more_ops_model, normwise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -79,6 +79,7 @@ def check_model(flat, x, y, s, block=0, tol=TOL, o=None, flags=0, precision=0, g
 
 CASES = {
     "all_ops": lambda: (all_ops_model().flat(), all_ops_point()),
+    "flow_collisions": lambda: (flow_collision_model().flat(), flow_collision_point()),
     "more_ops": lambda: (more_ops_model().flat(), (np.random.default_rng(2).uniform(0.2, 0.9, 6),
                                                    np.random.default_rng(3).standard_normal(10), 1.3)),
     "rosenbrock_1000": lambda: (lambda w: (w.flat, synth.rosenbrock_point(w, 0)))(synth.rosenbrock(1000)),
@@ -159,7 +160,7 @@ def test_pinned_launch_choices(choice):
     assert m.stat("eval_stage") == ("stage" in choice)
 
 
-@pytest.mark.parametrize("name", ["all_ops", "more_ops", "acopf_shunts", "pde_41", "goddard_2000", "two_stage_acopf"])
+@pytest.mark.parametrize("name", ["all_ops", "flow_collisions", "more_ops", "acopf_shunts", "pde_41", "goddard_2000", "two_stage_acopf"])
 def test_parity_lazy_loads(name):
     """Each pattern's inputs loaded one pattern ahead instead of at the top of the fused group (the
     third emission order the tuner searches) on every workload kind, with a register cap."""
@@ -169,7 +170,7 @@ def test_parity_lazy_loads(name):
     assert m.stat("eval_lazy") == 1
 
 
-@pytest.mark.parametrize("name", ["all_ops", "more_ops", "acopf_shunts", "pde_41", "goddard_2000", "two_stage_acopf"])
+@pytest.mark.parametrize("name", ["all_ops", "flow_collisions", "more_ops", "acopf_shunts", "pde_41", "goddard_2000", "two_stage_acopf"])
 def test_parity_two_warp_sets(name):
     """Two warp sets per instance (each a contiguous subset of a fused group's patterns) on every
     workload kind in FP64 (the mixed-precision tests cover the other precision), with a persistent
@@ -179,7 +180,7 @@ def test_parity_two_warp_sets(name):
     check_model(flat, x, y, s, flags=B.EXA_FLAG_NO_TUNE | B.EXA_FLAG_LANES2, block=128, grid_factor=1)
 
 
-@pytest.mark.parametrize("name", ["all_ops", "more_ops", "acopf_shunts", "pde_41", "goddard_2000", "two_stage_acopf"])
+@pytest.mark.parametrize("name", ["all_ops", "flow_collisions", "more_ops", "acopf_shunts", "pde_41", "goddard_2000", "two_stage_acopf"])
 @pytest.mark.parametrize("order", ["eager", "lazy"])
 def test_parity_smem_staging(name, order):
     """The next tile's inputs staged in shared memory by cp.async (double-buffered persistent tile

@@ -11,7 +11,7 @@ import scipy.sparse as sp
 import oracle
 import synth
 from paper_2608_16265_gb300.ir import Model, exp, sin
-from tests.helpers import all_ops_model, all_ops_point, dense_hess, dense_jac, more_ops_model, normwise
+from tests.helpers import all_ops_model, all_ops_point, flow_collision_model, flow_collision_point, dense_hess, dense_jac, more_ops_model, normwise
 
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_pins.json")))
 
@@ -196,6 +196,7 @@ def _cs_hessian(o, x, y, s, h=1e-30):
 
 CASES = [
     ("all_ops", lambda: (all_ops_model().flat(), all_ops_point())),
+    ("flow_collisions", lambda: (flow_collision_model().flat(), flow_collision_point())),
     ("more_ops", lambda: (more_ops_model().flat(), (np.random.default_rng(2).uniform(0.2, 0.9, 6),
                                                      np.random.default_rng(3).standard_normal(10), 1.3))),
     ("rosenbrock", lambda: (lambda w: (w.flat, synth.rosenbrock_point(w, 1)))(synth.rosenbrock(7))),
