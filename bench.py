@@ -143,10 +143,16 @@ KERNEL_KINDS = {0: "exa_all", 1: "exa_all_b", 2: "exa_first+exa_hess", 3: "exa_f
 
 def step_kernel(m, nbytes):
     """Name and algorithmic bytes of the evaluation kernel(s) of the model's full step: the COO
-    kernel's bytes plus, when the step forms the compressed Hessian sums, their writes."""
+    kernel's bytes plus, when the step forms the compressed Hessian sums, their writes, and when it
+    scatters a duplicate-free CSC from the kernel (EXA_FLAG_CSC_SCATTER), those writes."""
     kind = int(m.stat("eval_kernel_kind"))
-    extra = 8 * int(m.stat("nnzh_compressed")) if kind in (1, 3) else 0
-    return KERNEL_KINDS[kind], nbytes + extra
+    name, extra = KERNEL_KINDS[kind], 8 * int(m.stat("nnzh_compressed")) if kind in (1, 3) else 0
+    if m.stat("csc_direct"):
+        scat = [n for n, n_csc in ((m.nnzj, m.nnzj_csc), (m.nnzh, m.nnzh_csc)) if n == n_csc]
+        if scat:
+            extra += 8 * sum(scat)
+            name += " with CSC scatter"
+    return name, nbytes + extra
 
 
 def live_kernel_ms(m, step, n):
