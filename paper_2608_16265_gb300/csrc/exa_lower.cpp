@@ -1634,10 +1634,6 @@ static __device__ __forceinline__ float exa_d2f(const double d) {
 R"(
 static __device__ __forceinline__ void exa_sincos_red(const double a, float* s, float* c) {
   if (!(fabs(a) < 1.0e6)) { double sd, cd; sincos(a, &sd, &cd); *s = (float)sd; *c = (float)cd; return; }
-  if (__all_sync(__activemask(), (__double2hiint(a) & 0x7fffffff) < 0x3fe921fb)) {  // |a| < pi/4: q = 0, r = a
-    sincosf(exa_d2f(a), s, c);
-    return;
-  }
   const double q = rint(a * 0x1.45f306dc9c883p-1);
   const double r = fma(-q, 0x1.0b4611a626331p-34, fma(-q, 0x1.921fb54400000p+0, a));
   float sr, cr;

@@ -2,8 +2,7 @@
 reduction, minimax polynomials) compiled for the host with shims for the CUDA bit-cast intrinsics
 and checked against the host C library: within 1 ulp over a sweep of arguments next to multiples
 of pi/2, tiny, large and signed-zero arguments.  Host fma is correctly rounded like the device's,
-so the host build computes the same values as the kernels (each argument runs as a warp of its own,
-so arguments below pi/4 take the path that skips the reduction and the others the full one).  The polynomial coefficients in the
+so the host build computes the same values as the kernels.  The polynomial coefficients in the
 helper are the ones the Remez script beside it (csrc/gen_sincos_minimax.py) derives, and that script's
 error bound for them is checked independently of the script: the rounded polynomials are compared
 with mpmath's sin and cos on a grid that the script does not use."""
@@ -30,8 +29,6 @@ static inline int __double2loint(double d) { return (int)(unsigned)(__double_as_
 static inline int __double2hiint(double d) { return (int)(__double_as_longlong(d) >> 32); }
 static inline double __hiloint2double(int hi, int lo) {
   unsigned long long v = ((unsigned long long)(unsigned)hi << 32) | (unsigned)lo; double d; std::memcpy(&d, &v, 8); return d; }
-static inline unsigned __activemask() { return 1u; }  // one lane: the warp vote is the lane's own test
-static inline bool __all_sync(unsigned, bool p) { return p; }
 #define __device__
 #define __forceinline__ inline
 '''
