@@ -141,11 +141,15 @@ def read_counters(precision: str, kernel: str):
 KERNEL_KINDS = {0: "exa_all", 1: "exa_all_b", 2: "exa_first+exa_hess", 3: "exa_first+exa_hess_b"}
 
 
-def step_kernel(m, nbytes):
+def step_kernel(m, nbytes, step_bytes=None):
     """Name and algorithmic bytes of the evaluation kernel(s) of the model's full step: the COO
     kernel's bytes plus, when the step forms the compressed Hessian sums, their writes, and when it
-    scatters a duplicate-free CSC from the kernel (EXA_FLAG_CSC_SCATTER), those writes."""
+    scatters a duplicate-free CSC from the kernel (EXA_FLAG_CSC_SCATTER), those writes.  A fused
+    step (EXA_FLAG_FUSED_STEP: evaluation and reductions in one kernel) moves the whole step's
+    algorithmic bytes, `step_bytes`."""
     kind = int(m.stat("eval_kernel_kind"))
+    if m.stat("eval_fused_step") and kind in (0, 1) and step_bytes is not None:
+        return ("exa_step_b" if kind == 1 else "exa_step") + " (fused step)", step_bytes
     name, extra = KERNEL_KINDS[kind], 8 * int(m.stat("nnzh_compressed")) if kind in (1, 3) else 0
     if m.stat("csc_direct"):
         scat = [n for n, n_csc in ((m.nnzj, m.nnzj_csc), (m.nnzh, m.nnzh_csc)) if n == n_csc]
@@ -615,7 +619,7 @@ def run_exa(args):
     # (each written once) and the objective
     step_bytes = nbytes + 8 * (m.nvar + m.nnzj_csc + m.nnzh_csc + 1)
     peak, peak_kind = read_peaks()
-    kname, kbytes = step_kernel(m, nbytes)
+    kname, kbytes = step_kernel(m, nbytes, step_bytes)
     achieved = kbytes / (kern_ms * 1e-3) / 1e9
     ctr = read_counters(args.precision, kname)
     traffic = int(ctr["dram_bytes_per_nnz"] * nnz_rank) if ctr else None

@@ -186,6 +186,15 @@ enum {
                                   fused group (fewer values live); excludes EXA_FLAG_UPFRONT */
     EXA_FLAG_HOST_SERIAL = 8192, /* exa_eval_all_host on a batch: no member-chunk pipeline (inputs,
                                   graph, outputs one after another on the model stream) */
+    EXA_FLAG_FUSED_STEP = 16384, /* exa_eval_all with the Hessian runs one persistent kernel whose
+                                  CTAs take evaluation tiles and reductions (Jacobian and Hessian CSC,
+                                  gradient, constraint augmentations) from one work queue; a
+                                  member's reductions wait (bounded; EXA_E_TIMEOUT from
+                                  exa_check_status if the bound is hit) for that member's tiles, so
+                                  on a batch they overlap the evaluation of later members.  FP64
+                                  models only; excludes EXA_FLAG_STAGE_SMEM, EXA_FLAG_LANES2 and the
+                                  prefetch flags; with member chunks or EXA_FLAG_SPLIT the plain
+                                  graph is used */
     EXA_FLAG_STAGE_SMEM = 4096 /* staging depth 1: the tile loop copies the inputs of the CTA's next
                                   tile (data columns, x values indexed by the instance alone,
                                   constraint multipliers) into shared memory with cp.async while the
@@ -338,7 +347,7 @@ exa_status exa_compile_check(const exa_model_desc *desc, const exa_options *opt,
 /* Named statistics (host values): "nvrtc_ms", "create_ms", "tune_ms", "eval_regs", "eval_block",
  * "eval_regs_jac", "eval_regs_hess", "eval_tiles", "eval_grid", "eval_persist", "eval_min_blocks",
  * "eval_split", "eval_chunks", "eval_upfront", "eval_prefetch", "eval_wave_pct", "eval_lanes", "eval_lazy",
- * "eval_stage", "eval_dsmem", "graph_kernels", "csc_direct",
+ * "eval_stage", "eval_dsmem", "eval_fused_step", "graph_kernels", "csc_direct",
  * "hess_compressed", "nnzh_compressed", "grad_compact", "device_bytes", "n_patterns", "batch_members".
  * "eval_kernel_ms": milliseconds between CUDA events recorded on the model stream right before and
  * right after the evaluation kernel(s) of the latest exa_eval_all call (also inside its cached

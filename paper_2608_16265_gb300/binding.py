@@ -26,7 +26,7 @@ EXA_FP64, EXA_MIXED_FP32 = 0, 1
 EXA_FLAG_BOUNDS_CHECK, EXA_FLAG_NO_TUNE, EXA_FLAG_NO_FUSE, EXA_FLAG_NO_GRAPH = 1, 2, 4, 8
 EXA_FLAG_SPLIT, EXA_FLAG_CSC_SCATTER, EXA_FLAG_NO_HCOMP, EXA_FLAG_UPFRONT = 16, 32, 64, 128
 EXA_FLAG_PF_COLUMNS, EXA_FLAG_PF_GATHERS, EXA_FLAG_LANES2, EXA_FLAG_LAZY_LOADS = 256, 512, 1024, 2048
-EXA_FLAG_STAGE_SMEM, EXA_FLAG_HOST_SERIAL = 4096, 8192
+EXA_FLAG_STAGE_SMEM, EXA_FLAG_HOST_SERIAL, EXA_FLAG_FUSED_STEP = 4096, 8192, 16384
 STATUS_NAMES = ["EXA_OK", "EXA_E_INVALID", "EXA_E_OOM", "EXA_E_NVRTC", "EXA_E_CUDA", "EXA_E_BOUNDS",
                 "EXA_E_TIMEOUT", "EXA_E_UNSUPPORTED", "EXA_E_INTERNAL"]
 
@@ -284,6 +284,7 @@ class Model:
         flags |= EXA_FLAG_LANES2 if self.stat("eval_lanes") == 2 else 0
         flags |= EXA_FLAG_LAZY_LOADS if self.stat("eval_lazy") else 0
         flags |= EXA_FLAG_STAGE_SMEM if self.stat("eval_stage") else 0
+        flags |= EXA_FLAG_FUSED_STEP if self.stat("eval_fused_step") else 0
         persist = int(self.stat("eval_persist"))
         return dict(block=int(self.stat("eval_block")), min_blocks=int(self.stat("eval_min_blocks")),
                     grid_factor=persist if persist > 0 else -1, flags=flags, chunks=int(self.stat("eval_chunks")),

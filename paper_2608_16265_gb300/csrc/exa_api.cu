@@ -320,6 +320,16 @@ struct exa_model {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t fn[exa::M_COUNT] = {};
     int regs[exa::M_COUNT] = {};
+    // fused step (EXA_FLAG_FUSED_STEP): kernels exa_step (index 0, tiles of M_ALL) and exa_step_b
+    // (1, M_ALL_B), their work queues, per-member tile counts and the queue/tile counters
+    bool fused_step = false;
+    cudaKernel_t fn_step[2] = {};
+    ExaTask *d_items[2] = {};
+    int nitems[2] = {}, step_grid[2] = {};
+    bool step_ready[2] = {};
+    int *d_need[2] = {}, *d_sctr = nullptr;
+    std::vector<ExaTile> h_tiles[exa::M_COUNT];  // host copies of the tile lists
+    i64 objpart_n = 0;                           // objective partial slots allocated
     ExaPM *d_pm = nullptr;
     ExaTile *d_tiles[exa::M_COUNT] = {};
     int ntiles[exa::M_COUNT] = {};
@@ -416,6 +426,7 @@ extern "C" {
 static exa_status eval_all_launches(exa_model *m, const double *x, const double *y, double sigma, double *f,
                                     double *g, double *c, double *jac, double *hess, double *jac_csc,
                                     double *hess_csc);
+static exa_status prepare_step(exa_model *m);
 }
 
 namespace {
@@ -478,6 +489,15 @@ void free_all(exa_model *m) {
         if (*st) cudaStreamDestroy(*st);
         *st = nullptr;
     }
+    for (int i = 0; i < 2; i++) {
+        if (m->d_items[i]) cudaFree(m->d_items[i]);
+        if (m->d_need[i]) cudaFree(m->d_need[i]);
+        m->d_items[i] = nullptr;
+        m->d_need[i] = nullptr;
+        m->step_ready[i] = false;
+    }
+    if (m->d_sctr) cudaFree(m->d_sctr);
+    m->d_sctr = nullptr;
     for (int k = 0; k < exa::M_COUNT; k++) {
         if (m->d_tiles[k]) cudaFree(m->d_tiles[k]);
         m->d_tiles[k] = nullptr;
@@ -566,6 +586,12 @@ exa_status compile(exa_model *m, const std::string &src) {
         cudaFuncAttributes attr;
         CR(cudaFuncGetAttributes(&attr, (const void *)m->fn[k]));
         m->regs[k] = attr.numRegs;
+    }
+    for (int i = 0; i < 2; i++) {  // present only when generated with the fused step
+        m->fn_step[i] = nullptr;
+        m->step_ready[i] = false;
+        if (!m->fused_step) continue;
+        CR(cudaLibraryGetKernel(&m->fn_step[i], m->lib, i ? "exa_step_b" : "exa_step"));
     }
     return EXA_OK;
 }
@@ -941,7 +967,8 @@ exa_status setup_kernels(exa_model *m, int block, int min_blocks = 0) {
     cg.prefetch = m->lanes > 1 ? 0 : m->prefetch;
     cg.lanes = m->lanes;
     cg.lazy_loads = m->lazy_loads;
-    cg.stage = m->stage;
+    cg.stage = m->fused_step ? 0 : m->stage;
+    cg.fused_step = m->fused_step;
     std::string gerr;
     std::string src = exa::generate_source(m->pats, m->groups, cg, &gerr, m->dsmem);
     if (!gerr.empty()) return fail(m, EXA_E_INTERNAL, gerr);
@@ -972,10 +999,12 @@ exa_status setup_kernels(exa_model *m, int block, int min_blocks = 0) {
             }
         m->ntiles[k] = (int)tiles.size();
         m->mb_tile[k][nb] = m->ntiles[k];
+        m->h_tiles[k] = tiles;
         m->grid[k] = m->ntiles[k];
         m->pfd[k] = 0;
         if (m->d_tiles[k]) cudaFree(m->d_tiles[k]);
         m->d_tiles[k] = nullptr;
+        m->step_ready[0] = m->step_ready[1] = false;  // the fused step's queues index these tiles
         CR(cudaMalloc((void **)&m->d_tiles[k], sizeof(ExaTile) * std::max<size_t>(tiles.size(), 1)));
         if (!tiles.empty())
             CR(cudaMemcpy(m->d_tiles[k], tiles.data(), sizeof(ExaTile) * tiles.size(), cudaMemcpyHostToDevice));
@@ -1068,6 +1097,7 @@ exa_status autotune(exa_model *m) {
         cg.by_pattern = byp;
         cg.prefetch = pf;
         cg.lazy_loads = lazy;
+        cg.fused_step = m->fused_step;
         return cg;
     };
     {
@@ -1497,6 +1527,11 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
     m->lazy_loads = (o.flags & EXA_FLAG_LAZY_LOADS) != 0;
     m->stage = (o.flags & EXA_FLAG_STAGE_SMEM) != 0 && !m->bounds_check;
     m->host_serial = (o.flags & EXA_FLAG_HOST_SERIAL) != 0;
+    m->fused_step = (o.flags & EXA_FLAG_FUSED_STEP) != 0;
+    if (m->fused_step && (m->stage || m->lanes > 1 || m->prefetch))
+        return fail(m, EXA_E_INVALID, "EXA_FLAG_FUSED_STEP excludes staging, EXA_FLAG_LANES2 and the prefetch flags");
+    if (m->fused_step && m->precision != EXA_FP64)
+        return fail(m, EXA_E_INVALID, "EXA_FLAG_FUSED_STEP is for FP64 models");
     if (m->lazy_loads && !m->by_pattern) return fail(m, EXA_E_INVALID, "EXA_FLAG_LAZY_LOADS excludes EXA_FLAG_UPFRONT");
     if (m->lanes > 1 && m->prefetch) return fail(m, EXA_E_INVALID, "EXA_FLAG_LANES2 excludes the prefetch flags");
     if ((o.flags & EXA_FLAG_STAGE_SMEM) && (m->lanes > 1 || m->prefetch))
@@ -1715,12 +1750,14 @@ exa_status create_impl(const exa_model_desc *const *descs, int nb, const exa_opt
         i64 maxt = 1;
         for (const ExaPM &pm : m->h_pms) maxt += (pm.n_inst + 31) / 32;
         CR(dalloc(m, &m->d_objpart, maxt));
+        m->objpart_n = maxt;
     }
     const bool tune = !(o.flags & EXA_FLAG_NO_TUNE) && !o.block_threads && o.grid_factor == 0;
     if (tune)
         if (exa_status e = autotune(m)) return e;
     if (!tune || o.grid_factor != 0)
         if (exa_status e = apply_grid(m, std::max(o.grid_factor, 0))) return e;
+    if (exa_status e = prepare_step(m)) return e;
     CR(cudaDeviceSynchronize());
     m->create_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return EXA_OK;
@@ -2088,12 +2125,6 @@ static cudaError_t side_stream(cudaStream_t *s) {
     return cudaStreamCreateWithPriority(s, cudaStreamNonBlocking, hi);
 }
 
-// exa_eval_all over member chunks: for every chunk, its evaluation kernel(s) on the model stream,
-// then, on side stream 0 once that chunk's kernel has finished, its Jacobian CSC, Hessian CSC,
-// gradient and constraint reductions over the chunk's own ranges of every output (members own
-// contiguous ranges of variables, rows, tiles and CSC positions).  The evaluation of the next chunk
-// overlaps these reductions.  The objective sum follows the last evaluation; the host copies of
-// f, g, c follow the last reduction.  Same kernels, same per-element arithmetic as one chunk.
 // Records timing event ev (ev_k0 or ev_k1) on the model stream: plainly, or as an event-record node
 // while this library captures its own graph; not inside a capture the caller is making.
 static exa_status record_eval_event(exa_model *m, cudaEvent_t *ev) {
@@ -2108,6 +2139,12 @@ static exa_status record_eval_event(exa_model *m, cudaEvent_t *ev) {
     return EXA_OK;
 }
 
+// exa_eval_all over member chunks: for every chunk, its evaluation kernel(s) on the model stream,
+// then, on side stream 0 once that chunk's kernel has finished, its Jacobian CSC, Hessian CSC,
+// gradient and constraint reductions over the chunk's own ranges of every output (members own
+// contiguous ranges of variables, rows, tiles and CSC positions).  The evaluation of the next chunk
+// overlaps these reductions.  The objective sum follows the last evaluation; the host copies of
+// f, g, c follow the last reduction.  Same kernels, same per-element arithmetic as one chunk.
 static exa_status eval_all_chunked(exa_model *m, const double *x, const double *y, double sigma, double *f, double *g,
                                    double *c, double *jac_csc, double *hess_csc, ExaOut o,
                                    Mode mode, Mode hmode, bool split, bool jdirect, bool hdirect, bool hcomp) {
@@ -2219,6 +2256,126 @@ static exa_status eval_all_chunked(exa_model *m, const double *x, const double *
     return EXA_OK;
 }
 
+// Work queue of the fused step for kernel index i (0: exa_step over the M_ALL tiles, 1: exa_step_b
+// over the M_ALL_B tiles): every evaluation tile in member order, and each member's reductions
+// (Jacobian CSC, Hessian CSC, gradient, constraint augmentations, cut into pieces a CTA takes in
+// one go) placed two resident grids' worth of items (at most a quarter of the tiles) after that
+// member's last tile, so that by the time a CTA takes one the tiles it waits for are normally done.  Rebuilt when the tile lists or
+// the launch shape change.
+static exa_status build_step(exa_model *m, int i) {
+    const Mode mode = i ? exa::M_ALL_B : exa::M_ALL;
+    const int nb = m->nb;
+    int sms = 0, occ = 0;
+    CR(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
+    CR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)m->fn_step[i], m->block, 0));
+    const std::vector<ExaTile> &tiles = m->h_tiles[mode];
+    std::vector<int> need(nb, 0);
+    for (int b = 0; b < nb; b++) need[b] = m->mb_tile[mode][b + 1] - m->mb_tile[mode][b];
+    // reductions of member b: (kind, first, end) pieces
+    auto pieces = [&](int b, std::vector<ExaTask> &out) {
+        auto cut = [&](int kind, i64 lo, i64 hi, i64 step) {
+            for (i64 p = lo; p < hi; p += step) out.push_back({kind, b, (int)p, (int)std::min(hi, p + step)});
+        };
+        cut(1, m->mb_jcsc[b], m->mb_jcsc[b + 1], m->nnzj_csc == m->nnzj ? 8192 : 2048);
+        cut(2, m->mb_hcsc[b], m->mb_hcsc[b + 1], 2048);  // 2048 segments, or positions of a permutation
+        if (m->grad_compact) cut(3, m->mb_gseg[b], m->mb_gseg[b + 1], 2048);
+        else cut(3, m->xoff[b], m->xoff[b + 1], 2048);
+        cut(4, m->mb_arow[b], m->mb_arow[b + 1], 2048);
+    };
+    std::vector<ExaTask> items;
+    items.reserve(tiles.size() + 64 * (size_t)nb);
+    const i64 grid_est = (i64)std::max(occ, 1) * sms;
+    // items between a member's last tile and its reductions: two resident grids, or a quarter of
+    // the tiles when there are few (so that small batches still interleave)
+    const i64 lag = std::max<i64>(1, std::min<i64>(2 * grid_est, (i64)tiles.size() / 4));
+    std::vector<std::pair<i64, int>> pending;  // (queue position from which due, member)
+    int next_due = 0;
+    for (int b = 0; b < nb; b++) {
+        for (int t = m->mb_tile[mode][b]; t < m->mb_tile[mode][b + 1]; t++) {
+            items.push_back({0, b, t, t + 1});
+            while (next_due < (int)pending.size() && (i64)items.size() >= pending[next_due].first)
+                pieces(pending[next_due++].second, items);
+        }
+        pending.push_back({(i64)items.size() + lag, b});
+    }
+    while (next_due < (int)pending.size()) pieces(pending[next_due++].second, items);
+    if (items.size() > (size_t)INT32_MAX) return fail(m, EXA_E_UNSUPPORTED, "fused step queue too long");
+    if (m->d_items[i]) cudaFree(m->d_items[i]);
+    if (m->d_need[i]) cudaFree(m->d_need[i]);
+    m->d_items[i] = nullptr;
+    m->d_need[i] = nullptr;
+    CR(cudaMalloc((void **)&m->d_items[i], sizeof(ExaTask) * std::max<size_t>(items.size(), 1)));
+    CR(cudaMalloc((void **)&m->d_need[i], sizeof(int) * std::max(nb, 1)));
+    if (!m->d_sctr) CR(cudaMalloc((void **)&m->d_sctr, sizeof(int) * (nb + 1)));
+    if (!items.empty())
+        CR(cudaMemcpy(m->d_items[i], items.data(), sizeof(ExaTask) * items.size(), cudaMemcpyHostToDevice));
+    CR(cudaMemcpy(m->d_need[i], need.data(), sizeof(int) * nb, cudaMemcpyHostToDevice));
+    m->nitems[i] = (int)items.size();
+    // one CTA per resident slot (more would only queue), at most one objective partial per slot
+    m->step_grid[i] = (int)std::max<i64>(1, std::min<i64>({grid_est, (i64)items.size(), m->objpart_n}));
+    m->step_ready[i] = true;
+    return EXA_OK;
+}
+
+// Builds the fused step's queues that are missing (outside any stream capture: they allocate).
+static exa_status prepare_step(exa_model *m) {
+    if (!m->fused_step) return EXA_OK;
+    for (int i = 0; i < 2; i++)
+        if (m->fn_step[i] && !m->step_ready[i])
+            if (exa_status e = build_step(m, i)) return e;
+    return EXA_OK;
+}
+
+// The fused step: one exa_step[_b] launch (tiles and reductions from one queue), then the objective.
+static exa_status eval_fused_step(exa_model *m, int i, const double *x, const double *y, double sigma, ExaOut o,
+                                  double *f, double *g, double *c, double *jac_csc, double *hess_csc, bool jdirect,
+                                  bool hdirect, bool hcomp) {
+    if (!m->step_ready[i])
+        if (exa_status e = build_step(m, i)) return e;
+    const Mode mode = i ? exa::M_ALL_B : exa::M_ALL;
+    ExaStep st{};
+    st.ctr = m->d_sctr;
+    st.need = m->d_need[i];
+    st.items = m->d_items[i];
+    st.nitems = m->nitems[i];
+    st.spin_limit = 1 << 22;  // polls of about 0.2 us or more: about a second at least
+    for (ExaRed &r : st.r) r.how = -1;
+    if (jac_csc && !jdirect && m->nnzj_csc) {
+        st.r[0] = m->nnzj_csc == m->nnzj ? ExaRed{0, nullptr, m->d_jperm, nullptr, o.jac, jac_csc}
+                                           : ExaRed{1, m->d_jsegptr, m->d_jperm, nullptr, o.jac, jac_csc};
+    }
+    if (hess_csc && !hdirect && m->nnzh_csc) {
+        st.r[1] = hcomp                      ? ExaRed{1, m->d_hcsegptr, m->d_hcperm, nullptr, m->d_hcbuf, hess_csc}
+                  : m->nnzh_csc == m->nnzh ? ExaRed{0, nullptr, m->d_hperm, nullptr, o.hess, hess_csc}
+                                           : ExaRed{1, m->d_hsegptr, m->d_hperm, nullptr, o.hess, hess_csc};
+    }
+    if (g && m->nvar) {
+        if (m->grad_compact) {
+            CR(cudaMemsetAsync(g, 0, sizeof(double) * m->nvar, m->stream));
+            st.r[2] = ExaRed{3, m->d_gsegptr, m->d_gperm, m->d_gsegvar, m->d_gbuf, g};
+        } else {
+            st.r[2] = ExaRed{2, m->d_gptr, m->d_gperm, nullptr, m->d_gbuf, g};
+        }
+    }
+    if (c && m->n_aug_rows) st.r[3] = ExaRed{3, m->d_aptr, m->d_aperm, m->d_arows, m->d_abuf, c};
+    CR(cudaMemsetAsync(m->d_sctr, 0, sizeof(int) * (m->nb + 1), m->stream));
+    o.status = m->d_status;
+    ExaStructOut so{};
+    so.status = m->d_status;
+    const double *th = m->d_theta;
+    const ExaTile *tiles = m->d_tiles[mode];
+    int nt = m->ntiles[mode], pfd = 0;
+    void *args[] = {&tiles, &nt, &m->d_pm, &x, &y, &th, &sigma, &o, &so, &pfd, &st};
+    if (exa_status e = record_eval_event(m, &m->ev_k0)) return e;
+    CR(cudaLaunchKernel((const void *)m->fn_step[i], dim3(m->step_grid[i]), dim3(m->block), args, 0, m->stream));
+    if (exa_status e = record_eval_event(m, &m->ev_k1)) return e;
+    if (f) {
+        k_obj_final<<<1, 1024, 0, m->stream>>>(m->d_objpart, m->step_grid[i], f);
+        CR(cudaGetLastError());
+    }
+    return EXA_OK;
+}
+
 static exa_status eval_all_launches(exa_model *m, const double *x, const double *y, double sigma, double *f,
                                     double *g, double *c, double *jac, double *hess, double *jac_csc,
                                     double *hess_csc) {
@@ -2253,6 +2410,10 @@ static exa_status eval_all_launches(exa_model *m, const double *x, const double 
     const bool hcoo = o.hess != nullptr;
     Mode mode = !want_h ? exa::M_FIRST : (hcomp ? (hcoo ? exa::M_ALL_B : exa::M_ALL_C) : exa::M_ALL);
     const Mode hmode = hcomp ? (hcoo ? exa::M_HESS_B : exa::M_HESS_C) : exa::M_HESS;
+    if (m->fused_step && m->nchunks == 1 && !(want_h && m->split_all) && want_h &&
+        (mode == exa::M_ALL || mode == exa::M_ALL_B) && m->fn_step[mode == exa::M_ALL_B])
+        return eval_fused_step(m, mode == exa::M_ALL_B, x, y, sigma, o, f, g, c, jac_csc, hess_csc, jdirect, hdirect,
+                               hcomp);
     if (m->nchunks > 1)
         return eval_all_chunked(m, x, y, sigma, f, g, c, jac_csc, hess_csc, o, want_h ? mode : exa::M_FIRST,
                                 hmode, want_h && m->split_all, jdirect, hdirect, hcomp);
@@ -2346,6 +2507,7 @@ static exa_status eval_all_cached(exa_model *m, const double *x, const double *y
             return EXA_OK;
         }
     if (!m->cap_stream) CR(cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
+    if (exa_status e = prepare_step(m)) return e;  // allocations cannot happen inside the capture
     cudaStream_t user = m->stream;
     m->stream = m->cap_stream;
     CR(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -2594,6 +2756,7 @@ exa_status exa_compile_check(const exa_model_desc *desc, const exa_options *opt,
             cg.lanes = (o.flags & EXA_FLAG_LANES2) ? 2 : 1;
             cg.lazy_loads = (o.flags & EXA_FLAG_LAZY_LOADS) != 0;
             cg.stage = (o.flags & EXA_FLAG_STAGE_SMEM) != 0;
+            cg.fused_step = (o.flags & EXA_FLAG_FUSED_STEP) != 0;
             std::string gerr;
             std::string src = exa::generate_source(tmp.pats, tmp.groups, cg, &gerr);
             if (!gerr.empty()) s = fail(&tmp, EXA_E_INTERNAL, gerr);
@@ -2635,6 +2798,7 @@ exa_status exa_stat(const exa_model *m, const char *key, double *value) {
     else if (k == "eval_lanes") *value = m->lanes;
     else if (k == "eval_lazy") *value = m->lazy_loads;
     else if (k == "eval_stage") *value = m->stage;
+    else if (k == "eval_fused_step") *value = m->fused_step;
     else if (k == "eval_kernel_ms") {  // evaluation kernel(s) of the latest exa_eval_all step
         float ms = -1.0f;
         if (!m->ev_k_valid || cudaEventSynchronize(m->ev_k1) != cudaSuccess ||

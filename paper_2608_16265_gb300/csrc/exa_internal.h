@@ -56,6 +56,27 @@
     struct ExaStructOut {                                                                           \
         int *jrow, *jcol, *hrow, *hcol, *gvar, *arow, *hcrow, *hccol;                               \
         int *status;                                                                                \
+    };                                                                                              \
+    struct ExaTask {              /* one item of the fused step's work queue */                     \
+        int kind;                 /* 0: evaluation tile p0; k > 0: reduction r[k - 1] over [p0,p1) */\
+        int member;               /* batch member the tile belongs to / the reduction waits for */  \
+        int p0, p1;                                                                                 \
+    };                                                                                              \
+    struct ExaRed {               /* one reduction of the fused step */                             \
+        int how;                  /* -1 off; 0 dst[p] = src[perm[p]]; segment sums over           */\
+                                  /* perm[ptr[s] .. ptr[s+1]): 1 dst[s] from the first entry,     */\
+                                  /* 2 dst[s] from 0.0, 3 dst[rows[s]] plus the segment            */\
+        const int *ptr, *perm, *rows;                                                               \
+        const double *src;                                                                          \
+        double *dst;                                                                                \
+    };                                                                                              \
+    struct ExaStep {                                                                                \
+        int *ctr;                 /* ctr[0]: next queue item; ctr[1 + b]: finished tiles of b */     \
+        const int *need;          /* evaluation tiles of each member */                             \
+        const ExaTask *items;     /* the queue */                                                   \
+        int nitems;                                                                                 \
+        int spin_limit;           /* bound on a reduction's wait for its member's tiles */          \
+        ExaRed r[4];              /* Jacobian CSC, Hessian CSC, gradient, constraint augmentations */\
     };
 
 EXA_DEVICE_STRUCTS
@@ -146,6 +167,10 @@ struct CodegenOptions {
     // tile into a second buffer of per-thread slots (cp.async) while the current tile computes from
     // the first.  Excludes prefetch, warp sets and bounds checking.
     int stage = 0;
+    // Fused step kernels (exa_step, exa_step_b): the evaluation tiles of the M_ALL / M_ALL_B kernel
+    // and the step's reductions taken from one work queue (ExaStep).  Excludes staging, prefetch
+    // and warp sets.
+    bool fused_step = false;
 };
 // The warp sets of group g in kernel kind `mode` (positions in g.pats per set, in order): one set
 // with every active pattern, or `lanes` contiguous subsets of about equal outputs.

@@ -1681,12 +1681,86 @@ static const char *kFp64Helpers =
 #include "exa_fp64_sincos.inc"
     ;
 
+// Reductions of the fused step (ExaRed), run by one CTA over [p0, p1).  Values written by other
+// CTAs during the kernel (COO slots, compressed sums, gradient and augmentation buffers,
+// constraint base values) are read through L2 (ld.global.cg); the index arrays are constant.
+// Each segment is added in ascending order starting from its first entry (how 1), from 0.0 (how 2)
+// or from dst[rows[s]] (how 3): the additions of the two-pass CSC sums and of the segment kernels.
+static const char *kStepHelpers = R"(
+static __device__ __forceinline__ void exa_red_perm(const ExaRed& r, const int p0, const int p1) {
+  for (int base = p0 + (int)threadIdx.x; base < p1; base += EXA_BLOCK * 8) {
+    int q[8];
+    #pragma unroll
+    for (int u = 0; u < 8; u++) { const int p = base + u * EXA_BLOCK; q[u] = p < p1 ? __ldg(r.perm + p) : -1; }
+    double v[8];
+    #pragma unroll
+    for (int u = 0; u < 8; u++) v[u] = q[u] >= 0 ? __ldcg(r.src + q[u]) : 0.0;
+    #pragma unroll
+    for (int u = 0; u < 8; u++) if (q[u] >= 0) r.dst[base + u * EXA_BLOCK] = v[u];
+  }
+}
+static __device__ __forceinline__ void exa_red_seg(const ExaRed& r, const int p0, const int p1) {
+  for (int base = p0 + (int)threadIdx.x; base < p1; base += EXA_BLOCK * 4) {
+    int b[4], e[4], q0[4];
+    long long d[4];
+    double acc[4];
+    #pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int s = base + u * EXA_BLOCK;
+      b[u] = s < p1 ? __ldg(r.ptr + s) : 0;
+      e[u] = s < p1 ? __ldg(r.ptr + s + 1) : 0;
+      d[u] = r.how == 3 && s < p1 ? (long long)__ldg(r.rows + s) : (long long)s;
+    }
+    #pragma unroll
+    for (int u = 0; u < 4; u++) {
+      q0[u] = b[u] < e[u] ? __ldg(r.perm + b[u]) : -1;
+      acc[u] = r.how == 3 && base + u * EXA_BLOCK < p1 ? __ldcg(r.dst + d[u]) : 0.0;
+    }
+    #pragma unroll
+    for (int u = 0; u < 4; u++)
+      if (q0[u] >= 0) { const double v = __ldcg(r.src + q0[u]); acc[u] = r.how == 1 ? v : acc[u] + v; }
+    #pragma unroll
+    for (int u = 0; u < 4; u++) {
+      for (int q = b[u] + 1; q < e[u]; q++) acc[u] += __ldcg(r.src + __ldg(r.perm + q));
+      if (base + u * EXA_BLOCK < p1) r.dst[d[u]] = acc[u];
+    }
+  }
+}
+// A reduction item: wait (bounded) until every evaluation tile of its member has finished, then
+// run it.  The wait ends after spin_limit polls; the status word then records bit 2 and the item
+// runs on whatever is there, so the kernel always finishes.
+static __device__ void exa_step_task(const ExaStep& st, const ExaTask& tk, int* status) {
+  const ExaRed& r = st.r[tk.kind - 1];
+  if (r.how < 0) return;
+  if (threadIdx.x == 0) {
+    const int need = __ldg(st.need + tk.member);
+    const int* cnt = st.ctr + 1 + tk.member;
+    int v = 0, polls = 0;
+    for (;;) {
+      asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(cnt) : "memory");
+      if (v >= need) break;
+      if (++polls > st.spin_limit) { atomicOr(status, 2); break; }
+      __nanosleep(200);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  if (r.how == 0) exa_red_perm(r, tk.p0, tk.p1);
+  else exa_red_seg(r, tk.p0, tk.p1);
+}
+)";
+
 }  // namespace
 
 std::string generate_source(const std::vector<Pattern> &pats, const std::vector<Group> &groups,
                             const CodegenOptions &opt_in, std::string *err, int *dsmem) {
     CodegenOptions opt = opt_in;
     if (opt.lanes > 1) opt.prefetch = 0;  // one or the other
+    if (opt.fused_step) {  // the fused step kernels take plain tiles
+        opt.stage = 0;
+        opt.prefetch = 0;
+        opt.lanes = 1;
+    }
     if (opt.stage) {  // staging excludes L2 prefetch, warp sets and the bounds-checked indices
         opt.prefetch = 0;
         opt.lanes = 1;
@@ -1706,6 +1780,7 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
     if (mixed) src << kMixedHelpers;
     src << kExactHelpers;
     src << kFp64Helpers;
+    if (opt.fused_step) src << kStepHelpers;
     if (opt.stage)
         src << "// cp.async of one 8- or 4-byte input into a shared-memory slot (both addresses aligned to\n"
                "// the size: data columns, x and y are arrays of that element size)\n"
@@ -1897,6 +1972,56 @@ std::string generate_source(const std::vector<Pattern> &pats, const std::vector<
                    "  }\n";
         }
         src << "}\n";
+        if (opt.fused_step && (m == M_ALL || m == M_ALL_B)) {
+            // The fused step: every CTA takes items from one queue until it is empty; an evaluation
+            // tile is this kernel kind's tile, after which the CTA counts it for its member; a
+            // reduction item waits for its member's tiles (exa_step_task).  Items are queued so
+            // that a member's reductions come well after its tiles, and a tile never waits, so the
+            // kernel finishes whatever the number of resident CTAs.
+            src << "extern \"C\" __global__ void EXA_BOUNDS exa_step" << (m == M_ALL_B ? "_b" : "")
+                << "(const ExaTile* __restrict__ tiles, const int ntiles, const ExaPM* __restrict__ pms,"
+                   " const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ th,"
+                   " const double sigma, const ExaOut o, const ExaStructOut so, const int pfd, const ExaStep st) {\n"
+                   "  __shared__ double red[EXA_BLOCK / 32];\n"
+                   "  __shared__ double stage[EXA_BLOCK * " << smax << "];\n"
+                   "  __shared__ int s_item;\n"
+                   "  double* __restrict__ ws = stage + (threadIdx.x & ~31u) * " << smax << ";\n"
+                   "  double objv = 0.0;\n"
+                   "  for (;;) {\n"
+                   "    if (threadIdx.x == 0) s_item = atomicAdd(st.ctr, 1);\n"
+                   "    __syncthreads();\n"
+                   "    const int it = s_item;\n"
+                   "    __syncthreads();\n"
+                   "    if (it >= st.nitems) break;\n"
+                   "    const ExaTask tk = st.items[it];\n"
+                   "    if (tk.kind != 0) { exa_step_task(st, tk, o.status); continue; }\n"
+                   "    const ExaTile tl = tiles[tk.p0];\n"
+                   "    const ExaPM& pm = pms[tl.pm];\n"
+                   "    const int k0 = tl.begin + (int)threadIdx.x;\n"
+                   "    const bool act = k0 < pm.n_inst;\n"
+                   "    const int k = act ? k0 : (int)pm.n_inst - 1;\n"
+                   "    if (__any_sync(0xffffffffu, act)) {\n"
+                   "      switch (pm.grp) {\n";
+            for (int gi : gl)
+                src << "        case " << gi << ": grp" << gi << "_" << kModeName[m]
+                    << "(pm, k, act, x, y, th, sigma, o, so, objv, ws); break;\n";
+            src << "        default: break;\n      }\n    }\n"
+                   "    __syncthreads();\n"
+                   "    if (threadIdx.x == 0) { __threadfence(); atomicAdd(st.ctr + 1 + tk.member, 1); }\n"
+                   "  }\n"
+                   "  if (__any_sync(0xffffffffu, (__double_as_longlong(objv) << 1) != 0))\n"
+                   "    for (int off = 16; off > 0; off >>= 1) objv += __shfl_xor_sync(0xffffffffu, objv, off);\n"
+                   "  else\n"
+                   "    objv = 0.0;\n"
+                   "  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = objv;\n"
+                   "  __syncthreads();\n"
+                   "  if (threadIdx.x == 0) {\n"
+                   "    double s = 0.0;\n"
+                   "    for (int i = 0; i < EXA_BLOCK / 32; i++) s += red[i];\n"
+                   "    o.obj_part[blockIdx.x] = s;\n"
+                   "  }\n"
+                   "}\n";
+        }
     }
     return src.str();
 }

@@ -55,7 +55,8 @@ def test_generated_kernels_compile(name, flat):
 def test_generated_variants_compile(precision, upfront):
     """Every code-generator variant the tuner can pick compiles for sm_103a: both precisions, both
     emission orders, with and without a launch-bounds register cap, both L2 prefetch depths, two
-    warp sets per instance, inputs loaded one pattern ahead, inputs staged in shared memory, on the
+    warp sets per instance, inputs loaded one pattern ahead, inputs staged in shared memory, the
+    fused step kernels, on the
     two-stage ACOPF (all pattern kinds, scenario-indexed variables, per-scenario parameters)."""
     from paper_2608_16265_gb300 import binding
     flat = synth.two_stage_acopf(5, 7, 2, 3, seed=1).flat
@@ -68,6 +69,8 @@ def test_generated_variants_compile(precision, upfront):
     if not upfront:
         binding.exa_compile_check(flat, precision=precision, block=64, min_blocks=12,
                                   flags=flags | binding.EXA_FLAG_LAZY_LOADS)
+    binding.exa_compile_check(flat, precision=precision, block=64, min_blocks=14,  # fused step kernels
+                              flags=flags | binding.EXA_FLAG_FUSED_STEP)
     for lazy in ((0, binding.EXA_FLAG_LAZY_LOADS) if not upfront else (0,)):  # shared-memory staging
         binding.exa_compile_check(flat, precision=precision, block=128, min_blocks=4,
                                   flags=flags | lazy | binding.EXA_FLAG_STAGE_SMEM)

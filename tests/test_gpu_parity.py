@@ -193,13 +193,58 @@ def test_parity_smem_staging(name, order):
     assert m.stat("eval_stage") == 1 and m.stat("eval_dsmem") > 0
 
 
+@pytest.mark.parametrize("name", ["all_ops", "flow_collisions", "more_ops", "acopf_shunts", "pde_41", "goddard_2000",
+                                  "two_stage_acopf"])
+def test_parity_fused_step(name):
+    """The fused step (one persistent kernel taking evaluation tiles and the step's reductions from
+    one work queue) on every workload kind; a single model's reductions all wait for its tiles."""
+    B = _B()
+    flat, (x, y, s) = CASES[name]()
+    m, _ = check_model(flat, x, y, s, flags=B.EXA_FLAG_NO_TUNE | B.EXA_FLAG_FUSED_STEP, block=64)
+    assert m.stat("eval_fused_step") == 1
+
+
+@pytest.mark.parametrize("extra", ["", "no_hcomp", "scatter", "lazy"])
+def test_fused_step_batch(extra):
+    """The fused step on a batch, whose members' reductions are queued between later members' tiles
+    and wait for their own: every member against the oracle, and every output bit for bit against
+    the same configuration without the fused step (the objective, whose per-CTA partials differ,
+    within 1e-12); no wait may time out."""
+    B = _B()
+    wls = synth.acopf_batch(11, seed=5, bmin=20, bmax=300)
+    flats = [w.flat for w in wls]
+    flags = B.EXA_FLAG_NO_TUNE | {"": 0, "no_hcomp": B.EXA_FLAG_NO_HCOMP, "scatter": B.EXA_FLAG_CSC_SCATTER,
+                                  "lazy": B.EXA_FLAG_LAZY_LOADS}[extra]
+    prec = B.EXA_FP64
+    ref = B.exa_create_batch(flats, block=64, flags=flags, precision=prec)
+    fused = B.exa_create_batch(flats, block=64, flags=flags | B.EXA_FLAG_FUSED_STEP, precision=prec)
+    assert fused.stat("eval_fused_step") == 1
+    pts = [synth.acopf_point(w, i) for i, w in enumerate(wls)]
+    x = np.concatenate([p[0] for p in pts])
+    y = np.concatenate([p[1] for p in pts])
+    a = ref.eval_all(_t(x), _t(y), 1.0, csc=True)
+    for _ in range(2):  # the second call replays the cached graph
+        b = fused.eval_all(_t(x), _t(y), 1.0, csc=True)
+        fused.exa_check_status()
+        for k in a:
+            if k == "f":
+                fa, fb = float(_np(a["f"])[0]), float(_np(b["f"])[0])
+                assert abs(fa - fb) <= 1e-12 * abs(fa), (fa, fb)
+            else:
+                assert np.array_equal(_np(a[k]).view(np.uint64), _np(b[k]).view(np.uint64)), k
+    compare_batch_members(fused, wls, pts, b, range(len(wls)), TOL)
+
+
 def test_option_conflicts_are_rejected():
     B = _B()
     flat, _ = CASES["all_ops"]()
     for kw in (dict(block=32, flags=B.EXA_FLAG_LANES2), dict(block=64, flags=B.EXA_FLAG_LANES2 | B.EXA_FLAG_PF_COLUMNS),
                dict(block=64, flags=B.EXA_FLAG_LAZY_LOADS | B.EXA_FLAG_UPFRONT),
                dict(block=64, flags=B.EXA_FLAG_STAGE_SMEM | B.EXA_FLAG_LANES2),
-               dict(block=64, flags=B.EXA_FLAG_STAGE_SMEM | B.EXA_FLAG_PF_GATHERS)):
+               dict(block=64, flags=B.EXA_FLAG_STAGE_SMEM | B.EXA_FLAG_PF_GATHERS),
+               dict(block=64, flags=B.EXA_FLAG_FUSED_STEP | B.EXA_FLAG_STAGE_SMEM),
+               dict(block=64, flags=B.EXA_FLAG_FUSED_STEP | B.EXA_FLAG_LANES2),
+               dict(block=64, flags=B.EXA_FLAG_FUSED_STEP, precision=B.EXA_MIXED_FP32)):
         with pytest.raises(B.ExaError) as e:
             B.exa_create(flat, **kw)
         assert e.value.status == B.EXA_E_INVALID
