@@ -184,9 +184,15 @@ enum {
                                   f64 data, parameters, multipliers) are loaded just before the
                                   arithmetic of the pattern preceding it, not all at the top of the
                                   fused group (fewer values live); excludes EXA_FLAG_UPFRONT */
+    EXA_FLAG_STAGE_SMEM = 4096, /* staging depth 1: the tile loop copies the inputs of the CTA's next
+                                  tile (data columns, x values indexed by the instance alone,
+                                  constraint multipliers) into shared memory with cp.async while the
+                                  current tile computes from a second buffer; gathers through data
+                                  fields still load from global memory.  Excludes EXA_FLAG_LANES2 and
+                                  the prefetch flags; ignored with EXA_FLAG_BOUNDS_CHECK */
     EXA_FLAG_HOST_SERIAL = 8192, /* exa_eval_all_host on a batch: no member-chunk pipeline (inputs,
                                   graph, outputs one after another on the model stream) */
-    EXA_FLAG_FUSED_STEP = 16384, /* exa_eval_all with the Hessian runs one persistent kernel whose
+    EXA_FLAG_FUSED_STEP = 16384 /* exa_eval_all with the Hessian runs one persistent kernel whose
                                   CTAs take evaluation tiles and reductions (Jacobian and Hessian CSC,
                                   gradient, constraint augmentations) from one work queue; a
                                   member's reductions wait (bounded; EXA_E_TIMEOUT from
@@ -194,13 +200,7 @@ enum {
                                   on a batch they overlap the evaluation of later members.  FP64
                                   models only; excludes EXA_FLAG_STAGE_SMEM, EXA_FLAG_LANES2 and the
                                   prefetch flags; with member chunks or EXA_FLAG_SPLIT the plain
-                                  graph is used */
-    EXA_FLAG_STAGE_SMEM = 4096 /* staging depth 1: the tile loop copies the inputs of the CTA's next
-                                  tile (data columns, x values indexed by the instance alone,
-                                  constraint multipliers) into shared memory with cp.async while the
-                                  current tile computes from a second buffer; gathers through data
-                                  fields still load from global memory.  Excludes EXA_FLAG_LANES2 and
-                                  the prefetch flags; ignored with EXA_FLAG_BOUNDS_CHECK */
+                                  graph is used.  Not chosen by the autotuner */
 };
 
 /* Validate the descriptor (Sec. 3.4 SIMDFunction), lower every pattern to generated device
