@@ -336,6 +336,14 @@ exa_status exa_hprod(exa_model *m, const double *x, const double *y, double sigm
  * bounds checks since the last call (EXA_E_BOUNDS, EXA_E_TIMEOUT), clearing them. */
 exa_status exa_check_status(exa_model *m);
 
+/* Failure injection for tests of the fused step's bounded wait (EXA_FLAG_FUSED_STEP models only):
+ * the next exa_eval_all call starts `member`'s tile counter one below zero, so that it ends one
+ * short of the member's tiles; that member's reductions poll for a short bound (4096 polls), give
+ * up and run on what is there, the kernel finishes, and exa_check_status then reports
+ * EXA_E_TIMEOUT.  One call only (launched directly, not from the cached graph); later calls are
+ * normal.  EXA_E_INVALID for other models or a member out of range. */
+exa_status exa_debug_hold_step(exa_model *m, int32_t member);
+
 /* Validate the descriptor, generate the kernels and compile them with NVRTC for sm_103a without
  * touching any device (usable on a host without a GPU).  With the environment variable
  * EXA_DUMP_SOURCE set to a file name, this call and exa_create write the generated CUDA source

@@ -36,7 +36,7 @@ EXPORTS = ["exa_create", "exa_create_batch", "exa_destroy", "exa_last_error", "e
            "exa_jac_structure", "exa_jac_coord", "exa_hess_structure", "exa_hess_coord",
            "exa_jac_csc_structure", "exa_hess_csc_structure", "exa_jac_csc", "exa_hess_csc",
            "exa_eval_all", "exa_eval_all_host", "exa_jprod", "exa_jtprod", "exa_hprod", "exa_check_status",
-           "exa_compile_check", "exa_stat"]
+           "exa_debug_hold_step", "exa_compile_check", "exa_stat"]
 # Every function include/exa_probe.h declares (measurement, not part of the evaluation path).
 PROBE_EXPORTS = ["exa_probe_fp64_fma", "exa_probe_host_link"]
 
@@ -116,6 +116,7 @@ def load():
             "exa_jtprod": [vp, dp, dp, dp],
             "exa_hprod": [vp, dp, dp, C.c_double, dp, dp],
             "exa_check_status": [vp],
+            "exa_debug_hold_step": [vp, C.c_int32],
             "exa_compile_check": [C.POINTER(exa_model_desc), C.POINTER(exa_options), C.c_char_p, C.c_size_t],
             "exa_stat": [vp, C.c_char_p, C.POINTER(C.c_double)],
             "exa_probe_fp64_fma": [C.c_int32, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -326,6 +327,7 @@ class Model:
     def exa_jtprod(self, x, w, out): self._call("exa_jtprod", _ptr(x), _ptr(w), _ptr(out))
     def exa_hprod(self, x, y, s, v, out): self._call("exa_hprod", _ptr(x), _ptr(y), float(s), _ptr(v), _ptr(out))
     def exa_check_status(self): self._call("exa_check_status")
+    def exa_debug_hold_step(self, member): self._call("exa_debug_hold_step", int(member))
 
     def exa_set_theta(self, theta):
         t = np.ascontiguousarray(theta, dtype=np.float64)

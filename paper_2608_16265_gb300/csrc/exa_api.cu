@@ -330,6 +330,7 @@ struct exa_model {
     int *d_need[2] = {}, *d_sctr = nullptr;
     std::vector<ExaTile> h_tiles[exa::M_COUNT];  // host copies of the tile lists
     i64 objpart_n = 0;                           // objective partial slots allocated
+    int step_hold = -1;  // failure injection: member whose tile count the next fused step cannot reach
     ExaPM *d_pm = nullptr;
     ExaTile *d_tiles[exa::M_COUNT] = {};
     int ntiles[exa::M_COUNT] = {};
@@ -2359,6 +2360,13 @@ static exa_status eval_fused_step(exa_model *m, int i, const double *x, const do
     }
     if (c && m->n_aug_rows) st.r[3] = ExaRed{3, m->d_aptr, m->d_aperm, m->d_arows, m->d_abuf, c};
     CR(cudaMemsetAsync(m->d_sctr, 0, sizeof(int) * (m->nb + 1), m->stream));
+    if (m->step_hold >= 0 && m->step_hold < m->nb) {
+        // failure injection for one call: the member's count starts at -1, so it ends one short of
+        // its tiles and its reductions' waits run out after a short bound
+        CR(cudaMemsetAsync(m->d_sctr + 1 + m->step_hold, 0xff, sizeof(int), m->stream));
+        st.spin_limit = 1 << 12;
+        m->step_hold = -1;
+    }
     o.status = m->d_status;
     ExaStructOut so{};
     so.status = m->d_status;
@@ -2495,7 +2503,7 @@ static exa_status eval_all_cached(exa_model *m, const double *x, const double *y
                                   double *c, double *jac, double *hess, double *jac_csc, double *hess_csc) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CR(cudaStreamIsCapturing(m->stream, &cs));
-    if (!m->use_graphs || cs != cudaStreamCaptureStatusNone)
+    if (!m->use_graphs || cs != cudaStreamCaptureStatusNone || m->step_hold >= 0)
         return eval_all_launches(m, x, y, sigma, f, g, c, jac, hess, jac_csc, hess_csc);
     uint64_t sb;
     std::memcpy(&sb, &sigma, 8);
@@ -2720,6 +2728,14 @@ exa_status exa_hprod(exa_model *m, const double *x, const double *y, double sigm
     k_hprod_csc<<<grid_of(m->nvar, 256), 256, 0, m->stream>>>(m->d_hcolptr, m->d_hrowval, m->d_hcscbuf, m->d_hcsr_ptr,
                                                                m->d_hcsr_perm, m->d_hcolof, v, Hv, (int)m->nvar);
     CR(cudaGetLastError());
+    return EXA_OK;
+}
+
+exa_status exa_debug_hold_step(exa_model *m, int32_t member) {
+    if (exa_status e = check_model(m)) return e;
+    if (!m->fused_step) return fail(m, EXA_E_INVALID, "the model was not created with EXA_FLAG_FUSED_STEP");
+    if (member < 0 || member >= m->nb) return fail(m, EXA_E_INVALID, "no such batch member");
+    m->step_hold = member;
     return EXA_OK;
 }
 

@@ -235,6 +235,35 @@ def test_fused_step_batch(extra):
     compare_batch_members(fused, wls, pts, b, range(len(wls)), TOL)
 
 
+def test_fused_step_wait_times_out_and_recovers():
+    """The fused step's bounded wait, made to run out from the host: one member's tile counter
+    starts one short (exa_debug_hold_step), its reductions give up after their bound, the kernel
+    still finishes, exa_check_status reports EXA_E_TIMEOUT; the next call is normal and matches the
+    oracle.  No fault, no hang: the wait has a poll limit."""
+    B = _B()
+    wls = synth.acopf_batch(4, seed=9, bmin=20, bmax=120)
+    flats = [w.flat for w in wls]
+    m = B.exa_create_batch(flats, block=64, flags=B.EXA_FLAG_NO_TUNE | B.EXA_FLAG_FUSED_STEP)
+    pts = [synth.acopf_point(w, i) for i, w in enumerate(wls)]
+    x = _t(np.concatenate([p[0] for p in pts]))
+    y = _t(np.concatenate([p[1] for p in pts]))
+    m.eval_all(x, y, 1.0, csc=True)
+    m.exa_check_status()
+    m.exa_debug_hold_step(2)
+    m.eval_all(x, y, 1.0, csc=True)
+    with pytest.raises(B.ExaError) as e:
+        m.exa_check_status()
+    assert e.value.status == B.EXA_E_TIMEOUT
+    out = m.eval_all(x, y, 1.0, csc=True)
+    m.exa_check_status()
+    compare_batch_members(m, wls, pts, out, range(len(wls)), TOL)
+    with pytest.raises(B.ExaError):
+        m.exa_debug_hold_step(7)  # no such member
+    single = B.exa_create(wls[0].flat, flags=B.EXA_FLAG_NO_TUNE)
+    with pytest.raises(B.ExaError):
+        single.exa_debug_hold_step(0)  # not a fused-step model
+
+
 def test_option_conflicts_are_rejected():
     B = _B()
     flat, _ = CASES["all_ops"]()
